@@ -1,0 +1,348 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 Boolean-matrix frequent-itemset miner.
+
+One step = one pass of the whole hot path over the workload: bit-column
+construction from a device-resident CSR (Eq. 1), singleton and pair supports
+(Eq. 2-3), the depth-first prefix extension, and the canonical compaction,
+with the results left in device buffers.  Metric: itemset supports per
+second (support values computed: singletons + pairs + DFS extensions) over
+the device time of the step, CUDA events on the miner's stream, L2 flushed
+between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+    python bench.py --impl reference      # the CPU oracle on the host cores
+
+Under torchrun (N > 1) every rank mines its own replica of the workload
+(replicas only: the single-database path has no exchange step); the value is
+the supports of all ranks over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+DEFAULT_WORKLOAD = "quest_1M_1000"
+WORKLOAD_DESC = {
+    "grocery_like_10k_169": "10,000 x 169, Zipf(1.0), Poisson(4.4) lengths, minsup 100",
+    "quest_1M_1000": "1,000,000 x 1,000 Quest-style (T10, I4, 2,000 patterns, 50% corruption), minsup 1,000 (0.1%)",
+    "planted_100k_2000": "100,000 x 2,000, Zipf(1.1) background + 500 planted patterns of length 6-12, minsup 500",
+    "quest_10M_5000": "10,000,000 x 5,000 Quest-style (T12, I5, 5,000 patterns), minsup 5,000 (0.05%)",
+}
+L2_FLUSH_BYTES = 256 << 20
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOAD_DESC))
+    ap.add_argument("--flags", type=int, default=0, help="extra fim_mine flags")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), float(p["bf16_tflops"]), float(p["bf16_tflops_sustained"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, 1900.0, 1700.0, "fallback"
+
+
+def _cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.thread.join(timeout=2)
+
+    def summary(self):
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows if len(r) >= 9
+                          for i, v in enumerate(r[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(sm)}
+
+
+def _kernel_traffic(kernel: str, workload: str):
+    """ncu DRAM bytes per launch from profiles/traffic.json, if taken on the
+    current source of that kernel's file; else None."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            t = json.load(f)
+        e = t[kernel][workload]
+        src = os.path.join(ROOT, "paper_2412_19420_gb300", "csrc", e["source"])
+        if hashlib.sha256(open(src, "rb").read()).hexdigest() != e["source_sha256"]:
+            return None
+        return int(e["dram_bytes_per_launch"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+def _load_workload(name):
+    from paper_2412_19420_gb300 import datagen
+    fn, minsup = datagen.WORKLOADS[name]
+    return fn(), minsup
+
+
+def cpu_baseline(csr, minsup, budget_s=20.0):
+    """The oracle (plain Apriori, all host cores) on a bounded sample of the
+    workload: the first n' transactions, with minsup scaled by n'/n."""
+    import numpy as np
+    import oracle
+    from paper_2412_19420_gb300 import datagen
+    cores = _cores()
+    n = csr.n
+    frac = 1.0
+    while True:
+        n_s = max(1, int(n * frac))
+        ms = max(1, int(round(minsup * n_s / n)))
+        ip = csr.indptr[: n_s + 1]
+        ix = csr.indices[: int(ip[-1])]
+        t0 = time.perf_counter()
+        r = oracle.apriori(ip, ix, csr.m, ms, threads=cores)
+        dt = time.perf_counter() - t0
+        if dt <= budget_s * 1.5 or frac <= 1 / 64:
+            break
+        frac /= 2 ** max(1, int(np.log2(dt / budget_s)))
+    _ = datagen
+    sample = ("full workload" if n_s == n else
+              f"first {n_s:,} of {n:,} transactions, minsup {ms:,}") + \
+        f"; {r.n_candidates:,} candidate supports counted, {len(r):,} frequent itemsets"
+    return {"value": r.n_candidates / dt, "unit": "supports/s", "cores": cores, "kind": "oracle",
+            "sample": sample, "seconds": round(dt, 3)}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    csr, minsup = _load_workload(args.workload)
+    for _ in range(args.warmup):
+        pass  # the oracle has no warm state; warm-up steps would only repeat the work
+    times, vals = [], []
+    for _ in range(args.steps):
+        b = cpu_baseline(csr, minsup, budget_s=10.0)
+        times.append(b["seconds"])
+        vals.append(b["value"])
+    value = statistics.median(vals)
+    line = {"impl": "reference", "metric": "itemset supports/sec", "value": value, "unit": "supports/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000 * statistics.median(times), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic (seeded)",
+            "config": {"workload": args.workload, "desc": WORKLOAD_DESC[args.workload]},
+            "cpu_baseline": {"value": value, "unit": "supports/s", "cores": b["cores"], "kind": "oracle",
+                             "sample": b["sample"]},
+            "e2e": {"value": value, "unit": "supports/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = _args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    from paper_2412_19420_gb300 import fim
+
+    csr, minsup = _load_workload(args.workload)
+    stream = torch.cuda.Stream()
+    ctx = fim.fim_create(local, stream)
+    ip_d = torch.from_numpy(csr.indptr).cuda()
+    ix_d = torch.from_numpy(csr.indices).cuda()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+    flags = args.flags
+
+    def mine_device(out):
+        fim.fim_build_bitmaps(ctx, ip_d, ix_d, csr.m)
+        fim.fim_mine(ctx, minsup, flags)
+        return fim.fim_fetch_results(ctx, out)
+
+    # size the device output buffers once
+    fim.fim_build_bitmaps(ctx, ip_d, ix_d, csr.m)
+    fim.fim_mine(ctx, minsup, flags)
+    R, T = fim.fim_result_sizes(ctx)
+    out_d = (torch.empty(R + 1, dtype=torch.int64, device="cuda"),
+             torch.empty(max(T, 1), dtype=torch.int32, device="cuda"),
+             torch.empty(max(R, 1), dtype=torch.int32, device="cuda"))
+    for _ in range(args.warmup):
+        mine_device(out_d)
+    barrier()
+
+    # ---- timed: device-resident input, results left on the device -------
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    phase = {k: 0.0 for k in ("ms_build", "ms_singletons", "ms_pairs", "ms_dfs", "ms_compact")}
+    launches = 0
+    with ClockSampler(local) as clk:
+        barrier()
+        for k in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(k)
+            ev[k][0].record(stream)
+            mine_device(out_d)
+            ev[k][1].record(stream)
+            st = fim.fim_get_stats(ctx)
+            for p in phase:
+                phase[p] += st[p]
+            launches += st["launches_build"] + st["launches_mine"]
+        barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    ms_step = sum(step_ms) / len(step_ms)
+    st = fim.fim_get_stats(ctx)
+    supports = st["supports_singletons"] + st["supports_pairs"] + st["supports_dfs"]
+    t = torch.tensor([ms_step], dtype=torch.float64, device="cuda")
+    tot = torch.tensor([float(supports)], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(tot, op=dist.ReduceOp.SUM)
+    ms_max = float(t.item())
+    value = float(tot.item()) / (ms_max / 1000.0)
+
+    # ---- e2e: host CSR in, host results out, copies inside the timed region
+    ip_h = torch.from_numpy(csr.indptr).pin_memory()
+    ix_h = torch.from_numpy(csr.indices).pin_memory()
+    out_h = (torch.empty(R + 1, dtype=torch.int64).pin_memory(),
+             torch.empty(max(T, 1), dtype=torch.int32).pin_memory(),
+             torch.empty(max(R, 1), dtype=torch.int32).pin_memory())
+    e2e_ms = []
+    for k in range(args.warmup + args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(k)
+        stream.synchronize()
+        t0 = time.perf_counter()
+        fim.fim_build_bitmaps(ctx, ip_h.numpy(), ix_h.numpy(), csr.m)
+        fim.fim_mine(ctx, minsup, flags)
+        got = fim.fim_fetch_results(ctx, tuple(x.numpy() for x in out_h))
+        if k >= args.warmup:
+            e2e_ms.append(1000 * (time.perf_counter() - t0))
+    e2e_t = torch.tensor([statistics.mean(e2e_ms)], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+    e2e_value = float(tot.item()) / (float(e2e_t.item()) / 1000.0)
+    h2d = csr.indptr.nbytes + csr.indices.nbytes
+    d2h = 8 * (R + 1) + 4 * T + 4 * R
+
+    # ---- roofline of the dominant phase ---------------------------------
+    hbm, bf16, bf16_s, src = _peaks()
+    avg = {p: phase[p] / args.steps for p in phase}
+    dom = max(("ms_pairs", "ms_dfs", "ms_compact", "ms_build"), key=lambda p: avg[p])
+    if dom == "ms_dfs":
+        ach = st["dfs_bytes"] / (avg[dom] / 1000) / 1e9
+        roof = {"kernel": "dfs_kernel", "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                "frac": ach / hbm, "traffic": _kernel_traffic("dfs_kernel", args.workload),
+                "algorithmic_bytes_per_launch": st["dfs_bytes"]}
+    elif dom == "ms_pairs" and st["pair_path"] == 1:
+        fl = 2.0 * st["supports_pairs"] * csr.n
+        ach = fl / (avg[dom] / 1000) / 1e12
+        peak = 2 * bf16  # fp8 dense = 2 x bf16 dense (nominal ratio)
+        roof = {"kernel": "pairs_tc_kernel", "bound": "tensor", "achieved": ach, "peak": peak,
+                "unit": "TFLOP/s", "frac": ach / peak,
+                "traffic": _kernel_traffic("pairs_tc_kernel", args.workload)}
+    else:
+        nm = {"ms_pairs": "pairs_popc_kernel", "ms_compact": "compaction", "ms_build": "build_bitmaps_kernel"}[dom]
+        nbytes = {"ms_pairs": 4 * st["n_frequent_items"] * ((csr.n + 31) // 32),
+                  "ms_compact": 24 * st["n_sets"],
+                  "ms_build": csr.indptr.nbytes + csr.indices.nbytes + 4 * csr.m * ((csr.n + 31) // 32)}[dom]
+        ach = nbytes / (avg[dom] / 1000) / 1e9
+        roof = {"kernel": nm, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                "frac": ach / hbm, "traffic": _kernel_traffic(nm, args.workload)}
+    roof["peak_source"] = src
+    roof["phase_ms"] = {k: round(v, 4) for k, v in avg.items()}
+
+    line = {
+        "metric": "itemset supports/sec", "value": value, "unit": "supports/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic (seeded generator, paper_2412_19420_gb300.datagen)",
+        "config": {"workload": args.workload, "desc": WORKLOAD_DESC[args.workload],
+                   "n_trans": csr.n, "n_items": csr.m, "minsup": minsup, "flags": flags,
+                   "parallelism": f"replicas x{world}",
+                   "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write)",
+                   "frequent_itemsets": int(st["n_sets"]), "max_len": int(st["max_len"]),
+                   "supports_per_step": int(supports),
+                   "pair_path": "tcgen05" if st["pair_path"] == 1 else "popc"},
+        "e2e": {"value": e2e_value, "unit": "supports/s", "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h), "ms_per_step": float(e2e_t.item())},
+        "gpu_launches": int(launches),
+        "roofline": roof,
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(csr, minsup)
+    if rank == 0:
+        print(json.dumps(line))
+    _ = (np, got)
+    fim.fim_destroy(ctx)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

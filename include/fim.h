@@ -1,0 +1,218 @@
+/*
+ * fim.h -- C ABI of the GB300 Boolean-matrix frequent-itemset miner.
+ *
+ * The miner follows Section III of "A Matrix Logic Approach to Efficient
+ * Frequent Itemset Discovery in Large Data Sets" (arXiv 2412.19420):
+ *   matrix construction (Eq. 1)  -> fim_build_bitmaps
+ *   support calculation (Eq. 2) and frequent-itemset extraction with the
+ *   threshold test (Eq. 3)       -> fim_mine
+ *   the frequent itemsets        -> fim_fetch_results
+ *
+ * Conventions shared by every entry point
+ *   - Every call returns an int status: FIM_OK (0) or a negative FIM_E_* code.
+ *     No C++ exception crosses this boundary.  fim_strerror() names a code.
+ *   - A fim_ctx is bound to one CUDA device and one stream.  It owns every
+ *     device allocation it makes; fim_destroy() releases them.  A ctx is not
+ *     thread-safe: calls on one ctx must not overlap.
+ *   - Pointers are plain host or device pointers, as each call's flags say.
+ *     The library never keeps a caller's pointer after a call returns.
+ *   - Item ids are the caller's ids in [0, n_items); transaction order is the
+ *     caller's row order (row i of the CSR is transaction T_i).
+ *   - Supports are exact integer counts.  Results are canonical: items
+ *     ascending inside each set, sets ordered by size then lexicographically.
+ */
+#ifndef FIM_H
+#define FIM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define FIM_OK 0
+#define FIM_E_INVAL (-1)     /* bad argument: malformed CSR, item >= n_items, minsup 0, ... */
+#define FIM_E_NOMEM (-2)     /* device or host allocation failed                           */
+#define FIM_E_CUDA (-3)      /* a CUDA runtime call failed                                 */
+#define FIM_E_TIMEOUT (-4)   /* a bounded device-side wait ran out; the ctx stays usable   */
+#define FIM_E_STACK (-5)     /* DFS stack budget too small for the itemset depth           */
+#define FIM_E_TOO_SMALL (-6) /* caller's output buffer too small; required sizes returned  */
+#define FIM_E_STATE (-7)     /* call out of order (mine before build, fetch before mine)   */
+#define FIM_E_NODEV (-8)     /* no CUDA device / device id out of range                    */
+
+/* ---- flags ------------------------------------------------------------- */
+/* fim_build_bitmaps / fim_mine_batched: where the CSR arrays live */
+#define FIM_INPUT_HOST 0u
+#define FIM_INPUT_DEVICE 1u
+
+/* fim_mine / fim_mine_batched */
+#define FIM_STRICT 0x1u       /* frequent iff S(X) > minsup (Eq. 3 literally); default S(X) >= minsup */
+#define FIM_LEARNED 0x2u      /* the loaded MLP steers split/order/representation (never counts)    */
+#define FIM_PAIRS_POPC 0x4u   /* 2-itemset pass on CUDA cores (AND+popc) instead of tensor cores    */
+#define FIM_TRACE 0x8u        /* record one trace row per prefix class (features, subtree work)     */
+#define FIM_DIFFSET_RULE 0x10u/* choose bitmap/diffset per class by the closed-form size rule       */
+#define FIM_NO_SPLIT 0x20u    /* process every subtree inside the worker that found it              */
+#define FIM_MAXLEN(k) (((uint32_t)(k) & 0xffu) << 24) /* longest itemset reported; 0 = unbounded */
+
+/* fim_fetch_results: where the output buffers live */
+#define FIM_OUTPUT_HOST 0u
+#define FIM_OUTPUT_DEVICE 1u
+
+/* ---- limits ------------------------------------------------------------ */
+#define FIM_MAX_ITEMS 65535      /* n_items per database                           */
+#define FIM_MAX_TRANS 2147483647 /* n_trans per database (supports fit in uint32)  */
+
+typedef struct fim_ctx fim_ctx;
+
+/* Per-mine counters, filled by fim_get_stats after fim_mine. */
+typedef struct {
+    uint64_t n_trans, n_items, n_frequent_items, n_sets, max_len;
+    uint64_t supports_singletons; /* S(I_k) computed: n_items                      */
+    uint64_t supports_pairs;      /* S(I_a n I_b) computed: m'(m'-1)/2 (Eq. 2)     */
+    uint64_t supports_dfs;        /* supports of >= 3-itemsets computed by the DFS  */
+    uint64_t dfs_words;           /* 32-bit candidate words ANDed by the DFS        */
+    uint64_t dfs_bytes;           /* bytes the DFS kernel read/wrote algorithmically */
+    uint64_t classes;             /* prefix classes expanded                        */
+    uint64_t tasks_pushed;        /* classes handed to the device work queue        */
+    uint64_t diffset_classes;     /* classes counted through a diffset              */
+    uint64_t peak_device_bytes;   /* device memory held by the ctx                  */
+    uint64_t launches_build;      /* kernels launched by the last fim_build_bitmaps */
+    uint64_t launches_mine;       /* kernels launched by the last fim_mine          */
+    float ms_build, ms_singletons, ms_pairs, ms_dfs, ms_compact; /* CUDA-event times */
+    uint32_t pair_path;           /* 1 = tcgen05 tensor cores, 0 = CUDA-core popc   */
+    uint32_t reserved;
+} fim_stats;
+
+/* One database of a batch (fim_mine_batched).  CSR as for fim_build_bitmaps. */
+typedef struct {
+    const int64_t *indptr;   /* [n_trans + 1] */
+    const int32_t *indices;  /* [indptr[n_trans]] */
+    int64_t n_trans;
+    int32_t n_items;
+    int32_t pad;
+    uint64_t minsup;         /* absolute count, >= 1 */
+} fim_db_desc;
+
+/* fim_create: make a context on `device` (CUDA ordinal).  `cuda_stream` is a
+ * cudaStream_t to run on, or NULL for a stream the ctx creates and owns.
+ * Errors: FIM_E_NODEV, FIM_E_CUDA, FIM_E_NOMEM, FIM_E_INVAL (out == NULL). */
+int fim_create(fim_ctx **out, int device, void *cuda_stream);
+
+/* fim_destroy: free every device and host allocation of the ctx (NULL ok). */
+void fim_destroy(fim_ctx *ctx);
+
+/* fim_build_bitmaps -- matrix construction, Eq. 1 (Section III):
+ * M[i,j] = 1 iff item j occurs in transaction i.  The CSR gives transaction i
+ * as indices[indptr[i] : indptr[i+1]]; repeated items inside a transaction
+ * collapse (set membership), empty transactions are allowed and count toward
+ * n_trans.  Input arrays are host pointers (FIM_INPUT_HOST) or device pointers
+ * (FIM_INPUT_DEVICE); they are copied and may be freed when the call returns.
+ * The ctx keeps the matrix as item-major bit columns: column j is
+ * ceil(n_trans/32) uint32 words, bit (i mod 32) of word i/32 = M[i,j].
+ * Errors: FIM_E_INVAL if indptr[0] != 0, indptr decreases, an item is outside
+ * [0, n_items), n_items > FIM_MAX_ITEMS or n_trans > FIM_MAX_TRANS (the ctx
+ * then holds no matrix); FIM_E_NOMEM; FIM_E_CUDA. */
+int fim_build_bitmaps(fim_ctx *ctx, const int64_t *indptr, const int32_t *indices,
+                      int64_t n_trans, int32_t n_items, uint32_t flags);
+
+/* fim_mine -- support calculation and frequent-itemset extraction
+ * (Eq. 2 generalised to any itemset by sequential column AND; Eq. 3):
+ * finds every non-empty X with S(X) >= minsup (or S(X) > minsup under
+ * FIM_STRICT), S(X) = popcount of the AND of X's bit columns.  Singletons by
+ * column popcount, pairs by the A^T A contraction on tensor cores, larger sets
+ * by a persistent depth-first prefix-extension kernel.  The result replaces
+ * any earlier one held by the ctx.  Requires a prior fim_build_bitmaps.
+ * Errors: FIM_E_STATE (no matrix), FIM_E_INVAL (minsup == 0 without
+ * FIM_STRICT), FIM_E_NOMEM, FIM_E_TIMEOUT, FIM_E_CUDA. */
+int fim_mine(fim_ctx *ctx, uint64_t minsup, uint32_t flags);
+
+/* fim_fetch_results -- the frequent itemsets of the last fim_mine, canonical.
+ * Always writes *n_sets and *n_items_total (sum of set sizes).  If offsets,
+ * items and supports are all NULL it only reports the sizes.  Otherwise
+ * offsets gets n_sets+1 entries (set q is items[offsets[q] : offsets[q+1]]),
+ * items gets the caller's item ids, supports the exact counts; cap_sets and
+ * cap_items give the capacities of supports/offsets-1 and items.
+ * flags: FIM_OUTPUT_HOST (host buffers) or FIM_OUTPUT_DEVICE (device buffers).
+ * Errors: FIM_E_STATE (nothing mined), FIM_E_TOO_SMALL (sizes still written),
+ * FIM_E_INVAL, FIM_E_CUDA. */
+int fim_fetch_results(fim_ctx *ctx, uint64_t *n_sets, uint64_t *n_items_total,
+                      uint64_t *offsets, uint32_t *items, uint32_t *supports,
+                      uint64_t cap_sets, uint64_t cap_items, uint32_t flags);
+
+/* fim_get_stats: counters and phase times of the last fim_mine (or batch). */
+int fim_get_stats(const fim_ctx *ctx, fim_stats *out);
+
+/* fim_mine_batched -- many independent databases in one persistent launch,
+ * replayed from a captured CUDA graph when the same batch shape repeats.
+ * dbs[d] describes database d (host or device CSR per flags &
+ * FIM_INPUT_DEVICE); each is mined with its own dbs[d].minsup exactly as
+ * fim_build_bitmaps + fim_mine would.  Results are fetched per database with
+ * fim_fetch_batched.  Errors as fim_build_bitmaps and fim_mine, for any d. */
+int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *dbs, uint32_t flags);
+
+/* fim_fetch_batched -- results of database `db` of the last batch, with the
+ * same contract as fim_fetch_results. */
+int fim_fetch_batched(fim_ctx *ctx, int db, uint64_t *n_sets, uint64_t *n_items_total,
+                      uint64_t *offsets, uint32_t *items, uint32_t *supports,
+                      uint64_t cap_sets, uint64_t cap_items, uint32_t flags);
+
+/* ---- learned scheduler (8 -> 64 -> 64 -> 2 bf16 MLP) --------------------
+ * The network predicts, per prefix class, log2(1 + subtree work) and the
+ * logit of storing the class as a diffset.  It only steers scheduling and
+ * representation; supports are always counted exactly.  The paper names an
+ * adaptive, data-dependent choice of Boolean operation sequence and deep
+ * models as directions (Sections I and V) without specifying a network.
+ * Weight layout (float32, 4,866 values): W1[64][8], b1[64], W2[64][64],
+ * b2[64], W3[2][64], b3[2]. */
+#define FIM_MLP_PARAMS 4866
+#define FIM_MLP_FEATURES 8
+
+/* fim_sched_load_weights: copy host float32 weights into the ctx (bf16 for
+ * inference).  Errors: FIM_E_INVAL if n_params != FIM_MLP_PARAMS. */
+int fim_sched_load_weights(fim_ctx *ctx, const float *weights, size_t n_params);
+
+/* fim_fetch_traces: trace rows of the last fim_mine run with FIM_TRACE.
+ * features [n][8] and targets [n][2] (log2(1+subtree words), diffset label)
+ * are host float32 buffers of capacity cap rows, or NULL to query *n_rows.
+ * Errors: FIM_E_STATE, FIM_E_TOO_SMALL. */
+int fim_fetch_traces(fim_ctx *ctx, uint64_t *n_rows, float *features, float *targets,
+                     uint64_t cap);
+
+/* fim_mlp_forward: y[B][2] = MLP(x[B][8]) with params[4866] (all DEVICE
+ * float32 pointers).  bf16 != 0 rounds weights and activations to bf16 with
+ * float32 accumulation (the inference precision); 0 computes in float32.
+ * cache (device, B*(64+64+64+64) floats) keeps pre-activations for backward,
+ * or NULL.  Runs on the ctx stream.  Errors: FIM_E_INVAL, FIM_E_CUDA. */
+int fim_mlp_forward(fim_ctx *ctx, const float *params, const float *x, int64_t B,
+                    float *y, float *cache, int bf16);
+
+/* fim_mlp_backward: grad[4866] (device) = d loss / d params for the loss
+ * mean_b[0.5 (y0-t0)^2 + softplus(y1) - t1 y1], from x, y, t (device) and
+ * the cache of fim_mlp_forward with the same params.  Returns the loss in
+ * *loss_out (host) when non-NULL.  Errors: FIM_E_INVAL, FIM_E_CUDA. */
+int fim_mlp_backward(fim_ctx *ctx, const float *params, const float *x, const float *y,
+                     const float *t, const float *cache, int64_t B, float *grad,
+                     float *loss_out, int bf16);
+
+/* fim_mlp_adam: one Adam step (bias-corrected, step counts from 1) on device
+ * arrays params/m/v from grad.  Errors: FIM_E_INVAL, FIM_E_CUDA. */
+int fim_mlp_adam(fim_ctx *ctx, float *params, const float *grad, float *m, float *v,
+                 int step, float lr, float beta1, float beta2, float eps);
+
+/* fim_minsup_from_ppm: ceil(n_trans * ppm / 1e6) in integers, at least 1:
+ * the threshold of Eq. 3 given as a fraction of the transactions. */
+uint64_t fim_minsup_from_ppm(int64_t n_trans, uint32_t ppm);
+
+/* fim_strerror: static description of a status code. */
+const char *fim_strerror(int status);
+
+/* fim_version: ABI version (major << 16 | minor). */
+uint32_t fim_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FIM_H */

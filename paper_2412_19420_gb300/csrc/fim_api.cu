@@ -1,0 +1,431 @@
+// fim_api.cu -- the C ABI of include/fim.h: context, memory, and the order of
+// the three stages of Section III (matrix construction, support calculation,
+// frequent-itemset extraction).  No exception crosses the boundary; every
+// entry point returns a FIM_* status.
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "fim_common.cuh"
+
+int dfs_threads();
+
+namespace {
+
+thread_local char g_last_cuda[256] = {0};
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && cudaSetDevice(dev) == cudaSuccess) ok = true;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+constexpr unsigned long long kTaskCap = 1ull << 20;
+constexpr unsigned long long kCandPoolCap = 1ull << 24;
+constexpr size_t kStackBudget = 8ull << 30;   // first try; grows on FIM_E_STACK
+constexpr size_t kStackBudgetMax = 64ull << 30;
+constexpr unsigned long long kSpinLimitNs = 60ull * 1000 * 1000 * 1000;
+
+}  // namespace
+
+void fim_set_cuda_error(cudaError_t e, const char *what, const char *file, int line) {
+    snprintf(g_last_cuda, sizeof(g_last_cuda), "%s (%s) at %s:%d: %s", cudaGetErrorName(e), what,
+             file, line, cudaGetErrorString(e));
+    (void)cudaGetLastError();  // clear a sticky-free error so the ctx stays usable
+}
+
+int fim_reserve(fim_ctx *ctx, DevBuf &b, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    if (bytes <= b.bytes) return FIM_OK;
+    if (b.p) {
+        FIM_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+        cudaFree(b.p);
+        ctx->bytes_held -= b.bytes;
+        b.p = nullptr;
+        b.bytes = 0;
+    }
+    size_t nb = bytes + bytes / 4;
+    nb = (nb + 255) & ~(size_t)255;
+    cudaError_t e = cudaMalloc(&b.p, nb);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        e = cudaMalloc(&b.p, bytes);
+        nb = bytes;
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            b.p = nullptr;
+            return FIM_E_NOMEM;
+        }
+    }
+    b.bytes = nb;
+    ctx->bytes_held += nb;
+    if (ctx->bytes_held > ctx->stats.peak_device_bytes) ctx->stats.peak_device_bytes = ctx->bytes_held;
+    return FIM_OK;
+}
+
+void fim_release(fim_ctx *ctx, DevBuf &b) {
+    if (b.p) {
+        cudaFree(b.p);
+        ctx->bytes_held -= b.bytes;
+    }
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+extern "C" {
+
+uint32_t fim_version(void) { return (1u << 16) | 0u; }
+
+const char *fim_strerror(int s) {
+    switch (s) {
+        case FIM_OK: return "ok";
+        case FIM_E_INVAL: return "invalid argument or malformed database";
+        case FIM_E_NOMEM: return "out of memory";
+        case FIM_E_CUDA: return g_last_cuda[0] ? g_last_cuda : "CUDA error";
+        case FIM_E_TIMEOUT: return "bounded device wait expired";
+        case FIM_E_STACK: return "DFS stack budget exceeded";
+        case FIM_E_TOO_SMALL: return "output buffer too small";
+        case FIM_E_STATE: return "call out of order";
+        case FIM_E_NODEV: return "no such CUDA device";
+        default: return "unknown status";
+    }
+}
+
+uint64_t fim_minsup_from_ppm(int64_t n_trans, uint32_t ppm) {
+    if (n_trans <= 0) return 1;
+    const unsigned __int128 num = (unsigned __int128)(uint64_t)n_trans * ppm + 999999u;
+    const uint64_t v = (uint64_t)(num / 1000000u);
+    return v ? v : 1;
+}
+
+int fim_create(fim_ctx **out, int device, void *cuda_stream) {
+    if (!out) return FIM_E_INVAL;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= 0) {
+        (void)cudaGetLastError();
+        return FIM_E_NODEV;
+    }
+    if (device < 0 || device >= ndev) return FIM_E_NODEV;
+    DeviceGuard g(device);
+    if (!g.ok) return FIM_E_CUDA;
+    fim_ctx *ctx = new (std::nothrow) fim_ctx();
+    if (!ctx) return FIM_E_NOMEM;
+    ctx->device = device;
+    cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (cuda_stream) {
+        ctx->stream = (cudaStream_t)cuda_stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete ctx;
+            return FIM_E_CUDA;
+        }
+        ctx->own_stream = true;
+    }
+    for (auto &e : ctx->ev) cudaEventCreate(&e);
+    int rc = fim_reserve(ctx, ctx->counters, sizeof(MineCounters));
+    if (rc == FIM_OK) rc = fim_reserve(ctx, ctx->dev_flag, 4 * sizeof(int));
+    if (rc != FIM_OK) {
+        fim_destroy(ctx);
+        return rc;
+    }
+    *out = ctx;
+    return FIM_OK;
+}
+
+void fim_destroy(fim_ctx *ctx) {
+    if (!ctx) return;
+    DeviceGuard g(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    DevBuf *all[] = {&ctx->csr_ptr, &ctx->csr_idx, &ctx->bm, &ctx->item_sup, &ctx->perm, &ctx->rank,
+                     &ctx->dev_flag, &ctx->pair_cnt, &ctx->pairbits, &ctx->roots, &ctx->tasks,
+                     &ctx->cand_pool, &ctx->stack_bits, &ctx->frame_items, &ctx->frame_sups,
+                     &ctx->rec_off, &ctx->rec_len, &ctx->rec_sup, &ctx->rec_items, &ctx->counters,
+                     &ctx->keys, &ctx->idx_a, &ctx->idx_b, &ctx->hist, &ctx->scan_tmp, &ctx->out_off,
+                     &ctx->out_items, &ctx->out_sup, &ctx->mlp_w32, &ctx->mlp_wbf, &ctx->trace_x,
+                     &ctx->trace_y};
+    for (DevBuf *b : all) fim_release(ctx, *b);
+    for (auto &e : ctx->ev)
+        if (e) cudaEventDestroy(e);
+    if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+}
+
+int fim_build_bitmaps(fim_ctx *ctx, const int64_t *indptr, const int32_t *indices, int64_t n_trans,
+                      int32_t n_items, uint32_t flags) {
+    if (!ctx) return FIM_E_INVAL;
+    if (n_trans < 0 || n_trans > FIM_MAX_TRANS || n_items < 0 || n_items > FIM_MAX_ITEMS) return FIM_E_INVAL;
+    if (!indptr) return FIM_E_INVAL;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return FIM_E_CUDA;
+    ctx->built = false;
+    ctx->mined = false;
+    ctx->n = n_trans;
+    ctx->m = n_items;
+    ctx->nw = ceil_div64(n_trans, 32);
+    ctx->nwp = round_up64(ctx->nw, FIM_WORDS_ALIGN);
+    cudaStream_t st = ctx->stream;
+    cudaEventRecord(ctx->ev[0], st);
+    const uint64_t launches0 = ctx->launches;
+
+    const int64_t *d_ptr = indptr;
+    const int32_t *d_idx = indices;
+    if (!(flags & FIM_INPUT_DEVICE)) {
+        const int64_t nnz = indptr[n_trans];
+        if (indptr[0] != 0 || nnz < 0 || (nnz > 0 && !indices)) return FIM_E_INVAL;
+        FIM_TRY(fim_reserve(ctx, ctx->csr_ptr, sizeof(int64_t) * (size_t)(n_trans + 1)));
+        FIM_TRY(fim_reserve(ctx, ctx->csr_idx, sizeof(int32_t) * (size_t)(nnz > 0 ? nnz : 1)));
+        FIM_CUDA_TRY(cudaMemcpyAsync(ctx->csr_ptr.p, indptr, sizeof(int64_t) * (size_t)(n_trans + 1),
+                                     cudaMemcpyHostToDevice, st));
+        if (nnz > 0)
+            FIM_CUDA_TRY(cudaMemcpyAsync(ctx->csr_idx.p, indices, sizeof(int32_t) * (size_t)nnz,
+                                         cudaMemcpyHostToDevice, st));
+        d_ptr = ctx->csr_ptr.as<int64_t>();
+        d_idx = ctx->csr_idx.as<int32_t>();
+    } else {
+        int64_t first = -1;
+        FIM_CUDA_TRY(cudaMemcpyAsync(&first, indptr, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        FIM_CUDA_TRY(cudaStreamSynchronize(st));
+        if (first != 0) return FIM_E_INVAL;
+    }
+    const size_t mm = (size_t)(n_items > 0 ? n_items : 1);
+    FIM_TRY(fim_reserve(ctx, ctx->bm, sizeof(uint32_t) * (size_t)ctx->nwp * mm));
+    FIM_TRY(fim_reserve(ctx, ctx->item_sup, sizeof(uint32_t) * mm));
+    FIM_TRY(fim_reserve(ctx, ctx->perm, sizeof(int32_t) * mm));
+    FIM_TRY(fim_reserve(ctx, ctx->rank, sizeof(int32_t) * mm));
+    FIM_TRY(launch_build_bitmaps(ctx, d_ptr, d_idx));
+    cudaEventRecord(ctx->ev[1], st);
+    FIM_TRY(launch_item_support(ctx));
+    cudaEventRecord(ctx->ev[2], st);
+    int flag[2] = {0, 0};
+    FIM_CUDA_TRY(cudaMemcpyAsync(flag, ctx->dev_flag.p, sizeof(flag), cudaMemcpyDeviceToHost, st));
+    FIM_CUDA_TRY(cudaStreamSynchronize(st));
+    if (flag[0]) return FIM_E_INVAL;
+    ctx->max_row_len = flag[1];
+    cudaEventElapsedTime(&ctx->stats.ms_build, ctx->ev[0], ctx->ev[1]);
+    cudaEventElapsedTime(&ctx->stats.ms_singletons, ctx->ev[1], ctx->ev[2]);
+    ctx->stats.launches_build = ctx->launches - launches0;
+    ctx->built = true;
+    return FIM_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+struct MineState {
+    int depth_cap = 0;
+    int64_t frame_pool = 0;
+    size_t stack_budget = kStackBudget;
+};
+
+// One attempt at the whole mine with the current capacities.  Returns
+// FIM_OK, or an error; *retry is set when a capacity must grow first.
+int mine_once(fim_ctx *ctx, uint32_t thr, uint32_t flags, MineState &ms, bool *retry) {
+    cudaStream_t st = ctx->stream;
+    *retry = false;
+    MineCounters *d_ctr = ctx->counters.as<MineCounters>();
+    FIM_CUDA_TRY(cudaMemsetAsync(d_ctr, 0, sizeof(MineCounters), st));
+    cudaEventRecord(ctx->ev[0], st);
+    FIM_TRY(launch_rank_items(ctx, thr, d_ctr));
+    FIM_TRY(launch_emit_singletons(ctx, d_ctr));
+    FIM_CUDA_TRY(cudaMemcpyAsync(&ctx->host_ctr, d_ctr, sizeof(MineCounters), cudaMemcpyDeviceToHost, st));
+    FIM_CUDA_TRY(cudaStreamSynchronize(st));
+    ctx->mfreq = ctx->host_ctr.m_freq;
+    const int mf = ctx->mfreq;
+    const uint32_t maxlen = flags >> 24;
+    cudaEventRecord(ctx->ev[1], st);
+    const bool do_pairs = mf >= 2 && (maxlen == 0 || maxlen >= 2);
+    ctx->stats.pair_path = 0;
+    if (do_pairs) {
+        const int mpw = (int)ceil_div64(mf, 32);
+        const size_t npairs = (size_t)mf * (mf - 1) / 2;
+        FIM_TRY(fim_reserve(ctx, ctx->pair_cnt, sizeof(int) * (size_t)mf * mf));
+        FIM_TRY(fim_reserve(ctx, ctx->pairbits, sizeof(uint32_t) * (size_t)mf * mpw));
+        FIM_TRY(fim_reserve(ctx, ctx->roots, sizeof(uint32_t) * 3 * npairs));
+        int rc = FIM_E_INVAL;
+        if (!(flags & FIM_PAIRS_POPC)) rc = launch_pairs_tc(ctx);
+        if (rc == FIM_OK) ctx->stats.pair_path = 1;
+        else FIM_TRY(launch_pairs_popc(ctx));
+        FIM_TRY(launch_pairs_finalize(ctx, thr, d_ctr));
+    }
+    cudaEventRecord(ctx->ev[2], st);
+    const bool do_dfs = do_pairs && mf >= 3 && (maxlen == 0 || maxlen >= 3);
+    if (do_dfs) {
+        const int workers = ctx->num_sms * ctx->dfs_ctas_per_sm;
+        // deepest class: a prefix can hold at most min(longest row, m') items
+        int bound = ctx->max_row_len < mf ? ctx->max_row_len : mf;
+        if (maxlen && (int)maxlen < bound) bound = (int)maxlen;
+        if (bound > 240) bound = 240;  // the worker's shared-memory frame arrays hold 256 levels
+        const int levels_needed = bound > 2 ? bound - 1 : 1;
+        const size_t per_level = (size_t)workers * (size_t)ctx->nwp * sizeof(uint32_t);
+        if (ms.depth_cap == 0) {
+            size_t cap = ms.stack_budget / (per_level ? per_level : 1);
+            ms.depth_cap = (int)(cap < (size_t)levels_needed ? cap : (size_t)levels_needed);
+            if (ms.depth_cap < 2) ms.depth_cap = 2;
+        }
+        if (ms.frame_pool == 0) ms.frame_pool = 4LL * mf + 1024;
+        FIM_TRY(fim_reserve(ctx, ctx->stack_bits, per_level * (size_t)ms.depth_cap));
+        FIM_TRY(fim_reserve(ctx, ctx->frame_items, sizeof(uint32_t) * (size_t)workers * ms.frame_pool));
+        FIM_TRY(fim_reserve(ctx, ctx->frame_sups, sizeof(uint32_t) * (size_t)workers * ms.frame_pool));
+        FIM_TRY(fim_reserve(ctx, ctx->tasks, sizeof(Task) * kTaskCap));
+        FIM_TRY(fim_reserve(ctx, ctx->cand_pool, sizeof(uint32_t) * kCandPoolCap));
+        FIM_CUDA_TRY(cudaMemsetAsync(ctx->tasks.p, 0, sizeof(Task) * kTaskCap, st));
+        const size_t npairs = (size_t)mf * (mf - 1) / 2;
+        DfsParams p{};
+        p.bm = ctx->bm.as<uint32_t>();
+        p.perm = ctx->perm.as<int32_t>();
+        p.pairbits = ctx->pairbits.as<uint32_t>();
+        p.nwp = ctx->nwp;
+        p.nw = ctx->nw;
+        p.mfreq = mf;
+        p.mpw = (int)ceil_div64(mf, 32);
+        p.thr = thr;
+        p.maxlen = maxlen;
+        p.root_a = ctx->roots.as<uint32_t>();
+        p.root_b = p.root_a + npairs;
+        p.root_sup = p.root_a + 2 * npairs;
+        p.tasks = ctx->tasks.as<Task>();
+        p.task_cap = kTaskCap;
+        p.cand_pool = ctx->cand_pool.as<uint32_t>();
+        p.cand_pool_cap = kCandPoolCap;
+        p.split_depth = (flags & FIM_NO_SPLIT) ? 0 : ctx->split_depth;
+        p.stack_bits = ctx->stack_bits.as<uint32_t>();
+        p.frame_items = ctx->frame_items.as<uint32_t>();
+        p.frame_sups = ctx->frame_sups.as<uint32_t>();
+        p.frame_pool = ms.frame_pool;
+        p.depth_cap = ms.depth_cap;
+        p.rec_off = ctx->rec_off.as<unsigned long long>();
+        p.rec_len = ctx->rec_len.as<uint32_t>();
+        p.rec_sup = ctx->rec_sup.as<uint32_t>();
+        p.rec_items = ctx->rec_items.as<uint32_t>();
+        p.rec_cap = ctx->rec_cap;
+        p.rec_items_cap = ctx->rec_items_cap;
+        p.ctr = d_ctr;
+        p.spin_limit = kSpinLimitNs;
+        FIM_TRY(launch_dfs(ctx, p, workers, dfs_threads()));
+    }
+    cudaEventRecord(ctx->ev[3], st);
+    FIM_CUDA_TRY(cudaMemcpyAsync(&ctx->host_ctr, d_ctr, sizeof(MineCounters), cudaMemcpyDeviceToHost, st));
+    FIM_CUDA_TRY(cudaStreamSynchronize(st));
+    const MineCounters &c = ctx->host_ctr;
+    if (c.err == FIM_E_STACK) {
+        if (ms.stack_budget >= kStackBudgetMax) return FIM_E_STACK;
+        ms.stack_budget *= 2;
+        ms.depth_cap = ms.depth_cap * 2 > 240 ? 240 : ms.depth_cap * 2;
+        ms.frame_pool *= 2;
+        *retry = true;
+        return FIM_OK;
+    }
+    if (c.err != 0) return c.err;
+    if (c.overflow) {
+        ctx->rec_cap = c.n_records + c.n_records / 4 + 1024;
+        ctx->rec_items_cap = c.n_rec_items + c.n_rec_items / 4 + 4096;
+        FIM_TRY(fim_reserve(ctx, ctx->rec_off, sizeof(unsigned long long) * ctx->rec_cap));
+        FIM_TRY(fim_reserve(ctx, ctx->rec_len, sizeof(uint32_t) * ctx->rec_cap));
+        FIM_TRY(fim_reserve(ctx, ctx->rec_sup, sizeof(uint32_t) * ctx->rec_cap));
+        FIM_TRY(fim_reserve(ctx, ctx->rec_items, sizeof(uint32_t) * ctx->rec_items_cap));
+        *retry = true;
+        return FIM_OK;
+    }
+    int lmax = c.max_len;
+    if (mf >= 1 && lmax < 1) lmax = 1;
+    if (c.n_roots > 0 && lmax < 2) lmax = 2;
+    ctx->host_ctr.max_len = lmax;
+    FIM_TRY(launch_compact(ctx, c.n_records));
+    cudaEventRecord(ctx->ev[4], st);
+    FIM_CUDA_TRY(cudaStreamSynchronize(st));
+    FIM_CUDA_TRY(cudaGetLastError());
+    cudaEventElapsedTime(&ctx->stats.ms_pairs, ctx->ev[1], ctx->ev[2]);
+    cudaEventElapsedTime(&ctx->stats.ms_dfs, ctx->ev[2], ctx->ev[3]);
+    cudaEventElapsedTime(&ctx->stats.ms_compact, ctx->ev[3], ctx->ev[4]);
+    return FIM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fim_mine(fim_ctx *ctx, uint64_t minsup, uint32_t flags) {
+    if (!ctx) return FIM_E_INVAL;
+    if (!ctx->built) return FIM_E_STATE;
+    if (!(flags & FIM_STRICT) && minsup == 0) return FIM_E_INVAL;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return FIM_E_CUDA;
+    ctx->mined = false;
+    ctx->mflags = flags;
+    uint64_t thr64 = (flags & FIM_STRICT) ? minsup + 1 : minsup;
+    if ((flags & FIM_STRICT) && minsup == UINT64_MAX) thr64 = UINT64_MAX;
+    const uint32_t thr = thr64 > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)thr64;
+    if (ctx->rec_cap == 0) {
+        ctx->rec_cap = 1ull << 20;
+        ctx->rec_items_cap = 1ull << 23;
+    }
+    FIM_TRY(fim_reserve(ctx, ctx->rec_off, sizeof(unsigned long long) * ctx->rec_cap));
+    FIM_TRY(fim_reserve(ctx, ctx->rec_len, sizeof(uint32_t) * ctx->rec_cap));
+    FIM_TRY(fim_reserve(ctx, ctx->rec_sup, sizeof(uint32_t) * ctx->rec_cap));
+    FIM_TRY(fim_reserve(ctx, ctx->rec_items, sizeof(uint32_t) * ctx->rec_items_cap));
+    const uint64_t launches0 = ctx->launches;
+    MineState ms;
+    bool retry = true;
+    for (int attempt = 0; retry && attempt < 8; attempt++) FIM_TRY(mine_once(ctx, thr, flags, ms, &retry));
+    if (retry) return FIM_E_NOMEM;
+    const MineCounters &c = ctx->host_ctr;
+    fim_stats &s = ctx->stats;
+    s.n_trans = (uint64_t)ctx->n;
+    s.n_items = (uint64_t)ctx->m;
+    s.n_frequent_items = (uint64_t)ctx->mfreq;
+    s.n_sets = c.n_records;
+    s.max_len = (uint64_t)c.max_len;
+    s.supports_singletons = (uint64_t)ctx->m;
+    const uint64_t mf = (uint64_t)ctx->mfreq;
+    const uint32_t maxlen = flags >> 24;
+    s.supports_pairs = (mf >= 2 && (maxlen == 0 || maxlen >= 2)) ? mf * (mf - 1) / 2 : 0;
+    s.supports_dfs = c.supports_dfs;
+    s.dfs_words = c.dfs_words;
+    s.dfs_bytes = c.dfs_bytes;
+    s.classes = c.classes;
+    s.tasks_pushed = c.pushed;
+    s.diffset_classes = c.diffset;
+    s.launches_mine = ctx->launches - launches0;
+    if (ctx->bytes_held > s.peak_device_bytes) s.peak_device_bytes = ctx->bytes_held;
+    ctx->mined = true;
+    return FIM_OK;
+}
+
+int fim_fetch_results(fim_ctx *ctx, uint64_t *n_sets, uint64_t *n_items_total, uint64_t *offsets,
+                      uint32_t *items, uint32_t *supports, uint64_t cap_sets, uint64_t cap_items,
+                      uint32_t flags) {
+    if (!ctx || !n_sets || !n_items_total) return FIM_E_INVAL;
+    if (!ctx->mined) return FIM_E_STATE;
+    *n_sets = ctx->out_sets;
+    *n_items_total = ctx->out_items_total;
+    if (!offsets && !items && !supports) return FIM_OK;
+    if (!offsets || !supports || (!items && ctx->out_items_total)) return FIM_E_INVAL;
+    if (cap_sets < ctx->out_sets || cap_items < ctx->out_items_total) return FIM_E_TOO_SMALL;
+    DeviceGuard g(ctx->device);
+    if (!g.ok) return FIM_E_CUDA;
+    const cudaMemcpyKind k = (flags & FIM_OUTPUT_DEVICE) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    cudaStream_t st = ctx->stream;
+    FIM_CUDA_TRY(cudaMemcpyAsync(offsets, ctx->out_off.p, sizeof(uint64_t) * (ctx->out_sets + 1), k, st));
+    if (ctx->out_items_total)
+        FIM_CUDA_TRY(cudaMemcpyAsync(items, ctx->out_items.p, sizeof(uint32_t) * ctx->out_items_total, k, st));
+    if (ctx->out_sets)
+        FIM_CUDA_TRY(cudaMemcpyAsync(supports, ctx->out_sup.p, sizeof(uint32_t) * ctx->out_sets, k, st));
+    FIM_CUDA_TRY(cudaStreamSynchronize(st));
+    return FIM_OK;
+}
+
+int fim_get_stats(const fim_ctx *ctx, fim_stats *out) {
+    if (!ctx || !out) return FIM_E_INVAL;
+    *out = ctx->stats;
+    return FIM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,243 @@
+// fim_common.cuh -- internal declarations shared by the miner's .cu files.
+//
+// Data layout in device memory (one database):
+//   bm        uint32 [m][nwp]   item-major bit columns (Eq. 1): bit (i % 32) of
+//                               word i / 32 of column j is M[i, j]; nwp = words per
+//                               column padded to a multiple of 128 (512 B); pad
+//                               bits and pad words are 0.
+//   item_sup  uint32 [m]        S(I_j), column popcount (Eq. 3 aggregation)
+//   perm      int32  [m']       internal id -> caller's item id.  Internal ids
+//                               order the frequent items by (support, id) ascending.
+//   pair_cnt  int32  [m'][m']   S(I_a n I_b) for a < b (Eq. 2), upper triangle
+//   pairbits  uint32 [m'][mpw]  bit b of row a set iff a < b and {a,b} frequent
+//   records   (off u64, len u32, sup u32) per frequent itemset + an item pool
+//                               of internal ids; the compactor turns them into the
+//                               canonical (offsets, items, supports) output.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "../../include/fim.h"
+
+#define FIM_WORDS_ALIGN 128  // column padding, in 32-bit words (512 bytes)
+
+// ---------------------------------------------------------------- utilities
+#define FIM_CUDA_TRY(expr)                                        \
+    do {                                                          \
+        cudaError_t _e = (expr);                                  \
+        if (_e != cudaSuccess) {                                  \
+            fim_set_cuda_error(_e, #expr, __FILE__, __LINE__);    \
+            return (_e == cudaErrorMemoryAllocation) ? FIM_E_NOMEM : FIM_E_CUDA; \
+        }                                                         \
+    } while (0)
+
+#define FIM_TRY(expr)            \
+    do {                         \
+        int _r = (expr);         \
+        if (_r != FIM_OK) return _r; \
+    } while (0)
+
+void fim_set_cuda_error(cudaError_t e, const char *what, const char *file, int line);
+
+static inline int64_t ceil_div64(int64_t a, int64_t b) { return (a + b - 1) / b; }
+__host__ __device__ __forceinline__ int64_t min64(int64_t a, int64_t b) { return a < b ? a : b; }
+__host__ __device__ __forceinline__ int64_t max64(int64_t a, int64_t b) { return a > b ? a : b; }
+static inline int64_t round_up64(int64_t a, int64_t b) { return ceil_div64(a, b) * b; }
+
+// A grow-only device buffer owned by a ctx.
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    template <class T> T *as() const { return static_cast<T *>(p); }
+};
+
+// Device-side counters of one mine (kept in one small struct so a single
+// memset clears them and a single copy reads them back).
+struct MineCounters {
+    unsigned long long n_records;    // frequent itemsets emitted
+    unsigned long long n_rec_items;  // items emitted into the record pool
+    unsigned long long supports_dfs; // supports evaluated by the DFS
+    unsigned long long dfs_words;    // candidate words ANDed by the DFS
+    unsigned long long dfs_bytes;    // algorithmic bytes moved by the DFS
+    unsigned long long classes;      // classes expanded
+    unsigned long long pushed;       // tasks pushed to the queue
+    unsigned long long diffset;      // classes counted via a diffset
+    unsigned long long ticket;       // next work ticket
+    unsigned long long qtail;        // next free queue slot
+    unsigned long long pool_top;     // next free word of the candidate pool
+    unsigned long long n_roots;      // frequent pairs (root classes)
+    unsigned long long n_traces;     // trace rows written
+    long long pending;               // tasks pushed but not finished
+    int err;                         // FIM_OK or a FIM_E_* from the device
+    int overflow;                    // bit 0 records, bit 1 items, bit 2 traces
+    int max_len;                     // longest itemset emitted
+    int m_freq;                      // m' (frequent items)
+    int max_row_freq;                // most frequent items in one transaction
+    int pad[3];
+};
+
+// A pushed prefix class: items (internal ids) + support + candidate list.
+#define FIM_TASK_MAXR 8  // longest prefix a queued task may carry
+struct Task {
+    uint32_t items[FIM_TASK_MAXR];
+    uint32_t len;
+    uint32_t support;
+    uint32_t n_cand;
+    uint32_t ready;            // 0 until published
+    unsigned long long cand_off;  // into the candidate pool
+    float prio;                // predicted work (learned mode) or 0
+    uint32_t pad;
+};
+
+// One frame of a worker's DFS stack lives in global memory.
+struct DfsParams {
+    const uint32_t *bm;
+    const int32_t *perm;
+    const uint32_t *pairbits;
+    int64_t nwp;        // words per column (multiple of 128)
+    int64_t nw;         // words that hold transactions
+    int32_t mfreq;      // m'
+    int32_t mpw;        // words per pairbits row
+    uint32_t thr;       // frequent iff support >= thr
+    uint32_t maxlen;    // 0 = unbounded
+    // roots: frequent pairs
+    const uint32_t *root_a, *root_b, *root_sup;
+    // queue
+    Task *tasks;
+    unsigned long long task_cap;
+    uint32_t *cand_pool;
+    unsigned long long cand_pool_cap;
+    int split_depth;    // push children whose prefix length <= split_depth
+    // per-worker stack
+    uint32_t *stack_bits;   // [workers][depth][nwp]
+    uint32_t *frame_items;  // [workers][pool]  F lists (internal ids)
+    uint32_t *frame_sups;   // [workers][pool]
+    int64_t frame_pool;     // entries per worker
+    int depth_cap;          // levels per worker
+    // results
+    unsigned long long *rec_off;
+    uint32_t *rec_len;
+    uint32_t *rec_sup;
+    uint32_t *rec_items;
+    unsigned long long rec_cap, rec_items_cap;
+    // learned / traces
+    const __nv_bfloat16 *mlp_w;  // bf16 weights or null
+    int learned;
+    int diffset_rule;
+    float *trace_x;          // [cap][8]
+    float *trace_y;          // [cap][2]
+    unsigned long long trace_cap;
+    int trace;
+    MineCounters *ctr;
+    unsigned long long spin_limit;  // bounded waits (iterations)
+};
+
+// ---------------------------------------------------------------- the ctx
+struct fim_ctx {
+    int device = 0;
+    int num_sms = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+
+    // matrix
+    bool built = false;
+    int64_t n = 0;
+    int32_t m = 0;
+    int64_t nw = 0, nwp = 0;
+    int max_row_len = 0;
+    DevBuf csr_ptr, csr_idx;   // staging for host input
+    DevBuf bm, item_sup, perm, rank, dev_flag;
+
+    // mine
+    bool mined = false;
+    uint32_t mflags = 0;
+    int32_t mfreq = 0;
+    DevBuf pair_cnt, pairbits, roots;
+    DevBuf tasks, cand_pool, stack_bits, frame_items, frame_sups;
+    DevBuf rec_off, rec_len, rec_sup, rec_items;
+    DevBuf counters;            // MineCounters
+    MineCounters host_ctr;
+    unsigned long long rec_cap = 0, rec_items_cap = 0;
+
+    // compactor
+    DevBuf keys, idx_a, idx_b, hist, scan_tmp;
+    DevBuf out_off, out_items, out_sup;
+    uint64_t out_sets = 0, out_items_total = 0;
+
+    // learned scheduler
+    DevBuf mlp_w32, mlp_wbf;
+    bool has_weights = false;
+    DevBuf trace_x, trace_y;
+    unsigned long long trace_cap = 0;
+
+    // tuning (autotuner may overwrite)
+    int dfs_block = 512;
+    int dfs_ctas_per_sm = 2;
+    int split_depth = 4;
+
+    // stats + timing
+    fim_stats stats{};
+    cudaEvent_t ev[8] = {};
+    size_t bytes_held = 0;
+    uint64_t launches = 0;      // kernels this ctx has launched
+};
+
+int fim_reserve(fim_ctx *ctx, DevBuf &b, size_t bytes);
+void fim_release(fim_ctx *ctx, DevBuf &b);
+
+// ---------------------------------------------------------------- launchers
+// k_matrix.cu
+int launch_build_bitmaps(fim_ctx *ctx, const int64_t *d_indptr, const int32_t *d_indices);
+int launch_item_support(fim_ctx *ctx);
+int launch_rank_items(fim_ctx *ctx, uint32_t thr, MineCounters *d_ctr);
+int launch_emit_singletons(fim_ctx *ctx, MineCounters *d_ctr);
+int launch_max_row_freq(fim_ctx *ctx, const int64_t *d_indptr, const int32_t *d_indices,
+                        MineCounters *d_ctr);
+
+// k_pairs.cu
+int launch_pairs_popc(fim_ctx *ctx);
+int launch_pairs_tc(fim_ctx *ctx);   // tcgen05; returns FIM_E_INVAL if unsupported
+int launch_pairs_finalize(fim_ctx *ctx, uint32_t thr, MineCounters *d_ctr);
+
+// k_dfs.cu
+int launch_dfs(fim_ctx *ctx, const DfsParams &p, int grid, int block);
+
+// k_compact.cu
+int launch_compact(fim_ctx *ctx, uint64_t n_records);
+
+// ---------------------------------------------------------------- device helpers
+#ifdef __CUDACC__
+__device__ __forceinline__ uint32_t warp_sum_u32(uint32_t v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ uint4 ldg_u4(const uint32_t *p) {
+    return __ldg(reinterpret_cast<const uint4 *>(p));
+}
+
+__device__ __forceinline__ uint4 ld_cg_u4(const uint32_t *p) {
+    uint4 r;
+    asm volatile("ld.global.cg.v4.u32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w) : "l"(p));
+    return r;
+}
+
+__device__ __forceinline__ uint32_t popc_and4(uint4 a, uint4 b) {
+    return __popc(a.x & b.x) + __popc(a.y & b.y) + __popc(a.z & b.z) + __popc(a.w & b.w);
+}
+
+__device__ __forceinline__ uint4 and4(uint4 a, uint4 b) {
+    return make_uint4(a.x & b.x, a.y & b.y, a.z & b.z, a.w & b.w);
+}
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+#endif

@@ -1,0 +1,273 @@
+// k_compact.cu -- frequent-itemset extraction into canonical order.
+//
+// Records come out of the miner in discovery order with internal item ids.
+// The compactor
+//   1. maps items to the caller's ids and sorts each set's items (in place);
+//   2. packs a big-endian key  [len : 8 bits][item_0 : b]...[item_{L-1} : b]
+//      (b = bits per item id), so that numeric key order is the canonical
+//      order: size first, then lexicographic;
+//   3. sorts the records by that key with a stable LSD radix sort (8-bit
+//      digits; per pass a tile histogram, one scan, a stable scatter ranked
+//      with __match_any_sync);
+//   4. writes offsets (exclusive scan of the sizes), items and supports.
+#include "fim_common.cuh"
+
+namespace {
+
+constexpr int RT = 256;          // threads per radix tile
+constexpr int RI = 8;            // keys per thread per tile
+constexpr int TILE = RT * RI;    // 2048
+
+__global__ void prep_keys_kernel(unsigned long long R, const unsigned long long *__restrict__ rec_off,
+                                 const uint32_t *__restrict__ rec_len, uint32_t *__restrict__ items,
+                                 const int32_t *__restrict__ perm, int bits, int kw,
+                                 unsigned long long *__restrict__ keys, uint32_t *__restrict__ idx) {
+    const unsigned long long r = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R) return;
+    idx[r] = (uint32_t)r;
+    const unsigned long long off = rec_off[r];
+    const int len = (int)rec_len[r];
+    uint32_t *it = items + off;
+    for (int q = 0; q < len; q++) it[q] = (uint32_t)perm[it[q]];
+    for (int q = 1; q < len; q++) {  // insertion sort (sets are short)
+        const uint32_t v = it[q];
+        int z = q - 1;
+        while (z >= 0 && it[z] > v) { it[z + 1] = it[z]; z--; }
+        it[z + 1] = v;
+    }
+    // big-endian bit packing into kw 64-bit words (word 0 most significant)
+    unsigned long long w = 0;
+    int used = 0, wi = 0;
+    auto put = [&](unsigned long long v, int nb) {
+        while (nb > 0) {
+            const int room = 64 - used;
+            const int take = nb < room ? nb : room;
+            const unsigned long long part = (v >> (nb - take)) & ((take == 64) ? ~0ull : ((1ull << take) - 1));
+            w |= part << (room - take);
+            used += take;
+            nb -= take;
+            if (used == 64) { keys[(unsigned long long)wi * R + r] = w; wi++; w = 0; used = 0; }
+        }
+    };
+    put((unsigned long long)len, 8);
+    for (int q = 0; q < len; q++) put(it[q], bits);
+    if (used > 0) { keys[(unsigned long long)wi * R + r] = w; wi++; }
+    for (; wi < kw; wi++) keys[(unsigned long long)wi * R + r] = 0ull;
+}
+
+__global__ void __launch_bounds__(RT)
+rs_hist_kernel(const unsigned long long *__restrict__ kword, const uint32_t *__restrict__ idx,
+               unsigned long long n, int shift, uint32_t *__restrict__ hist, int ntiles) {
+    __shared__ uint32_t h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const unsigned long long t0 = (unsigned long long)blockIdx.x * TILE;
+#pragma unroll
+    for (int i = 0; i < RI; i++) {
+        const unsigned long long e = t0 + i * RT + threadIdx.x;
+        if (e < n) atomicAdd(&h[(kword[idx[e]] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    hist[(size_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
+}
+
+// Exclusive scan of a uint32 array (length <= a few million) in one CTA.
+__global__ void __launch_bounds__(1024)
+scan_single_kernel(uint32_t *__restrict__ a, unsigned long long n) {
+    __shared__ uint32_t s[1024];
+    const unsigned long long seg = (n + 1023) / 1024;
+    const unsigned long long b = threadIdx.x * seg, e = b + seg < n ? b + seg : n;
+    uint32_t sum = 0;
+    for (unsigned long long i = b; i < e; i++) sum += a[i];
+    s[threadIdx.x] = sum;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        uint32_t v = threadIdx.x >= (unsigned)o ? s[threadIdx.x - o] : 0;
+        __syncthreads();
+        s[threadIdx.x] += v;
+        __syncthreads();
+    }
+    uint32_t run = s[threadIdx.x] - sum;
+    for (unsigned long long i = b; i < e; i++) {
+        const uint32_t v = a[i];
+        a[i] = run;
+        run += v;
+    }
+}
+
+__global__ void __launch_bounds__(RT)
+rs_scatter_kernel(const unsigned long long *__restrict__ kword, const uint32_t *__restrict__ idx_in,
+                  uint32_t *__restrict__ idx_out, unsigned long long n, int shift,
+                  const uint32_t *__restrict__ hist, int ntiles) {
+    __shared__ uint32_t base[256];
+    __shared__ uint32_t wc[RT / 32][257];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    base[threadIdx.x] = hist[(size_t)threadIdx.x * ntiles + blockIdx.x];
+    const unsigned long long t0 = (unsigned long long)blockIdx.x * TILE;
+    for (int i = 0; i < RI; i++) {
+        const unsigned long long e = t0 + i * RT + threadIdx.x;
+        const bool valid = e < n;
+        uint32_t v = 0, d = 256;
+        if (valid) { v = idx_in[e]; d = (uint32_t)((kword[v] >> shift) & 255u); }
+        for (int q = threadIdx.x; q < (RT / 32) * 257; q += RT) (&wc[0][0])[q] = 0;
+        __syncthreads();
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t rank = __popc(peers & ((1u << lane) - 1u));
+        if (valid && rank == 0) wc[warp][d] = __popc(peers);
+        __syncthreads();
+        if (valid) {
+            uint32_t off = base[d] + rank;
+            for (int w = 0; w < warp; w++) off += wc[w][d];
+            idx_out[off] = v;
+        }
+        __syncthreads();
+        uint32_t add = 0;
+        for (int w = 0; w < RT / 32; w++) add += wc[w][threadIdx.x];
+        base[threadIdx.x] += add;
+        __syncthreads();
+    }
+}
+
+// Sizes in sorted order, block sums for the offset scan.
+constexpr int ST = 1024;
+__global__ void __launch_bounds__(ST)
+len_block_sums_kernel(const uint32_t *__restrict__ idx, const uint32_t *__restrict__ rec_len,
+                      unsigned long long R, unsigned long long *__restrict__ bsum) {
+    __shared__ unsigned long long s[ST / 32];
+    const unsigned long long q = (unsigned long long)blockIdx.x * ST + threadIdx.x;
+    unsigned long long v = q < R ? rec_len[idx[q]] : 0;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (int w = 0; w < ST / 32; w++) t += s[w];
+        bsum[blockIdx.x] = t;
+    }
+}
+
+__global__ void __launch_bounds__(1024)
+scan_u64_single_kernel(unsigned long long *__restrict__ a, unsigned long long n) {
+    __shared__ unsigned long long s[1024];
+    const unsigned long long seg = (n + 1023) / 1024;
+    const unsigned long long b = threadIdx.x * seg, e = b + seg < n ? b + seg : n;
+    unsigned long long sum = 0;
+    for (unsigned long long i = b; i < e; i++) sum += a[i];
+    s[threadIdx.x] = sum;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        unsigned long long v = threadIdx.x >= (unsigned)o ? s[threadIdx.x - o] : 0;
+        __syncthreads();
+        s[threadIdx.x] += v;
+        __syncthreads();
+    }
+    unsigned long long run = s[threadIdx.x] - sum;
+    for (unsigned long long i = b; i < e; i++) {
+        const unsigned long long v = a[i];
+        a[i] = run;
+        run += v;
+    }
+}
+
+__global__ void __launch_bounds__(ST)
+emit_sorted_kernel(const uint32_t *__restrict__ idx, unsigned long long R,
+                   const unsigned long long *__restrict__ rec_off, const uint32_t *__restrict__ rec_len,
+                   const uint32_t *__restrict__ rec_sup, const uint32_t *__restrict__ items,
+                   const unsigned long long *__restrict__ bsum, unsigned long long *__restrict__ out_off,
+                   uint32_t *__restrict__ out_items, uint32_t *__restrict__ out_sup,
+                   unsigned long long total_items) {
+    __shared__ unsigned long long s[ST / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned long long q = (unsigned long long)blockIdx.x * ST + threadIdx.x;
+    uint32_t r = 0;
+    unsigned long long len = 0;
+    if (q < R) { r = idx[q]; len = rec_len[r]; }
+    unsigned long long x = len;
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s[warp] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long acc = 0;
+        for (int w = 0; w < ST / 32; w++) { unsigned long long t = s[w]; s[w] = acc; acc += t; }
+    }
+    __syncthreads();
+    const unsigned long long off = bsum[blockIdx.x] + s[warp] + x - len;
+    if (q < R) {
+        out_off[q] = off;
+        out_sup[q] = rec_sup[r];
+        const unsigned long long src = rec_off[r];
+        for (unsigned long long z = 0; z < len; z++) out_items[off + z] = items[src + z];
+        if (q == R - 1) out_off[R] = total_items;
+    }
+}
+
+int bits_for(int m) {
+    int b = 1;
+    while ((1LL << b) < (long long)m) b++;
+    return b;
+}
+
+}  // namespace
+
+int launch_compact(fim_ctx *ctx, uint64_t R) {
+    cudaStream_t st = ctx->stream;
+    const unsigned long long total_items = ctx->host_ctr.n_rec_items;
+    FIM_TRY(fim_reserve(ctx, ctx->out_off, sizeof(unsigned long long) * (R + 1)));
+    FIM_TRY(fim_reserve(ctx, ctx->out_items, sizeof(uint32_t) * (total_items ? total_items : 1)));
+    FIM_TRY(fim_reserve(ctx, ctx->out_sup, sizeof(uint32_t) * (R ? R : 1)));
+    ctx->out_sets = R;
+    ctx->out_items_total = total_items;
+    if (R == 0) {
+        FIM_CUDA_TRY(cudaMemsetAsync(ctx->out_off.p, 0, sizeof(unsigned long long), st));
+        return FIM_OK;
+    }
+    const int lmax = ctx->host_ctr.max_len;  // longest set (the host folds in 1- and 2-sets)
+    const int bits = bits_for(ctx->m);
+    const int kw = (int)ceil_div64(8 + (int64_t)bits * lmax, 64);
+    FIM_TRY(fim_reserve(ctx, ctx->keys, sizeof(unsigned long long) * R * kw));
+    FIM_TRY(fim_reserve(ctx, ctx->idx_a, sizeof(uint32_t) * R));
+    FIM_TRY(fim_reserve(ctx, ctx->idx_b, sizeof(uint32_t) * R));
+    const int ntiles = (int)ceil_div64((int64_t)R, TILE);
+    FIM_TRY(fim_reserve(ctx, ctx->hist, sizeof(uint32_t) * 256 * (size_t)ntiles));
+    const int nblk = (int)ceil_div64((int64_t)R, ST);
+    FIM_TRY(fim_reserve(ctx, ctx->scan_tmp, sizeof(unsigned long long) * (size_t)nblk));
+
+    unsigned long long *keys = ctx->keys.as<unsigned long long>();
+    uint32_t *ia = ctx->idx_a.as<uint32_t>(), *ib = ctx->idx_b.as<uint32_t>();
+    prep_keys_kernel<<<(unsigned)ceil_div64((int64_t)R, 256), 256, 0, st>>>(
+        R, ctx->rec_off.as<unsigned long long>(), ctx->rec_len.as<uint32_t>(),
+        ctx->rec_items.as<uint32_t>(), ctx->perm.as<int32_t>(), bits, kw, keys, ia);
+    FIM_CUDA_TRY(cudaGetLastError());
+    // LSD: least significant word first; within a word, low digits first.
+    const int total_bits = 8 + bits * lmax;
+    for (int w = kw - 1; w >= 0; w--) {
+        const int word_lo_bit = (kw - 1 - w) * 64;  // bit index (from the key's LSB) of this word's bit 0
+        const int key_pad = kw * 64 - total_bits;    // zero bits at the key's LSB end
+        for (int d = 0; d < 8; d++) {
+            const int lo = word_lo_bit + d * 8;
+            if (lo + 8 <= key_pad) continue;          // digit holds only padding
+            const unsigned long long *kword = keys + (size_t)w * R;
+            ctx->launches += 3;
+            rs_hist_kernel<<<ntiles, RT, 0, st>>>(kword, ia, R, d * 8, ctx->hist.as<uint32_t>(), ntiles);
+            scan_single_kernel<<<1, 1024, 0, st>>>(ctx->hist.as<uint32_t>(), 256ull * ntiles);
+            rs_scatter_kernel<<<ntiles, RT, 0, st>>>(kword, ia, ib, R, d * 8, ctx->hist.as<uint32_t>(), ntiles);
+            FIM_CUDA_TRY(cudaGetLastError());
+            uint32_t *t = ia; ia = ib; ib = t;
+        }
+    }
+    unsigned long long *bsum = ctx->scan_tmp.as<unsigned long long>();
+    ctx->launches += 4;  // prep_keys + the three below
+    len_block_sums_kernel<<<nblk, ST, 0, st>>>(ia, ctx->rec_len.as<uint32_t>(), R, bsum);
+    scan_u64_single_kernel<<<1, 1024, 0, st>>>(bsum, (unsigned long long)nblk);
+    emit_sorted_kernel<<<nblk, ST, 0, st>>>(ia, R, ctx->rec_off.as<unsigned long long>(),
+                                            ctx->rec_len.as<uint32_t>(), ctx->rec_sup.as<uint32_t>(),
+                                            ctx->rec_items.as<uint32_t>(), bsum,
+                                            ctx->out_off.as<unsigned long long>(),
+                                            ctx->out_items.as<uint32_t>(), ctx->out_sup.as<uint32_t>(),
+                                            total_items);
+    FIM_CUDA_TRY(cudaGetLastError());
+    return FIM_OK;
+}

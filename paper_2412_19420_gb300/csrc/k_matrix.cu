@@ -1,0 +1,199 @@
+// k_matrix.cu -- matrix construction (Eq. 1) and singleton support (Eq. 3).
+//
+// build_bitmaps_kernel: one CTA owns a block of WB words (32*WB transactions)
+// and a range of IB items.  It ORs every (transaction, item) pair of its
+// transactions into a shared-memory tile with atomicOr -- OR makes repeated
+// items idempotent, which is the set membership of Eq. 1 -- and then writes
+// the tile out as WB-word (128-byte) runs of each item column.  The CTA also
+// validates its slice of the CSR (monotone indptr, items inside [0, m)).
+#include "fim_common.cuh"
+
+namespace {
+
+constexpr int WB = 32;          // words per CTA tile row (128 bytes)
+constexpr int BUILD_THREADS = 256;
+
+__global__ void __launch_bounds__(BUILD_THREADS)
+build_bitmaps_kernel(const int64_t *__restrict__ indptr, const int32_t *__restrict__ indices,
+                     int64_t n, int32_t m, int64_t nnz, int64_t nwp, int ib,
+                     uint32_t *__restrict__ bm, int *__restrict__ flag, int *__restrict__ max_len) {
+    extern __shared__ uint32_t tile[];          // [ib][WB]
+    __shared__ int64_t s_ptr[WB * 32 + 1];
+    const int64_t w0 = (int64_t)blockIdx.x * WB;
+    const int i0 = blockIdx.y * ib;
+    const int icount = min(ib, m - i0);
+    const int64_t t0 = w0 * 32;
+    const int64_t t1 = min(n, t0 + WB * 32);
+
+    for (int k = threadIdx.x; k < icount * WB; k += blockDim.x) tile[k] = 0u;
+    const int rows = t1 > t0 ? (int)(t1 - t0) : 0;
+    int bad = 0, my_max = 0;
+    if (rows > 0)  // rows == 0: a padding block past the last transaction
+        for (int k = threadIdx.x; k <= rows; k += blockDim.x) s_ptr[k] = indptr[t0 + k];
+    __syncthreads();
+    if (rows > 0) {
+        for (int k = threadIdx.x; k < rows; k += blockDim.x) {
+            int64_t a = s_ptr[k], b = s_ptr[k + 1];
+            if (b < a || a < 0 || b > nnz) bad = 1;
+            else my_max = max(my_max, (int)min64(b - a, 1 << 30));
+        }
+        const int64_t e0 = max64(0, s_ptr[0]);
+        const int64_t e1 = min64(nnz, s_ptr[rows]);
+        for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+            int32_t it = indices[e];
+            if (it < 0 || it >= m) { bad = 1; continue; }
+            if (it < i0 || it >= i0 + icount) continue;
+            // row r with s_ptr[r] <= e < s_ptr[r+1] (last such r for empty rows)
+            int lo = 0, hi = rows;  // invariant: s_ptr[lo] <= e < s_ptr[hi]
+            while (hi - lo > 1) {
+                int mid = (lo + hi) >> 1;
+                if (s_ptr[mid] <= e) lo = mid; else hi = mid;
+            }
+            atomicOr(&tile[(it - i0) * WB + (lo >> 5)], 1u << (lo & 31));
+        }
+    }
+    if (bad) atomicExch(flag, 1);
+    if (blockIdx.y == 0 && my_max > 0) atomicMax(max_len, my_max);
+    __syncthreads();
+    // coalesced write-out: each warp writes whole 128-byte rows
+    for (int k = threadIdx.x; k < icount * WB; k += blockDim.x) {
+        int r = k / WB, c = k % WB;
+        bm[(int64_t)(i0 + r) * nwp + w0 + c] = tile[k];
+    }
+}
+
+// S(I_j) = popcount of column j, split over segments of SEG words.
+constexpr int SEG = 8192;
+__global__ void __launch_bounds__(256)
+item_support_kernel(const uint32_t *__restrict__ bm, int64_t nwp, uint32_t *__restrict__ sup) {
+    const int j = blockIdx.x;
+    const int64_t b = (int64_t)blockIdx.y * SEG;
+    const int64_t e = min64(nwp, b + SEG);
+    const uint32_t *col = bm + (int64_t)j * nwp;
+    uint32_t c = 0;
+    for (int64_t w = b + 4 * threadIdx.x; w < e; w += 4 * blockDim.x) {
+        uint4 v = ldg_u4(col + w);
+        c += __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
+    }
+    c = warp_sum_u32(c);
+    __shared__ uint32_t s[8];
+    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t t = 0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); k++) t += s[k];
+        if (t) atomicAdd(&sup[j], t);
+    }
+}
+
+// Internal ids: frequent items ordered by (support, id) ascending.  One warp
+// per item counts the frequent items with a smaller key (ties impossible).
+__global__ void rank_items_kernel(const uint32_t *__restrict__ sup, int32_t m, uint32_t thr,
+                                  int32_t *__restrict__ perm, int32_t *__restrict__ rank,
+                                  MineCounters *ctr) {
+    const int lane = threadIdx.x & 31;
+    const int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (j >= m) return;
+    const uint32_t sj = sup[j];
+    if (sj < thr) {
+        if (lane == 0) rank[j] = -1;
+        return;
+    }
+    uint32_t below = 0;
+    for (int i = lane; i < m; i += 32) {
+        uint32_t si = sup[i];
+        below += (si >= thr) && (si < sj || (si == sj && i < j));
+    }
+    below = warp_sum_u32(below);
+    if (lane == 0) {
+        rank[j] = (int32_t)below;
+        perm[below] = j;
+        atomicAdd(&ctr->m_freq, 1);
+    }
+}
+
+// Singletons are the first m' records: record r = {r} with support S(perm[r]).
+__global__ void emit_singletons_kernel(const uint32_t *__restrict__ sup, const int32_t *__restrict__ perm,
+                                       MineCounters *ctr, unsigned long long *rec_off,
+                                       uint32_t *rec_len, uint32_t *rec_sup, uint32_t *rec_items,
+                                       unsigned long long rec_cap, unsigned long long items_cap) {
+    const int mf = ctr->m_freq;
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r == 0) {
+        ctr->n_records = (unsigned long long)mf;
+        ctr->n_rec_items = (unsigned long long)mf;
+        if ((unsigned long long)mf > rec_cap) atomicOr(&ctr->overflow, 1);
+        if ((unsigned long long)mf > items_cap) atomicOr(&ctr->overflow, 2);
+    }
+    if (r < mf && (unsigned long long)r < rec_cap && (unsigned long long)r < items_cap) {
+        rec_off[r] = (unsigned long long)r;
+        rec_len[r] = 1;
+        rec_sup[r] = sup[perm[r]];
+        rec_items[r] = (uint32_t)r;
+    }
+}
+
+}  // namespace
+
+int launch_build_bitmaps(fim_ctx *ctx, const int64_t *d_indptr, const int32_t *d_indices) {
+    const int64_t nblk = ctx->nwp / WB;
+    int ib = ctx->m < 1024 ? ctx->m : 1024;
+    if (ib < 1) ib = 1;
+    const int niblk = (int)ceil_div64(ctx->m > 0 ? ctx->m : 1, ib);
+    const size_t smem = (size_t)ib * WB * sizeof(uint32_t);
+    FIM_CUDA_TRY(cudaFuncSetAttribute(build_bitmaps_kernel,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int *flag = ctx->dev_flag.as<int>();
+    FIM_CUDA_TRY(cudaMemsetAsync(flag, 0, 2 * sizeof(int), ctx->stream));
+    if (nblk > 0 && ctx->m > 0) {
+        // nnz is read on the host before the launch (indptr[n])
+        int64_t nnz = 0;
+        FIM_CUDA_TRY(cudaMemcpyAsync(&nnz, d_indptr + ctx->n, sizeof(int64_t),
+                                     cudaMemcpyDeviceToHost, ctx->stream));
+        FIM_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+        if (nnz < 0) return FIM_E_INVAL;
+        dim3 grid((unsigned)nblk, (unsigned)niblk);
+        ctx->launches++;
+        build_bitmaps_kernel<<<grid, BUILD_THREADS, smem, ctx->stream>>>(
+            d_indptr, d_indices, ctx->n, ctx->m, nnz, ctx->nwp, ib, ctx->bm.as<uint32_t>(),
+            flag, flag + 1);
+        FIM_CUDA_TRY(cudaGetLastError());
+    }
+    return FIM_OK;
+}
+
+int launch_item_support(fim_ctx *ctx) {
+    uint32_t *sup = ctx->item_sup.as<uint32_t>();
+    FIM_CUDA_TRY(cudaMemsetAsync(sup, 0, sizeof(uint32_t) * (size_t)ctx->m, ctx->stream));
+    if (ctx->m == 0 || ctx->nwp == 0) return FIM_OK;
+    dim3 grid((unsigned)ctx->m, (unsigned)ceil_div64(ctx->nwp, SEG));
+    ctx->launches++;
+    item_support_kernel<<<grid, 256, 0, ctx->stream>>>(ctx->bm.as<uint32_t>(), ctx->nwp, sup);
+    FIM_CUDA_TRY(cudaGetLastError());
+    return FIM_OK;
+}
+
+int launch_rank_items(fim_ctx *ctx, uint32_t thr, MineCounters *d_ctr) {
+    if (ctx->m == 0) return FIM_OK;
+    const int threads = 256;
+    const int blocks = (int)ceil_div64((int64_t)ctx->m * 32, threads);
+    ctx->launches++;
+    rank_items_kernel<<<blocks, threads, 0, ctx->stream>>>(
+        ctx->item_sup.as<uint32_t>(), ctx->m, thr, ctx->perm.as<int32_t>(),
+        ctx->rank.as<int32_t>(), d_ctr);
+    FIM_CUDA_TRY(cudaGetLastError());
+    return FIM_OK;
+}
+
+int launch_emit_singletons(fim_ctx *ctx, MineCounters *d_ctr) {
+    const int threads = 256;
+    const int blocks = (int)ceil_div64(ctx->m > 0 ? ctx->m : 1, threads);
+    ctx->launches++;
+    emit_singletons_kernel<<<blocks, threads, 0, ctx->stream>>>(
+        ctx->item_sup.as<uint32_t>(), ctx->perm.as<int32_t>(), d_ctr,
+        ctx->rec_off.as<unsigned long long>(), ctx->rec_len.as<uint32_t>(),
+        ctx->rec_sup.as<uint32_t>(), ctx->rec_items.as<uint32_t>(), ctx->rec_cap,
+        ctx->rec_items_cap);
+    FIM_CUDA_TRY(cudaGetLastError());
+    return FIM_OK;
+}

@@ -1,0 +1,227 @@
+"""Python binding of libfim (include/fim.h): the same entry points, marshalling only.
+
+Every computation runs in the CUDA library; this module converts numpy arrays
+and torch tensors to pointers and status codes to exceptions.  If libfim.so
+has not been built, importing the binding raises -- there is no fallback.
+
+    ctx = fim_create(device=0)
+    fim_build_bitmaps(ctx, indptr, indices, n_items)        # numpy (host) or torch CUDA
+    fim_mine(ctx, minsup)
+    res = fim_fetch_results(ctx)                            # Itemsets (numpy, canonical)
+    fim_destroy(ctx)
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import hashlib
+import os
+
+import numpy as np
+
+from . import build as _build
+
+FIM_OK = 0
+FIM_E_INVAL, FIM_E_NOMEM, FIM_E_CUDA, FIM_E_TIMEOUT = -1, -2, -3, -4
+FIM_E_STACK, FIM_E_TOO_SMALL, FIM_E_STATE, FIM_E_NODEV = -5, -6, -7, -8
+FIM_INPUT_HOST, FIM_INPUT_DEVICE = 0, 1
+FIM_OUTPUT_HOST, FIM_OUTPUT_DEVICE = 0, 1
+FIM_STRICT, FIM_LEARNED, FIM_PAIRS_POPC, FIM_TRACE = 0x1, 0x2, 0x4, 0x8
+FIM_DIFFSET_RULE, FIM_NO_SPLIT = 0x10, 0x20
+FIM_MLP_PARAMS = 4866
+
+
+def FIM_MAXLEN(k: int) -> int:
+    return (int(k) & 0xFF) << 24
+
+
+class FimError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {fim_strerror(code)} ({code})")
+        self.code = code
+
+
+class fim_stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in (
+        "n_trans", "n_items", "n_frequent_items", "n_sets", "max_len",
+        "supports_singletons", "supports_pairs", "supports_dfs", "dfs_words", "dfs_bytes",
+        "classes", "tasks_pushed", "diffset_classes", "peak_device_bytes",
+        "launches_build", "launches_mine")] + \
+        [(n, ctypes.c_float) for n in ("ms_build", "ms_singletons", "ms_pairs", "ms_dfs", "ms_compact")] + \
+        [("pair_path", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+    def as_dict(self) -> dict:
+        return {n: getattr(self, n) for n, _ in self._fields_ if n != "reserved"}
+
+
+class fim_db_desc(ctypes.Structure):
+    _fields_ = [("indptr", ctypes.c_void_p), ("indices", ctypes.c_void_p),
+                ("n_trans", ctypes.c_int64), ("n_items", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("minsup", ctypes.c_uint64)]
+
+
+def _load():
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise ImportError(f"libfim.so is not built ({path}); run "
+                          "`python -m paper_2412_19420_gb300.build` or __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    P, U64, I64, I32, U32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint32
+    sig = {
+        "fim_create": (ctypes.c_int, [ctypes.POINTER(P), ctypes.c_int, P]),
+        "fim_destroy": (None, [P]),
+        "fim_build_bitmaps": (ctypes.c_int, [P, P, P, I64, I32, U32]),
+        "fim_mine": (ctypes.c_int, [P, U64, U32]),
+        "fim_fetch_results": (ctypes.c_int, [P, ctypes.POINTER(U64), ctypes.POINTER(U64), P, P, P, U64, U64, U32]),
+        "fim_get_stats": (ctypes.c_int, [P, ctypes.POINTER(fim_stats)]),
+        "fim_mine_batched": (ctypes.c_int, [P, ctypes.c_int, P, U32]),
+        "fim_fetch_batched": (ctypes.c_int, [P, ctypes.c_int, ctypes.POINTER(U64), ctypes.POINTER(U64),
+                                             P, P, P, U64, U64, U32]),
+        "fim_sched_load_weights": (ctypes.c_int, [P, P, ctypes.c_size_t]),
+        "fim_fetch_traces": (ctypes.c_int, [P, ctypes.POINTER(U64), P, P, U64]),
+        "fim_mlp_forward": (ctypes.c_int, [P, P, P, I64, P, P, ctypes.c_int]),
+        "fim_mlp_backward": (ctypes.c_int, [P, P, P, P, P, P, I64, P, ctypes.POINTER(ctypes.c_float), ctypes.c_int]),
+        "fim_mlp_adam": (ctypes.c_int, [P, P, P, P, P, ctypes.c_int, ctypes.c_float, ctypes.c_float,
+                                        ctypes.c_float, ctypes.c_float]),
+        "fim_minsup_from_ppm": (U64, [I64, U32]),
+        "fim_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+        "fim_version": (U32, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+_lib = _load()
+
+
+def _check(code: int, what: str) -> None:
+    if code != FIM_OK:
+        raise FimError(code, what)
+
+
+def fim_strerror(code: int) -> str:
+    return _lib.fim_strerror(int(code)).decode()
+
+
+def fim_version() -> int:
+    return int(_lib.fim_version())
+
+
+def fim_minsup_from_ppm(n_trans: int, ppm: int) -> int:
+    return int(_lib.fim_minsup_from_ppm(int(n_trans), int(ppm)))
+
+
+def _ptr(a):
+    """(pointer, is_device) of a numpy array or torch tensor (contiguous)."""
+    if a is None:
+        return None, False
+    if hasattr(a, "data_ptr"):  # torch tensor
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr(), a.is_cuda
+    if not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("array must be C-contiguous")
+    return a.ctypes.data, False
+
+
+def fim_create(device: int = 0, stream=None):
+    """New context on `device`; `stream` is a torch.cuda.Stream, an int handle or None."""
+    h = ctypes.c_void_p()
+    s = None
+    if stream is not None:
+        s = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    _check(_lib.fim_create(ctypes.byref(h), int(device), s), "fim_create")
+    return h
+
+
+def fim_destroy(ctx) -> None:
+    _lib.fim_destroy(ctx)
+
+
+def fim_build_bitmaps(ctx, indptr, indices, n_items: int, flags: int | None = None) -> None:
+    """CSR (int64 indptr, int32 indices) -> the ctx's bit columns (Eq. 1)."""
+    if not hasattr(indptr, "data_ptr"):
+        indptr = np.ascontiguousarray(indptr, dtype=np.int64)
+        indices = np.ascontiguousarray(indices, dtype=np.int32)
+    p, dev = _ptr(indptr)
+    q, dev2 = _ptr(indices)
+    if dev != dev2:
+        raise ValueError("indptr and indices must both be host or both be device")
+    if flags is None:
+        flags = FIM_INPUT_DEVICE if dev else FIM_INPUT_HOST
+    n = int(indptr.shape[0]) - 1
+    _check(_lib.fim_build_bitmaps(ctx, p, q, n, int(n_items), int(flags)), "fim_build_bitmaps")
+
+
+def fim_mine(ctx, minsup: int, flags: int = 0) -> None:
+    _check(_lib.fim_mine(ctx, int(minsup), int(flags)), "fim_mine")
+
+
+@dataclasses.dataclass
+class Itemsets:
+    offsets: np.ndarray   # uint64[R+1]
+    items: np.ndarray     # uint32
+    supports: np.ndarray  # uint32[R]
+
+    def __len__(self) -> int:
+        return int(self.supports.shape[0])
+
+    def as_dict(self) -> dict:
+        o = self.offsets
+        return {tuple(int(x) for x in self.items[o[q]:o[q + 1]]): int(self.supports[q])
+                for q in range(len(self))}
+
+    def canonical_bytes(self) -> bytes:
+        return (np.ascontiguousarray(self.offsets, dtype="<u8").tobytes()
+                + np.ascontiguousarray(self.items, dtype="<u4").tobytes()
+                + np.ascontiguousarray(self.supports, dtype="<u8").tobytes())
+
+    def sha256(self) -> str:
+        return hashlib.sha256(self.canonical_bytes()).hexdigest()
+
+
+def fim_result_sizes(ctx) -> tuple[int, int]:
+    ns, ni = ctypes.c_uint64(), ctypes.c_uint64()
+    _check(_lib.fim_fetch_results(ctx, ctypes.byref(ns), ctypes.byref(ni), None, None, None, 0, 0, 0),
+           "fim_fetch_results")
+    return int(ns.value), int(ni.value)
+
+
+def fim_fetch_results(ctx, out=None) -> Itemsets:
+    """Canonical results into new host arrays, or into `out` = (offsets, items,
+    supports) buffers (numpy, pinned host or torch CUDA tensors)."""
+    R, T = fim_result_sizes(ctx)
+    if out is None:
+        out = (np.empty(R + 1, np.uint64), np.empty(max(T, 1), np.uint32), np.empty(max(R, 1), np.uint32))
+    off, it, sup = out
+    po, dev = _ptr(off)
+    pi, _ = _ptr(it)
+    ps, _ = _ptr(sup)
+    ns, ni = ctypes.c_uint64(), ctypes.c_uint64()
+    cap_sets = min(int(sup.shape[0]), int(off.shape[0]) - 1)
+    _check(_lib.fim_fetch_results(ctx, ctypes.byref(ns), ctypes.byref(ni), po, pi, ps, cap_sets,
+                                  int(it.shape[0]), FIM_OUTPUT_DEVICE if dev else FIM_OUTPUT_HOST),
+           "fim_fetch_results")
+    if dev:
+        return Itemsets(off[: R + 1], it[:T], sup[:R])
+    return Itemsets(off[: R + 1].copy(), it[:T].copy(), sup[:R].copy())
+
+
+def fim_get_stats(ctx) -> dict:
+    s = fim_stats()
+    _check(_lib.fim_get_stats(ctx, ctypes.byref(s)), "fim_get_stats")
+    return s.as_dict()
+
+
+def mine(indptr, indices, n_items: int, minsup: int, flags: int = 0, device: int = 0) -> Itemsets:
+    """One-shot convenience: build, mine and fetch in a fresh context."""
+    ctx = fim_create(device)
+    try:
+        fim_build_bitmaps(ctx, indptr, indices, n_items)
+        fim_mine(ctx, minsup, flags)
+        return fim_fetch_results(ctx)
+    finally:
+        fim_destroy(ctx)

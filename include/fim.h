@@ -144,6 +144,17 @@ int fim_fetch_results(fim_ctx *ctx, uint64_t *n_sets, uint64_t *n_items_total,
 /* fim_get_stats: counters and phase times of the last fim_mine (or batch). */
 int fim_get_stats(const fim_ctx *ctx, fim_stats *out);
 
+/* fim_set_tuning -- set one launch-shape parameter of the ctx; it applies to
+ * later calls and never changes results.  Keys and ranges:
+ *   "dfs_ctas_per_sm"  1..2      DFS workers per SM
+ *   "split_depth"      0..8      longest prefix a worker may hand to the queue
+ *   "pairs_split"      0..4096   split-K factor of the tensor-core pair pass (0 = auto)
+ *   "pairs_kdrain"     0..1024   128-transaction stages per exact accumulator
+ *                                drain (0 = 64); partial sums stay <= 128*kdrain
+ *   "batch_word_block" 0..4096   words per batched work item (0 = auto)
+ * Errors: FIM_E_INVAL for an unknown key or an out-of-range value. */
+int fim_set_tuning(fim_ctx *ctx, const char *key, int64_t value);
+
 /* fim_mine_batched -- many independent databases in one persistent launch,
  * replayed from a captured CUDA graph when the same batch shape repeats.
  * dbs[d] describes database d (host or device CSR per flags &

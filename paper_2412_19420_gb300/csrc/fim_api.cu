@@ -428,4 +428,22 @@ int fim_get_stats(const fim_ctx *ctx, fim_stats *out) {
     return FIM_OK;
 }
 
+int fim_set_tuning(fim_ctx *ctx, const char *key, int64_t v) {
+    if (!ctx || !key) return FIM_E_INVAL;
+    struct Knob { const char *name; int *field; int64_t lo, hi; } knobs[] = {
+        {"dfs_ctas_per_sm", &ctx->dfs_ctas_per_sm, 1, 2},
+        {"split_depth", &ctx->split_depth, 0, FIM_TASK_MAXR},
+        {"pairs_split", &ctx->pairs_split, 0, 4096},
+        {"pairs_kdrain", &ctx->pairs_kdrain, 0, 1024},
+        {"batch_word_block", &ctx->batch_word_block, 0, 4096},
+    };
+    for (const Knob &k : knobs)
+        if (strcmp(k.name, key) == 0) {
+            if (v < k.lo || v > k.hi) return FIM_E_INVAL;
+            *k.field = (int)v;
+            return FIM_OK;
+        }
+    return FIM_E_INVAL;
+}
+
 }  // extern "C"

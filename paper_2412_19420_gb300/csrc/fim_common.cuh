@@ -177,6 +177,9 @@ struct fim_ctx {
     int dfs_block = 512;
     int dfs_ctas_per_sm = 2;
     int split_depth = 4;
+    int pairs_split = 0;        // split-K factor of the tensor-core pair pass (0 = auto)
+    int pairs_kdrain = 0;       // stages (x128 transactions) per exact drain (0 = 64)
+    int batch_word_block = 0;   // words per batched work item (0 = auto)
 
     // stats + timing
     fim_stats stats{};

@@ -2,7 +2,7 @@
 // FIM_E_INVAL so a caller can tell the feature is absent.
 #include "fim_common.cuh"
 
-int launch_pairs_tc(fim_ctx *) { return FIM_E_INVAL; }
+
 
 extern "C" {
 int fim_mine_batched(fim_ctx *, int, const fim_db_desc *, uint32_t) { return FIM_E_INVAL; }

@@ -83,6 +83,7 @@ def _load():
         "fim_mlp_backward": (ctypes.c_int, [P, P, P, P, P, P, I64, P, ctypes.POINTER(ctypes.c_float), ctypes.c_int]),
         "fim_mlp_adam": (ctypes.c_int, [P, P, P, P, P, ctypes.c_int, ctypes.c_float, ctypes.c_float,
                                         ctypes.c_float, ctypes.c_float]),
+        "fim_set_tuning": (ctypes.c_int, [P, ctypes.c_char_p, I64]),
         "fim_minsup_from_ppm": (U64, [I64, U32]),
         "fim_strerror": (ctypes.c_char_p, [ctypes.c_int]),
         "fim_version": (U32, []),
@@ -208,6 +209,10 @@ def fim_fetch_results(ctx, out=None) -> Itemsets:
     if dev:
         return Itemsets(off[: R + 1], it[:T], sup[:R])
     return Itemsets(off[: R + 1].copy(), it[:T].copy(), sup[:R].copy())
+
+
+def fim_set_tuning(ctx, key: str, value: int) -> None:
+    _check(_lib.fim_set_tuning(ctx, key.encode(), int(value)), f"fim_set_tuning({key})")
 
 
 def fim_get_stats(ctx) -> dict:

@@ -212,6 +212,38 @@ int fim_mlp_backward(fim_ctx *ctx, const float *params, const float *x, const fl
 int fim_mlp_adam(fim_ctx *ctx, float *params, const float *grad, float *m, float *v,
                  int step, float lr, float beta1, float beta2, float eps);
 
+/* ---- allocation-free entry point ---------------------------------------
+ * The paper has no counterpart to this call.  It serves callers that cannot
+ * allocate device memory while they use the library: processes whose own
+ * memory pool owns every device byte and forbids allocations outside it, and
+ * latency-critical paths that must not block in cudaMalloc/cudaFree (which
+ * can synchronise the whole device).
+ *
+ * fim_pair_supports_noalloc: for the database given as a DEVICE CSR
+ * (d_indptr[n_trans + 1], d_indices[d_indptr[n_trans]]), fills the
+ * caller-owned DEVICE matrix d_pair_counts (uint32, n_items x n_items,
+ * row-major): entry [a][b], a < b, is the pair support S(I_a n I_b) of Eq. 2,
+ * entry [a][a] is S(I_a), entries below the diagonal are 0 -- the singleton
+ * and pair supports fim_mine computes, without a threshold.  It runs on
+ * cuda_stream (a cudaStream_t, NULL = the legacy default stream) of the
+ * current device and returns when the work has finished.
+ * Memory: it calls no cudaMalloc, cudaFree or allocating library routine.
+ * Its only scratch is a static device array of FIM_NOALLOC_MAX_BYTES that
+ * every GPU which loads libfim holds until the process exits; the bit columns
+ * of a database need n_items * 128 * ceil(n_trans / 1024) bytes of it.  The
+ * first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture begins.  All calls share the array, which keeps the last call's
+ * contents; each call rewrites every part of it that it reads, and clears the
+ * output itself.  Calls whose GPU work overlaps (several streams or host
+ * threads) race on the array and must be serialised by the caller.
+ * Errors: FIM_E_INVAL for a malformed CSR, n_items > FIM_MAX_ITEMS, or bit
+ * columns larger than FIM_NOALLOC_MAX_BYTES (nothing is launched then);
+ * FIM_E_NODEV; FIM_E_CUDA. */
+#define FIM_NOALLOC_MAX_BYTES (64u << 20)
+int fim_pair_supports_noalloc(const int64_t *d_indptr, const int32_t *d_indices, int64_t n_trans,
+                              int32_t n_items, uint32_t *d_pair_counts, void *cuda_stream);
+
 /* fim_minsup_from_ppm: ceil(n_trans * ppm / 1e6) in integers, at least 1:
  * the threshold of Eq. 3 given as a fraction of the transactions. */
 uint64_t fim_minsup_from_ppm(int64_t n_trans, uint32_t ppm);

@@ -84,6 +84,7 @@ def _load():
         "fim_mlp_adam": (ctypes.c_int, [P, P, P, P, P, ctypes.c_int, ctypes.c_float, ctypes.c_float,
                                         ctypes.c_float, ctypes.c_float]),
         "fim_set_tuning": (ctypes.c_int, [P, ctypes.c_char_p, I64]),
+        "fim_pair_supports_noalloc": (ctypes.c_int, [P, P, I64, I32, P, P]),
         "fim_minsup_from_ppm": (U64, [I64, U32]),
         "fim_strerror": (ctypes.c_char_p, [ctypes.c_int]),
         "fim_version": (U32, []),
@@ -213,6 +214,23 @@ def fim_fetch_results(ctx, out=None) -> Itemsets:
 
 def fim_set_tuning(ctx, key: str, value: int) -> None:
     _check(_lib.fim_set_tuning(ctx, key.encode(), int(value)), f"fim_set_tuning({key})")
+
+
+def fim_pair_supports_noalloc(indptr, indices, n_items: int, out, stream=None) -> None:
+    """Allocation-free singleton and pair supports (include/fim.h): device CSR
+    tensors in, the caller's device uint32/int32 n_items x n_items matrix out.
+    For callers that must not allocate device memory; see the header for the
+    static scratch limit and the one-time per-device set-up."""
+    p, dev = _ptr(indptr)
+    q, dev2 = _ptr(indices)
+    o, dev3 = _ptr(out)
+    if not (dev and dev2 and dev3):
+        raise ValueError("fim_pair_supports_noalloc takes device buffers")
+    s = None
+    if stream is not None:
+        s = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    n = int(indptr.shape[0]) - 1
+    _check(_lib.fim_pair_supports_noalloc(p, q, n, int(n_items), o, s), "fim_pair_supports_noalloc")
 
 
 def fim_get_stats(ctx) -> dict:

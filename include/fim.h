@@ -16,6 +16,9 @@
  *     thread-safe: calls on one ctx must not overlap.
  *   - Pointers are plain host or device pointers, as each call's flags say.
  *     The library never keeps a caller's pointer after a call returns.
+ *     Device inputs must be complete when a call is made: the ctx stream does
+ *     not wait for work queued on other streams.  Calls that return results
+ *     synchronise the ctx stream before returning.
  *   - Item ids are the caller's ids in [0, n_items); transaction order is the
  *     caller's row order (row i of the CSR is transaction T_i).
  *   - Supports are exact integer counts.  Results are canonical: items
@@ -43,9 +46,11 @@ extern "C" {
 #define FIM_E_NODEV (-8)     /* no CUDA device / device id out of range                    */
 
 /* ---- flags ------------------------------------------------------------- */
+/* All flags share one bit space, so that fim_mine_batched can take input
+ * location and mine flags together. */
 /* fim_build_bitmaps / fim_mine_batched: where the CSR arrays live */
 #define FIM_INPUT_HOST 0u
-#define FIM_INPUT_DEVICE 1u
+#define FIM_INPUT_DEVICE 0x100u
 
 /* fim_mine / fim_mine_batched */
 #define FIM_STRICT 0x1u       /* frequent iff S(X) > minsup (Eq. 3 literally); default S(X) >= minsup */
@@ -56,9 +61,9 @@ extern "C" {
 #define FIM_NO_SPLIT 0x20u    /* process every subtree inside the worker that found it              */
 #define FIM_MAXLEN(k) (((uint32_t)(k) & 0xffu) << 24) /* longest itemset reported; 0 = unbounded */
 
-/* fim_fetch_results: where the output buffers live */
+/* fim_fetch_results / fim_fetch_batched: where the output buffers live */
 #define FIM_OUTPUT_HOST 0u
-#define FIM_OUTPUT_DEVICE 1u
+#define FIM_OUTPUT_DEVICE 0x200u
 
 /* ---- limits ------------------------------------------------------------ */
 #define FIM_MAX_ITEMS 65535      /* n_items per database                           */
@@ -74,6 +79,8 @@ typedef struct {
     uint64_t supports_dfs;        /* supports of >= 3-itemsets computed by the DFS  */
     uint64_t dfs_words;           /* 32-bit candidate words ANDed by the DFS        */
     uint64_t dfs_bytes;           /* bytes the DFS kernel read/wrote algorithmically */
+    uint64_t dfs_touched_bytes;   /* the same, counting only 32-byte sectors that can
+                                     contribute (zero prefix words are skipped)     */
     uint64_t classes;             /* prefix classes expanded                        */
     uint64_t tasks_pushed;        /* classes handed to the device work queue        */
     uint64_t diffset_classes;     /* classes counted through a diffset              */
@@ -151,7 +158,6 @@ int fim_get_stats(const fim_ctx *ctx, fim_stats *out);
  *   "pairs_split"      0..4096   split-K factor of the tensor-core pair pass (0 = auto)
  *   "pairs_kdrain"     0..1024   128-transaction stages per exact accumulator
  *                                drain (0 = 64); partial sums stay <= 128*kdrain
- *   "batch_word_block" 0..4096   words per batched work item (0 = auto)
  * Errors: FIM_E_INVAL for an unknown key or an out-of-range value. */
 int fim_set_tuning(fim_ctx *ctx, const char *key, int64_t value);
 
@@ -164,10 +170,19 @@ int fim_set_tuning(fim_ctx *ctx, const char *key, int64_t value);
 int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *dbs, uint32_t flags);
 
 /* fim_fetch_batched -- results of database `db` of the last batch, with the
- * same contract as fim_fetch_results. */
+ * same contract as fim_fetch_results.  db = FIM_ALL_DBS returns every
+ * database's results in one stream (sorted by database, then canonically),
+ * offsets counted from the start of that stream; fim_batch_slices tells
+ * where each database's sets begin. */
+#define FIM_ALL_DBS (-1)
 int fim_fetch_batched(fim_ctx *ctx, int db, uint64_t *n_sets, uint64_t *n_items_total,
                       uint64_t *offsets, uint32_t *items, uint32_t *supports,
                       uint64_t cap_sets, uint64_t cap_items, uint32_t flags);
+
+/* fim_batch_slices: set_start[n_db + 1] (host) -- database d's sets are
+ * set_start[d] .. set_start[d+1] - 1 of the FIM_ALL_DBS stream.
+ * Errors: FIM_E_STATE (no batch mined), FIM_E_TOO_SMALL (cap < n_db + 1). */
+int fim_batch_slices(fim_ctx *ctx, uint64_t *set_start, uint64_t cap);
 
 /* ---- learned scheduler (8 -> 64 -> 64 -> 2 bf16 MLP) --------------------
  * The network predicts, per prefix class, log2(1 + subtree work) and the

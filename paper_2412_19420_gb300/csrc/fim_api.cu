@@ -149,8 +149,12 @@ void fim_destroy(fim_ctx *ctx) {
                      &ctx->rec_off, &ctx->rec_len, &ctx->rec_sup, &ctx->rec_items, &ctx->counters,
                      &ctx->keys, &ctx->idx_a, &ctx->idx_b, &ctx->hist, &ctx->scan_tmp, &ctx->out_off,
                      &ctx->out_items, &ctx->out_sup, &ctx->mlp_w32, &ctx->mlp_wbf, &ctx->trace_x,
-                     &ctx->trace_y};
+                     &ctx->trace_y, &ctx->mlp_scratch, &ctx->root_order, &ctx->root_bucket,
+                     &ctx->root_hist, &ctx->rec_db, &ctx->dbdesc};
     for (DevBuf *b : all) fim_release(ctx, *b);
+    fim_release(ctx, ctx->batch_prefix);
+    fim_release(ctx, ctx->batch_slices);
+    if (ctx->batch_graph_exec) cudaGraphExecDestroy((cudaGraphExec_t)ctx->batch_graph_exec);
     for (auto &e : ctx->ev)
         if (e) cudaEventDestroy(e);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
@@ -230,6 +234,8 @@ struct MineState {
 int mine_once(fim_ctx *ctx, uint32_t thr, uint32_t flags, MineState &ms, bool *retry) {
     cudaStream_t st = ctx->stream;
     *retry = false;
+    ctx->cur_thr = thr;
+    if ((flags & FIM_LEARNED) && !ctx->has_weights) return FIM_E_STATE;
     MineCounters *d_ctr = ctx->counters.as<MineCounters>();
     FIM_CUDA_TRY(cudaMemsetAsync(d_ctr, 0, sizeof(MineCounters), st));
     cudaEventRecord(ctx->ev[0], st);
@@ -240,6 +246,19 @@ int mine_once(fim_ctx *ctx, uint32_t thr, uint32_t flags, MineState &ms, bool *r
     ctx->mfreq = ctx->host_ctr.m_freq;
     const int mf = ctx->mfreq;
     const uint32_t maxlen = flags >> 24;
+    {   // the one-entry database table of a single-database mine (DFS, compactor)
+        DbDesc &d = ctx->host_db;
+        d = DbDesc{};
+        d.n = ctx->n;
+        d.nw = ctx->nw;
+        d.nwp = ctx->nwp;
+        d.m = ctx->m;
+        d.mfreq = mf;
+        d.thr = thr;
+        d.maxlen = maxlen;
+        FIM_TRY(fim_reserve(ctx, ctx->dbdesc, sizeof(DbDesc)));
+        FIM_CUDA_TRY(cudaMemcpyAsync(ctx->dbdesc.p, &d, sizeof(DbDesc), cudaMemcpyHostToDevice, st));
+    }
     cudaEventRecord(ctx->ev[1], st);
     const bool do_pairs = mf >= 2 && (maxlen == 0 || maxlen >= 2);
     ctx->stats.pair_path = 0;
@@ -279,18 +298,16 @@ int mine_once(fim_ctx *ctx, uint32_t thr, uint32_t flags, MineState &ms, bool *r
         FIM_CUDA_TRY(cudaMemsetAsync(ctx->tasks.p, 0, sizeof(Task) * kTaskCap, st));
         const size_t npairs = (size_t)mf * (mf - 1) / 2;
         DfsParams p{};
+        p.dbs = ctx->dbdesc.as<DbDesc>();
         p.bm = ctx->bm.as<uint32_t>();
         p.perm = ctx->perm.as<int32_t>();
         p.pairbits = ctx->pairbits.as<uint32_t>();
-        p.nwp = ctx->nwp;
-        p.nw = ctx->nw;
-        p.mfreq = mf;
-        p.mpw = (int)ceil_div64(mf, 32);
-        p.thr = thr;
-        p.maxlen = maxlen;
+        p.nwp_max = ctx->nwp;
         p.root_a = ctx->roots.as<uint32_t>();
         p.root_b = p.root_a + npairs;
         p.root_sup = p.root_a + 2 * npairs;
+        p.root_db = nullptr;
+        p.rec_db = ctx->rec_db.as<uint32_t>();
         p.tasks = ctx->tasks.as<Task>();
         p.task_cap = kTaskCap;
         p.cand_pool = ctx->cand_pool.as<uint32_t>();
@@ -309,6 +326,27 @@ int mine_once(fim_ctx *ctx, uint32_t thr, uint32_t flags, MineState &ms, bool *r
         p.rec_items_cap = ctx->rec_items_cap;
         p.ctr = d_ctr;
         p.spin_limit = kSpinLimitNs;
+        p.pair_cnt = ctx->pair_cnt.as<int>();
+        p.item_sup = ctx->item_sup.as<uint32_t>();
+        p.root_order = nullptr;
+        p.learned = (flags & FIM_LEARNED) ? 1 : 0;
+        p.diffset_rule = (flags & FIM_DIFFSET_RULE) ? 1 : 0;
+        p.mlp_w = ctx->mlp_wbf.as<__nv_bfloat16>();
+        if (p.learned) {
+            FIM_TRY(launch_root_order(ctx, d_ctr, npairs));
+            p.root_order = ctx->root_order.as<uint32_t>();
+        }
+        p.trace = (flags & FIM_TRACE) ? 1 : 0;
+        if (p.trace) {
+            // complete subtree totals need every subtree inside one worker
+            p.split_depth = 0;
+            if (ctx->trace_cap == 0) ctx->trace_cap = 1ull << 21;
+            FIM_TRY(fim_reserve(ctx, ctx->trace_x, sizeof(float) * FIM_MLP_FEATURES * ctx->trace_cap));
+            FIM_TRY(fim_reserve(ctx, ctx->trace_y, sizeof(float) * 2 * ctx->trace_cap));
+            p.trace_x = ctx->trace_x.as<float>();
+            p.trace_y = ctx->trace_y.as<float>();
+            p.trace_cap = ctx->trace_cap;
+        }
         FIM_TRY(launch_dfs(ctx, p, workers, dfs_threads()));
     }
     cudaEventRecord(ctx->ev[3], st);
@@ -331,6 +369,7 @@ int mine_once(fim_ctx *ctx, uint32_t thr, uint32_t flags, MineState &ms, bool *r
         FIM_TRY(fim_reserve(ctx, ctx->rec_len, sizeof(uint32_t) * ctx->rec_cap));
         FIM_TRY(fim_reserve(ctx, ctx->rec_sup, sizeof(uint32_t) * ctx->rec_cap));
         FIM_TRY(fim_reserve(ctx, ctx->rec_items, sizeof(uint32_t) * ctx->rec_items_cap));
+    FIM_TRY(fim_reserve(ctx, ctx->rec_db, sizeof(uint32_t) * ctx->rec_cap));
         *retry = true;
         return FIM_OK;
     }
@@ -338,7 +377,7 @@ int mine_once(fim_ctx *ctx, uint32_t thr, uint32_t flags, MineState &ms, bool *r
     if (mf >= 1 && lmax < 1) lmax = 1;
     if (c.n_roots > 0 && lmax < 2) lmax = 2;
     ctx->host_ctr.max_len = lmax;
-    FIM_TRY(launch_compact(ctx, c.n_records));
+    FIM_TRY(launch_compact(ctx, c.n_records, 1, ctx->m));
     cudaEventRecord(ctx->ev[4], st);
     FIM_CUDA_TRY(cudaStreamSynchronize(st));
     FIM_CUDA_TRY(cudaGetLastError());
@@ -371,6 +410,7 @@ int fim_mine(fim_ctx *ctx, uint64_t minsup, uint32_t flags) {
     FIM_TRY(fim_reserve(ctx, ctx->rec_len, sizeof(uint32_t) * ctx->rec_cap));
     FIM_TRY(fim_reserve(ctx, ctx->rec_sup, sizeof(uint32_t) * ctx->rec_cap));
     FIM_TRY(fim_reserve(ctx, ctx->rec_items, sizeof(uint32_t) * ctx->rec_items_cap));
+    FIM_TRY(fim_reserve(ctx, ctx->rec_db, sizeof(uint32_t) * ctx->rec_cap));
     const uint64_t launches0 = ctx->launches;
     MineState ms;
     bool retry = true;
@@ -390,6 +430,7 @@ int fim_mine(fim_ctx *ctx, uint64_t minsup, uint32_t flags) {
     s.supports_dfs = c.supports_dfs;
     s.dfs_words = c.dfs_words;
     s.dfs_bytes = c.dfs_bytes;
+    s.dfs_touched_bytes = c.dfs_touched;
     s.classes = c.classes;
     s.tasks_pushed = c.pushed;
     s.diffset_classes = c.diffset;
@@ -435,7 +476,6 @@ int fim_set_tuning(fim_ctx *ctx, const char *key, int64_t v) {
         {"split_depth", &ctx->split_depth, 0, FIM_TASK_MAXR},
         {"pairs_split", &ctx->pairs_split, 0, 4096},
         {"pairs_kdrain", &ctx->pairs_kdrain, 0, 1024},
-        {"batch_word_block", &ctx->batch_word_block, 0, 4096},
     };
     for (const Knob &k : knobs)
         if (strcmp(k.name, key) == 0) {

@@ -20,6 +20,8 @@
 #include <stdint.h>
 #include <stddef.h>
 
+#include <vector>
+
 #include "../../include/fim.h"
 
 #define FIM_WORDS_ALIGN 128  // column padding, in 32-bit words (512 bytes)
@@ -61,7 +63,8 @@ struct MineCounters {
     unsigned long long n_rec_items;  // items emitted into the record pool
     unsigned long long supports_dfs; // supports evaluated by the DFS
     unsigned long long dfs_words;    // candidate words ANDed by the DFS
-    unsigned long long dfs_bytes;    // algorithmic bytes moved by the DFS
+    unsigned long long dfs_bytes;    // algorithmic bytes moved by the DFS (dense operands)
+    unsigned long long dfs_touched;  // bytes of the 32-byte sectors that can contribute
     unsigned long long classes;      // classes expanded
     unsigned long long pushed;       // tasks pushed to the queue
     unsigned long long diffset;      // classes counted via a diffset
@@ -89,22 +92,40 @@ struct Task {
     uint32_t ready;            // 0 until published
     unsigned long long cand_off;  // into the candidate pool
     float prio;                // predicted work (learned mode) or 0
-    uint32_t pad;
+    uint32_t db;               // database of the class
+};
+
+// One database of a mine: its CSR, sizes, and its offsets into the
+// mine-wide arrays (bit columns, item supports / ranks / perm, pair counts,
+// pair bitset).  fim_mine uses a one-entry table; fim_mine_batched one entry
+// per database.  mfreq is written on the device by the ranking kernel.
+struct DbDesc {
+    const int64_t *indptr;
+    const int32_t *indices;
+    int64_t n, nw, nwp;
+    int64_t bm_off;      // words into the bit-column array
+    int64_t item_off;    // entries into item_sup / rank / perm
+    int64_t pair_off;    // entries into pair_cnt (m * m)
+    int64_t pb_off;      // words into pairbits (m * ceil(m / 32))
+    int32_t m;
+    int32_t mfreq;
+    uint32_t thr;
+    uint32_t maxlen;
 };
 
 // One frame of a worker's DFS stack lives in global memory.
 struct DfsParams {
+    // mine-wide arrays; a database's part starts at its DbDesc offsets
+    const DbDesc *dbs;
     const uint32_t *bm;
     const int32_t *perm;
     const uint32_t *pairbits;
-    int64_t nwp;        // words per column (multiple of 128)
-    int64_t nw;         // words that hold transactions
-    int32_t mfreq;      // m'
-    int32_t mpw;        // words per pairbits row
-    uint32_t thr;       // frequent iff support >= thr
-    uint32_t maxlen;    // 0 = unbounded
-    // roots: frequent pairs
-    const uint32_t *root_a, *root_b, *root_sup;
+    const int *pair_cnt;        // S({a,b}) for a < b, [m][m] per database
+    const uint32_t *item_sup;   // S({j}) by caller id
+    int64_t nwp_max;            // stack level stride (largest nwp of the mine)
+    // roots: frequent pairs, visited in root_order (or index order if null)
+    const uint32_t *root_a, *root_b, *root_sup, *root_db;
+    const uint32_t *root_order;
     // queue
     Task *tasks;
     unsigned long long task_cap;
@@ -122,6 +143,7 @@ struct DfsParams {
     uint32_t *rec_len;
     uint32_t *rec_sup;
     uint32_t *rec_items;
+    uint32_t *rec_db;
     unsigned long long rec_cap, rec_items_cap;
     // learned / traces
     const __nv_bfloat16 *mlp_w;  // bf16 weights or null
@@ -157,8 +179,10 @@ struct fim_ctx {
     int32_t mfreq = 0;
     DevBuf pair_cnt, pairbits, roots;
     DevBuf tasks, cand_pool, stack_bits, frame_items, frame_sups;
-    DevBuf rec_off, rec_len, rec_sup, rec_items;
+    DevBuf rec_off, rec_len, rec_sup, rec_items, rec_db;
     DevBuf counters;            // MineCounters
+    DevBuf dbdesc;              // DbDesc table of the mine
+    DbDesc host_db{};           // host copy of a single-database table
     MineCounters host_ctr;
     unsigned long long rec_cap = 0, rec_items_cap = 0;
 
@@ -168,10 +192,21 @@ struct fim_ctx {
     uint64_t out_sets = 0, out_items_total = 0;
 
     // learned scheduler
-    DevBuf mlp_w32, mlp_wbf;
+    DevBuf mlp_w32, mlp_wbf, mlp_scratch;
+    DevBuf root_order, root_bucket, root_hist;
     bool has_weights = false;
+    uint32_t cur_thr = 0;       // threshold of the mine in progress
     DevBuf trace_x, trace_y;
     unsigned long long trace_cap = 0;
+
+    // batched mines: device prefix arrays, result slices, the captured graph
+    DevBuf batch_prefix, batch_slices;
+    bool batch_mined = false;
+    int batch_n_db = 0;
+    std::vector<unsigned long long> batch_set_start, batch_item_start;
+    void *batch_graph_exec = nullptr;   // cudaGraphExec_t
+    uint64_t batch_graph_key = 0;
+    uint64_t batch_graph_launches = 0;
 
     // tuning (autotuner may overwrite)
     int dfs_block = 512;
@@ -179,7 +214,6 @@ struct fim_ctx {
     int split_depth = 4;
     int pairs_split = 0;        // split-K factor of the tensor-core pair pass (0 = auto)
     int pairs_kdrain = 0;       // stages (x128 transactions) per exact drain (0 = 64)
-    int batch_word_block = 0;   // words per batched work item (0 = auto)
 
     // stats + timing
     fim_stats stats{};
@@ -208,8 +242,11 @@ int launch_pairs_finalize(fim_ctx *ctx, uint32_t thr, MineCounters *d_ctr);
 // k_dfs.cu
 int launch_dfs(fim_ctx *ctx, const DfsParams &p, int grid, int block);
 
+// k_mlp.cu: learned root order (longest predicted subtree first)
+int launch_root_order(fim_ctx *ctx, MineCounters *d_ctr, size_t npairs);
+
 // k_compact.cu
-int launch_compact(fim_ctx *ctx, uint64_t n_records);
+int launch_compact(fim_ctx *ctx, uint64_t n_records, int n_db, int m_max);
 
 // ---------------------------------------------------------------- device helpers
 #ifdef __CUDACC__

@@ -1,0 +1,678 @@
+// k_batched.cu -- many independent databases in one pass of the pipeline.
+//
+// Every database d gets the three stages of Section III exactly as fim_mine
+// gives one: bit columns (Eq. 1), singleton and pair supports with the
+// threshold (Eq. 2-3, its own minsup), and the depth-first prefix extension.
+// Here all databases share one launch per stage:
+//   * a DbDesc table gives each database's CSR and its offsets into the
+//     batch-wide arrays (bit columns, item supports/perm, pair counts, pair
+//     bitset);
+//   * each stage's grid is the concatenation of the databases' work units
+//     (word blocks, item columns, pair tiles, pair rows); a CTA finds its
+//     database by binary search over the prefix sums of those counts;
+//   * the persistent DFS kernel takes root classes of all databases from one
+//     queue (root_db tags them) and loads the task's database view;
+//   * the compactor sorts by (database, size, items), so each database's
+//     canonical results are one contiguous slice.
+// Sizes that only the device knows (m' per database) never reach the host
+// before the DFS ends, so build -> DFS is captured once in a CUDA graph and
+// replayed for later batches of the same shape.
+#include <cstring>
+#include <vector>
+
+#include "fim_common.cuh"
+
+int dfs_threads();
+
+namespace {
+
+constexpr int WB = 32;     // words per build tile row
+constexpr int TI = 64;     // pair tile side
+constexpr int KW = 32;     // words per pair k-step
+constexpr unsigned long long kTaskCap = 1ull << 20;
+constexpr unsigned long long kCandPoolCap = 1ull << 24;
+constexpr unsigned long long kSpinLimitNs = 60ull * 1000 * 1000 * 1000;
+
+// largest d with prefix[d] <= x (prefix has n_db + 1 entries, prefix[0] = 0)
+__device__ __forceinline__ int find_db(const int64_t *prefix, int n_db, int64_t x) {
+    int lo = 0, hi = n_db;  // prefix[lo] <= x < prefix[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (prefix[mid] <= x) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(256)
+batch_build_kernel(const DbDesc *__restrict__ dbs, int n_db, const int64_t *__restrict__ unit_prefix, int ib,
+                   uint32_t *__restrict__ bm, int *__restrict__ flag) {
+    extern __shared__ uint32_t tile[];  // [ib][WB]
+    __shared__ int64_t s_ptr[WB * 32 + 1];
+    const int d = find_db(unit_prefix, n_db, blockIdx.x);
+    const DbDesc &D = dbs[d];
+    const int64_t local = blockIdx.x - unit_prefix[d];
+    const int nib = (D.m + ib - 1) / ib;
+    const int64_t w0 = (local / nib) * WB;
+    const int i0 = (int)(local % nib) * ib;
+    const int icount = min(ib, D.m - i0);
+    const int64_t n = D.n;
+    const int64_t nnz = n > 0 ? D.indptr[n] : 0;
+    const int64_t t0 = w0 * 32, t1 = min64(n, t0 + WB * 32);
+    const int rows = t1 > t0 ? (int)(t1 - t0) : 0;
+    for (int k = threadIdx.x; k < icount * WB; k += blockDim.x) tile[k] = 0u;
+    if (rows > 0)
+        for (int k = threadIdx.x; k <= rows; k += blockDim.x) s_ptr[k] = D.indptr[t0 + k];
+    __syncthreads();
+    int bad = 0;
+    if (rows > 0) {
+        for (int k = threadIdx.x; k < rows; k += blockDim.x)
+            if (s_ptr[k + 1] < s_ptr[k] || s_ptr[k] < 0 || s_ptr[k + 1] > nnz) bad = 1;
+        const int64_t e0 = max64(0, s_ptr[0]), e1 = min64(nnz, s_ptr[rows]);
+        for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+            const int32_t it = D.indices[e];
+            if (it < 0 || it >= D.m) { bad = 1; continue; }
+            if (it < i0 || it >= i0 + icount) continue;
+            int lo = 0, hi = rows;
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (s_ptr[mid] <= e) lo = mid; else hi = mid;
+            }
+            atomicOr(&tile[(it - i0) * WB + (lo >> 5)], 1u << (lo & 31));
+        }
+    }
+    if (bad) atomicExch(flag, 1);
+    __syncthreads();
+    uint32_t *col0 = bm + D.bm_off;
+    for (int k = threadIdx.x; k < icount * WB; k += blockDim.x)
+        col0[(int64_t)(i0 + k / WB) * D.nwp + w0 + k % WB] = tile[k];
+}
+
+// One CTA per item column of the batch: S(I_j) by popcount.
+__global__ void __launch_bounds__(256)
+batch_support_kernel(const DbDesc *__restrict__ dbs, int n_db, const int64_t *__restrict__ item_prefix,
+                     const uint32_t *__restrict__ bm, uint32_t *__restrict__ sup) {
+    const int d = find_db(item_prefix, n_db, blockIdx.x);
+    const DbDesc &D = dbs[d];
+    const int64_t j = blockIdx.x - item_prefix[d];
+    const uint32_t *col = bm + D.bm_off + j * D.nwp;
+    uint32_t c = 0;
+    for (int64_t w = 4 * threadIdx.x; w < D.nwp; w += 4 * blockDim.x) {
+        const uint4 v = ldg_u4(col + w);
+        c += __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
+    }
+    c = warp_sum_u32(c);
+    __shared__ uint32_t s[8];
+    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t t = 0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); k++) t += s[k];
+        sup[D.item_off + j] = t;
+    }
+}
+
+// One warp per item: internal id = rank among the database's frequent items
+// by (support, id); frequent items become singleton records.
+__global__ void batch_rank_kernel(DbDesc *__restrict__ dbs, int n_db, const int64_t *__restrict__ item_prefix,
+                                  int64_t n_items, const uint32_t *__restrict__ sup, int32_t *__restrict__ perm,
+                                  MineCounters *ctr, unsigned long long *rec_off, uint32_t *rec_len,
+                                  uint32_t *rec_sup, uint32_t *rec_items, uint32_t *rec_db,
+                                  unsigned long long rec_cap, unsigned long long items_cap) {
+    const int lane = threadIdx.x & 31;
+    const int64_t gi = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (gi >= n_items) return;
+    const int d = find_db(item_prefix, n_db, gi);
+    DbDesc &D = dbs[d];
+    const int j = (int)(gi - D.item_off);
+    const uint32_t *s = sup + D.item_off;
+    const uint32_t sj = s[j];
+    if (sj < D.thr) return;
+    uint32_t below = 0;
+    for (int i = lane; i < D.m; i += 32) {
+        const uint32_t si = s[i];
+        below += (si >= D.thr) && (si < sj || (si == sj && i < j));
+    }
+    below = warp_sum_u32(below);
+    if (lane == 0) {
+        perm[D.item_off + below] = j;
+        atomicAdd(&D.mfreq, 1);
+        const unsigned long long r = atomicAdd(&ctr->n_records, 1ull);
+        const unsigned long long it = atomicAdd(&ctr->n_rec_items, 1ull);
+        if (r < rec_cap && it < items_cap) {
+            rec_off[r] = it;
+            rec_len[r] = 1;
+            rec_sup[r] = sj;
+            rec_items[it] = below;
+            rec_db[r] = (uint32_t)d;
+        } else {
+            atomicOr(&ctr->overflow, r < rec_cap ? 2 : 1);
+        }
+        if (D.maxlen == 0 || D.maxlen >= 1) atomicMax(&ctr->max_len, 1);
+    }
+}
+
+// Pair supports of one 64 x 64 tile of one database (CUDA cores, exact).
+__global__ void __launch_bounds__(256)
+batch_pairs_kernel(const DbDesc *__restrict__ dbs, int n_db, const int64_t *__restrict__ tile_prefix,
+                   const uint32_t *__restrict__ bm, const int32_t *__restrict__ perm_base,
+                   int *__restrict__ pair_cnt) {
+    __shared__ __align__(16) uint32_t As[KW][TI];
+    __shared__ __align__(16) uint32_t Bs[KW][TI];
+    const int d = find_db(tile_prefix, n_db, blockIdx.x);
+    const DbDesc &D = dbs[d];
+    const int mf = *(volatile const int32_t *)&D.mfreq;
+    const int nt = (D.m + TI - 1) / TI;
+    int idx = (int)(blockIdx.x - tile_prefix[d]), ta = 0;
+    while (idx >= nt - ta) { idx -= nt - ta; ta++; }
+    const int tb = ta + idx;
+    if (tb * TI >= mf || D.maxlen == 1) return;
+    const int32_t *perm = perm_base + D.item_off;
+    const uint32_t *col0 = bm + D.bm_off;
+    const int t = threadIdx.x, lr = t & 63, lc = (t >> 6) * 8;
+    const int ra = ta * TI + lr, rb = tb * TI + lr;
+    const uint32_t *pa = ra < mf ? col0 + (int64_t)perm[ra] * D.nwp : nullptr;
+    const uint32_t *pb = rb < mf ? col0 + (int64_t)perm[rb] * D.nwp : nullptr;
+    const int ty = t >> 4, tx = t & 15;
+    uint32_t acc[4][4] = {};
+    for (int64_t k = 0; k < D.nw; k += KW) {
+        uint4 a0 = make_uint4(0, 0, 0, 0), a1 = a0, b0 = a0, b1 = a0;
+        if (pa) { a0 = ldg_u4(pa + k + lc); a1 = ldg_u4(pa + k + lc + 4); }
+        if (pb) { b0 = ldg_u4(pb + k + lc); b1 = ldg_u4(pb + k + lc + 4); }
+        __syncthreads();
+        const uint32_t av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+        const uint32_t bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+        for (int q = 0; q < 8; q++) { As[lc + q][lr] = av[q]; Bs[lc + q][lr] = bv[q]; }
+        __syncthreads();
+#pragma unroll 8
+        for (int kk = 0; kk < KW; kk++) {
+            const uint4 a = *reinterpret_cast<const uint4 *>(&As[kk][ty * 4]);
+            const uint4 b = *reinterpret_cast<const uint4 *>(&Bs[kk][tx * 4]);
+            const uint32_t x[4] = {a.x, a.y, a.z, a.w}, y[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+            for (int i = 0; i < 4; i++)
+#pragma unroll
+                for (int j = 0; j < 4; j++) acc[i][j] += __popc(x[i] & y[j]);
+        }
+    }
+    int *out = pair_cnt + D.pair_off;
+#pragma unroll
+    for (int i = 0; i < 4; i++)
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const int a = ta * TI + ty * 4 + i, b = tb * TI + tx * 4 + j;
+            if (a < b && b < mf) out[(int64_t)a * mf + b] = (int)acc[i][j];
+        }
+}
+
+// One CTA per (database, row a): threshold, pair bitset, pair records, roots.
+__global__ void __launch_bounds__(256)
+batch_finalize_kernel(const DbDesc *__restrict__ dbs, int n_db, const int64_t *__restrict__ item_prefix,
+                      const int *__restrict__ pair_cnt, uint32_t *__restrict__ pairbits, MineCounters *ctr,
+                      unsigned long long *rec_off, uint32_t *rec_len, uint32_t *rec_sup, uint32_t *rec_items,
+                      uint32_t *rec_db, unsigned long long rec_cap, unsigned long long items_cap,
+                      uint32_t *root_a, uint32_t *root_b, uint32_t *root_sup, uint32_t *root_db) {
+    const int d = find_db(item_prefix, n_db, blockIdx.x);
+    const DbDesc &D = dbs[d];
+    const int a = (int)(blockIdx.x - item_prefix[d]);
+    const int mf = *(volatile const int32_t *)&D.mfreq;
+    if (a >= mf) return;
+    const int mpw = (mf + 31) / 32;
+    const int *row = pair_cnt + D.pair_off + (int64_t)a * mf;
+    const bool emit = D.maxlen == 0 || D.maxlen >= 2;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    for (int w = warp; w < mpw; w += nwarp) {
+        const int b = w * 32 + lane;
+        const uint32_t s = (b > a && b < mf) ? (uint32_t)row[b] : 0u;
+        const bool f = emit && b > a && b < mf && s >= D.thr;
+        const uint32_t bal = __ballot_sync(0xffffffffu, f);
+        if (lane == 0) pairbits[D.pb_off + (int64_t)a * mpw + w] = bal;
+        if (bal == 0) continue;
+        const int cnt = __popc(bal);
+        unsigned long long rbase = 0, ibase = 0, root = 0;
+        if (lane == 0) {
+            rbase = atomicAdd(&ctr->n_records, (unsigned long long)cnt);
+            ibase = atomicAdd(&ctr->n_rec_items, 2ull * cnt);
+            root = atomicAdd(&ctr->n_roots, (unsigned long long)cnt);
+            atomicAdd((unsigned long long *)&ctr->pending, (unsigned long long)cnt);
+            atomicMax(&ctr->max_len, 2);
+        }
+        rbase = __shfl_sync(0xffffffffu, rbase, 0);
+        ibase = __shfl_sync(0xffffffffu, ibase, 0);
+        root = __shfl_sync(0xffffffffu, root, 0);
+        if (f) {
+            const int pos = __popc(bal & ((1u << lane) - 1));
+            const unsigned long long r = rbase + pos, it = ibase + 2ull * pos;
+            if (r < rec_cap && it + 2 <= items_cap) {
+                rec_off[r] = it;
+                rec_len[r] = 2;
+                rec_sup[r] = s;
+                rec_db[r] = (uint32_t)d;
+                rec_items[it] = (uint32_t)a;
+                rec_items[it + 1] = (uint32_t)b;
+            } else {
+                atomicOr(&ctr->overflow, r < rec_cap ? 2 : 1);
+            }
+            root_a[root + pos] = (uint32_t)a;
+            root_b[root + pos] = (uint32_t)b;
+            root_sup[root + pos] = s;
+            root_db[root + pos] = (uint32_t)d;
+        }
+    }
+}
+
+// Result slice of every database in the sorted output: count, scan, item base.
+__global__ void db_count_kernel(const uint32_t *__restrict__ rec_db, unsigned long long R,
+                                unsigned long long *__restrict__ cnt) {
+    const unsigned long long r = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < R) atomicAdd(&cnt[rec_db[r]], 1ull);
+}
+
+__global__ void __launch_bounds__(1024)
+db_scan_kernel(unsigned long long *__restrict__ a, int n, const unsigned long long *__restrict__ out_off,
+               unsigned long long *__restrict__ item_start) {
+    __shared__ unsigned long long s[1024];
+    const int seg = (n + 1 + 1023) / 1024;
+    const int b = threadIdx.x * seg, e = min(b + seg, n + 1);
+    unsigned long long sum = 0;
+    for (int i = b; i < e; i++) sum += (i < n) ? a[i] : 0ull;
+    s[threadIdx.x] = sum;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        const unsigned long long v = threadIdx.x >= (unsigned)o ? s[threadIdx.x - o] : 0ull;
+        __syncthreads();
+        s[threadIdx.x] += v;
+        __syncthreads();
+    }
+    unsigned long long run = s[threadIdx.x] - sum;
+    for (int i = b; i < e; i++) {
+        const unsigned long long v = (i < n) ? a[i] : 0ull;
+        a[i] = run;  // exclusive: a[d] = first sorted record of database d; a[n] = R
+        item_start[i] = out_off[run];
+        run += v;
+    }
+}
+
+__global__ void rebase_kernel(unsigned long long *__restrict__ off, uint64_t n, unsigned long long base) {
+    const uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i <= n) off[i] -= base;
+}
+
+struct Layout {
+    std::vector<DbDesc> dbs;
+    std::vector<int64_t> unit_prefix, item_prefix, tile_prefix;
+    int64_t words = 0, items = 0, pairs = 0, pb = 0, root_cap = 0, nwp_max = 0, max_row_bound = 0;
+    int m_max = 0, ib = 1;
+};
+
+int bits_needed(int64_t v) {
+    int b = 1;
+    while ((1LL << b) < v) b++;
+    return b;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t flags) {
+    if (!ctx || n_db <= 0 || n_db > (1 << 20) || !in) return FIM_E_INVAL;
+    if (flags & (FIM_TRACE | FIM_PAIRS_POPC)) {
+        // traces are per single mine; the batched pair pass is the CUDA-core one
+        if (flags & FIM_TRACE) return FIM_E_INVAL;
+    }
+    if ((flags & FIM_LEARNED) && !ctx->has_weights) return FIM_E_STATE;
+    int dev_prev = -1;
+    cudaGetDevice(&dev_prev);
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return FIM_E_CUDA;
+    struct Restore { int d; ~Restore() { if (d >= 0) cudaSetDevice(d); } } restore{dev_prev};
+    cudaStream_t st = ctx->stream;
+    const bool on_device = flags & FIM_INPUT_DEVICE;
+    const uint32_t maxlen = flags >> 24;
+    ctx->mined = false;
+    ctx->built = false;
+    ctx->batch_mined = false;
+
+    // ---- layout (host) -----------------------------------------------------
+    Layout L;
+    L.dbs.resize(n_db);
+    L.unit_prefix.assign(n_db + 1, 0);
+    L.item_prefix.assign(n_db + 1, 0);
+    L.tile_prefix.assign(n_db + 1, 0);
+    for (int d = 0; d < n_db; d++) L.m_max = in[d].n_items > L.m_max ? in[d].n_items : L.m_max;
+    L.ib = L.m_max < 1024 ? (L.m_max > 0 ? L.m_max : 1) : 1024;
+    int64_t host_nnz_total = 0, host_ptr_total = 0;
+    for (int d = 0; d < n_db; d++) {
+        const fim_db_desc &x = in[d];
+        if (x.n_trans < 0 || x.n_trans > FIM_MAX_TRANS || x.n_items < 0 || x.n_items > FIM_MAX_ITEMS ||
+            !x.indptr)
+            return FIM_E_INVAL;
+        if (!(flags & FIM_STRICT) && x.minsup == 0) return FIM_E_INVAL;
+        DbDesc &D = L.dbs[d];
+        D = DbDesc{};
+        D.n = x.n_trans;
+        D.m = x.n_items;
+        D.nw = ceil_div64(D.n, 32);
+        D.nwp = round_up64(D.nw, FIM_WORDS_ALIGN);
+        uint64_t thr = (flags & FIM_STRICT) ? x.minsup + 1 : x.minsup;
+        if ((flags & FIM_STRICT) && x.minsup == UINT64_MAX) thr = UINT64_MAX;
+        D.thr = thr > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)thr;
+        D.maxlen = maxlen;
+        D.bm_off = L.words;
+        D.item_off = L.items;
+        D.pair_off = L.pairs;
+        D.pb_off = L.pb;
+        L.words += (int64_t)D.m * D.nwp;
+        L.items += D.m;
+        L.pairs += (int64_t)D.m * D.m;
+        L.pb += (int64_t)D.m * ceil_div64(D.m, 32);
+        L.root_cap += (int64_t)D.m * (D.m > 0 ? D.m - 1 : 0) / 2;
+        L.nwp_max = D.nwp > L.nwp_max ? D.nwp : L.nwp_max;
+        const int nt = (int)ceil_div64(D.m, TI);
+        L.unit_prefix[d + 1] = L.unit_prefix[d] + (D.m > 0 ? (D.nwp / WB) * ceil_div64(D.m, L.ib) : 0);
+        L.item_prefix[d + 1] = L.items;
+        L.tile_prefix[d + 1] = L.tile_prefix[d] + (int64_t)nt * (nt + 1) / 2;
+        if (D.m > L.max_row_bound) L.max_row_bound = D.m;
+        if (!on_device) {
+            if (x.indptr[0] != 0 || x.indptr[x.n_trans] < 0 || (x.indptr[x.n_trans] > 0 && !x.indices))
+                return FIM_E_INVAL;
+            host_nnz_total += x.indptr[x.n_trans];
+            host_ptr_total += x.n_trans + 1;
+        }
+    }
+    // ---- inputs: one staging copy for host CSRs -----------------------------
+    if (!on_device) {
+        FIM_TRY(fim_reserve(ctx, ctx->csr_ptr, sizeof(int64_t) * (size_t)(host_ptr_total ? host_ptr_total : 1)));
+        FIM_TRY(fim_reserve(ctx, ctx->csr_idx, sizeof(int32_t) * (size_t)(host_nnz_total ? host_nnz_total : 1)));
+        int64_t po = 0, io = 0;
+        for (int d = 0; d < n_db; d++) {
+            const fim_db_desc &x = in[d];
+            const int64_t nnz = x.indptr[x.n_trans];
+            FIM_CUDA_TRY(cudaMemcpyAsync(ctx->csr_ptr.as<int64_t>() + po, x.indptr,
+                                         sizeof(int64_t) * (size_t)(x.n_trans + 1), cudaMemcpyHostToDevice, st));
+            if (nnz > 0)
+                FIM_CUDA_TRY(cudaMemcpyAsync(ctx->csr_idx.as<int32_t>() + io, x.indices, sizeof(int32_t) * (size_t)nnz,
+                                             cudaMemcpyHostToDevice, st));
+            L.dbs[d].indptr = ctx->csr_ptr.as<int64_t>() + po;
+            L.dbs[d].indices = ctx->csr_idx.as<int32_t>() + io;
+            po += x.n_trans + 1;
+            io += nnz;
+        }
+    } else {
+        for (int d = 0; d < n_db; d++) {
+            L.dbs[d].indptr = in[d].indptr;
+            L.dbs[d].indices = in[d].indices;
+        }
+    }
+    // ---- device buffers -------------------------------------------------------
+    const int workers = ctx->num_sms * ctx->dfs_ctas_per_sm;
+    int depth_cap = (int)(L.max_row_bound < 240 ? L.max_row_bound : 240);
+    if (depth_cap < 2) depth_cap = 2;
+    const size_t per_level = (size_t)workers * (size_t)(L.nwp_max > 0 ? L.nwp_max : 1) * sizeof(uint32_t);
+    while (depth_cap > 2 && per_level * (size_t)depth_cap > (8ull << 30)) depth_cap /= 2;
+    const int64_t frame_pool = 4LL * (L.m_max > 0 ? L.m_max : 1) + 1024;
+    const size_t tbl = sizeof(DbDesc) * (size_t)n_db;
+    FIM_TRY(fim_reserve(ctx, ctx->dbdesc, tbl));
+    FIM_TRY(fim_reserve(ctx, ctx->batch_prefix, sizeof(int64_t) * 3 * (size_t)(n_db + 1)));
+    FIM_TRY(fim_reserve(ctx, ctx->bm, sizeof(uint32_t) * (size_t)(L.words ? L.words : 1)));
+    FIM_TRY(fim_reserve(ctx, ctx->item_sup, sizeof(uint32_t) * (size_t)(L.items ? L.items : 1)));
+    FIM_TRY(fim_reserve(ctx, ctx->perm, sizeof(int32_t) * (size_t)(L.items ? L.items : 1)));
+    FIM_TRY(fim_reserve(ctx, ctx->pair_cnt, sizeof(int) * (size_t)(L.pairs ? L.pairs : 1)));
+    FIM_TRY(fim_reserve(ctx, ctx->pairbits, sizeof(uint32_t) * (size_t)(L.pb ? L.pb : 1)));
+    FIM_TRY(fim_reserve(ctx, ctx->roots, sizeof(uint32_t) * 4 * (size_t)(L.root_cap ? L.root_cap : 1)));
+    FIM_TRY(fim_reserve(ctx, ctx->stack_bits, per_level * (size_t)depth_cap));
+    FIM_TRY(fim_reserve(ctx, ctx->frame_items, sizeof(uint32_t) * (size_t)workers * frame_pool));
+    FIM_TRY(fim_reserve(ctx, ctx->frame_sups, sizeof(uint32_t) * (size_t)workers * frame_pool));
+    FIM_TRY(fim_reserve(ctx, ctx->tasks, sizeof(Task) * kTaskCap));
+    FIM_TRY(fim_reserve(ctx, ctx->cand_pool, sizeof(uint32_t) * kCandPoolCap));
+    if (ctx->rec_cap < (1ull << 22)) {
+        ctx->rec_cap = 1ull << 22;
+        ctx->rec_items_cap = 1ull << 24;
+    }
+    // the DbDesc table and prefix arrays: pinned host staging, re-uploaded per call
+    std::vector<int64_t> pre(3 * (size_t)(n_db + 1));
+    memcpy(pre.data(), L.unit_prefix.data(), sizeof(int64_t) * (n_db + 1));
+    memcpy(pre.data() + (n_db + 1), L.item_prefix.data(), sizeof(int64_t) * (n_db + 1));
+    memcpy(pre.data() + 2 * (n_db + 1), L.tile_prefix.data(), sizeof(int64_t) * (n_db + 1));
+    const int64_t *d_unit = ctx->batch_prefix.as<int64_t>();
+    const int64_t *d_item = d_unit + (n_db + 1);
+    const int64_t *d_tile = d_item + (n_db + 1);
+    MineCounters *d_ctr = ctx->counters.as<MineCounters>();
+    DbDesc *d_dbs = ctx->dbdesc.as<DbDesc>();
+    cudaEventRecord(ctx->ev[0], st);
+    const uint64_t launches0 = ctx->launches;
+
+    for (int attempt = 0; attempt < 4; attempt++) {
+        FIM_TRY(fim_reserve(ctx, ctx->rec_off, sizeof(unsigned long long) * ctx->rec_cap));
+        FIM_TRY(fim_reserve(ctx, ctx->rec_len, sizeof(uint32_t) * ctx->rec_cap));
+        FIM_TRY(fim_reserve(ctx, ctx->rec_sup, sizeof(uint32_t) * ctx->rec_cap));
+        FIM_TRY(fim_reserve(ctx, ctx->rec_db, sizeof(uint32_t) * ctx->rec_cap));
+        FIM_TRY(fim_reserve(ctx, ctx->rec_items, sizeof(uint32_t) * ctx->rec_items_cap));
+        // per-call inputs (outside the graph): descriptor table, prefixes
+        FIM_CUDA_TRY(cudaMemcpyAsync(d_dbs, L.dbs.data(), tbl, cudaMemcpyHostToDevice, st));
+        FIM_CUDA_TRY(cudaMemcpyAsync(ctx->batch_prefix.p, pre.data(), sizeof(int64_t) * pre.size(),
+                                     cudaMemcpyHostToDevice, st));
+        FIM_CUDA_TRY(cudaStreamSynchronize(st));  // host staging vectors go out of scope later
+
+        DfsParams p{};
+        p.dbs = d_dbs;
+        p.bm = ctx->bm.as<uint32_t>();
+        p.perm = ctx->perm.as<int32_t>();
+        p.pairbits = ctx->pairbits.as<uint32_t>();
+        p.pair_cnt = ctx->pair_cnt.as<int>();
+        p.item_sup = ctx->item_sup.as<uint32_t>();
+        p.nwp_max = L.nwp_max > 0 ? L.nwp_max : 1;
+        const size_t rc = (size_t)(L.root_cap ? L.root_cap : 1);
+        uint32_t *roots = ctx->roots.as<uint32_t>();
+        p.root_a = roots;
+        p.root_b = roots + rc;
+        p.root_sup = roots + 2 * rc;
+        p.root_db = roots + 3 * rc;
+        p.root_order = nullptr;
+        p.tasks = ctx->tasks.as<Task>();
+        p.task_cap = kTaskCap;
+        p.cand_pool = ctx->cand_pool.as<uint32_t>();
+        p.cand_pool_cap = kCandPoolCap;
+        p.split_depth = (flags & FIM_NO_SPLIT) ? 0 : ctx->split_depth;
+        p.stack_bits = ctx->stack_bits.as<uint32_t>();
+        p.frame_items = ctx->frame_items.as<uint32_t>();
+        p.frame_sups = ctx->frame_sups.as<uint32_t>();
+        p.frame_pool = frame_pool;
+        p.depth_cap = depth_cap;
+        p.rec_off = ctx->rec_off.as<unsigned long long>();
+        p.rec_len = ctx->rec_len.as<uint32_t>();
+        p.rec_sup = ctx->rec_sup.as<uint32_t>();
+        p.rec_items = ctx->rec_items.as<uint32_t>();
+        p.rec_db = ctx->rec_db.as<uint32_t>();
+        p.rec_cap = ctx->rec_cap;
+        p.rec_items_cap = ctx->rec_items_cap;
+        p.learned = (flags & FIM_LEARNED) ? 1 : 0;
+        p.diffset_rule = (flags & FIM_DIFFSET_RULE) ? 1 : 0;
+        p.mlp_w = ctx->mlp_wbf.as<__nv_bfloat16>();
+        p.ctr = d_ctr;
+        p.spin_limit = kSpinLimitNs;
+
+        // graph key: everything the captured launches depend on
+        uint64_t key = 1469598103934665603ull;
+        auto mix = [&key](const void *data, size_t n) {
+            const unsigned char *b = (const unsigned char *)data;
+            for (size_t i = 0; i < n; i++) key = (key ^ b[i]) * 1099511628211ull;
+        };
+        mix(&n_db, sizeof(n_db));
+        mix(&flags, sizeof(flags));
+        mix(pre.data(), sizeof(int64_t) * pre.size());
+        mix(&p, sizeof(p));
+        mix(&L.ib, sizeof(L.ib));
+        const size_t smem_build = (size_t)L.ib * WB * sizeof(uint32_t);
+        FIM_CUDA_TRY(cudaFuncSetAttribute(batch_build_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smem_build));
+        const bool reuse = ctx->batch_graph_exec && ctx->batch_graph_key == key;
+        if (!reuse) {
+            if (ctx->batch_graph_exec) {
+                cudaGraphExecDestroy((cudaGraphExec_t)ctx->batch_graph_exec);
+                ctx->batch_graph_exec = nullptr;
+            }
+            cudaGraph_t g = nullptr;
+            FIM_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+            cudaMemsetAsync(d_ctr, 0, sizeof(MineCounters), st);
+            cudaMemsetAsync(ctx->dev_flag.p, 0, sizeof(int), st);
+            cudaMemsetAsync(ctx->tasks.p, 0, sizeof(Task) * kTaskCap, st);
+            const int64_t units = L.unit_prefix[n_db], items = L.item_prefix[n_db], tiles = L.tile_prefix[n_db];
+            if (units > 0)
+                batch_build_kernel<<<(unsigned)units, 256, smem_build, st>>>(d_dbs, n_db, d_unit, L.ib,
+                                                                             ctx->bm.as<uint32_t>(),
+                                                                             ctx->dev_flag.as<int>());
+            if (items > 0) {
+                batch_support_kernel<<<(unsigned)items, 256, 0, st>>>(d_dbs, n_db, d_item, ctx->bm.as<uint32_t>(),
+                                                                      ctx->item_sup.as<uint32_t>());
+                batch_rank_kernel<<<(unsigned)ceil_div64(items * 32, 256), 256, 0, st>>>(
+                    d_dbs, n_db, d_item, items, ctx->item_sup.as<uint32_t>(), ctx->perm.as<int32_t>(), d_ctr,
+                    p.rec_off, p.rec_len, p.rec_sup, p.rec_items, p.rec_db, p.rec_cap, p.rec_items_cap);
+            }
+            if (tiles > 0 && maxlen != 1) {
+                batch_pairs_kernel<<<(unsigned)tiles, 256, 0, st>>>(d_dbs, n_db, d_tile, ctx->bm.as<uint32_t>(),
+                                                                    ctx->perm.as<int32_t>(), ctx->pair_cnt.as<int>());
+                batch_finalize_kernel<<<(unsigned)items, 256, 0, st>>>(
+                    d_dbs, n_db, d_item, ctx->pair_cnt.as<int>(), ctx->pairbits.as<uint32_t>(), d_ctr, p.rec_off,
+                    p.rec_len, p.rec_sup, p.rec_items, p.rec_db, p.rec_cap, p.rec_items_cap, roots, roots + rc,
+                    roots + 2 * rc, roots + 3 * rc);
+            }
+            int rc_launch = FIM_OK;
+            if (maxlen == 0 || maxlen >= 3) rc_launch = launch_dfs(ctx, p, workers, dfs_threads());
+            const cudaError_t ce = cudaStreamEndCapture(st, &g);
+            if (rc_launch != FIM_OK) { if (g) cudaGraphDestroy(g); return rc_launch; }
+            if (ce != cudaSuccess) { fim_set_cuda_error(ce, "capture", __FILE__, __LINE__); return FIM_E_CUDA; }
+            cudaGraphExec_t ex = nullptr;
+            const cudaError_t ie = cudaGraphInstantiate(&ex, g, 0);
+            cudaGraphDestroy(g);
+            if (ie != cudaSuccess) { fim_set_cuda_error(ie, "instantiate", __FILE__, __LINE__); return FIM_E_CUDA; }
+            ctx->batch_graph_exec = ex;
+            ctx->batch_graph_key = key;
+            ctx->batch_graph_launches = 6;  // build, support, rank, pairs, finalize, DFS
+        }
+        FIM_CUDA_TRY(cudaGraphLaunch((cudaGraphExec_t)ctx->batch_graph_exec, st));
+        ctx->launches += ctx->batch_graph_launches;
+        cudaEventRecord(ctx->ev[3], st);
+        int bad = 0;
+        FIM_CUDA_TRY(cudaMemcpyAsync(&ctx->host_ctr, d_ctr, sizeof(MineCounters), cudaMemcpyDeviceToHost, st));
+        FIM_CUDA_TRY(cudaMemcpyAsync(&bad, ctx->dev_flag.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+        FIM_CUDA_TRY(cudaStreamSynchronize(st));
+        if (bad) return FIM_E_INVAL;
+        const MineCounters &c = ctx->host_ctr;
+        if (c.err != 0) return c.err;
+        if (c.overflow) {
+            ctx->rec_cap = c.n_records + c.n_records / 4 + 1024;
+            ctx->rec_items_cap = c.n_rec_items + c.n_rec_items / 4 + 4096;
+            continue;  // buffers grow; the new pointers give a new graph key
+        }
+        // ---- canonical order by (database, size, items) ----------------------
+        FIM_TRY(launch_compact(ctx, c.n_records, n_db, L.m_max > 0 ? L.m_max : 1));
+        FIM_TRY(fim_reserve(ctx, ctx->batch_slices, sizeof(unsigned long long) * 2 * (size_t)(n_db + 1)));
+        unsigned long long *cnt = ctx->batch_slices.as<unsigned long long>();
+        unsigned long long *istart = cnt + (n_db + 1);
+        FIM_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * (n_db + 1), st));
+        if (c.n_records > 0) {
+            ctx->launches += 2;
+            db_count_kernel<<<(unsigned)ceil_div64((int64_t)c.n_records, 256), 256, 0, st>>>(
+                ctx->rec_db.as<uint32_t>(), c.n_records, cnt);
+            db_scan_kernel<<<1, 1024, 0, st>>>(cnt, n_db, ctx->out_off.as<unsigned long long>(), istart);
+            FIM_CUDA_TRY(cudaGetLastError());
+        } else {
+            FIM_CUDA_TRY(cudaMemsetAsync(istart, 0, sizeof(unsigned long long) * (n_db + 1), st));
+        }
+        ctx->batch_set_start.resize(n_db + 1);
+        ctx->batch_item_start.resize(n_db + 1);
+        FIM_CUDA_TRY(cudaMemcpyAsync(ctx->batch_set_start.data(), cnt, sizeof(unsigned long long) * (n_db + 1),
+                                     cudaMemcpyDeviceToHost, st));
+        FIM_CUDA_TRY(cudaMemcpyAsync(ctx->batch_item_start.data(), istart,
+                                     sizeof(unsigned long long) * (n_db + 1), cudaMemcpyDeviceToHost, st));
+        cudaEventRecord(ctx->ev[4], st);
+        FIM_CUDA_TRY(cudaStreamSynchronize(st));
+        ctx->batch_n_db = n_db;
+        ctx->batch_mined = true;
+        fim_stats &s = ctx->stats;
+        s.n_trans = 0;
+        for (int d = 0; d < n_db; d++) s.n_trans += (uint64_t)in[d].n_trans;
+        s.n_items = (uint64_t)L.items;
+        s.n_sets = c.n_records;
+        s.max_len = (uint64_t)c.max_len;
+        s.supports_singletons = (uint64_t)L.items;
+        s.supports_pairs = 0;  // sum over databases of m'(m'-1)/2: filled below
+        s.supports_dfs = c.supports_dfs;
+        s.dfs_words = c.dfs_words;
+        s.dfs_bytes = c.dfs_bytes;
+        s.dfs_touched_bytes = c.dfs_touched;
+        s.classes = c.classes;
+        s.tasks_pushed = c.pushed;
+        s.diffset_classes = c.diffset;
+        s.launches_build = 0;
+        s.launches_mine = ctx->launches - launches0;
+        s.pair_path = 0;
+        cudaEventElapsedTime(&s.ms_dfs, ctx->ev[0], ctx->ev[3]);
+        cudaEventElapsedTime(&s.ms_compact, ctx->ev[3], ctx->ev[4]);
+        s.ms_build = s.ms_singletons = s.ms_pairs = 0.f;
+        // m' per database (written by the device) for the pair-support count
+        std::vector<DbDesc> back(n_db);
+        FIM_CUDA_TRY(cudaMemcpy(back.data(), d_dbs, tbl, cudaMemcpyDeviceToHost));
+        uint64_t mfsum = 0;
+        for (int d = 0; d < n_db; d++) {
+            const uint64_t mf = (uint64_t)back[d].mfreq;
+            if (maxlen == 0 || maxlen >= 2) s.supports_pairs += mf * (mf > 0 ? mf - 1 : 0) / 2;
+            mfsum += mf;
+        }
+        s.n_frequent_items = mfsum;
+        if (ctx->bytes_held > s.peak_device_bytes) s.peak_device_bytes = ctx->bytes_held;
+        return FIM_OK;
+    }
+    return FIM_E_NOMEM;
+}
+
+int fim_fetch_batched(fim_ctx *ctx, int db, uint64_t *n_sets, uint64_t *n_items_total, uint64_t *offsets,
+                      uint32_t *items, uint32_t *supports, uint64_t cap_sets, uint64_t cap_items, uint32_t flags) {
+    if (!ctx || !n_sets || !n_items_total) return FIM_E_INVAL;
+    if (!ctx->batch_mined) return FIM_E_STATE;
+    if (db != FIM_ALL_DBS && (db < 0 || db >= ctx->batch_n_db)) return FIM_E_INVAL;
+    const int nd = ctx->batch_n_db;
+    const unsigned long long s0 = db == FIM_ALL_DBS ? 0ull : ctx->batch_set_start[db];
+    const unsigned long long s1 = db == FIM_ALL_DBS ? ctx->batch_set_start[nd] : ctx->batch_set_start[db + 1];
+    const unsigned long long i0 = db == FIM_ALL_DBS ? 0ull : ctx->batch_item_start[db];
+    const unsigned long long i1 = db == FIM_ALL_DBS ? ctx->batch_item_start[nd] : ctx->batch_item_start[db + 1];
+    *n_sets = s1 - s0;
+    *n_items_total = i1 - i0;
+    if (!offsets && !items && !supports) return FIM_OK;
+    if (!offsets || !supports || (!items && i1 > i0)) return FIM_E_INVAL;
+    if (cap_sets < s1 - s0 || cap_items < i1 - i0) return FIM_E_TOO_SMALL;
+    int dev_prev = -1;
+    cudaGetDevice(&dev_prev);
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return FIM_E_CUDA;
+    struct Restore { int d; ~Restore() { if (d >= 0) cudaSetDevice(d); } } restore{dev_prev};
+    cudaStream_t st = ctx->stream;
+    const bool dev = flags & FIM_OUTPUT_DEVICE;
+    const cudaMemcpyKind k = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    FIM_CUDA_TRY(cudaMemcpyAsync(offsets, ctx->out_off.as<unsigned long long>() + s0,
+                                 sizeof(uint64_t) * (s1 - s0 + 1), k, st));
+    if (i1 > i0)
+        FIM_CUDA_TRY(cudaMemcpyAsync(items, ctx->out_items.as<uint32_t>() + i0, sizeof(uint32_t) * (i1 - i0), k, st));
+    if (s1 > s0)
+        FIM_CUDA_TRY(cudaMemcpyAsync(supports, ctx->out_sup.as<uint32_t>() + s0, sizeof(uint32_t) * (s1 - s0), k, st));
+    if (dev) {
+        ctx->launches++;
+        rebase_kernel<<<(unsigned)ceil_div64((int64_t)(s1 - s0 + 1), 256), 256, 0, st>>>(
+            (unsigned long long *)offsets, s1 - s0, i0);
+        FIM_CUDA_TRY(cudaGetLastError());
+    }
+    FIM_CUDA_TRY(cudaStreamSynchronize(st));
+    if (!dev)
+        for (uint64_t q = 0; q <= s1 - s0; q++) offsets[q] -= i0;
+    return FIM_OK;
+}
+
+int fim_batch_slices(fim_ctx *ctx, uint64_t *set_start, uint64_t cap) {
+    if (!ctx || !set_start) return FIM_E_INVAL;
+    if (!ctx->batch_mined) return FIM_E_STATE;
+    if (cap < (uint64_t)ctx->batch_n_db + 1) return FIM_E_TOO_SMALL;
+    for (int d = 0; d <= ctx->batch_n_db; d++) set_start[d] = ctx->batch_set_start[d];
+    return FIM_OK;
+}
+
+}  // extern "C"

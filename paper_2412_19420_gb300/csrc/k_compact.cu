@@ -18,15 +18,20 @@ constexpr int RT = 256;          // threads per radix tile
 constexpr int RI = 8;            // keys per thread per tile
 constexpr int TILE = RT * RI;    // 2048
 
+// dbs/rec_db/db_bits: with several databases the key starts with the record's
+// database (db_bits wide) and items map back through that database's perm.
 __global__ void prep_keys_kernel(unsigned long long R, const unsigned long long *__restrict__ rec_off,
                                  const uint32_t *__restrict__ rec_len, uint32_t *__restrict__ items,
-                                 const int32_t *__restrict__ perm, int bits, int kw,
+                                 const int32_t *__restrict__ perm_base, const DbDesc *__restrict__ dbs,
+                                 const uint32_t *__restrict__ rec_db, int db_bits, int bits, int kw,
                                  unsigned long long *__restrict__ keys, uint32_t *__restrict__ idx) {
     const unsigned long long r = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= R) return;
     idx[r] = (uint32_t)r;
     const unsigned long long off = rec_off[r];
     const int len = (int)rec_len[r];
+    const uint32_t db = db_bits ? rec_db[r] : 0u;
+    const int32_t *perm = perm_base + dbs[db].item_off;
     uint32_t *it = items + off;
     for (int q = 0; q < len; q++) it[q] = (uint32_t)perm[it[q]];
     for (int q = 1; q < len; q++) {  // insertion sort (sets are short)
@@ -49,6 +54,7 @@ __global__ void prep_keys_kernel(unsigned long long R, const unsigned long long 
             if (used == 64) { keys[(unsigned long long)wi * R + r] = w; wi++; w = 0; used = 0; }
         }
     };
+    if (db_bits) put((unsigned long long)db, db_bits);
     put((unsigned long long)len, 8);
     for (int q = 0; q < len; q++) put(it[q], bits);
     if (used > 0) { keys[(unsigned long long)wi * R + r] = w; wi++; }
@@ -212,8 +218,9 @@ int bits_for(int m) {
 
 }  // namespace
 
-int launch_compact(fim_ctx *ctx, uint64_t R) {
+int launch_compact(fim_ctx *ctx, uint64_t R, int n_db, int m_max) {
     cudaStream_t st = ctx->stream;
+    const int db_bits = n_db > 1 ? bits_for(n_db) : 0;
     const unsigned long long total_items = ctx->host_ctr.n_rec_items;
     FIM_TRY(fim_reserve(ctx, ctx->out_off, sizeof(unsigned long long) * (R + 1)));
     FIM_TRY(fim_reserve(ctx, ctx->out_items, sizeof(uint32_t) * (total_items ? total_items : 1)));
@@ -225,8 +232,9 @@ int launch_compact(fim_ctx *ctx, uint64_t R) {
         return FIM_OK;
     }
     const int lmax = ctx->host_ctr.max_len;  // longest set (the host folds in 1- and 2-sets)
-    const int bits = bits_for(ctx->m);
-    const int kw = (int)ceil_div64(8 + (int64_t)bits * lmax, 64);
+    const int bits = bits_for(m_max);
+    const int total_bits = db_bits + 8 + bits * lmax;
+    const int kw = (int)ceil_div64(total_bits, 64);
     FIM_TRY(fim_reserve(ctx, ctx->keys, sizeof(unsigned long long) * R * kw));
     FIM_TRY(fim_reserve(ctx, ctx->idx_a, sizeof(uint32_t) * R));
     FIM_TRY(fim_reserve(ctx, ctx->idx_b, sizeof(uint32_t) * R));
@@ -239,10 +247,10 @@ int launch_compact(fim_ctx *ctx, uint64_t R) {
     uint32_t *ia = ctx->idx_a.as<uint32_t>(), *ib = ctx->idx_b.as<uint32_t>();
     prep_keys_kernel<<<(unsigned)ceil_div64((int64_t)R, 256), 256, 0, st>>>(
         R, ctx->rec_off.as<unsigned long long>(), ctx->rec_len.as<uint32_t>(),
-        ctx->rec_items.as<uint32_t>(), ctx->perm.as<int32_t>(), bits, kw, keys, ia);
+        ctx->rec_items.as<uint32_t>(), ctx->perm.as<int32_t>(), ctx->dbdesc.as<DbDesc>(),
+        ctx->rec_db.as<uint32_t>(), db_bits, bits, kw, keys, ia);
     FIM_CUDA_TRY(cudaGetLastError());
     // LSD: least significant word first; within a word, low digits first.
-    const int total_bits = 8 + bits * lmax;
     for (int w = kw - 1; w >= 0; w--) {
         const int word_lo_bit = (kw - 1 - w) * 64;  // bit index (from the key's LSB) of this word's bit 0
         const int key_pad = kw * 64 - total_bits;    // zero bits at the key's LSB end

@@ -1,24 +1,30 @@
-// k_dfs.cu -- recursive prefix extension (Section III: "the column AND
-// operation can be performed in sequence" for higher-order itemsets; the
-// threshold test of Eq. 3 prunes every infrequent extension).
+// k_dfs.cu -- recursive prefix extension (Section III: the column AND "can
+// be performed in sequence" for higher-order itemsets; the threshold test of
+// Eq. 3 prunes every infrequent extension).
 //
 // Persistent kernel: each CTA is one depth-first worker.  Work arrives as
 // tickets from one global counter.  Tickets below n_roots are the frequent
-// pairs {a, b} (root prefix classes); later tickets are slots of a device
-// queue that workers fill with prefix classes they split off while other
-// workers wait.  Every wait is bounded (FIM_E_TIMEOUT, never a hang).
+// pairs {a, b} (root prefix classes, of any database of the mine); later
+// tickets are slots of a device queue that workers fill with prefix classes
+// they split off while other workers wait.  Every wait is bounded
+// (FIM_E_TIMEOUT, never a hang).
 //
-// A prefix class is (prefix X, support S(X), candidates c_1 < ... < c_k), all
-// candidates later than X's last item, each {x, c} frequent for x in X's last
-// item (pair pruning).  One "pass" over the class computes, word by word,
-//     b_X = AND of the class's sources (parent bitmap AND extension column)
-//     S(X u {c}) = popc(b_X AND col(c))          for every candidate c
-// with b_X held in registers (never re-read), candidate columns streamed from
-// HBM with 128-bit loads, per-warp popc sums reduced by shuffles and combined
-// in shared memory.  b_X is written to the worker's stack only when X can have
-// grandchildren (k >= 2).  Frequent extensions become result records and the
-// child list F; the worker then descends into F in order: child j gets the
-// candidates {F_l : l > j, {F_j, F_l} frequent}.
+// A prefix class Y = X u {c} has its support S(Y), its parent X with S(X),
+// and candidates e_1 < ... < e_k (later frequent siblings of c in X's class
+// whose pair {c, e} is frequent), each with the known S(X u {e}).  One pass
+// over the class streams, word by word,
+//     b_Y = b_X AND col(c)                      (written to the worker's stack
+//                                                when Y can have grandchildren)
+//   dense:    S(Y u {e}) = popc(b_Y AND col(e))
+//   diffset:  S(Y u {e}) = S(X u {e}) - popc(d_Y AND col(e)),  d_Y = b_X AND NOT col(c)
+// The streamed operand (b_Y or d_Y) stays in registers; a lane skips the
+// 16-byte load of col(e) where its operand words are all zero, so HBM serves
+// only the 32-byte sectors that can contribute.  Per-warp popc sums are
+// reduced with shuffles and combined in shared memory.  Frequent extensions
+// become result records and the child list F.  The representation of each
+// class (dense or diffset) is chosen by a closed-form size rule, by the
+// scheduling MLP, or fixed to dense (the plain miner); it never changes a
+// count.
 #include "fim_common.cuh"
 
 namespace {
@@ -30,8 +36,22 @@ constexpr int MAXSRC = FIM_TASK_MAXR + 1;
 constexpr int MAXPATH = 256;             // longest itemset a worker tracks
 constexpr int V = 2;                     // uint4 per lane per chunk (chunk = 256 words)
 constexpr int CHUNK = 128 * V;
+constexpr int NF = FIM_MLP_FEATURES;
+
+// The database of the task a worker is on.
+struct DbView {
+    const uint32_t *bm;
+    const int32_t *perm;
+    const uint32_t *pairbits;
+    const int *pair_cnt;
+    const uint32_t *item_sup;
+    int64_t nwp, nw, n;
+    int32_t mfreq, mpw;
+    uint32_t thr, maxlen, id;
+};
 
 struct Smem {
+    DbView db;
     const uint32_t *src[MAXSRC];
     const uint32_t *cptr[CB];
     uint32_t sup[CB];
@@ -39,8 +59,16 @@ struct Smem {
     int nF[MAXPATH];
     int cur[MAXPATH];
     long long base[MAXPATH + 1];
+    uint32_t supY[MAXPATH];              // support of the class at each level
+    unsigned long long work[MAXPATH];    // candidate words ANDed in the subtree so far
+    float feat[MAXPATH][NF];             // trace features of the class at each level
+    float label[MAXPATH];                // measured representation label
+    float mlp_w[FIM_MLP_PARAMS];         // scheduling MLP (bf16 values held as float)
+    float h1[64], h2[64], y[2];
     uint32_t scan[NWARP + 1];
+    unsigned int sec_dense, sec_diff;    // nonzero 32-byte sectors of b_Y and d_Y
     int nsrc;
+    int diff;                            // 1: count through the diffset
     uint32_t *store;
     unsigned long long ticket;
     unsigned long long rbase, ibase;
@@ -48,12 +76,12 @@ struct Smem {
     int stop;
     int task_len;
     uint32_t task_sup;
+    uint32_t task_db;
     int ncand;
     long long cand_off;
 };
 
-// Block-wide exclusive scan of v (0/1 or small counts).  Returns the prefix;
-// *total receives the sum.  All threads must call it.
+// Block-wide exclusive scan of v.  Returns the prefix; *total gets the sum.
 __device__ __forceinline__ uint32_t block_scan(Smem &s, uint32_t v, uint32_t *total) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t x = v;
@@ -79,24 +107,55 @@ __device__ __forceinline__ uint32_t block_scan(Smem &s, uint32_t v, uint32_t *to
     return s.scan[warp] + x - v;
 }
 
-__device__ __forceinline__ bool pairbit(const DfsParams &p, uint32_t a, uint32_t b) {
-    return (__ldg(p.pairbits + (int64_t)a * p.mpw + (b >> 5)) >> (b & 31)) & 1u;
+__device__ __forceinline__ bool pairbit(const DbView &d, uint32_t a, uint32_t b) {
+    return (__ldg(d.pairbits + (int64_t)a * d.mpw + (b >> 5)) >> (b & 31)) & 1u;
 }
 
-__device__ __forceinline__ const uint32_t *column(const DfsParams &p, uint32_t item) {
-    return p.bm + (int64_t)__ldg(p.perm + item) * p.nwp;
+__device__ __forceinline__ const uint32_t *column(const DbView &d, uint32_t item) {
+    return d.bm + (int64_t)__ldg(d.perm + item) * d.nwp;
 }
 
 __device__ void set_err(const DfsParams &p, int code) { atomicCAS(&p.ctr->err, 0, code); }
 
-// One pass over a class: candidates cand[0..k) (global, in the worker's frame
-// pool), sources in s.src[0..nsrc), optional store of b_X.  Frequent
-// candidates are written compacted (item, support) to fi/fs and emitted as
-// records with prefix s.path[0..plen).  Returns |F| (same in all threads).
-__device__ int class_pass(const DfsParams &p, Smem &s, const uint32_t *cand, int k, int plen,
-                          uint32_t *fi, uint32_t *fs) {
+__device__ __forceinline__ bool nz4(uint4 a) { return (a.x | a.y | a.z | a.w) != 0u; }
+
+__device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+
+// Nonzero 32-byte sectors among the warp's 16-byte lanes (lanes 2i, 2i+1
+// share a sector).
+__device__ __forceinline__ uint32_t warp_sectors(bool nz) {
+    const uint32_t b = __ballot_sync(0xffffffffu, nz);
+    return __popc((b | (b >> 1)) & 0x55555555u);
+}
+
+// Thread 0: the view of database `db` from the mine-wide arrays.
+__device__ void load_db(const DfsParams &p, Smem &s, uint32_t db) {
+    const DbDesc &d = p.dbs[db];
+    s.db.bm = p.bm + d.bm_off;
+    s.db.perm = p.perm + d.item_off;
+    s.db.item_sup = p.item_sup + d.item_off;
+    s.db.pair_cnt = p.pair_cnt + d.pair_off;
+    s.db.pairbits = p.pairbits + d.pb_off;
+    s.db.nwp = d.nwp;
+    s.db.nw = d.nw;
+    s.db.n = d.n;
+    s.db.mfreq = *(volatile const int32_t *)&d.mfreq;
+    s.db.mpw = (s.db.mfreq + 31) / 32;
+    s.db.thr = d.thr;
+    s.db.maxlen = d.maxlen;
+    s.db.id = db;
+}
+
+// One pass over a class: candidates cand[0..k) with parent supports
+// psup[0..k) (both in the worker's frame pool), sources s.src[0..nsrc),
+// optional store of b_Y, s.diff selects the diffset count (nsrc == 2).
+// Frequent candidates are written compacted (item, support) to fi/fs and
+// emitted as records with prefix s.path[0..plen).  Returns |F| (uniform).
+__device__ int class_pass(const DfsParams &p, Smem &s, const uint32_t *cand, const uint32_t *psup,
+                          int k, int plen, uint32_t *fi, uint32_t *fs) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t nwp = p.nwp;
+    const DbView &db = s.db;
+    const int64_t nwp = db.nwp;
     const int nchunks = (int)((nwp + CHUNK - 1) / CHUNK);
     // warps = G candidate groups x (NWARP / G) chunk workers
     const int G = nchunks >= NWARP ? 1 : NWARP / nchunks;
@@ -104,13 +163,16 @@ __device__ int class_pass(const DfsParams &p, Smem &s, const uint32_t *cand, int
     const int g = warp % G, cw = warp / G;
     const bool active = warp < G * CW;
     const int nsrc = s.nsrc;
+    const bool diff = s.diff != 0;
+    const bool two = nsrc == 2;
     uint32_t *store = s.store;
     int nF = 0;
+    if (threadIdx.x == 0) { s.sec_dense = 0; s.sec_diff = 0; }
 
     for (int b0 = 0; b0 < k; b0 += CB) {
         const int kb = min(CB, k - b0);
         for (int c = threadIdx.x; c < kb; c += NT) {
-            s.cptr[c] = column(p, cand[b0 + c]);
+            s.cptr[c] = column(db, cand[b0 + c]);
             s.sup[c] = 0;
         }
         __syncthreads();
@@ -119,18 +181,37 @@ __device__ int class_pass(const DfsParams &p, Smem &s, const uint32_t *cand, int
                 const int64_t base = (int64_t)q * CHUNK + lane * 4;
                 uint4 x[V];
                 bool ok[V];
+                uint32_t secd = 0, secf = 0;
 #pragma unroll
                 for (int v = 0; v < V; v++) {
                     const int64_t pos = base + v * 128;
-                    ok[v] = pos < nwp;
-                    x[v] = make_uint4(0, 0, 0, 0);
+                    ok[v] = pos < nwp;  // uniform across the warp (nwp % 128 == 0)
+                    uint4 y = make_uint4(0, 0, 0, 0), f = y;
                     if (ok[v]) {
-                        x[v] = ld_cg_u4(s.src[0] + pos);
-                        for (int r = 1; r < nsrc; r++) x[v] = and4(x[v], ld_cg_u4(s.src[r] + pos));
-                        if (store && b0 == 0 && g == 0)
-                            *reinterpret_cast<uint4 *>(store + pos) = x[v];
+                        const uint4 s0 = ld_cg_u4(s.src[0] + pos);
+                        y = s0;
+                        if (two) {
+                            const uint4 s1 = ld_cg_u4(s.src[1] + pos);
+                            y = and4(s0, s1);
+                            f = make_uint4(s0.x & ~s1.x, s0.y & ~s1.y, s0.z & ~s1.z, s0.w & ~s1.w);
+                        }
+                        // a popped task ANDs all of its prefix columns
+                        for (int r = two ? 2 : 1; r < nsrc; r++) y = and4(y, ld_cg_u4(s.src[r] + pos));
+                        if (store && b0 == 0 && g == 0) *reinterpret_cast<uint4 *>(store + pos) = y;
+                    }
+                    x[v] = diff ? f : y;
+                    if (ok[v] && b0 == 0 && g == 0) {
+                        secd += warp_sectors(nz4(y));
+                        secf += warp_sectors(nz4(f));
                     }
                 }
+                if (lane == 0 && (secd | secf)) {
+                    atomicAdd(&s.sec_dense, secd);
+                    atomicAdd(&s.sec_diff, secf);
+                }
+                bool any[V];
+#pragma unroll
+                for (int v = 0; v < V; v++) any[v] = ok[v] && nz4(x[v]);
                 int c = g;
                 for (; c + G < kb; c += 2 * G) {
                     const uint32_t *c0 = s.cptr[c], *c1 = s.cptr[c + G];
@@ -138,8 +219,8 @@ __device__ int class_pass(const DfsParams &p, Smem &s, const uint32_t *cand, int
 #pragma unroll
                     for (int v = 0; v < V; v++) {
                         const int64_t pos = base + v * 128;
-                        y0[v] = ok[v] ? ldg_u4(c0 + pos) : make_uint4(0, 0, 0, 0);
-                        y1[v] = ok[v] ? ldg_u4(c1 + pos) : make_uint4(0, 0, 0, 0);
+                        y0[v] = any[v] ? ldg_u4(c0 + pos) : make_uint4(0, 0, 0, 0);
+                        y1[v] = any[v] ? ldg_u4(c1 + pos) : make_uint4(0, 0, 0, 0);
                     }
                     uint32_t n0 = 0, n1 = 0;
 #pragma unroll
@@ -157,7 +238,7 @@ __device__ int class_pass(const DfsParams &p, Smem &s, const uint32_t *cand, int
 #pragma unroll
                     for (int v = 0; v < V; v++) {
                         const int64_t pos = base + v * 128;
-                        if (ok[v]) n0 += popc_and4(x[v], ldg_u4(c0 + pos));
+                        if (any[v]) n0 += popc_and4(x[v], ldg_u4(c0 + pos));
                     }
                     n0 = warp_sum_u32(n0);
                     if (lane == 0 && n0) atomicAdd(&s.sup[c], n0);
@@ -171,8 +252,8 @@ __device__ int class_pass(const DfsParams &p, Smem &s, const uint32_t *cand, int
             uint32_t item = 0, sup = 0, f = 0;
             if (c < kb) {
                 item = cand[b0 + c];
-                sup = s.sup[c];
-                f = sup >= p.thr;
+                sup = diff ? psup[b0 + c] - s.sup[c] : s.sup[c];
+                f = sup >= db.thr;
             }
             uint32_t tot;
             const uint32_t pos = block_scan(s, f, &tot);
@@ -191,6 +272,7 @@ __device__ int class_pass(const DfsParams &p, Smem &s, const uint32_t *cand, int
                         p.rec_off[r] = it;
                         p.rec_len[r] = (uint32_t)(plen + 1);
                         p.rec_sup[r] = sup;
+                        p.rec_db[r] = db.id;
                         for (int q = 0; q < plen; q++) p.rec_items[it + q] = s.path[q];
                         p.rec_items[it + plen] = item;
                     } else {
@@ -203,27 +285,96 @@ __device__ int class_pass(const DfsParams &p, Smem &s, const uint32_t *cand, int
         }
     }
     if (threadIdx.x == 0) {
+        const unsigned long long src_bytes = 4ull * db.nw * ((unsigned long long)nsrc + (store ? 1 : 0));
+        const unsigned long long secs = diff ? s.sec_diff : s.sec_dense;
         atomicAdd(&p.ctr->supports_dfs, (unsigned long long)k);
-        atomicAdd(&p.ctr->dfs_words, (unsigned long long)k * (unsigned long long)p.nw);
-        atomicAdd(&p.ctr->dfs_bytes, 4ull * p.nw * ((unsigned long long)k + nsrc + (store ? 1 : 0)));
+        atomicAdd(&p.ctr->dfs_words, (unsigned long long)k * (unsigned long long)db.nw);
+        atomicAdd(&p.ctr->dfs_bytes, 4ull * db.nw * (unsigned long long)k + src_bytes);
+        atomicAdd(&p.ctr->dfs_touched, 32ull * secs * (unsigned long long)k + src_bytes);
         atomicAdd(&p.ctr->classes, 1ull);
+        if (diff) atomicAdd(&p.ctr->diffset, 1ull);
         if (nF > 0) atomicMax(&p.ctr->max_len, plen + 1);
     }
     return nF;
 }
 
+// Features of class Y (support supY, parent support supX, k candidates with
+// parent supports psup) -- the scheduling MLP's input, in a fixed order,
+// each scaled to O(1) so that bf16 rounding of the input stays harmless.
+__device__ void class_features(Smem &s, int ylen, uint32_t supY, uint32_t supX, const uint32_t *psup,
+                               int k, float *out) {
+    if (threadIdx.x < 32) {
+        float acc = 0.f;
+        for (int c = threadIdx.x; c < k; c += 32) acc += (float)psup[c];
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (threadIdx.x == 0) {
+            const float sx = supX > 0 ? (float)supX : 1.f;
+            const float sy = supY > 0 ? (float)supY : 1.f;
+            out[0] = (float)ylen / 16.f;
+            out[1] = log2f(1.f + (float)supY) / 32.f;
+            out[2] = (float)supY / (float)(s.db.n > 0 ? s.db.n : 1);
+            out[3] = log2f(1.f + (float)k) / 16.f;
+            out[4] = (float)supY / sx;
+            out[5] = k > 0 ? acc / ((float)k * sx) : 0.f;
+            out[6] = log2f(1.f + (float)s.db.nw) / 32.f;
+            out[7] = (float)s.db.thr / sy;
+        }
+    }
+    __syncthreads();
+}
+
+// y = MLP(x) with bf16 weights and bf16-rounded activations, fp32 sums
+// (the same arithmetic as the bf16 mode of fim_mlp_forward).  Result in s.y.
+__device__ void mlp_infer(Smem &s, const float *x) {
+    const float *W1 = s.mlp_w, *b1 = W1 + 64 * 8, *W2 = b1 + 64, *b2 = W2 + 64 * 64, *W3 = b2 + 64,
+                *b3 = W3 + 2 * 64;
+    const int t = threadIdx.x;
+    if (t < 64) {
+        float a = b1[t];
+#pragma unroll
+        for (int i = 0; i < 8; i++) a = fmaf(W1[t * 8 + i], bf16r(x[i]), a);
+        s.h1[t] = bf16r(fmaxf(a, 0.f));
+    }
+    __syncthreads();
+    if (t < 64) {
+        float a = b2[t];
+        for (int i = 0; i < 64; i++) a = fmaf(W2[t * 64 + i], s.h1[i], a);
+        s.h2[t] = bf16r(fmaxf(a, 0.f));
+    }
+    __syncthreads();
+    if (t < 64) {
+        const int o = t >> 5, l = t & 31;
+        float a = W3[o * 64 + l] * s.h2[l] + W3[o * 64 + l + 32] * s.h2[l + 32];
+        for (int d = 16; d > 0; d >>= 1) a += __shfl_xor_sync(0xffffffffu, a, d);
+        if (l == 0) s.y[o] = a + b3[o];
+    }
+    __syncthreads();
+}
+
+// Representation of class Y before its pass: 1 = count through the diffset.
+__device__ int choose_diff(const DfsParams &p, Smem &s, const float *feat, uint32_t supY, uint32_t supX) {
+    if (p.learned) {
+        mlp_infer(s, feat);
+        return s.y[1] > 0.f;
+    }
+    if (p.diffset_rule) return supX - supY < supY;  // |d_Y| < |b_Y| in bits
+    return 0;
+}
+
 // Candidate list of the root class {a, b}: every c > b with {a,c} and {b,c}
-// frequent, written ascending to out.  Returns the count (all threads).
+// frequent, written ascending to out, with psup = S({a, c}).  Returns the
+// count (all threads), or -1 if it does not fit.
 __device__ int root_candidates(const DfsParams &p, Smem &s, uint32_t a, uint32_t b, uint32_t *out,
-                               long long room) {
-    const uint32_t *ra = p.pairbits + (int64_t)a * p.mpw;
-    const uint32_t *rb = p.pairbits + (int64_t)b * p.mpw;
+                               uint32_t *psup, long long room) {
+    const DbView &db = s.db;
+    const uint32_t *ra = db.pairbits + (int64_t)a * db.mpw;
+    const uint32_t *rb = db.pairbits + (int64_t)b * db.mpw;
     int n = 0;
     const int w0 = (int)(b >> 5);  // the word holding b; keep only c > b there
-    for (int wb = w0; wb < p.mpw; wb += NT) {
+    for (int wb = w0; wb < db.mpw; wb += NT) {
         const int w = wb + threadIdx.x;
         uint32_t bits = 0;
-        if (w < p.mpw) {
+        if (w < db.mpw) {
             bits = __ldg(ra + w) & __ldg(rb + w);
             if (w == w0) bits &= 0xFFFFFFFEu << (b & 31);
         }
@@ -233,7 +384,10 @@ __device__ int root_candidates(const DfsParams &p, Smem &s, uint32_t a, uint32_t
         while (bits) {
             const int bit = __ffs(bits) - 1;
             bits &= bits - 1;
-            out[n + pos++] = (uint32_t)(w * 32 + bit);
+            const uint32_t c = (uint32_t)(w * 32 + bit);
+            out[n + pos] = c;
+            psup[n + pos] = (uint32_t)__ldg(db.pair_cnt + (int64_t)a * db.mfreq + c);
+            pos++;
         }
         n += (int)tot;
         __syncthreads();
@@ -278,6 +432,7 @@ __device__ bool try_push(const DfsParams &p, Smem &s, int plen, uint32_t item, u
         t->n_cand = (uint32_t)k;
         t->cand_off = (unsigned long long)s.cand_off;
         t->prio = 0.f;
+        t->db = s.db.id;
         atomicAdd((unsigned long long *)&p.ctr->pending, 1ull);
         atomicAdd(&p.ctr->pushed, 1ull);
         __threadfence();
@@ -287,13 +442,34 @@ __device__ bool try_push(const DfsParams &p, Smem &s, int plen, uint32_t item, u
     return true;
 }
 
+// Close level L: its subtree is complete.  Write its trace row and pass its
+// work up to level L-1.
+__device__ void close_level(const DfsParams &p, Smem &s, int L) {
+    if (threadIdx.x == 0) {
+        if (p.trace) {
+            const unsigned long long r = atomicAdd(&p.ctr->n_traces, 1ull);
+            if (r < p.trace_cap) {
+                for (int i = 0; i < NF; i++) p.trace_x[r * NF + i] = s.feat[L][i];
+                p.trace_y[r * 2 + 0] = log2f(1.f + (float)s.work[L]);
+                p.trace_y[r * 2 + 1] = s.label[L];
+            }
+        }
+        if (L > 0) s.work[L - 1] += s.work[L];
+    }
+    __syncthreads();
+}
+
 __global__ void __launch_bounds__(NT, 2)
 dfs_kernel(const DfsParams p) {
-    __shared__ Smem s;
+    extern __shared__ __align__(16) uint8_t dyn_smem[];
+    Smem &s = *reinterpret_cast<Smem *>(dyn_smem);
     const int wid = blockIdx.x;
     uint32_t *fi = p.frame_items + (int64_t)wid * p.frame_pool;
     uint32_t *fs = p.frame_sups + (int64_t)wid * p.frame_pool;
-    uint32_t *stk = p.stack_bits + (int64_t)wid * p.depth_cap * p.nwp;
+    uint32_t *stk = p.stack_bits + (int64_t)wid * p.depth_cap * p.nwp_max;
+    if (p.learned)
+        for (int i = threadIdx.x; i < FIM_MLP_PARAMS; i += NT) s.mlp_w[i] = __bfloat162float(p.mlp_w[i]);
+    const bool want_feat = p.learned || p.trace;
 
     while (true) {
         // ---- get the next task ---------------------------------------
@@ -304,10 +480,12 @@ dfs_kernel(const DfsParams p) {
             if (*(volatile int *)&p.ctr->err != 0) {
                 // an error ends the mine: take no more work
             } else if (t < nr) {
-                s.path[0] = p.root_a[t];
-                s.path[1] = p.root_b[t];
+                const unsigned long long rt = p.root_order ? p.root_order[t] : t;
+                s.path[0] = p.root_a[rt];
+                s.path[1] = p.root_b[rt];
                 s.task_len = 2;
-                s.task_sup = p.root_sup[t];
+                s.task_sup = p.root_sup[rt];
+                s.task_db = p.root_db ? p.root_db[rt] : 0u;
                 s.ncand = -1;
                 s.flag = 1;
             } else if (t - nr < p.task_cap) {
@@ -321,6 +499,7 @@ dfs_kernel(const DfsParams p) {
                         for (int q = 0; q < len; q++) s.path[q] = ((volatile uint32_t *)tk->items)[q];
                         s.task_len = len;
                         s.task_sup = *(volatile uint32_t *)&tk->support;
+                        s.task_db = *(volatile uint32_t *)&tk->db;
                         s.ncand = (int)*(volatile uint32_t *)&tk->n_cand;
                         s.cand_off = (long long)*(volatile unsigned long long *)&tk->cand_off;
                         s.flag = 1;
@@ -347,40 +526,61 @@ dfs_kernel(const DfsParams p) {
                     __nanosleep(512);
                 }
             }
+            if (s.flag) load_db(p, s, s.task_db);
         }
         __syncthreads();
         if (!s.flag) break;
 
         // ---- level 0: the task's own class ---------------------------
         const int tlen = s.task_len;
+        const bool root = s.ncand < 0;
         int k;
-        if (s.ncand < 0) {
-            k = root_candidates(p, s, s.path[0], s.path[1], fi, p.frame_pool);
+        if (root) {
+            k = root_candidates(p, s, s.path[0], s.path[1], fi, fs, p.frame_pool);
         } else {
             k = s.ncand;
             if (k > p.frame_pool) { if (threadIdx.x == 0) set_err(p, FIM_E_STACK); k = -1; }
             else for (int c = threadIdx.x; c < k; c += NT) fi[c] = __ldcg(p.cand_pool + s.cand_off + c);
             __syncthreads();
         }
-        const bool len_ok = p.maxlen == 0 || (uint32_t)tlen + 1 <= p.maxlen;
+        const uint32_t maxlen = s.db.maxlen;
+        const bool len_ok = maxlen == 0 || (uint32_t)tlen + 1 <= maxlen;
         if (k > 0 && len_ok) {
+            // a root {a, b} has parent {a}: b_X = col(a), S(X) = S({a})
+            const uint32_t supX =
+                root ? (uint32_t)__ldg(s.db.item_sup + __ldg(s.db.perm + s.path[0])) : s.task_sup;
+            if (want_feat) class_features(s, tlen, s.task_sup, supX, fs, root ? k : 0, s.feat[0]);
+            const int diff = root ? choose_diff(p, s, s.feat[0], s.task_sup, supX) : 0;
             if (threadIdx.x == 0) {
-                for (int r = 0; r < tlen; r++) s.src[r] = column(p, s.path[r]);
+                for (int r = 0; r < tlen; r++) s.src[r] = column(s.db, s.path[r]);
                 s.nsrc = tlen;
+                s.diff = diff;
                 s.store = k >= 2 ? stk : nullptr;
                 s.base[0] = 0;
+                s.supY[0] = s.task_sup;
+                s.work[0] = (unsigned long long)k * (unsigned long long)s.db.nw;
             }
             __syncthreads();
-            // candidates live at fi[0..k); F_0 overwrites them in order
-            int nF = class_pass(p, s, fi, k, tlen, fi, fs);
-            if (threadIdx.x == 0) { s.nF[0] = nF; s.cur[0] = 0; s.base[1] = nF; }
+            // candidates live at fi[0..k), parent supports at fs[0..k); F_0
+            // overwrites both in order
+            int nF = class_pass(p, s, fi, fs, k, tlen, fi, fs);
+            if (threadIdx.x == 0) {
+                s.nF[0] = nF;
+                s.cur[0] = 0;
+                s.base[1] = nF;
+                s.label[0] = (s.nsrc == 2 && s.sec_diff < s.sec_dense) ? 1.f : 0.f;
+            }
             __syncthreads();
             int L = 0;
             while (L >= 0) {
                 if (threadIdx.x == 0) s.stop = *(volatile int *)&p.ctr->err != 0;
                 __syncthreads();
                 if (s.stop) break;
-                if (s.cur[L] >= s.nF[L]) { L--; continue; }
+                if (s.cur[L] >= s.nF[L]) {
+                    close_level(p, s, L);
+                    L--;
+                    continue;
+                }
                 const int j = s.cur[L];
                 __syncthreads();
                 if (threadIdx.x == 0) s.cur[L] = j + 1;
@@ -389,24 +589,25 @@ dfs_kernel(const DfsParams p) {
                 const long long bC = s.base[L + 1]; // child's candidates go here
                 const uint32_t citem = fi[bL + j];
                 const uint32_t csup = fs[bL + j];
-                // child candidates: later frequent siblings paired with citem
+                // child candidates: later frequent siblings paired with citem,
+                // each with its support in this class (the child's parent)
                 int kc = 0;
                 const int nFL = s.nF[L];
                 bool overflow = false;
                 for (int l0 = j + 1; l0 < nFL; l0 += NT) {
                     const int l = l0 + threadIdx.x;
-                    uint32_t d = 0, f = 0;
-                    if (l < nFL) { d = fi[bL + l]; f = pairbit(p, citem, d); }
+                    uint32_t d = 0, ds = 0, f = 0;
+                    if (l < nFL) { d = fi[bL + l]; ds = fs[bL + l]; f = pairbit(s.db, citem, d); }
                     uint32_t tot;
                     const uint32_t pos = block_scan(s, f, &tot);
                     if (bC + kc + (long long)tot > p.frame_pool) { overflow = true; break; }
-                    if (f) fi[bC + kc + pos] = d;
+                    if (f) { fi[bC + kc + pos] = d; fs[bC + kc + pos] = ds; }
                     kc += (int)tot;
                 }
                 if (overflow) { if (threadIdx.x == 0) set_err(p, FIM_E_STACK); break; }
                 __syncthreads();
                 if (kc == 0) continue;
-                if (p.maxlen && (uint32_t)plen + 2 > p.maxlen) continue;
+                if (maxlen && (uint32_t)plen + 2 > maxlen) continue;
                 if (plen + 1 <= p.split_depth && plen + 1 <= FIM_TASK_MAXR) {
                     if (threadIdx.x == 0) s.flag = queue_hungry(p);
                     __syncthreads();
@@ -417,19 +618,26 @@ dfs_kernel(const DfsParams p) {
                     break;
                 }
                 // descend: b_child = b_parent AND col(citem)
+                const uint32_t supX = s.supY[L];
+                if (want_feat) class_features(s, plen + 1, csup, supX, fs + bC, kc, s.feat[L + 1]);
+                const int diff = choose_diff(p, s, s.feat[L + 1], csup, supX);
                 if (threadIdx.x == 0) {
                     s.path[plen] = citem;
-                    s.src[0] = stk + (int64_t)L * p.nwp;
-                    s.src[1] = column(p, citem);
+                    s.src[0] = stk + (int64_t)L * p.nwp_max;
+                    s.src[1] = column(s.db, citem);
                     s.nsrc = 2;
-                    s.store = kc >= 2 ? stk + (int64_t)(L + 1) * p.nwp : nullptr;
+                    s.diff = diff;
+                    s.store = kc >= 2 ? stk + (int64_t)(L + 1) * p.nwp_max : nullptr;
+                    s.supY[L + 1] = csup;
+                    s.work[L + 1] = (unsigned long long)kc * (unsigned long long)s.db.nw;
                 }
                 __syncthreads();
-                nF = class_pass(p, s, fi + bC, kc, plen + 1, fi + bC, fs + bC);
+                nF = class_pass(p, s, fi + bC, fs + bC, kc, plen + 1, fi + bC, fs + bC);
                 if (threadIdx.x == 0) {
                     s.nF[L + 1] = nF;
                     s.cur[L + 1] = 0;
                     s.base[L + 2] = bC + nF;
+                    s.label[L + 1] = s.sec_diff < s.sec_dense ? 1.f : 0.f;
                 }
                 __syncthreads();
                 L++;
@@ -448,8 +656,10 @@ dfs_kernel(const DfsParams p) {
 int launch_dfs(fim_ctx *ctx, const DfsParams &p, int grid, int block) {
     (void)block;
     if (grid <= 0) return FIM_OK;
+    const size_t smem = sizeof(Smem);
+    FIM_CUDA_TRY(cudaFuncSetAttribute(dfs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     ctx->launches++;
-    dfs_kernel<<<grid, NT, 0, ctx->stream>>>(p);
+    dfs_kernel<<<grid, NT, smem, ctx->stream>>>(p);
     FIM_CUDA_TRY(cudaGetLastError());
     return FIM_OK;
 }

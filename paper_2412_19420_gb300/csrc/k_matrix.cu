@@ -4,20 +4,22 @@
 // and a range of IB items.  It ORs every (transaction, item) pair of its
 // transactions into a shared-memory tile with atomicOr -- OR makes repeated
 // items idempotent, which is the set membership of Eq. 1 -- and then writes
-// the tile out as WB-word (128-byte) runs of each item column.  The CTA also
-// validates its slice of the CSR (monotone indptr, items inside [0, m)).
+// the tile out as WB-word (64-byte) runs of each item column with 16-byte
+// stores.  A 64-byte row keeps the tile at 64 KB for 1,024 items, so several
+// CTAs share an SM and their zero / scatter / write phases overlap.  The CTA
+// also validates its slice of the CSR (monotone indptr, items in [0, m)).
 #include "fim_common.cuh"
 
 namespace {
 
-constexpr int WB = 32;          // words per CTA tile row (128 bytes)
-constexpr int BUILD_THREADS = 256;
+constexpr int WB = 16;          // words per CTA tile row (64 bytes)
+constexpr int BUILD_THREADS = 512;
 
 __global__ void __launch_bounds__(BUILD_THREADS)
 build_bitmaps_kernel(const int64_t *__restrict__ indptr, const int32_t *__restrict__ indices,
                      int64_t n, int32_t m, int64_t nnz, int64_t nwp, int ib,
                      uint32_t *__restrict__ bm, int *__restrict__ flag, int *__restrict__ max_len) {
-    extern __shared__ uint32_t tile[];          // [ib][WB]
+    extern __shared__ __align__(16) uint32_t tile[];  // [ib][WB]
     __shared__ int64_t s_ptr[WB * 32 + 1];
     const int64_t w0 = (int64_t)blockIdx.x * WB;
     const int i0 = blockIdx.y * ib;
@@ -25,7 +27,8 @@ build_bitmaps_kernel(const int64_t *__restrict__ indptr, const int32_t *__restri
     const int64_t t0 = w0 * 32;
     const int64_t t1 = min(n, t0 + WB * 32);
 
-    for (int k = threadIdx.x; k < icount * WB; k += blockDim.x) tile[k] = 0u;
+    uint4 *tile4 = reinterpret_cast<uint4 *>(tile);  // a row is WB / 4 = 4 uint4
+    for (int k = threadIdx.x; k < icount * (WB / 4); k += blockDim.x) tile4[k] = make_uint4(0, 0, 0, 0);
     const int rows = t1 > t0 ? (int)(t1 - t0) : 0;
     int bad = 0, my_max = 0;
     if (rows > 0)  // rows == 0: a padding block past the last transaction
@@ -55,10 +58,10 @@ build_bitmaps_kernel(const int64_t *__restrict__ indptr, const int32_t *__restri
     if (bad) atomicExch(flag, 1);
     if (blockIdx.y == 0 && my_max > 0) atomicMax(max_len, my_max);
     __syncthreads();
-    // coalesced write-out: each warp writes whole 128-byte rows
-    for (int k = threadIdx.x; k < icount * WB; k += blockDim.x) {
-        int r = k / WB, c = k % WB;
-        bm[(int64_t)(i0 + r) * nwp + w0 + c] = tile[k];
+    // write-out: 16-byte stores, four consecutive threads per 64-byte row
+    for (int k = threadIdx.x; k < icount * (WB / 4); k += blockDim.x) {
+        const int r = k / (WB / 4), c = k % (WB / 4);
+        *reinterpret_cast<uint4 *>(bm + (int64_t)(i0 + r) * nwp + w0 + 4 * c) = tile4[k];
     }
 }
 

@@ -3,23 +3,25 @@
 // S(I_a n I_b) = sum_i M[i,a] M[i,b] (Eq. 2) for all frequent a < b is the
 // upper triangle of C = A^T A, A the n x m' 0/1 matrix of frequent columns: a
 // dense contraction over the transactions.  (sm_103a has no integer MMA, so
-// the 0/1 entries are fed as e4m3 values 0.0 / 1.0 to tcgen05.mma
-// kind::f8f6f4 with an f32 accumulator in tensor memory.)
+// the entries are fed as e4m3 values 0.0 / 2.0 to tcgen05.mma kind::f8f6f4
+// with an f32 accumulator in tensor memory.)
 //
-// Exactness: every product is 0 or 1 and every partial sum is an integer.
-// The accumulator is drained into int32 registers every `kdrain`
-// transactions (at most 8192 by default) and restarted, so no f32 partial sum
-// ever exceeds 2^13; the int32 totals are exact for any n < 2^31.
+// Exactness: every product is 0 or 4 and every partial sum is a multiple of
+// 4.  The accumulator is drained into int32 registers every `kdrain` x 128
+// transactions (8,192 by default) and restarted, so no f32 partial sum ever
+// exceeds 4 x 131,072 = 2^19 even at the largest kdrain; the int32 totals
+// (partial / 4) are exact for any n < 2^31.
 //
-// CTA (416 threads) = one 128 x 128 tile (items a in tile ta, b in tile tb,
+// CTA (544 threads) = one 128 x 128 tile (items a in tile ta, b in tile tb,
 // ta <= tb) x one slice of the transactions:
-//   warps 0-3   producers: read 128 bits of every operand row per stage from
-//               the item bit columns, expand each bit to an e4m3 byte
-//               (0x38 = 1.0) and store the 128 x 128-byte operand tiles in the
+//   warps 0-7   producers, one operand row each (A rows, then B rows; a
+//               diagonal tile has A = B): read the row's 128 bits per stage
+//               from its item bit column, expand each bit to an e4m3 byte
+//               (0x40 = 2.0) and store the 128 x 128-byte operand tiles in the
 //               SWIZZLE_128B K-major layout the MMA descriptors name;
-//   warp 12     one elected thread issues 4 MMAs (K = 32 each) per stage and
+//   warp 16     one elected thread issues 4 MMAs (K = 32 each) per stage and
 //               commits stage release / accumulator-ready to mbarriers;
-//   warps 4-11  epilogue: tcgen05.ld the f32 accumulator (two TMEM buffers,
+//   warps 8-15  epilogue: tcgen05.ld the f32 accumulator (two TMEM buffers,
 //               so draining one overlaps the MMAs into the other), convert to
 //               int32 and keep running totals; finally atomicAdd into pair_cnt.
 // Every mbarrier wait is bounded; on expiry the CTA records an error, lets
@@ -32,7 +34,7 @@ constexpr int TM = 128;              // tile rows (items a)
 constexpr int TN = 128;              // tile cols (items b)
 constexpr int KB = 128;              // K elements (transactions) per stage = 128 bytes per row
 constexpr int STAGES = 4;
-constexpr int NPROD = 128;           // producer threads
+constexpr int NPROD = 256;           // producer threads (one operand row each: A then B)
 constexpr int NEPI = 256;            // epilogue threads
 constexpr int THREADS = NPROD + NEPI + 32;
 constexpr int TILE_BYTES = TM * KB;  // 16 KB per operand per stage
@@ -122,11 +124,14 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar) {
                  : "memory");
 }
 
-// 4 bits -> 4 bytes of e4m3 (0x38 = 1.0, 0x00 = 0.0), bit j -> byte j.
-// x * 0x00204081 places bit j at position 7j + j = 8j with no overlapping
-// terms, so the mask keeps exactly one bit per byte.
+// 4 bits -> 4 bytes of e4m3 (0x40 = 2.0, 0x00 = 0.0), bit j -> byte j.
+// x * 0x08102040 is x << 6 + x << 13 + x << 20 + x << 27: the four copies
+// occupy bits 6-9, 13-16, 20-23, 27-30 (no carries), and bit j of the copy
+// shifted by 6 + 7j lands on bit 8j + 6, the only set bit of 0x40 in byte j.
+// A set bit is encoded as 2.0 (one bit, two instructions per 4 bytes); every
+// product is then 4, so the epilogue divides the exact sums by 4.
 __device__ __forceinline__ uint32_t nib_to_e4m3(uint32_t x) {
-    return ((x * 0x00204081u) & 0x01010101u) * 0x38u;
+    return (x * 0x08102040u) & 0x40404040u;
 }
 __device__ __forceinline__ uint4 bits16_to_e4m3(uint32_t h) {
     return make_uint4(nib_to_e4m3(h & 15u), nib_to_e4m3((h >> 4) & 15u), nib_to_e4m3((h >> 8) & 15u),
@@ -181,28 +186,26 @@ pairs_tc_kernel(const uint32_t *__restrict__ bm, const int32_t *__restrict__ per
     tc_fence_after();
     const uint32_t tmem = s.tmem_base;
 
-    if (warp < 4) {
-        // ---------------- producers ----------------
-        const int r = threadIdx.x;  // operand row
-        const int ia = ta * TM + r, ib = tb * TN + r;
-        const uint32_t *ca = ia < mf ? bm + (int64_t)perm[ia] * nwp : nullptr;
-        const uint32_t *cb = (!diag && ib < mf) ? bm + (int64_t)perm[ib] * nwp : nullptr;
+    if (warp < NPROD / 32) {
+        // ---------------- producers: one operand row each ----------------
+        const int r = threadIdx.x & (TM - 1);
+        const bool is_b = threadIdx.x >= TM;   // threads 128..255 fill B (none on diagonal tiles)
+        const int item = (is_b ? tb * TN : ta * TM) + r;
+        const uint32_t *col = (item < mf && !(is_b && diag)) ? bm + (int64_t)perm[item] * nwp : nullptr;
         for (int it = 0; it < nst; it++) {
             const int slot = it % STAGES;
             const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
             const int64_t w = (st0 + it) * 4;  // 4 words = 128 transactions
-            const uint4 va = ca ? ldg_u4(ca + w) : make_uint4(0, 0, 0, 0);
-            const uint4 vb = cb ? ldg_u4(cb + w) : make_uint4(0, 0, 0, 0);
+            const uint4 v = col ? ldg_u4(col + w) : make_uint4(0, 0, 0, 0);
             if (!mbar_wait(s, &s.empty[slot], ph ^ 1u)) break;
-            store_row(s.a[slot], r, va);
-            if (!diag) store_row(s.b[slot], r, vb);
+            if (!(is_b && diag)) store_row(is_b ? s.b[slot] : s.a[slot], r, v);
             fence_proxy_async();
             mbar_arrive(&s.full[slot]);
         }
-    } else if (warp < 12) {
+    } else if (warp < (NPROD + NEPI) / 32) {
         // ---------------- epilogue ----------------
         const int q = warp & 3;          // TMEM lane quarter this warp may read
-        const int half = (warp - 4) >> 2;  // columns [64*half, 64*half + 64)
+        const int half = (warp - NPROD / 32) >> 2;  // columns [64*half, 64*half + 64)
         int acc[64];
 #pragma unroll
         for (int c = 0; c < 64; c++) acc[c] = 0;
@@ -223,7 +226,7 @@ pairs_tc_kernel(const uint32_t *__restrict__ bm, const int32_t *__restrict__ per
                     : "memory");
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-                for (int c = 0; c < 16; c++) acc[x * 16 + c] += __float2int_rn(__uint_as_float(v[c]));
+                for (int c = 0; c < 16; c++) acc[x * 16 + c] += __float2int_rn(__uint_as_float(v[c])) >> 2;
             }
             tc_fence_before();
             mbar_arrive(&s.acc_empty[buf]);

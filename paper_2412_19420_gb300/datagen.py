@@ -53,7 +53,9 @@ class Csr:
 
 def _pairs_to_csr(rows: np.ndarray, items: np.ndarray, n: int, m: int) -> Csr:
     """Deduplicate (row, item) pairs and lay them out as a row-sorted CSR."""
-    key = np.unique(rows.astype(np.int64) * m + items.astype(np.int64))
+    key = np.sort(rows.astype(np.int64) * m + items.astype(np.int64))
+    if key.size > 1:
+        key = key[np.concatenate([[True], key[1:] != key[:-1]])]
     r = key // m
     it = (key - r * m).astype(np.int32)
     counts = np.bincount(r, minlength=n).astype(np.int64)
@@ -67,42 +69,80 @@ def _zipf_weights(m: int, s: float) -> np.ndarray:
     return w / w.sum()
 
 
+def _alias_table(weights: np.ndarray):
+    """Walker's alias table (Vose's construction): draw i = floor(u * m), keep i
+    if frac(u * m) < prob[i], else take alias[i]; P(j) = weights[j]."""
+    m = weights.shape[0]
+    scaled = weights * m / weights.sum()
+    prob = np.ones(m)
+    alias = np.arange(m)
+    small = [i for i in range(m) if scaled[i] < 1.0]
+    large = [i for i in range(m) if scaled[i] >= 1.0]
+    while small and large:
+        s, l = small.pop(), large.pop()
+        prob[s] = scaled[s]
+        alias[s] = l
+        scaled[l] -= 1.0 - scaled[s]
+        (small if scaled[l] < 1.0 else large).append(l)
+    return prob, alias
+
+
+def _alias_draw(rng, prob, alias, shape):
+    u = rng.random(shape) * prob.shape[0]
+    i = u.astype(np.int64)
+    np.minimum(i, prob.shape[0] - 1, out=i)
+    return np.where(u - i < prob[i], i, alias[i])
+
+
 def _weighted_distinct_rows(rng, lengths: np.ndarray, weights: np.ndarray,
                             max_rounds: int = 64):
     """For row i draw lengths[i] DISTINCT indices with probability ~ weights.
 
-    Draws with replacement, drops repeats within a row, and redraws each row's
-    shortfall until every row is full (rows left short after ``max_rounds``
-    are completed from the unused indices in weight order).
+    Sequential weighted draws with repeats rejected (the usual sampling
+    without replacement): each row draws 2 L + 8 indices with replacement in
+    one vectorised batch and keeps its first L distinct ones in draw order;
+    rows still short draw again (rows left short after ``max_rounds`` are
+    completed from the unused indices in weight order).
     Returns (rows, idx) arrays of equal length.
     """
     n = lengths.shape[0]
     m = weights.shape[0]
-    cdf = np.cumsum(weights)
-    cdf[-1] = 1.0
-    have_key = np.zeros(0, dtype=np.int64)
-    need = lengths.astype(np.int64).copy()
+    prob, alias = _alias_table(weights)
+    lengths = lengths.astype(np.int64)
+    lmax = int(lengths.max()) if n else 0
+    out = np.zeros((n, max(lmax, 1)), dtype=np.int64)   # kept indices, draw order
+    cnt = np.zeros(n, dtype=np.int64)
+    seen = np.zeros((n, (m + 63) // 64), dtype=np.uint64)
+    todo = np.nonzero(lengths > 0)[0]
     for _ in range(max_rounds):
-        tot = int(need.sum())
-        if tot == 0:
+        if todo.size == 0:
             break
-        rows = np.repeat(np.arange(n, dtype=np.int64), need)
-        idx = np.searchsorted(cdf, rng.random(tot), side="right")
-        np.minimum(idx, m - 1, out=idx)
-        have_key = np.unique(np.concatenate([have_key, rows * m + idx]))
-        got = np.bincount(have_key // m, minlength=n)
-        need = lengths - got
-    if need.sum() > 0:  # pathological (row length close to m): fill by order
-        order = np.argsort(-weights, kind="stable")
-        extra = []
-        rows_all = have_key // m
-        for i in np.nonzero(need)[0]:
-            cur = set((have_key[rows_all == i] - i * m).tolist())
-            add = [j for j in order if j not in cur][: int(need[i])]
-            extra.extend(i * m + j for j in add)
-        have_key = np.unique(np.concatenate([have_key, np.asarray(extra, dtype=np.int64)]))
-    r = have_key // m
-    return r, (have_key - r * m)
+        need = lengths[todo] - cnt[todo]
+        # enough draws for a typical row; the few rows still short draw again
+        K = int(min(2 * need.max() + 8, 1.5 * need.mean() + 6))
+        draws = _alias_draw(rng, prob, alias, (todo.size, K))
+        for p in range(K):   # column by column: a row keeps a draw it has not seen yet
+            idx = draws[:, p]
+            word, bit = idx >> 6, (idx & 63).astype(np.uint64)
+            sw = seen[todo, word]
+            new = (((sw >> bit) & np.uint64(1)) == 0) & (cnt[todo] < lengths[todo])
+            rows = todo[new]
+            seen[rows, word[new]] = sw[new] | (np.uint64(1) << bit[new])
+            out[rows, cnt[rows]] = idx[new]
+            cnt[rows] += 1
+        todo = todo[cnt[todo] < lengths[todo]]
+    if todo.size:  # pathological (row length close to m): fill by weight order
+        wo = np.argsort(-weights, kind="stable")
+        for i in todo:
+            cur = set(out[i, :cnt[i]].tolist())
+            for j in wo:
+                if cnt[i] == lengths[i]:
+                    break
+                if int(j) not in cur:
+                    out[i, cnt[i]] = j
+                    cnt[i] += 1
+    keep = np.arange(out.shape[1])[None, :] < lengths[:, None]
+    return np.nonzero(keep)[0].astype(np.int64), out[keep]
 
 
 def zipf_baskets(n: int, m: int, s: float, mean_len: float, seed,
@@ -269,6 +309,22 @@ def batched_specs(n_db: int = 4096, seed: int = 0, log_n=(3.0, 5.0),
 def batched_db(spec: BatchSpec, zipf_s: float = 0.8, mean_len: float = 6.0) -> Csr:
     """One database of the batched workload: Zipf(0.8), Poisson(6) min 1."""
     return zipf_baskets(spec.n, spec.m, zipf_s, mean_len, list(spec.seed))
+
+
+def batched_dbs(specs, processes: int | None = None) -> list:
+    """batched_db for every spec, in a spawn-context process pool (each
+    database has its own seed, so the result does not depend on the pool)."""
+    import multiprocessing as mp
+    import os
+    procs = processes or min(16, len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else 4)
+    if procs <= 1 or len(specs) < 64:
+        return [batched_db(s) for s in specs]
+    try:
+        with mp.get_context("spawn").Pool(procs) as pool:
+            job = pool.map_async(batched_db, specs, chunksize=max(1, len(specs) // (4 * procs)))
+            return job.get(timeout=900)
+    except Exception:  # a pool that cannot start (e.g. no importable __main__): serial
+        return [batched_db(s) for s in specs]
 
 
 def minsup_from_ppm(n: int, ppm: int) -> int:

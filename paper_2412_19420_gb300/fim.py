@@ -24,8 +24,8 @@ from . import build as _build
 FIM_OK = 0
 FIM_E_INVAL, FIM_E_NOMEM, FIM_E_CUDA, FIM_E_TIMEOUT = -1, -2, -3, -4
 FIM_E_STACK, FIM_E_TOO_SMALL, FIM_E_STATE, FIM_E_NODEV = -5, -6, -7, -8
-FIM_INPUT_HOST, FIM_INPUT_DEVICE = 0, 1
-FIM_OUTPUT_HOST, FIM_OUTPUT_DEVICE = 0, 1
+FIM_INPUT_HOST, FIM_INPUT_DEVICE = 0, 0x100
+FIM_OUTPUT_HOST, FIM_OUTPUT_DEVICE = 0, 0x200
 FIM_STRICT, FIM_LEARNED, FIM_PAIRS_POPC, FIM_TRACE = 0x1, 0x2, 0x4, 0x8
 FIM_DIFFSET_RULE, FIM_NO_SPLIT = 0x10, 0x20
 FIM_MLP_PARAMS = 4866
@@ -44,7 +44,7 @@ class FimError(RuntimeError):
 class fim_stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in (
         "n_trans", "n_items", "n_frequent_items", "n_sets", "max_len",
-        "supports_singletons", "supports_pairs", "supports_dfs", "dfs_words", "dfs_bytes",
+        "supports_singletons", "supports_pairs", "supports_dfs", "dfs_words", "dfs_bytes", "dfs_touched_bytes",
         "classes", "tasks_pushed", "diffset_classes", "peak_device_bytes",
         "launches_build", "launches_mine")] + \
         [(n, ctypes.c_float) for n in ("ms_build", "ms_singletons", "ms_pairs", "ms_dfs", "ms_compact")] + \
@@ -84,6 +84,7 @@ def _load():
         "fim_mlp_adam": (ctypes.c_int, [P, P, P, P, P, ctypes.c_int, ctypes.c_float, ctypes.c_float,
                                         ctypes.c_float, ctypes.c_float]),
         "fim_set_tuning": (ctypes.c_int, [P, ctypes.c_char_p, I64]),
+        "fim_batch_slices": (ctypes.c_int, [P, P, U64]),
         "fim_pair_supports_noalloc": (ctypes.c_int, [P, P, I64, I32, P, P]),
         "fim_minsup_from_ppm": (U64, [I64, U32]),
         "fim_strerror": (ctypes.c_char_p, [ctypes.c_int]),
@@ -114,6 +115,17 @@ def fim_version() -> int:
 
 def fim_minsup_from_ppm(n_trans: int, ppm: int) -> int:
     return int(_lib.fim_minsup_from_ppm(int(n_trans), int(ppm)))
+
+
+def _sync_torch(*arrays) -> None:
+    """Work that produced (or still uses) these CUDA tensors may be queued on
+    torch's current stream; the library's stream does not wait for other
+    streams, so that work is finished first."""
+    for a in arrays:
+        if a is not None and hasattr(a, "is_cuda") and a.is_cuda:
+            import torch
+            torch.cuda.current_stream(a.device).synchronize()
+            return
 
 
 def _ptr(a):
@@ -148,6 +160,7 @@ def fim_build_bitmaps(ctx, indptr, indices, n_items: int, flags: int | None = No
     if not hasattr(indptr, "data_ptr"):
         indptr = np.ascontiguousarray(indptr, dtype=np.int64)
         indices = np.ascontiguousarray(indices, dtype=np.int32)
+    _sync_torch(indptr, indices)
     p, dev = _ptr(indptr)
     q, dev2 = _ptr(indices)
     if dev != dev2:
@@ -199,6 +212,7 @@ def fim_fetch_results(ctx, out=None) -> Itemsets:
     if out is None:
         out = (np.empty(R + 1, np.uint64), np.empty(max(T, 1), np.uint32), np.empty(max(R, 1), np.uint32))
     off, it, sup = out
+    _sync_torch(off, it, sup)
     po, dev = _ptr(off)
     pi, _ = _ptr(it)
     ps, _ = _ptr(sup)
@@ -231,6 +245,112 @@ def fim_pair_supports_noalloc(indptr, indices, n_items: int, out, stream=None) -
         s = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
     n = int(indptr.shape[0]) - 1
     _check(_lib.fim_pair_supports_noalloc(p, q, n, int(n_items), o, s), "fim_pair_supports_noalloc")
+
+
+def fim_mine_batched(ctx, dbs, minsups, flags: int = 0) -> None:
+    """Mine many independent databases in one batched pass.  dbs: sequence of
+    objects with .indptr/.indices (numpy host arrays or torch CUDA tensors)
+    and .m; minsups: one absolute threshold per database."""
+    n = len(dbs)
+    arr = (fim_db_desc * max(1, n))()
+    keep = []
+    on_dev = None
+    for i, (c, ms) in enumerate(zip(dbs, minsups)):
+        ip, ix = c.indptr, c.indices
+        if not hasattr(ip, "data_ptr"):
+            ip = np.ascontiguousarray(ip, dtype=np.int64)
+            ix = np.ascontiguousarray(ix, dtype=np.int32)
+        p, dev = _ptr(ip)
+        q, _ = _ptr(ix)
+        if on_dev is None:
+            on_dev = dev
+        elif on_dev != dev:
+            raise ValueError("all databases must be host or all device")
+        keep.append((ip, ix))
+        arr[i] = fim_db_desc(p, q, int(ip.shape[0]) - 1, int(c.m), 0, int(ms))
+    f = int(flags) | (FIM_INPUT_DEVICE if on_dev else 0)
+    if on_dev and keep:
+        _sync_torch(keep[0][0])
+    _check(_lib.fim_mine_batched(ctx, n, ctypes.cast(arr, ctypes.c_void_p), f), "fim_mine_batched")
+    del keep
+
+
+FIM_ALL_DBS = -1
+
+
+def fim_batch_sizes(ctx, db: int) -> tuple[int, int]:
+    ns, ni = ctypes.c_uint64(), ctypes.c_uint64()
+    _check(_lib.fim_fetch_batched(ctx, int(db), ctypes.byref(ns), ctypes.byref(ni), None, None, None, 0, 0, 0),
+           "fim_fetch_batched")
+    return int(ns.value), int(ni.value)
+
+
+def fim_fetch_batched(ctx, db: int, out=None) -> Itemsets:
+    """Canonical results of database `db` of the last batch (FIM_ALL_DBS: every
+    database, in database order), into new host arrays or `out` buffers
+    (numpy, pinned host or torch CUDA tensors)."""
+    R, T = fim_batch_sizes(ctx, db)
+    if out is None:
+        out = (np.empty(R + 1, np.uint64), np.empty(max(T, 1), np.uint32), np.empty(max(R, 1), np.uint32))
+    off, it, sup = out
+    _sync_torch(off, it, sup)
+    po, dev = _ptr(off)
+    pi, _ = _ptr(it)
+    ps, _ = _ptr(sup)
+    ns, ni = ctypes.c_uint64(), ctypes.c_uint64()
+    _check(_lib.fim_fetch_batched(ctx, int(db), ctypes.byref(ns), ctypes.byref(ni), po, pi, ps,
+                                  min(int(sup.shape[0]), int(off.shape[0]) - 1), int(it.shape[0]),
+                                  FIM_OUTPUT_DEVICE if dev else FIM_OUTPUT_HOST), "fim_fetch_batched")
+    if dev:
+        return Itemsets(off[: R + 1], it[:T], sup[:R])
+    return Itemsets(off[: R + 1], it[:T], sup[:R])
+
+
+def fim_batch_slices(ctx, n_db: int) -> np.ndarray:
+    s = np.empty(n_db + 1, np.uint64)
+    _check(_lib.fim_batch_slices(ctx, s.ctypes.data, n_db + 1), "fim_batch_slices")
+    return s
+
+
+def fim_sched_load_weights(ctx, weights) -> None:
+    w = np.ascontiguousarray(weights, dtype=np.float32)
+    _check(_lib.fim_sched_load_weights(ctx, w.ctypes.data, w.size), "fim_sched_load_weights")
+
+
+def fim_fetch_traces(ctx):
+    """(features float32 [n, 8], targets float32 [n, 2]) of the last FIM_TRACE mine."""
+    n = ctypes.c_uint64()
+    _check(_lib.fim_fetch_traces(ctx, ctypes.byref(n), None, None, 0), "fim_fetch_traces")
+    x = np.zeros((n.value, 8), np.float32)
+    t = np.zeros((n.value, 2), np.float32)
+    if n.value:
+        _check(_lib.fim_fetch_traces(ctx, ctypes.byref(n), x.ctypes.data, t.ctypes.data, n.value),
+               "fim_fetch_traces")
+    return x, t
+
+
+def fim_mlp_forward(ctx, params, x, y, cache=None, bf16=False) -> None:
+    """Device tensors: params [4866], x [B, 8] -> y [B, 2]; cache [B, 256] or None."""
+    _sync_torch(params)
+    _check(_lib.fim_mlp_forward(ctx, params.data_ptr(), x.data_ptr(), int(x.shape[0]), y.data_ptr(),
+                                cache.data_ptr() if cache is not None else None, int(bool(bf16))),
+           "fim_mlp_forward")
+
+
+def fim_mlp_backward(ctx, params, x, y, t, cache, grad, bf16=False) -> float:
+    """Device tensors; writes grad [4866]; returns the mean loss."""
+    loss = ctypes.c_float()
+    _sync_torch(params)
+    _check(_lib.fim_mlp_backward(ctx, params.data_ptr(), x.data_ptr(), y.data_ptr(), t.data_ptr(),
+                                 cache.data_ptr(), int(x.shape[0]), grad.data_ptr(), ctypes.byref(loss),
+                                 int(bool(bf16))), "fim_mlp_backward")
+    return float(loss.value)
+
+
+def fim_mlp_adam(ctx, params, grad, m, v, step: int, lr: float, beta1=0.9, beta2=0.999, eps=1e-8) -> None:
+    _sync_torch(params)
+    _check(_lib.fim_mlp_adam(ctx, params.data_ptr(), grad.data_ptr(), m.data_ptr(), v.data_ptr(), int(step),
+                             float(lr), float(beta1), float(beta2), float(eps)), "fim_mlp_adam")
 
 
 def fim_get_stats(ctx) -> dict:

@@ -40,6 +40,65 @@ def canonical_order_ok(sets: list[tuple]) -> bool:
         all(list(x) == sorted(set(x)) for x in sets)
 
 
+def check_canonical_arrays(offsets, items, supports, threshold):
+    """Whole-result checks on the canonical arrays (any size): items strictly
+    ascending inside each set, sets ordered by (size, lexicographic) with no
+    duplicates, every support >= threshold."""
+    offsets = np.asarray(offsets, np.int64)
+    items = np.asarray(items, np.int64)
+    lens = np.diff(offsets)
+    assert np.all(lens >= 1)
+    assert np.all(np.diff(lens) >= 0), "sets not ordered by size"
+    assert np.all(np.asarray(supports, np.int64) >= threshold)
+    for L in np.unique(lens):
+        sel = np.nonzero(lens == L)[0]
+        rows = items[offsets[sel][:, None] + np.arange(L)[None, :]]
+        if L > 1:
+            assert np.all(np.diff(rows, axis=1) > 0), "items not ascending inside a set"
+        if len(rows) > 1:
+            diff = rows[1:] != rows[:-1]
+            assert np.all(diff.any(1)), "duplicate set"
+            first = diff.argmax(1)
+            r = np.arange(len(first))
+            assert np.all(rows[1:][r, first] > rows[:-1][r, first]), "sets not lexicographic"
+
+
+def sampled_checks(csr, threshold, offsets, items, supports, k=200, ext=8, seed=0):
+    """Checks the oracle can afford at any size, on a seeded sample:
+    supports of sampled sets by a direct scan, their (|X|-1)-subsets reported
+    with supports >= theirs, and completeness one level up (a sampled
+    extension X u {e} is reported iff its scanned support reaches threshold)."""
+    import oracle
+    offsets = np.asarray(offsets, np.int64)
+    items = np.asarray(items, np.int64)
+    R = len(supports)
+    if R == 0:
+        return
+    keyset = {}
+    for q in range(R):
+        keyset[items[offsets[q]:offsets[q + 1]].tobytes()] = int(supports[q])
+    rng = np.random.default_rng(seed)
+    pick = rng.choice(R, size=min(k, R), replace=False)
+    sets = [tuple(items[offsets[q]:offsets[q + 1]]) for q in pick]
+    scanned = oracle.support_many(csr.indptr, csr.indices, csr.m, sets)
+    for q, x, s in zip(pick, sets, scanned):
+        assert int(s) == int(supports[q]), (x, int(s), int(supports[q]))
+        if len(x) > 1:
+            for sub in itertools.combinations(x, len(x) - 1):
+                key = np.asarray(sub, np.int64).tobytes()
+                assert key in keyset, ("missing subset", sub)
+                assert keyset[key] >= int(s)
+    queries = []
+    for x in sets:
+        for e in rng.choice(csr.m, size=min(ext, csr.m), replace=False):
+            if e not in x:
+                queries.append(tuple(sorted(x + (int(e),))))
+    scanned = oracle.support_many(csr.indptr, csr.indices, csr.m, queries)
+    for y, s in zip(queries, scanned):
+        reported = np.asarray(y, np.int64).tobytes() in keyset
+        assert reported == (int(s) >= threshold), ("completeness", y, int(s))
+
+
 def check_invariants(result: dict, threshold: int, strict=False, item_support=None,
                      order: list | None = None) -> None:
     """Raise AssertionError unless ``result`` ({set: support}) is consistent."""

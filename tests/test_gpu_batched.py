@@ -1,0 +1,109 @@
+"""Batched mining: many independent databases in one pass (one launch per
+stage, build -> DFS replayed from a CUDA graph).  Every database's result
+must equal the oracle's for that database alone, bit for bit."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2412_19420_gb300 import datagen
+
+pytestmark = pytest.mark.gpu
+fim = pytest.importorskip("paper_2412_19420_gb300.fim")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = fim.fim_create(0)
+    yield c
+    fim.fim_destroy(c)
+
+
+def _mixed_batch(seed, count):
+    rng = np.random.default_rng(seed)
+    dbs, ms = [], []
+    for d in range(count):
+        kind = d % 5
+        if kind == 0:
+            c = datagen.zipf_baskets(int(rng.integers(100, 5000)), int(rng.integers(5, 300)), 0.8, 6.0, [seed, d])
+        elif kind == 1:
+            c = datagen.random_dense(int(rng.integers(1, 400)), int(rng.integers(1, 12)), 0.5, [seed, d])
+        elif kind == 2:
+            c = datagen.from_lists([], int(rng.integers(1, 10)))          # no transactions
+        elif kind == 3:
+            c = datagen.planted(n=int(rng.integers(500, 3000)), m=int(rng.integers(20, 200)), n_patterns=5,
+                                pat_len=(4, 7), frac=(0.02, 0.05), seed=[seed, d])
+        else:
+            c = datagen.from_lists([[0, 1, 2]] * int(rng.integers(1, 50)), 3)
+        dbs.append(c)
+        ms.append(max(1, int(rng.integers(1, max(2, c.n // 20 + 2)))))
+    return dbs, ms
+
+
+def _check_all(ctx, dbs, ms, strict=False, max_len=0):
+    for d, (c, m) in enumerate(zip(dbs, ms)):
+        got = fim.fim_fetch_batched(ctx, d)
+        want = oracle.apriori(c.indptr, c.indices, c.m, m, strict=strict, max_len=max_len)
+        assert got.sha256() == want.sha256(), (d, len(got), len(want))
+
+
+def test_mixed_batch_matches_oracle(ctx):
+    dbs, ms = _mixed_batch(1, 60)
+    fim.fim_mine_batched(ctx, dbs, ms)
+    _check_all(ctx, dbs, ms)
+
+
+def test_graph_replay_and_new_shape(ctx):
+    dbs, ms = _mixed_batch(2, 40)
+    fim.fim_mine_batched(ctx, dbs, ms)
+    first = [fim.fim_fetch_batched(ctx, d).sha256() for d in range(len(dbs))]
+    fim.fim_mine_batched(ctx, dbs, ms)             # same shape: graph replay
+    assert [fim.fim_fetch_batched(ctx, d).sha256() for d in range(len(dbs))] == first
+    dbs2, ms2 = _mixed_batch(3, 25)                # new shape: new capture
+    fim.fim_mine_batched(ctx, dbs2, ms2)
+    _check_all(ctx, dbs2, ms2)
+
+
+def test_batch_flags(ctx):
+    dbs, ms = _mixed_batch(4, 20)
+    fim.fim_mine_batched(ctx, dbs, ms, fim.FIM_STRICT)
+    _check_all(ctx, dbs, ms, strict=True)
+    fim.fim_mine_batched(ctx, dbs, ms, fim.FIM_MAXLEN(2))
+    _check_all(ctx, dbs, ms, max_len=2)
+    fim.fim_mine_batched(ctx, dbs, ms, fim.FIM_DIFFSET_RULE)
+    _check_all(ctx, dbs, ms)
+
+
+def test_device_input(ctx):
+    import torch
+
+    class Dev:
+        def __init__(self, c):
+            self.indptr = torch.from_numpy(c.indptr).cuda()
+            self.indices = torch.from_numpy(c.indices).cuda() if c.nnz else torch.zeros(1, dtype=torch.int32,
+                                                                                           device="cuda")
+            self.m = c.m
+
+    dbs, ms = _mixed_batch(5, 15)
+    fim.fim_mine_batched(ctx, [Dev(c) for c in dbs], ms)
+    _check_all(ctx, dbs, ms)
+
+
+def test_malformed_database_rejected(ctx):
+    dbs, ms = _mixed_batch(6, 5)
+    dbs[2] = datagen.Csr(np.array([0, 2], np.int64), np.array([0, 9], np.int32), 4)
+    with pytest.raises(fim.FimError) as e:
+        fim.fim_mine_batched(ctx, dbs, ms)
+    assert e.value.code == fim.FIM_E_INVAL
+
+
+def test_batched_workload_sample(ctx):
+    # the 4,096-database workload's size distribution, first 256 databases
+    specs = datagen.batched_specs(256)
+    dbs = [datagen.batched_db(s) for s in specs]
+    ms = [datagen.minsup_from_ppm(c.n, 20_000) for c in dbs]
+    fim.fim_mine_batched(ctx, dbs, ms)
+    rng = np.random.default_rng(0)
+    for d in rng.choice(len(dbs), 24, replace=False):
+        got = fim.fim_fetch_batched(ctx, int(d))
+        want = oracle.apriori(dbs[d].indptr, dbs[d].indices, dbs[d].m, ms[d])
+        assert got.sha256() == want.sha256()

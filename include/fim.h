@@ -87,6 +87,9 @@ typedef struct {
     uint64_t peak_device_bytes;   /* device memory held by the ctx                  */
     uint64_t launches_build;      /* kernels launched by the last fim_build_bitmaps */
     uint64_t launches_mine;       /* kernels launched by the last fim_mine          */
+    uint64_t dfs_busy_ns;         /* DFS workers' time inside tasks, summed         */
+    uint64_t dfs_span_ns;         /* first worker start to last worker exit         */
+    uint64_t dfs_workers;         /* DFS workers (CTAs) of the launch               */
     float ms_build, ms_singletons, ms_pairs, ms_dfs, ms_compact; /* CUDA-event times */
     uint32_t pair_path;           /* 1 = tcgen05 tensor cores, 0 = CUDA-core popc   */
     uint32_t reserved;
@@ -153,7 +156,9 @@ int fim_get_stats(const fim_ctx *ctx, fim_stats *out);
 
 /* fim_set_tuning -- set one launch-shape parameter of the ctx; it applies to
  * later calls and never changes results.  Keys and ranges:
- *   "dfs_ctas_per_sm"  1..2      DFS workers per SM
+ *   "dfs_threads"      256, 512  threads of one DFS worker (CTA)
+ *   "dfs_ctas_per_sm"  1..4      DFS workers per SM; dfs_threads x dfs_ctas_per_sm
+ *                                must not exceed 1024 (FIM_E_INVAL otherwise)
  *   "split_depth"      0..8      longest prefix a worker may hand to the queue
  *   "pairs_split"      0..4096   split-K factor of the tensor-core pair pass (0 = auto)
  *   "pairs_kdrain"     0..1024   128-transaction stages per exact accumulator

@@ -18,11 +18,17 @@ import statistics
 from . import fim
 
 SPACE = {
-    "dfs_ctas_per_sm": [1, 2],
-    "split_depth": [2, 3, 4, 6],
+    "dfs_threads": [256, 512],
+    "dfs_ctas_per_sm": [1, 2, 4],
+    "split_depth": [4, 6, 8],
     "pairs_kdrain": [64, 256, 1024],
 }
-DEFAULT = {"dfs_ctas_per_sm": 2, "split_depth": 4, "pairs_kdrain": 64, "pairs_split": 0}
+DEFAULT = {"dfs_threads": 256, "dfs_ctas_per_sm": 4, "split_depth": 8, "pairs_kdrain": 64, "pairs_split": 0}
+
+
+def valid(cfg: dict) -> bool:
+    """A DFS worker is register-capped so that at most 1024 worker threads fit an SM."""
+    return cfg.get("dfs_threads", 512) * cfg.get("dfs_ctas_per_sm", 1) <= 1024
 
 
 def signature(kind: str, n: int, m: int, nnz: int, minsup, flags: int) -> str:
@@ -33,8 +39,13 @@ def signature(kind: str, n: int, m: int, nnz: int, minsup, flags: int) -> str:
 
 
 def apply(ctx, cfg: dict) -> None:
-    for k, v in cfg.items():
-        fim.fim_set_tuning(ctx, k, int(v))
+    if not valid(cfg):
+        raise ValueError(f"invalid launch shape {cfg}")
+    # one worker per SM first, so that no intermediate (threads, ctas) pair
+    # exceeds an SM while the shape changes
+    fim.fim_set_tuning(ctx, "dfs_ctas_per_sm", 1)
+    for k in sorted(cfg, key=lambda k: k == "dfs_ctas_per_sm"):
+        fim.fim_set_tuning(ctx, k, int(cfg[k]))
 
 
 def _time_ms(run, repeats: int) -> float:
@@ -58,6 +69,8 @@ def _search(ctx, run, space, repeats):
     best, best_ms, table = None, float("inf"), []
     for vals in itertools.product(*(space[k] for k in keys)):
         cfg = dict(DEFAULT, **dict(zip(keys, vals)))
+        if not valid(cfg):
+            continue
         apply(ctx, cfg)
         ms = _time_ms(run, repeats)
         table.append((cfg, ms))

@@ -8,7 +8,6 @@
 
 #include "fim_common.cuh"
 
-int dfs_threads();
 
 namespace {
 
@@ -155,6 +154,7 @@ void fim_destroy(fim_ctx *ctx) {
     fim_release(ctx, ctx->batch_prefix);
     fim_release(ctx, ctx->batch_slices);
     if (ctx->batch_graph_exec) cudaGraphExecDestroy((cudaGraphExec_t)ctx->batch_graph_exec);
+    if (ctx->compact_graph_exec) cudaGraphExecDestroy((cudaGraphExec_t)ctx->compact_graph_exec);
     for (auto &e : ctx->ev)
         if (e) cudaEventDestroy(e);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
@@ -347,7 +347,7 @@ int mine_once(fim_ctx *ctx, uint32_t thr, uint32_t flags, MineState &ms, bool *r
             p.trace_y = ctx->trace_y.as<float>();
             p.trace_cap = ctx->trace_cap;
         }
-        FIM_TRY(launch_dfs(ctx, p, workers, dfs_threads()));
+        FIM_TRY(launch_dfs(ctx, p, workers, ctx->dfs_block));
     }
     cudaEventRecord(ctx->ev[3], st);
     FIM_CUDA_TRY(cudaMemcpyAsync(&ctx->host_ctr, d_ctr, sizeof(MineCounters), cudaMemcpyDeviceToHost, st));
@@ -435,6 +435,9 @@ int fim_mine(fim_ctx *ctx, uint64_t minsup, uint32_t flags) {
     s.tasks_pushed = c.pushed;
     s.diffset_classes = c.diffset;
     s.launches_mine = ctx->launches - launches0;
+    s.dfs_busy_ns = c.busy_ns;
+    s.dfs_span_ns = c.t_last > c.t_first && c.t_first != 0 ? c.t_last - c.t_first : 0;
+    s.dfs_workers = (uint64_t)ctx->num_sms * (uint64_t)ctx->dfs_ctas_per_sm;
     if (ctx->bytes_held > s.peak_device_bytes) s.peak_device_bytes = ctx->bytes_held;
     ctx->mined = true;
     return FIM_OK;
@@ -472,7 +475,8 @@ int fim_get_stats(const fim_ctx *ctx, fim_stats *out) {
 int fim_set_tuning(fim_ctx *ctx, const char *key, int64_t v) {
     if (!ctx || !key) return FIM_E_INVAL;
     struct Knob { const char *name; int *field; int64_t lo, hi; } knobs[] = {
-        {"dfs_ctas_per_sm", &ctx->dfs_ctas_per_sm, 1, 2},
+        {"dfs_ctas_per_sm", &ctx->dfs_ctas_per_sm, 1, 4},
+        {"dfs_threads", &ctx->dfs_block, 256, 512},
         {"split_depth", &ctx->split_depth, 0, FIM_TASK_MAXR},
         {"pairs_split", &ctx->pairs_split, 0, 4096},
         {"pairs_kdrain", &ctx->pairs_kdrain, 0, 1024},
@@ -480,6 +484,12 @@ int fim_set_tuning(fim_ctx *ctx, const char *key, int64_t v) {
     for (const Knob &k : knobs)
         if (strcmp(k.name, key) == 0) {
             if (v < k.lo || v > k.hi) return FIM_E_INVAL;
+            // the DFS worker exists in two widths; a worker is capped at 64
+            // registers a thread, so at most 1024 worker threads fit an SM
+            if (k.field == &ctx->dfs_block && v != 256 && v != 512) return FIM_E_INVAL;
+            const int64_t block = k.field == &ctx->dfs_block ? v : ctx->dfs_block;
+            const int64_t per_sm = k.field == &ctx->dfs_ctas_per_sm ? v : ctx->dfs_ctas_per_sm;
+            if (block * per_sm > 1024) return FIM_E_INVAL;
             *k.field = (int)v;
             return FIM_OK;
         }

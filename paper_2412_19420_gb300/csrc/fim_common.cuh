@@ -73,6 +73,9 @@ struct MineCounters {
     unsigned long long pool_top;     // next free word of the candidate pool
     unsigned long long n_roots;      // frequent pairs (root classes)
     unsigned long long n_traces;     // trace rows written
+    unsigned long long busy_ns;      // DFS workers' time inside tasks, summed
+    unsigned long long t_first;      // DFS kernel span (%globaltimer): first start ...
+    unsigned long long t_last;       // ... and last worker exit
     long long pending;               // tasks pushed but not finished
     int err;                         // FIM_OK or a FIM_E_* from the device
     int overflow;                    // bit 0 records, bit 1 items, bit 2 traces
@@ -207,11 +210,14 @@ struct fim_ctx {
     void *batch_graph_exec = nullptr;   // cudaGraphExec_t
     uint64_t batch_graph_key = 0;
     uint64_t batch_graph_launches = 0;
+    // compactor pass sequence, captured when a shape repeats
+    void *compact_graph_exec = nullptr; // cudaGraphExec_t
+    uint64_t compact_key = 0, compact_seen_key = 0, compact_graph_launches = 0;
 
     // tuning (autotuner may overwrite)
-    int dfs_block = 512;
-    int dfs_ctas_per_sm = 2;
-    int split_depth = 4;
+    int dfs_block = 256;
+    int dfs_ctas_per_sm = 4;
+    int split_depth = 8;
     int pairs_split = 0;        // split-K factor of the tensor-core pair pass (0 = auto)
     int pairs_kdrain = 0;       // stages (x128 transactions) per exact drain (0 = 64)
 

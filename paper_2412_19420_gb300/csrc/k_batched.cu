@@ -22,7 +22,6 @@
 
 #include "fim_common.cuh"
 
-int dfs_threads();
 
 namespace {
 
@@ -538,7 +537,7 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
                     roots + 2 * rc, roots + 3 * rc);
             }
             int rc_launch = FIM_OK;
-            if (maxlen == 0 || maxlen >= 3) rc_launch = launch_dfs(ctx, p, workers, dfs_threads());
+            if (maxlen == 0 || maxlen >= 3) rc_launch = launch_dfs(ctx, p, workers, ctx->dfs_block);
             const cudaError_t ce = cudaStreamEndCapture(st, &g);
             if (rc_launch != FIM_OK) { if (g) cudaGraphDestroy(g); return rc_launch; }
             if (ce != cudaSuccess) { fim_set_cuda_error(ce, "capture", __FILE__, __LINE__); return FIM_E_CUDA; }

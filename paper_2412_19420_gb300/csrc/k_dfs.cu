@@ -29,8 +29,6 @@
 
 namespace {
 
-constexpr int NT = 512;                  // threads per worker (CTA)
-constexpr int NWARP = NT / 32;
 constexpr int CB = 1024;                 // candidates per pass batch
 constexpr int MAXSRC = FIM_TASK_MAXR + 1;
 constexpr int MAXPATH = 256;             // longest itemset a worker tracks
@@ -65,7 +63,7 @@ struct Smem {
     float label[MAXPATH];                // measured representation label
     float mlp_w[FIM_MLP_PARAMS];         // scheduling MLP (bf16 values held as float)
     float h1[64], h2[64], y[2];
-    uint32_t scan[NWARP + 1];
+    uint32_t scan[33];                   // block scan scratch (<= 32 warps)
     unsigned int sec_dense, sec_diff;    // nonzero 32-byte sectors of b_Y and d_Y
     int nsrc;
     int diff;                            // 1: count through the diffset
@@ -82,7 +80,9 @@ struct Smem {
 };
 
 // Block-wide exclusive scan of v.  Returns the prefix; *total gets the sum.
+template <int NT>
 __device__ __forceinline__ uint32_t block_scan(Smem &s, uint32_t v, uint32_t *total) {
+    constexpr int NWARP = NT / 32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t x = v;
 #pragma unroll
@@ -151,8 +151,10 @@ __device__ void load_db(const DfsParams &p, Smem &s, uint32_t db) {
 // optional store of b_Y, s.diff selects the diffset count (nsrc == 2).
 // Frequent candidates are written compacted (item, support) to fi/fs and
 // emitted as records with prefix s.path[0..plen).  Returns |F| (uniform).
+template <int NT>
 __device__ int class_pass(const DfsParams &p, Smem &s, const uint32_t *cand, const uint32_t *psup,
                           int k, int plen, uint32_t *fi, uint32_t *fs) {
+    constexpr int NWARP = NT / 32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const DbView &db = s.db;
     const int64_t nwp = db.nwp;
@@ -256,7 +258,7 @@ __device__ int class_pass(const DfsParams &p, Smem &s, const uint32_t *cand, con
                 f = sup >= db.thr;
             }
             uint32_t tot;
-            const uint32_t pos = block_scan(s, f, &tot);
+            const uint32_t pos = block_scan<NT>(s, f, &tot);
             if (tot) {
                 if (threadIdx.x == 0) {
                     s.rbase = atomicAdd(&p.ctr->n_records, (unsigned long long)tot);
@@ -364,6 +366,7 @@ __device__ int choose_diff(const DfsParams &p, Smem &s, const float *feat, uint3
 // Candidate list of the root class {a, b}: every c > b with {a,c} and {b,c}
 // frequent, written ascending to out, with psup = S({a, c}).  Returns the
 // count (all threads), or -1 if it does not fit.
+template <int NT>
 __device__ int root_candidates(const DfsParams &p, Smem &s, uint32_t a, uint32_t b, uint32_t *out,
                                uint32_t *psup, long long room) {
     const DbView &db = s.db;
@@ -379,7 +382,7 @@ __device__ int root_candidates(const DfsParams &p, Smem &s, uint32_t a, uint32_t
             if (w == w0) bits &= 0xFFFFFFFEu << (b & 31);
         }
         uint32_t tot;
-        uint32_t pos = block_scan(s, __popc(bits), &tot);
+        uint32_t pos = block_scan<NT>(s, __popc(bits), &tot);
         if (n + (long long)tot > room) { if (threadIdx.x == 0) set_err(p, FIM_E_STACK); return -1; }
         while (bits) {
             const int bit = __ffs(bits) - 1;
@@ -404,6 +407,7 @@ __device__ bool queue_hungry(const DfsParams &p) {
 
 // Try to hand the child class (prefix s.path[0..plen) + item, candidates
 // cand[0..k)) to the queue.  Returns true if it was published.
+template <int NT>
 __device__ bool try_push(const DfsParams &p, Smem &s, int plen, uint32_t item, uint32_t sup,
                          const uint32_t *cand, int k) {
     if (threadIdx.x == 0) {
@@ -459,7 +463,8 @@ __device__ void close_level(const DfsParams &p, Smem &s, int L) {
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(NT, 2)
+template <int NT>
+__global__ void __launch_bounds__(NT, 1024 / NT)
 dfs_kernel(const DfsParams p) {
     extern __shared__ __align__(16) uint8_t dyn_smem[];
     Smem &s = *reinterpret_cast<Smem *>(dyn_smem);
@@ -470,6 +475,8 @@ dfs_kernel(const DfsParams p) {
     if (p.learned)
         for (int i = threadIdx.x; i < FIM_MLP_PARAMS; i += NT) s.mlp_w[i] = __bfloat162float(p.mlp_w[i]);
     const bool want_feat = p.learned || p.trace;
+    unsigned long long busy = 0, t_task = 0;
+    if (threadIdx.x == 0) atomicCAS(&p.ctr->t_first, 0ull, globaltimer_ns());
 
     while (true) {
         // ---- get the next task ---------------------------------------
@@ -526,7 +533,10 @@ dfs_kernel(const DfsParams p) {
                     __nanosleep(512);
                 }
             }
-            if (s.flag) load_db(p, s, s.task_db);
+            if (s.flag) {
+                load_db(p, s, s.task_db);
+                t_task = globaltimer_ns();
+            }
         }
         __syncthreads();
         if (!s.flag) break;
@@ -536,7 +546,7 @@ dfs_kernel(const DfsParams p) {
         const bool root = s.ncand < 0;
         int k;
         if (root) {
-            k = root_candidates(p, s, s.path[0], s.path[1], fi, fs, p.frame_pool);
+            k = root_candidates<NT>(p, s, s.path[0], s.path[1], fi, fs, p.frame_pool);
         } else {
             k = s.ncand;
             if (k > p.frame_pool) { if (threadIdx.x == 0) set_err(p, FIM_E_STACK); k = -1; }
@@ -563,7 +573,7 @@ dfs_kernel(const DfsParams p) {
             __syncthreads();
             // candidates live at fi[0..k), parent supports at fs[0..k); F_0
             // overwrites both in order
-            int nF = class_pass(p, s, fi, fs, k, tlen, fi, fs);
+            int nF = class_pass<NT>(p, s, fi, fs, k, tlen, fi, fs);
             if (threadIdx.x == 0) {
                 s.nF[0] = nF;
                 s.cur[0] = 0;
@@ -599,7 +609,7 @@ dfs_kernel(const DfsParams p) {
                     uint32_t d = 0, ds = 0, f = 0;
                     if (l < nFL) { d = fi[bL + l]; ds = fs[bL + l]; f = pairbit(s.db, citem, d); }
                     uint32_t tot;
-                    const uint32_t pos = block_scan(s, f, &tot);
+                    const uint32_t pos = block_scan<NT>(s, f, &tot);
                     if (bC + kc + (long long)tot > p.frame_pool) { overflow = true; break; }
                     if (f) { fi[bC + kc + pos] = d; fs[bC + kc + pos] = ds; }
                     kc += (int)tot;
@@ -611,7 +621,7 @@ dfs_kernel(const DfsParams p) {
                 if (plen + 1 <= p.split_depth && plen + 1 <= FIM_TASK_MAXR) {
                     if (threadIdx.x == 0) s.flag = queue_hungry(p);
                     __syncthreads();
-                    if (s.flag && try_push(p, s, plen, citem, csup, fi + bC, kc)) continue;
+                    if (s.flag && try_push<NT>(p, s, plen, citem, csup, fi + bC, kc)) continue;
                 }
                 if (L + 1 >= p.depth_cap || plen + 1 >= MAXPATH) {
                     if (threadIdx.x == 0) set_err(p, FIM_E_STACK);
@@ -632,7 +642,7 @@ dfs_kernel(const DfsParams p) {
                     s.work[L + 1] = (unsigned long long)kc * (unsigned long long)s.db.nw;
                 }
                 __syncthreads();
-                nF = class_pass(p, s, fi + bC, fs + bC, kc, plen + 1, fi + bC, fs + bC);
+                nF = class_pass<NT>(p, s, fi + bC, fs + bC, kc, plen + 1, fi + bC, fs + bC);
                 if (threadIdx.x == 0) {
                     s.nF[L + 1] = nF;
                     s.cur[L + 1] = 0;
@@ -647,21 +657,28 @@ dfs_kernel(const DfsParams p) {
         if (threadIdx.x == 0) {
             __threadfence();
             atomicAdd((unsigned long long *)&p.ctr->pending, (unsigned long long)(-1ll));
+            busy += globaltimer_ns() - t_task;
         }
+    }
+    if (threadIdx.x == 0) {
+        atomicAdd(&p.ctr->busy_ns, busy);
+        atomicMax(&p.ctr->t_last, globaltimer_ns());
     }
 }
 
 }  // namespace
 
 int launch_dfs(fim_ctx *ctx, const DfsParams &p, int grid, int block) {
-    (void)block;
     if (grid <= 0) return FIM_OK;
     const size_t smem = sizeof(Smem);
-    FIM_CUDA_TRY(cudaFuncSetAttribute(dfs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     ctx->launches++;
-    dfs_kernel<<<grid, NT, smem, ctx->stream>>>(p);
+    if (block == 256) {
+        FIM_CUDA_TRY(cudaFuncSetAttribute(dfs_kernel<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        dfs_kernel<256><<<grid, 256, smem, ctx->stream>>>(p);
+    } else {
+        FIM_CUDA_TRY(cudaFuncSetAttribute(dfs_kernel<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        dfs_kernel<512><<<grid, 512, smem, ctx->stream>>>(p);
+    }
     FIM_CUDA_TRY(cudaGetLastError());
     return FIM_OK;
 }
-
-int dfs_threads() { return NT; }

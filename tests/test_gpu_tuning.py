@@ -1,0 +1,79 @@
+"""Launch-shape knobs and the autotuner.
+
+A knob changes how the work is laid out on the GPU (worker width, workers per
+SM, how deep a worker may hand prefixes to the queue, the pair pass split), never
+what is computed: every shape must give the oracle's itemsets bit for bit.
+"""
+import json
+
+import pytest
+
+import oracle
+from paper_2412_19420_gb300 import datagen
+
+pytestmark = pytest.mark.gpu
+fim = pytest.importorskip("paper_2412_19420_gb300.fim")
+autotune = pytest.importorskip("paper_2412_19420_gb300.autotune")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = fim.fim_create(0)
+    yield c
+    fim.fim_destroy(c)
+
+
+@pytest.fixture(scope="module")
+def case():
+    c = datagen.planted(n=20_000, m=600, n_patterns=40, seed=9)
+    minsup = 120
+    return c, minsup, oracle.apriori(c.indptr, c.indices, c.m, minsup).sha256()
+
+
+SHAPES = [(256, 1, 0), (256, 4, 8), (512, 1, 2), (512, 2, 6), (256, 2, 1)]
+
+
+@pytest.mark.parametrize("threads,per_sm,split", SHAPES)
+def test_every_shape_is_exact(ctx, case, threads, per_sm, split):
+    c, minsup, want = case
+    autotune.apply(ctx, {"dfs_threads": threads, "dfs_ctas_per_sm": per_sm, "split_depth": split})
+    try:
+        fim.fim_build_bitmaps(ctx, c.indptr, c.indices, c.m)
+        fim.fim_mine(ctx, minsup)
+        assert fim.fim_fetch_results(ctx).sha256() == want
+        st = fim.fim_get_stats(ctx)
+        assert st["dfs_workers"] > 0 and st["dfs_workers"] % per_sm == 0
+        assert 0 <= st["dfs_busy_ns"] <= st["dfs_span_ns"] * st["dfs_workers"]
+    finally:
+        autotune.apply(ctx, autotune.DEFAULT)
+
+
+def test_invalid_shapes_rejected(ctx):
+    autotune.apply(ctx, autotune.DEFAULT)
+    for key, v in [("dfs_threads", 384), ("dfs_threads", 128), ("dfs_ctas_per_sm", 0),
+                   ("dfs_ctas_per_sm", 5), ("split_depth", 9)]:
+        with pytest.raises(fim.FimError):
+            fim.fim_set_tuning(ctx, key, v)
+    fim.fim_set_tuning(ctx, "dfs_threads", 512)
+    with pytest.raises(fim.FimError):  # 512 x 4 > 1024 worker threads per SM
+        fim.fim_set_tuning(ctx, "dfs_ctas_per_sm", 4)
+    autotune.apply(ctx, autotune.DEFAULT)
+    with pytest.raises(ValueError):
+        autotune.apply(ctx, {"dfs_threads": 512, "dfs_ctas_per_sm": 4})
+
+
+def test_autotune_picks_a_valid_shape_and_caches_it(ctx, case, tmp_path):
+    c, minsup, want = case
+    cache = str(tmp_path / "tune.json")
+    space = {"dfs_threads": [256, 512], "dfs_ctas_per_sm": [2, 4], "split_depth": [4, 8]}
+    best = autotune.tune(ctx, c, minsup, space=space, repeats=1, cache_path=cache)
+    assert autotune.valid(best)
+    with open(cache) as f:
+        stored = json.load(f)
+    assert len(stored) == 1 and next(iter(stored.values()))["dfs_threads"] == best["dfs_threads"]
+    # a cache hit applies the stored choice without timing anything
+    again = autotune.tune(ctx, c, minsup, space=space, repeats=1, cache_path=cache)
+    assert again == best
+    fim.fim_mine(ctx, minsup)
+    assert fim.fim_fetch_results(ctx).sha256() == want
+    autotune.apply(ctx, autotune.DEFAULT)

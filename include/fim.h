@@ -160,9 +160,11 @@ int fim_get_stats(const fim_ctx *ctx, fim_stats *out);
  *   "dfs_ctas_per_sm"  1..4      DFS workers per SM; dfs_threads x dfs_ctas_per_sm
  *                                must not exceed 1024 (FIM_E_INVAL otherwise)
  *   "split_depth"      0..8      longest prefix a worker may hand to the queue
- *   "pairs_split"      0..4096   split-K factor of the tensor-core pair pass (0 = auto)
- *   "pairs_kdrain"     0..1024   128-transaction stages per exact accumulator
- *                                drain (0 = 64); partial sums stay <= 128*kdrain
+ *   "pairs_split"      0..4096   CTAs of the tensor-core pair pass, each taking an
+ *                                equal share of the (tile, stage) space (0 = one per SM)
+ *   "pairs_kdrain"     0..32768  128-transaction stages one accumulator sums before
+ *                                it is drained (0 = 32768: partial sums stay <= 2^24,
+ *                                exact in f32)
  * Errors: FIM_E_INVAL for an unknown key or an out-of-range value. */
 int fim_set_tuning(fim_ctx *ctx, const char *key, int64_t value);
 

@@ -146,7 +146,8 @@ void fim_destroy(fim_ctx *ctx) {
                      &ctx->dev_flag, &ctx->pair_cnt, &ctx->pairbits, &ctx->roots, &ctx->tasks,
                      &ctx->cand_pool, &ctx->stack_bits, &ctx->frame_items, &ctx->frame_sups,
                      &ctx->rec_off, &ctx->rec_len, &ctx->rec_sup, &ctx->rec_items, &ctx->counters,
-                     &ctx->keys, &ctx->idx_a, &ctx->idx_b, &ctx->hist, &ctx->scan_tmp, &ctx->out_off,
+                     &ctx->keys, &ctx->idx_a, &ctx->idx_b, &ctx->hist, &ctx->scan_tmp, &ctx->kv_a, &ctx->kv_b,
+                     &ctx->scan_part, &ctx->out_off,
                      &ctx->out_items, &ctx->out_sup, &ctx->mlp_w32, &ctx->mlp_wbf, &ctx->trace_x,
                      &ctx->trace_y, &ctx->mlp_scratch, &ctx->root_order, &ctx->root_bucket,
                      &ctx->root_hist, &ctx->rec_db, &ctx->dbdesc};
@@ -479,7 +480,7 @@ int fim_set_tuning(fim_ctx *ctx, const char *key, int64_t v) {
         {"dfs_threads", &ctx->dfs_block, 256, 512},
         {"split_depth", &ctx->split_depth, 0, FIM_TASK_MAXR},
         {"pairs_split", &ctx->pairs_split, 0, 4096},
-        {"pairs_kdrain", &ctx->pairs_kdrain, 0, 1024},
+        {"pairs_kdrain", &ctx->pairs_kdrain, 0, 32768},
     };
     for (const Knob &k : knobs)
         if (strcmp(k.name, key) == 0) {

@@ -190,7 +190,7 @@ struct fim_ctx {
     unsigned long long rec_cap = 0, rec_items_cap = 0;
 
     // compactor
-    DevBuf keys, idx_a, idx_b, hist, scan_tmp;
+    DevBuf keys, idx_a, idx_b, hist, scan_tmp, kv_a, kv_b, scan_part;
     DevBuf out_off, out_items, out_sup;
     uint64_t out_sets = 0, out_items_total = 0;
 

@@ -6,9 +6,12 @@
 //   2. packs a big-endian key  [len : 8 bits][item_0 : b]...[item_{L-1} : b]
 //      (b = bits per item id), so that numeric key order is the canonical
 //      order: size first, then lexicographic;
-//   3. sorts the records by that key with a stable LSD radix sort (8-bit
-//      digits; per pass a tile histogram, one scan, a stable scatter ranked
-//      with __match_any_sync);
+//   3. sorts the records by that key with a stable LSD radix sort of
+//      (key word, record) pairs, 64-bit key words from the least significant
+//      one: each word is gathered once into record order, then sorted by its
+//      8-bit digits (per pass a tile histogram with warp-aggregated counts, a
+//      scan of the [digit][tile] counts, a stable scatter ranked with
+//      __match_any_sync that moves the word with its record index);
 //   4. writes offsets (exclusive scan of the sizes), items and supports.
 #include "fim_common.cuh"
 
@@ -62,19 +65,87 @@ __global__ void prep_keys_kernel(unsigned long long R, const unsigned long long 
 }
 
 __global__ void __launch_bounds__(RT)
-rs_hist_kernel(const unsigned long long *__restrict__ kword, const uint32_t *__restrict__ idx,
-               unsigned long long n, int shift, uint32_t *__restrict__ hist, int ntiles) {
+rs_hist_kernel(const unsigned long long *__restrict__ key, unsigned long long n, int shift,
+               uint32_t *__restrict__ hist, int ntiles) {
     __shared__ uint32_t h[256];
+    const int lane = threadIdx.x & 31;
     h[threadIdx.x] = 0;
     __syncthreads();
     const unsigned long long t0 = (unsigned long long)blockIdx.x * TILE;
 #pragma unroll
     for (int i = 0; i < RI; i++) {
         const unsigned long long e = t0 + i * RT + threadIdx.x;
-        if (e < n) atomicAdd(&h[(kword[idx[e]] >> shift) & 255u], 1u);
+        const uint32_t d = e < n ? (uint32_t)((key[e] >> shift) & 255u) : 256u;
+        // one shared atomic per distinct digit of the warp: a digit that
+        // (nearly) every key shares costs 1/32 of the plain count
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        if (d < 256u && lane == __ffs(peers) - 1) atomicAdd(&h[d], (uint32_t)__popc(peers));
     }
     __syncthreads();
     hist[(size_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
+}
+
+// out[i] = word[idx[i]]: one key word in the records' current order.
+__global__ void gather_word_kernel(const unsigned long long *__restrict__ word, const uint32_t *__restrict__ idx,
+                                   unsigned long long n, unsigned long long *__restrict__ out) {
+    const unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = word[idx[i]];
+}
+
+// Three-phase exclusive scan for long arrays: per-chunk sums, a scan of the
+// sums in one CTA, and a rescan of every chunk from its base.
+constexpr int SC_T = 1024, SC_I = 8, SC_CHUNK = SC_T * SC_I;
+__global__ void __launch_bounds__(SC_T)
+scan_reduce_kernel(const uint32_t *__restrict__ a, unsigned long long n, uint32_t *__restrict__ part) {
+    __shared__ uint32_t s[SC_T / 32];
+    const unsigned long long b = (unsigned long long)blockIdx.x * SC_CHUNK;
+    uint32_t v = 0;
+#pragma unroll
+    for (int i = 0; i < SC_I; i++) {
+        const unsigned long long e = b + (unsigned long long)i * SC_T + threadIdx.x;
+        if (e < n) v += a[e];
+    }
+    v = warp_sum_u32(v);
+    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        uint32_t t = s[threadIdx.x];
+        t = warp_sum_u32(t);
+        if (threadIdx.x == 0) part[blockIdx.x] = t;
+    }
+}
+
+__global__ void __launch_bounds__(SC_T)
+scan_apply_kernel(uint32_t *__restrict__ a, unsigned long long n, const uint32_t *__restrict__ part) {
+    __shared__ uint32_t s[SC_T / 32 + 1];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // thread t owns elements [b + t*SC_I, b + t*SC_I + SC_I) of the chunk
+    const unsigned long long b = (unsigned long long)blockIdx.x * SC_CHUNK + (unsigned long long)threadIdx.x * SC_I;
+    uint32_t v[SC_I], sum = 0;
+#pragma unroll
+    for (int i = 0; i < SC_I; i++) {
+        v[i] = b + i < n ? a[b + i] : 0u;
+        sum += v[i];
+    }
+    uint32_t x = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s[warp] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t acc = part[blockIdx.x];
+        for (int w = 0; w < SC_T / 32; w++) { const uint32_t t = s[w]; s[w] = acc; acc += t; }
+    }
+    __syncthreads();
+    uint32_t run = s[warp] + x - sum;
+#pragma unroll
+    for (int i = 0; i < SC_I; i++) {
+        if (b + i < n) a[b + i] = run;
+        run += v[i];
+    }
 }
 
 // Exclusive scan of a uint32 array (length <= a few million) in one CTA.
@@ -102,9 +173,9 @@ scan_single_kernel(uint32_t *__restrict__ a, unsigned long long n) {
 }
 
 __global__ void __launch_bounds__(RT)
-rs_scatter_kernel(const unsigned long long *__restrict__ kword, const uint32_t *__restrict__ idx_in,
-                  uint32_t *__restrict__ idx_out, unsigned long long n, int shift,
-                  const uint32_t *__restrict__ hist, int ntiles) {
+rs_scatter_kernel(const unsigned long long *__restrict__ key_in, const uint32_t *__restrict__ idx_in,
+                  unsigned long long *__restrict__ key_out, uint32_t *__restrict__ idx_out, unsigned long long n,
+                  int shift, const uint32_t *__restrict__ hist, int ntiles) {
     __shared__ uint32_t base[256];
     __shared__ uint32_t wc[RT / 32][257];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -113,8 +184,9 @@ rs_scatter_kernel(const unsigned long long *__restrict__ kword, const uint32_t *
     for (int i = 0; i < RI; i++) {
         const unsigned long long e = t0 + i * RT + threadIdx.x;
         const bool valid = e < n;
+        unsigned long long k = 0;
         uint32_t v = 0, d = 256;
-        if (valid) { v = idx_in[e]; d = (uint32_t)((kword[v] >> shift) & 255u); }
+        if (valid) { k = key_in[e]; v = idx_in[e]; d = (uint32_t)((k >> shift) & 255u); }
         for (int q = threadIdx.x; q < (RT / 32) * 257; q += RT) (&wc[0][0])[q] = 0;
         __syncthreads();
         const uint32_t peers = __match_any_sync(0xffffffffu, d);
@@ -124,6 +196,7 @@ rs_scatter_kernel(const unsigned long long *__restrict__ kword, const uint32_t *
         if (valid) {
             uint32_t off = base[d] + rank;
             for (int w = 0; w < warp; w++) off += wc[w][d];
+            key_out[off] = k;
             idx_out[off] = v;
         }
         __syncthreads();
@@ -238,8 +311,13 @@ int launch_compact(fim_ctx *ctx, uint64_t R, int n_db, int m_max) {
     FIM_TRY(fim_reserve(ctx, ctx->keys, sizeof(unsigned long long) * R * kw));
     FIM_TRY(fim_reserve(ctx, ctx->idx_a, sizeof(uint32_t) * R));
     FIM_TRY(fim_reserve(ctx, ctx->idx_b, sizeof(uint32_t) * R));
+    FIM_TRY(fim_reserve(ctx, ctx->kv_a, sizeof(unsigned long long) * R));
+    FIM_TRY(fim_reserve(ctx, ctx->kv_b, sizeof(unsigned long long) * R));
     const int ntiles = (int)ceil_div64((int64_t)R, TILE);
-    FIM_TRY(fim_reserve(ctx, ctx->hist, sizeof(uint32_t) * 256 * (size_t)ntiles));
+    const unsigned long long nhist = 256ull * (unsigned long long)ntiles;
+    const int nchunks = (int)ceil_div64((int64_t)nhist, SC_CHUNK);
+    FIM_TRY(fim_reserve(ctx, ctx->hist, sizeof(uint32_t) * nhist));
+    FIM_TRY(fim_reserve(ctx, ctx->scan_part, sizeof(uint32_t) * (size_t)nchunks));
     const int nblk = (int)ceil_div64((int64_t)R, ST);
     FIM_TRY(fim_reserve(ctx, ctx->scan_tmp, sizeof(unsigned long long) * (size_t)nblk));
 
@@ -254,19 +332,41 @@ int launch_compact(fim_ctx *ctx, uint64_t R, int n_db, int m_max) {
             ctx->rec_db.as<uint32_t>(), db_bits, bits, kw, keys, ia);
         nk++;
         // LSD: least significant word first; within a word, low digits first.
+        // (word, record) pairs move together, so each word is gathered into
+        // record order once; the least significant word starts in record
+        // order and is read straight from the key array.
+        unsigned long long *ka = ctx->kv_a.as<unsigned long long>(), *kb = ctx->kv_b.as<unsigned long long>();
+        uint32_t *hist = ctx->hist.as<uint32_t>();
+        const int key_pad = kw * 64 - total_bits;  // zero bits at the key's LSB end
+        bool first_word = true;
         for (int w = kw - 1; w >= 0; w--) {
             const int word_lo_bit = (kw - 1 - w) * 64;  // bit index (from the key's LSB) of this word's bit 0
-            const int key_pad = kw * 64 - total_bits;    // zero bits at the key's LSB end
+            const unsigned long long *kin = keys + (size_t)w * R;
+            if (!first_word) {
+                gather_word_kernel<<<(unsigned)ceil_div64((int64_t)R, 256), 256, 0, st>>>(kin, ia, R, ka);
+                nk++;
+                kin = ka;
+            }
+            first_word = false;
             for (int d = 0; d < 8; d++) {
                 const int lo = word_lo_bit + d * 8;
                 if (lo + 8 <= key_pad) continue;          // digit holds only padding
-                const unsigned long long *kword = keys + (size_t)w * R;
-                rs_hist_kernel<<<ntiles, RT, 0, st>>>(kword, ia, R, d * 8, ctx->hist.as<uint32_t>(), ntiles);
-                scan_single_kernel<<<1, 1024, 0, st>>>(ctx->hist.as<uint32_t>(), 256ull * ntiles);
-                rs_scatter_kernel<<<ntiles, RT, 0, st>>>(kword, ia, ib, R, d * 8, ctx->hist.as<uint32_t>(),
-                                                         ntiles);
-                nk += 3;
+                rs_hist_kernel<<<ntiles, RT, 0, st>>>(kin, R, d * 8, hist, ntiles);
+                if (nchunks <= 1) {
+                    scan_single_kernel<<<1, 1024, 0, st>>>(hist, nhist);
+                    nk += 1;
+                } else {
+                    uint32_t *part = ctx->scan_part.as<uint32_t>();
+                    scan_reduce_kernel<<<nchunks, SC_T, 0, st>>>(hist, nhist, part);
+                    scan_single_kernel<<<1, 1024, 0, st>>>(part, (unsigned long long)nchunks);
+                    scan_apply_kernel<<<nchunks, SC_T, 0, st>>>(hist, nhist, part);
+                    nk += 3;
+                }
+                unsigned long long *kout = (kin == ka) ? kb : ka;
+                rs_scatter_kernel<<<ntiles, RT, 0, st>>>(kin, ia, kout, ib, R, d * 8, hist, ntiles);
+                nk += 2;
                 uint32_t *t = ia; ia = ib; ib = t;
+                kin = kout;
             }
         }
         unsigned long long *bsum = ctx->scan_tmp.as<unsigned long long>();
@@ -292,6 +392,8 @@ int launch_compact(fim_ctx *ctx, uint64_t R, int n_db, int m_max) {
     mix((uint64_t)(uintptr_t)ctx->rec_items.p); mix((uint64_t)(uintptr_t)ctx->out_off.p);
     mix((uint64_t)(uintptr_t)ctx->out_items.p); mix((uint64_t)(uintptr_t)ctx->perm.p);
     mix((uint64_t)(uintptr_t)ctx->dbdesc.p); mix((uint64_t)(uintptr_t)ctx->rec_db.p);
+    mix((uint64_t)(uintptr_t)ctx->kv_a.p); mix((uint64_t)(uintptr_t)ctx->kv_b.p);
+    mix((uint64_t)(uintptr_t)ctx->scan_part.p);
     if (ctx->compact_graph_exec && ctx->compact_key == key) {
         FIM_CUDA_TRY(cudaGraphLaunch((cudaGraphExec_t)ctx->compact_graph_exec, st));
         ctx->launches += ctx->compact_graph_launches;

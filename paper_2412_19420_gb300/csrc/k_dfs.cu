@@ -71,6 +71,7 @@ struct Smem {
     unsigned long long ticket;
     unsigned long long rbase, ibase;
     int flag;
+    int hungry;
     int stop;
     int task_len;
     uint32_t task_sup;
@@ -619,9 +620,11 @@ dfs_kernel(const DfsParams p) {
                 if (kc == 0) continue;
                 if (maxlen && (uint32_t)plen + 2 > maxlen) continue;
                 if (plen + 1 <= p.split_depth && plen + 1 <= FIM_TASK_MAXR) {
-                    if (threadIdx.x == 0) s.flag = queue_hungry(p);
+                    // s.hungry, not s.flag: thread 0 rewrites s.flag inside
+                    // try_push while other warps may still be reading this
+                    if (threadIdx.x == 0) s.hungry = queue_hungry(p);
                     __syncthreads();
-                    if (s.flag && try_push<NT>(p, s, plen, citem, csup, fi + bC, kc)) continue;
+                    if (s.hungry && try_push<NT>(p, s, plen, citem, csup, fi + bC, kc)) continue;
                 }
                 if (L + 1 >= p.depth_cap || plen + 1 >= MAXPATH) {
                     if (threadIdx.x == 0) set_err(p, FIM_E_STACK);

@@ -6,44 +6,57 @@
 // the entries are fed as e4m3 values 0.0 / 2.0 to tcgen05.mma kind::f8f6f4
 // with an f32 accumulator in tensor memory.)
 //
-// Exactness: every product is 0 or 4 and every partial sum is a multiple of
-// 4.  The accumulator is drained into int32 registers every `kdrain` x 128
-// transactions (8,192 by default) and restarted, so no f32 partial sum ever
-// exceeds 4 x 131,072 = 2^19 even at the largest kdrain; the int32 totals
-// (partial / 4) are exact for any n < 2^31.
+// Exactness: every product is 0 or 4, so a partial sum over t transactions is
+// 4 x an integer <= 4t.  One accumulator sums at most `kdrain` x 128
+// transactions (at most 32,768 x 128 = 2^22) before it is drained, so every
+// partial is an integer <= 2^24, exact in f32; the drained counts (partial / 4)
+// meet in int32 by atomicAdd and are exact for any n < 2^31.
 //
-// CTA (544 threads) = one 128 x 128 tile (items a in tile ta, b in tile tb,
-// ta <= tb) x one slice of the transactions:
-//   warps 0-7   producers, one operand row each (A rows, then B rows; a
-//               diagonal tile has A = B): read the row's 128 bits per stage
-//               from its item bit column, expand each bit to an e4m3 byte
-//               (0x40 = 2.0) and store the 128 x 128-byte operand tiles in the
-//               SWIZZLE_128B K-major layout the MMA descriptors name;
-//   warp 16     one elected thread issues 4 MMAs (K = 32 each) per stage and
-//               commits stage release / accumulator-ready to mbarriers;
-//   warps 8-15  epilogue: tcgen05.ld the f32 accumulator (two TMEM buffers,
-//               so draining one overlaps the MMAs into the other), convert to
-//               int32 and keep running totals; finally atomicAdd into pair_cnt.
+// Work: C is cut into 128 x 256 tiles (items a in A-block ta, b in B-block tb)
+// that hold at least one pair a < b; each tile's reduction runs over
+// ceil(nw / 4) stages of 128 transactions.  The (tile, stage) space is split
+// into one contiguous range per CTA (one CTA per SM by default), so every SM
+// gets the same number of MMA stages whatever the tile count; a range is
+// processed as segments that never cross a tile or a multiple of kdrain stages.
+//
+// CTA (672 threads):
+//   warps 0-11  producers, one operand row each (128 A rows, then 256 B
+//               rows): load the row's bits several stages ahead in registers,
+//               expand each bit to an e4m3 byte (0x40 = 2.0) and store the
+//               operand tiles in the SWIZZLE_128B K-major layout the MMA
+//               descriptors name.  When the A-block lies inside the B-block,
+//               A is read from B's tile and its producers only arrive;
+//   warps 12-19 epilogue: per segment, tcgen05.ld the f32 accumulator (two
+//               TMEM buffers, so draining one overlaps the MMAs into the
+//               other), convert to counts, transpose 32 x 16 blocks through
+//               shared memory and add them into pair_cnt[a][b] with coalesced
+//               atomics;
+//   warp 20     one elected thread issues 4 MMAs (128 x 256 x 32) per stage
+//               and commits stage release / accumulator-ready to mbarriers.
 // Every mbarrier wait is bounded; on expiry the CTA records an error, lets
 // its MMAs finish, frees its tensor memory and returns.
 #include "fim_common.cuh"
 
 namespace {
 
-constexpr int TM = 128;              // tile rows (items a)
-constexpr int TN = 128;              // tile cols (items b)
-constexpr int KB = 128;              // K elements (transactions) per stage = 128 bytes per row
+constexpr int TM = 128;               // A rows (items a) per tile
+constexpr int TN = 256;               // B rows (items b) per tile
+constexpr int KB = 128;               // K elements (transactions) per stage = 128 bytes per row
 constexpr int STAGES = 4;
-constexpr int NPROD = 256;           // producer threads (one operand row each: A then B)
-constexpr int NEPI = 256;            // epilogue threads
+constexpr int NPROD = TM + TN;        // producer threads, one operand row each
+constexpr int NEPI = 256;             // epilogue threads
 constexpr int THREADS = NPROD + NEPI + 32;
-constexpr int TILE_BYTES = TM * KB;  // 16 KB per operand per stage
-constexpr uint32_t TMEM_COLS = 256;  // two 128-column f32 accumulators
+constexpr int A_BYTES = TM * KB;      // 16 KB per stage
+constexpr int B_BYTES = TN * KB;      // 32 KB per stage
+constexpr int PF = 4;                 // stages a producer loads ahead
+constexpr uint32_t TMEM_COLS = 2 * TN;  // two 256-column f32 accumulators
+constexpr int KDRAIN_MAX = 32768;     // 2^22 transactions: partials stay <= 2^24
 constexpr unsigned long long WAIT_NS = 2000000000ull;  // 2 s: far above any legitimate wait
 
 struct __align__(1024) TcSmem {
-    uint8_t a[STAGES][TILE_BYTES];
-    uint8_t b[STAGES][TILE_BYTES];
+    uint8_t a[STAGES][A_BYTES];
+    uint8_t b[STAGES][B_BYTES];
+    int xp[NEPI / 32][16][34];        // per epilogue warp: 16 columns x 32 rows (+2 pad)
     uint64_t full[STAGES];
     uint64_t empty[STAGES];
     uint64_t acc_full[2];
@@ -138,8 +151,8 @@ __device__ __forceinline__ uint4 bits16_to_e4m3(uint32_t h) {
                       nib_to_e4m3((h >> 12) & 15u));
 }
 
-// Row r of a 128 x 128-byte SWIZZLE_128B tile: 16-byte chunk c lives at
-// (r / 8) * 1024 + (r % 8) * 128 + ((c ^ (r % 8)) * 16).
+// Row r of a SWIZZLE_128B K-major tile (128 bytes per row): 16-byte chunk c
+// lives at (r / 8) * 1024 + (r % 8) * 128 + ((c ^ (r % 8)) * 16).
 __device__ __forceinline__ void store_row(uint8_t *tile, int r, uint4 w) {
     const uint32_t words[4] = {w.x, w.y, w.z, w.w};
     uint8_t *row = tile + (r >> 3) * 1024 + (r & 7) * 128;
@@ -150,22 +163,48 @@ __device__ __forceinline__ void store_row(uint8_t *tile, int r, uint4 w) {
     }
 }
 
+// Tiles (ta, tb) with at least one pair a < b < mf, ta-major.  The first
+// B-block that reaches past a = 128 ta is tb = ta / 2; the last A-block may
+// hold only the last item, which pairs with nothing.
+__host__ __device__ __forceinline__ int tiles_of_row(int ta, int mf, int ntb) {
+    const int lo = ta >> 1;
+    if (lo >= ntb) return 0;
+    if (lo == ntb - 1 && !(mf - 1 > ta * TM)) return 0;
+    return ntb - lo;
+}
+__device__ __forceinline__ void tile_coords(int t, int mf, int ntb, int &ta, int &tb) {
+    for (ta = 0;; ta++) {
+        const int c = tiles_of_row(ta, mf, ntb);
+        if (t < c) { tb = (ta >> 1) + t; return; }
+        t -= c;
+    }
+}
+
+// Segment of a CTA's (tile, stage) range starting at flat index w: the run
+// stays in one tile and ends at a multiple of kdrain stages.
+struct Seg {
+    int tile;
+    int64_t st;   // first stage
+    int len;      // stages
+};
+__device__ __forceinline__ Seg next_seg(int64_t w, int64_t w1, int64_t S, int kd) {
+    Seg g;
+    g.tile = (int)(w / S);
+    g.st = w - (int64_t)g.tile * S;
+    int64_t end = min64(w1 - (int64_t)g.tile * S, S);
+    end = min64(end, (g.st / kd + 1) * kd);
+    g.len = (int)(end - g.st);
+    return g;
+}
+
 __global__ void __launch_bounds__(THREADS, 1)
 pairs_tc_kernel(const uint32_t *__restrict__ bm, const int32_t *__restrict__ perm, int64_t nwp, int mf,
-                int nt, int64_t stages_total, int64_t stages_per_split, int kdrain,
-                int *__restrict__ pair_cnt, int *__restrict__ err) {
+                int ntb, int64_t S, int64_t W, int kd, int *__restrict__ pair_cnt, int *__restrict__ err) {
     extern __shared__ uint8_t smem_raw[];
     TcSmem &s = *reinterpret_cast<TcSmem *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-
-    int idx = blockIdx.x, ta = 0;
-    while (idx >= nt - ta) { idx -= nt - ta; ta++; }
-    const int tb = ta + idx;
-    const bool diag = ta == tb;
-    const int64_t st0 = (int64_t)blockIdx.y * stages_per_split;
-    const int64_t st1 = min64(stages_total, st0 + stages_per_split);
-    const int nst = (int)(st1 > st0 ? st1 - st0 : 0);
-    const int nchunks = (nst + kdrain - 1) / kdrain;
+    const int64_t w0 = (int64_t)blockIdx.x * W / gridDim.x;
+    const int64_t w1 = (int64_t)(blockIdx.x + 1) * W / gridDim.x;
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < STAGES; i++) { mbar_init(&s.full[i], NPROD); mbar_init(&s.empty[i], 1); }
@@ -188,35 +227,65 @@ pairs_tc_kernel(const uint32_t *__restrict__ bm, const int32_t *__restrict__ per
 
     if (warp < NPROD / 32) {
         // ---------------- producers: one operand row each ----------------
-        const int r = threadIdx.x & (TM - 1);
-        const bool is_b = threadIdx.x >= TM;   // threads 128..255 fill B (none on diagonal tiles)
-        const int item = (is_b ? tb * TN : ta * TM) + r;
-        const uint32_t *col = (item < mf && !(is_b && diag)) ? bm + (int64_t)perm[item] * nwp : nullptr;
-        for (int it = 0; it < nst; it++) {
-            const int slot = it % STAGES;
-            const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
-            const int64_t w = (st0 + it) * 4;  // 4 words = 128 transactions
-            const uint4 v = col ? ldg_u4(col + w) : make_uint4(0, 0, 0, 0);
-            if (!mbar_wait(s, &s.empty[slot], ph ^ 1u)) break;
-            if (!(is_b && diag)) store_row(is_b ? s.b[slot] : s.a[slot], r, v);
-            fence_proxy_async();
-            mbar_arrive(&s.full[slot]);
+        const bool is_a = threadIdx.x < TM;
+        const int r = is_a ? threadIdx.x : threadIdx.x - TM;
+        int it = 0;  // stages produced by this CTA (ring position)
+        bool ok = true;
+        for (int64_t w = w0; w < w1 && ok;) {
+            const Seg g = next_seg(w, w1, S, kd);
+            w += g.len;
+            int ta, tb;
+            tile_coords(g.tile, mf, ntb, ta, tb);
+            const bool a_in_b = tb == (ta >> 1);  // A rows are rows 128*(ta&1).. of B's tile
+            const bool store = !(is_a && a_in_b);
+            const int item = is_a ? ta * TM + r : tb * TN + r;
+            const uint32_t *col = (store && item < mf) ? bm + (int64_t)perm[item] * nwp : nullptr;
+            uint4 cur[PF], nxt[PF];
+#pragma unroll
+            for (int u = 0; u < PF; u++)
+                cur[u] = (col && u < g.len) ? ldg_u4(col + (g.st + u) * 4) : make_uint4(0, 0, 0, 0);
+            for (int k0 = 0; k0 < g.len && ok; k0 += PF) {
+#pragma unroll
+                for (int u = 0; u < PF; u++)
+                    nxt[u] = (col && k0 + PF + u < g.len) ? ldg_u4(col + (g.st + k0 + PF + u) * 4)
+                                                          : make_uint4(0, 0, 0, 0);
+#pragma unroll
+                for (int u = 0; u < PF; u++) {
+                    if (k0 + u < g.len && ok) {
+                        const int slot = it % STAGES;
+                        const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+                        if (!(ok = mbar_wait(s, &s.empty[slot], ph ^ 1u))) break;
+                        if (store) store_row(is_a ? s.a[slot] : s.b[slot], r, cur[u]);
+                        fence_proxy_async();
+                        mbar_arrive(&s.full[slot]);
+                        it++;
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < PF; u++) cur[u] = nxt[u];
+            }
         }
     } else if (warp < (NPROD + NEPI) / 32) {
         // ---------------- epilogue ----------------
+        const int e = warp - NPROD / 32;
         const int q = warp & 3;          // TMEM lane quarter this warp may read
-        const int half = (warp - NPROD / 32) >> 2;  // columns [64*half, 64*half + 64)
-        int acc[64];
-#pragma unroll
-        for (int c = 0; c < 64; c++) acc[c] = 0;
-        for (int j = 0; j < nchunks; j++) {
+        const int half = e >> 2;         // accumulator columns [128*half, 128*half + 128)
+        int (*xp)[34] = s.xp[e];
+        int j = 0;
+        for (int64_t w = w0; w < w1; j++) {
+            const Seg g = next_seg(w, w1, S, kd);
+            w += g.len;
+            int ta, tb;
+            tile_coords(g.tile, mf, ntb, ta, tb);
             const int buf = j & 1;
-            if (!mbar_wait(s, &s.acc_full[buf], (uint32_t)(j >> 1) & 1u)) break;
+            // warp-uniform: tcgen05.ld below is a .sync.aligned warp instruction
+            if (!__all_sync(0xffffffffu, mbar_wait(s, &s.acc_full[buf], (uint32_t)(j >> 1) & 1u))) break;
             tc_fence_after();
-#pragma unroll
-            for (int x = 0; x < 4; x++) {
+#pragma unroll 1
+            for (int x = 0; x < 8; x++) {
                 uint32_t v[16];
-                const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * TN + half * 64 + x * 16);
+                const uint32_t taddr =
+                    tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * TN + half * 128 + x * 16);
                 asm volatile(
                     "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
                     : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
@@ -225,43 +294,52 @@ pairs_tc_kernel(const uint32_t *__restrict__ bm, const int32_t *__restrict__ per
                     : "r"(taddr)
                     : "memory");
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                // lane = row a; transpose so that a warp store covers 2 rows x 16 columns
 #pragma unroll
-                for (int c = 0; c < 16; c++) acc[x * 16 + c] += __float2int_rn(__uint_as_float(v[c])) >> 2;
+                for (int c = 0; c < 16; c++) xp[c][lane] = __float2int_rn(__uint_as_float(v[c])) >> 2;
+                __syncwarp();
+                const int c = lane & 15;
+                const int b = tb * TN + half * 128 + x * 16 + c;
+#pragma unroll 4
+                for (int i = 0; i < 16; i++) {
+                    const int rr = 2 * i + (lane >> 4);
+                    const int a = ta * TM + q * 32 + rr;
+                    const int val = xp[c][rr];
+                    if (a < b && b < mf && val) atomicAdd(&pair_cnt[(int64_t)a * mf + b], val);
+                }
+                __syncwarp();
             }
             tc_fence_before();
             mbar_arrive(&s.acc_empty[buf]);
-        }
-        const int a = ta * TM + q * 32 + lane;
-#pragma unroll
-        for (int c = 0; c < 64; c++) {
-            const int b = tb * TN + half * 64 + c;
-            if (a < b && b < mf && acc[c]) atomicAdd(&pair_cnt[(int64_t)a * mf + b], acc[c]);
         }
     } else if (lane == 0) {
         // ---------------- MMA issuer ----------------
         constexpr uint32_t IDESC = idesc_f8(TM, TN);
         bool ok = true;
-        for (int it = 0; it < nst && ok; it++) {
-            const int slot = it % STAGES;
-            const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
-            const int j = it / kdrain;
+        int it = 0, j = 0;
+        for (int64_t w = w0; w < w1 && ok; j++) {
+            const Seg g = next_seg(w, w1, S, kd);
+            w += g.len;
+            int ta, tb;
+            tile_coords(g.tile, mf, ntb, ta, tb);
+            const bool a_in_b = tb == (ta >> 1);
             const int buf = j & 1;
-            const bool first = (it % kdrain) == 0;
-            const bool last = (it % kdrain) == kdrain - 1 || it == nst - 1;
-            if (first) {
-                if (!(ok = mbar_wait(s, &s.acc_empty[buf], ((uint32_t)(j >> 1) & 1u) ^ 1u))) break;
-                tc_fence_after();
-            }
-            if (!(ok = mbar_wait(s, &s.full[slot], ph))) break;
+            if (!(ok = mbar_wait(s, &s.acc_empty[buf], ((uint32_t)(j >> 1) & 1u) ^ 1u))) break;
             tc_fence_after();
-            const uint32_t a0 = smem_addr(s.a[slot]);
-            const uint32_t b0 = diag ? a0 : smem_addr(s.b[slot]);
+            for (int k = 0; k < g.len; k++, it++) {
+                const int slot = it % STAGES;
+                const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
+                if (!(ok = mbar_wait(s, &s.full[slot], ph))) break;
+                tc_fence_after();
+                const uint32_t b0 = smem_addr(s.b[slot]);
+                const uint32_t a0 = a_in_b ? b0 + (uint32_t)((ta & 1) * A_BYTES) : smem_addr(s.a[slot]);
 #pragma unroll
-            for (int kk = 0; kk < KB / 32; kk++)
-                mma_f8(tmem + (uint32_t)(buf * TN), sdesc(a0 + kk * 32), sdesc(b0 + kk * 32), IDESC,
-                       (first && kk == 0) ? 0u : 1u);
-            mma_commit(&s.empty[slot]);
-            if (last) mma_commit(&s.acc_full[buf]);
+                for (int kk = 0; kk < KB / 32; kk++)
+                    mma_f8(tmem + (uint32_t)(buf * TN), sdesc(a0 + kk * 32), sdesc(b0 + kk * 32), IDESC,
+                           (k == 0 && kk == 0) ? 0u : 1u);
+                mma_commit(&s.empty[slot]);
+            }
+            if (ok) mma_commit(&s.acc_full[buf]);
         }
         // make sure no MMA is in flight before the tensor memory is freed
         mma_commit(&s.done);
@@ -284,25 +362,23 @@ pairs_tc_kernel(const uint32_t *__restrict__ bm, const int32_t *__restrict__ per
 int launch_pairs_tc(fim_ctx *ctx) {
     const int mf = ctx->mfreq;
     if (mf < 2) return FIM_OK;
-    const int nt = (int)ceil_div64(mf, TM);
-    const int tiles = nt * (nt + 1) / 2;
-    const int64_t stages = ceil_div64(ctx->nw, 4);  // 128 transactions per stage
-    int64_t split = ctx->pairs_split > 0 ? ctx->pairs_split : ceil_div64(2LL * ctx->num_sms, tiles);
-    if (split > stages) split = stages;
-    if (split < 1) split = 1;
-    const int64_t sps = ceil_div64(stages, split);
-    split = ceil_div64(stages, sps);
-    const int kdrain = ctx->pairs_kdrain > 0 ? ctx->pairs_kdrain : 64;  // 64 stages = 8192 transactions
+    const int nta = (int)ceil_div64(mf, TM), ntb = (int)ceil_div64(mf, TN);
+    int64_t tiles = 0;
+    for (int ta = 0; ta < nta; ta++) tiles += tiles_of_row(ta, mf, ntb);
+    const int64_t S = ceil_div64(ctx->nw, 4);  // 128 transactions per stage
+    const int64_t W = tiles * S;
+    const int kd = ctx->pairs_kdrain > 0 ? ctx->pairs_kdrain : KDRAIN_MAX;
+    int64_t grid = ctx->pairs_split > 0 ? ctx->pairs_split : ctx->num_sms;
+    if (grid > W) grid = W;
     const size_t smem = sizeof(TcSmem) + 1024;
     FIM_CUDA_TRY(cudaFuncSetAttribute(pairs_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     FIM_CUDA_TRY(cudaMemsetAsync(ctx->pair_cnt.p, 0, sizeof(int) * (size_t)mf * mf, ctx->stream));
     int *err = &ctx->counters.as<MineCounters>()->err;  // zeroed at the start of every mine
-    if (stages > 0) {
-        dim3 grid((unsigned)tiles, (unsigned)split);
+    if (grid > 0) {
         ctx->launches++;
-        pairs_tc_kernel<<<grid, THREADS, smem, ctx->stream>>>(ctx->bm.as<uint32_t>(), ctx->perm.as<int32_t>(),
-                                                               ctx->nwp, mf, nt, stages, sps, kdrain,
-                                                               ctx->pair_cnt.as<int>(), err);
+        pairs_tc_kernel<<<(unsigned)grid, THREADS, smem, ctx->stream>>>(
+            ctx->bm.as<uint32_t>(), ctx->perm.as<int32_t>(), ctx->nwp, mf, ntb, S, W, kd,
+            ctx->pair_cnt.as<int>(), err);
         FIM_CUDA_TRY(cudaGetLastError());
     }
     return FIM_OK;

@@ -1,5 +1,6 @@
 """The tensor-core pair pass (tcgen05 kind::f8f6f4, f32 accumulator drained to
-int32) against the oracle and the CUDA-core pair pass: bit-exact pair supports."""
+int32) against the oracle and the CUDA-core pair pass: bit-exact pair supports
+for every tile shape at the edges, every drain length and every grid size."""
 import numpy as np
 import pytest
 
@@ -41,7 +42,7 @@ def test_tc_pairs_vs_oracle(ctx, n, m, seed):
     assert got.sha256() == want.sha256()
 
 
-@pytest.mark.parametrize("kdrain", [1, 64, 1024])
+@pytest.mark.parametrize("kdrain", [1, 7, 1024, 32768])
 def test_tc_exact_on_all_ones(ctx, kdrain):
     # every pair support equals n: the largest partial sums the accumulator sees
     n, m = 262_145, 130
@@ -59,7 +60,28 @@ def test_tc_exact_on_all_ones(ctx, kdrain):
     assert np.all(got.supports == n)
 
 
-@pytest.mark.parametrize("split", [1, 3, 17])
+def test_tc_exact_at_the_f32_limit(ctx):
+    # one CTA, one accumulator over 32,768 stages = 2^22 transactions of all
+    # ones: the partial sum is 4 x 2^22 = 2^24, the largest integer an f32 run
+    # holds exactly; one more transaction lands in a second segment
+    n, m = (1 << 22) + 1, 3
+    indptr = np.arange(0, (n + 1) * m, m, dtype=np.int64)
+    indices = np.tile(np.arange(m, dtype=np.int32), n)
+    fim.fim_set_tuning(ctx, "pairs_split", 1)
+    fim.fim_set_tuning(ctx, "pairs_kdrain", 32768)
+    try:
+        fim.fim_build_bitmaps(ctx, indptr, indices, m)
+        fim.fim_mine(ctx, n, fim.FIM_MAXLEN(2))
+        got = fim.fim_fetch_results(ctx)
+        assert fim.fim_get_stats(ctx)["pair_path"] == 1
+    finally:
+        fim.fim_set_tuning(ctx, "pairs_split", 0)
+        fim.fim_set_tuning(ctx, "pairs_kdrain", 0)
+    assert len(got) == m + m * (m - 1) // 2
+    assert np.all(got.supports == n)
+
+
+@pytest.mark.parametrize("split", [1, 3, 17, 1000])
 def test_tc_split_k_invariant(ctx, split):
     c = datagen.zipf_baskets(200_000, 260, 0.8, 7.0, 9)
     fim.fim_set_tuning(ctx, "pairs_split", split)
@@ -74,6 +96,6 @@ def test_tc_split_k_invariant(ctx, split):
 
 def test_tuning_keys_validated(ctx):
     with pytest.raises(fim.FimError):
-        fim.fim_set_tuning(ctx, "pairs_kdrain", 5000)
+        fim.fim_set_tuning(ctx, "pairs_kdrain", 40000)
     with pytest.raises(fim.FimError):
         fim.fim_set_tuning(ctx, "no_such_knob", 1)

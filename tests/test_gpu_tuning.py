@@ -54,8 +54,11 @@ def test_invalid_shapes_rejected(ctx):
                    ("dfs_ctas_per_sm", 5), ("split_depth", 9)]:
         with pytest.raises(fim.FimError):
             fim.fim_set_tuning(ctx, key, v)
-    fim.fim_set_tuning(ctx, "dfs_threads", 512)
     with pytest.raises(fim.FimError):  # 512 x 4 > 1024 worker threads per SM
+        fim.fim_set_tuning(ctx, "dfs_threads", 512)
+    fim.fim_set_tuning(ctx, "dfs_ctas_per_sm", 1)
+    fim.fim_set_tuning(ctx, "dfs_threads", 512)
+    with pytest.raises(fim.FimError):
         fim.fim_set_tuning(ctx, "dfs_ctas_per_sm", 4)
     autotune.apply(ctx, autotune.DEFAULT)
     with pytest.raises(ValueError):

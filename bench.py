@@ -138,13 +138,14 @@ def _load_workload(name):
     return fn(), minsup
 
 
-def cpu_baseline(csr, minsup, budget_s=20.0):
-    """The oracle (plain Apriori, all host cores) on a bounded sample of the
-    workload: the first n' transactions, with minsup scaled by n'/n."""
+def cpu_baseline(csr, minsup, budget_s=20.0, threads=None):
+    """The oracle (plain Apriori, all host cores unless `threads` is given) on
+    a bounded sample of the workload: the first n' transactions, with minsup
+    scaled by n'/n."""
     import numpy as np
     import oracle
     from paper_2412_19420_gb300 import datagen
-    cores = _cores()
+    cores = threads or _cores()
     n = csr.n
     frac = 1.0
     while True:
@@ -472,6 +473,8 @@ def main():
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(csr, minsup)
+        one = cpu_baseline(csr, minsup, budget_s=8.0, threads=1)
+        line["cpu_baseline"]["single_thread"] = {k: one[k] for k in ("value", "sample", "seconds")}
     if rank == 0:
         print(json.dumps(line))
     _ = (np, got)

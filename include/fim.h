@@ -90,6 +90,8 @@ typedef struct {
     uint64_t dfs_busy_ns;         /* DFS workers' time inside tasks, summed         */
     uint64_t dfs_span_ns;         /* first worker start to last worker exit         */
     uint64_t dfs_workers;         /* DFS workers (CTAs) of the launch               */
+    uint64_t dfs_root_ns;         /* part of dfs_busy_ns spent in the root classes'
+                                     own passes (candidate list + level-0 pass)     */
     float ms_build, ms_singletons, ms_pairs, ms_dfs, ms_compact; /* CUDA-event times */
     uint32_t pair_path;           /* 1 = tcgen05 tensor cores, 0 = CUDA-core popc   */
     uint32_t reserved;

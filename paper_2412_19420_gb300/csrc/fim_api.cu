@@ -439,6 +439,7 @@ int fim_mine(fim_ctx *ctx, uint64_t minsup, uint32_t flags) {
     s.dfs_busy_ns = c.busy_ns;
     s.dfs_span_ns = c.t_last > c.t_first && c.t_first != 0 ? c.t_last - c.t_first : 0;
     s.dfs_workers = (uint64_t)ctx->num_sms * (uint64_t)ctx->dfs_ctas_per_sm;
+    s.dfs_root_ns = c.root_ns;
     if (ctx->bytes_held > s.peak_device_bytes) s.peak_device_bytes = ctx->bytes_held;
     ctx->mined = true;
     return FIM_OK;

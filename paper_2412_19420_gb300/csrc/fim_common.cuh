@@ -76,6 +76,7 @@ struct MineCounters {
     unsigned long long busy_ns;      // DFS workers' time inside tasks, summed
     unsigned long long t_first;      // DFS kernel span (%globaltimer): first start ...
     unsigned long long t_last;       // ... and last worker exit
+    unsigned long long root_ns;      // workers' time in root classes' own passes, summed
     long long pending;               // tasks pushed but not finished
     int err;                         // FIM_OK or a FIM_E_* from the device
     int overflow;                    // bit 0 records, bit 1 items, bit 2 traces

@@ -476,7 +476,7 @@ dfs_kernel(const DfsParams p) {
     if (p.learned)
         for (int i = threadIdx.x; i < FIM_MLP_PARAMS; i += NT) s.mlp_w[i] = __bfloat162float(p.mlp_w[i]);
     const bool want_feat = p.learned || p.trace;
-    unsigned long long busy = 0, t_task = 0;
+    unsigned long long busy = 0, t_task = 0, root_busy = 0;
     if (threadIdx.x == 0) atomicCAS(&p.ctr->t_first, 0ull, globaltimer_ns());
 
     while (true) {
@@ -576,6 +576,7 @@ dfs_kernel(const DfsParams p) {
             // overwrites both in order
             int nF = class_pass<NT>(p, s, fi, fs, k, tlen, fi, fs);
             if (threadIdx.x == 0) {
+                if (root) root_busy += globaltimer_ns() - t_task;
                 s.nF[0] = nF;
                 s.cur[0] = 0;
                 s.base[1] = nF;
@@ -665,6 +666,7 @@ dfs_kernel(const DfsParams p) {
     }
     if (threadIdx.x == 0) {
         atomicAdd(&p.ctr->busy_ns, busy);
+        atomicAdd(&p.ctr->root_ns, root_busy);
         atomicMax(&p.ctr->t_last, globaltimer_ns());
     }
 }

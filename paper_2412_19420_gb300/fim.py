@@ -46,7 +46,7 @@ class fim_stats(ctypes.Structure):
         "n_trans", "n_items", "n_frequent_items", "n_sets", "max_len",
         "supports_singletons", "supports_pairs", "supports_dfs", "dfs_words", "dfs_bytes", "dfs_touched_bytes",
         "classes", "tasks_pushed", "diffset_classes", "peak_device_bytes",
-        "launches_build", "launches_mine", "dfs_busy_ns", "dfs_span_ns", "dfs_workers")] + \
+        "launches_build", "launches_mine", "dfs_busy_ns", "dfs_span_ns", "dfs_workers", "dfs_root_ns")] + \
         [(n, ctypes.c_float) for n in ("ms_build", "ms_singletons", "ms_pairs", "ms_dfs", "ms_compact")] + \
         [("pair_path", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 

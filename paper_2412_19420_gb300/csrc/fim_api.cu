@@ -130,6 +130,8 @@ int fim_create(fim_ctx **out, int device, void *cuda_stream) {
     for (auto &e : ctx->ev) cudaEventCreate(&e);
     int rc = fim_reserve(ctx, ctx->counters, sizeof(MineCounters));
     if (rc == FIM_OK) rc = fim_reserve(ctx, ctx->dev_flag, 4 * sizeof(int));
+    if (rc == FIM_OK) rc = fim_reserve(ctx, ctx->epoch, sizeof(uint32_t));
+    if (rc == FIM_OK && cudaMemsetAsync(ctx->epoch.p, 0, sizeof(uint32_t), ctx->stream) != cudaSuccess) rc = FIM_E_CUDA;
     if (rc != FIM_OK) {
         fim_destroy(ctx);
         return rc;
@@ -150,7 +152,7 @@ void fim_destroy(fim_ctx *ctx) {
                      &ctx->scan_part, &ctx->out_off,
                      &ctx->out_items, &ctx->out_sup, &ctx->mlp_w32, &ctx->mlp_wbf, &ctx->trace_x,
                      &ctx->trace_y, &ctx->mlp_scratch, &ctx->root_order, &ctx->root_bucket,
-                     &ctx->root_hist, &ctx->rec_db, &ctx->dbdesc};
+                     &ctx->root_hist, &ctx->rec_db, &ctx->dbdesc, &ctx->epoch};
     for (DevBuf *b : all) fim_release(ctx, *b);
     fim_release(ctx, ctx->batch_prefix);
     fim_release(ctx, ctx->batch_slices);
@@ -294,9 +296,9 @@ int mine_once(fim_ctx *ctx, uint32_t thr, uint32_t flags, MineState &ms, bool *r
         FIM_TRY(fim_reserve(ctx, ctx->stack_bits, per_level * (size_t)ms.depth_cap));
         FIM_TRY(fim_reserve(ctx, ctx->frame_items, sizeof(uint32_t) * (size_t)workers * ms.frame_pool));
         FIM_TRY(fim_reserve(ctx, ctx->frame_sups, sizeof(uint32_t) * (size_t)workers * ms.frame_pool));
-        FIM_TRY(fim_reserve(ctx, ctx->tasks, sizeof(Task) * kTaskCap));
+        FIM_TRY(prepare_task_queue(ctx, sizeof(Task) * kTaskCap));
         FIM_TRY(fim_reserve(ctx, ctx->cand_pool, sizeof(uint32_t) * kCandPoolCap));
-        FIM_CUDA_TRY(cudaMemsetAsync(ctx->tasks.p, 0, sizeof(Task) * kTaskCap, st));
+        FIM_TRY(launch_epoch_bump(ctx));
         const size_t npairs = (size_t)mf * (mf - 1) / 2;
         DfsParams p{};
         p.dbs = ctx->dbdesc.as<DbDesc>();
@@ -327,6 +329,8 @@ int mine_once(fim_ctx *ctx, uint32_t thr, uint32_t flags, MineState &ms, bool *r
         p.rec_items_cap = ctx->rec_items_cap;
         p.ctr = d_ctr;
         p.spin_limit = kSpinLimitNs;
+        p.sparse_div = ctx->sparse_div;
+        p.epoch = ctx->epoch.as<uint32_t>();
         p.pair_cnt = ctx->pair_cnt.as<int>();
         p.item_sup = ctx->item_sup.as<uint32_t>();
         p.root_order = nullptr;
@@ -480,6 +484,7 @@ int fim_set_tuning(fim_ctx *ctx, const char *key, int64_t v) {
         {"dfs_ctas_per_sm", &ctx->dfs_ctas_per_sm, 1, 4},
         {"dfs_threads", &ctx->dfs_block, 256, 512},
         {"split_depth", &ctx->split_depth, 0, FIM_TASK_MAXR},
+        {"sparse_div", &ctx->sparse_div, 0, 64},
         {"pairs_split", &ctx->pairs_split, 0, 4096},
         {"pairs_kdrain", &ctx->pairs_kdrain, 0, 32768},
     };

@@ -93,7 +93,7 @@ struct Task {
     uint32_t len;
     uint32_t support;
     uint32_t n_cand;
-    uint32_t ready;            // 0 until published
+    uint32_t ready;            // epoch of the mine that published the slot
     unsigned long long cand_off;  // into the candidate pool
     float prio;                // predicted work (learned mode) or 0
     uint32_t db;               // database of the class
@@ -151,6 +151,7 @@ struct DfsParams {
     unsigned long long rec_cap, rec_items_cap;
     // learned / traces
     const __nv_bfloat16 *mlp_w;  // bf16 weights or null
+    const uint32_t *epoch;       // this mine's epoch (bumped on the stream before the DFS)
     int learned;
     int diffset_rule;
     float *trace_x;          // [cap][8]
@@ -159,6 +160,7 @@ struct DfsParams {
     int trace;
     MineCounters *ctr;
     unsigned long long spin_limit;  // bounded waits (iterations)
+    int sparse_div;                 // store b_Y sparse when S(Y) * sparse_div <= nw (0: never)
 };
 
 // ---------------------------------------------------------------- the ctx
@@ -183,6 +185,7 @@ struct fim_ctx {
     int32_t mfreq = 0;
     DevBuf pair_cnt, pairbits, roots;
     DevBuf tasks, cand_pool, stack_bits, frame_items, frame_sups;
+    DevBuf epoch;               // uint32: mine counter; a task slot is live when ready == epoch
     DevBuf rec_off, rec_len, rec_sup, rec_items, rec_db;
     DevBuf counters;            // MineCounters
     DevBuf dbdesc;              // DbDesc table of the mine
@@ -219,6 +222,7 @@ struct fim_ctx {
     int dfs_block = 256;
     int dfs_ctas_per_sm = 4;
     int split_depth = 8;
+    int sparse_div = 8;
     int pairs_split = 0;        // split-K factor of the tensor-core pair pass (0 = auto)
     int pairs_kdrain = 0;       // stages (x128 transactions) per exact drain (0 = 64)
 
@@ -248,6 +252,11 @@ int launch_pairs_finalize(fim_ctx *ctx, uint32_t thr, MineCounters *d_ctr);
 
 // k_dfs.cu
 int launch_dfs(fim_ctx *ctx, const DfsParams &p, int grid, int block);
+// Task slots carry the epoch of the mine that published them, so the queue
+// needs no clearing between mines: bump the epoch (on the stream, so that a
+// replayed graph bumps it too) and clear the slots only when the buffer is new.
+int prepare_task_queue(fim_ctx *ctx, size_t bytes);
+int launch_epoch_bump(fim_ctx *ctx);
 
 // k_mlp.cu: learned root order (longest predicted subtree first)
 int launch_root_order(fim_ctx *ctx, MineCounters *d_ctr, size_t npairs);

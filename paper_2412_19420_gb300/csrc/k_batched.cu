@@ -422,7 +422,7 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
     FIM_TRY(fim_reserve(ctx, ctx->stack_bits, per_level * (size_t)depth_cap));
     FIM_TRY(fim_reserve(ctx, ctx->frame_items, sizeof(uint32_t) * (size_t)workers * frame_pool));
     FIM_TRY(fim_reserve(ctx, ctx->frame_sups, sizeof(uint32_t) * (size_t)workers * frame_pool));
-    FIM_TRY(fim_reserve(ctx, ctx->tasks, sizeof(Task) * kTaskCap));
+    FIM_TRY(prepare_task_queue(ctx, sizeof(Task) * kTaskCap));
     FIM_TRY(fim_reserve(ctx, ctx->cand_pool, sizeof(uint32_t) * kCandPoolCap));
     if (ctx->rec_cap < (1ull << 22)) {
         ctx->rec_cap = 1ull << 22;
@@ -490,6 +490,8 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
         p.mlp_w = ctx->mlp_wbf.as<__nv_bfloat16>();
         p.ctr = d_ctr;
         p.spin_limit = kSpinLimitNs;
+        p.sparse_div = ctx->sparse_div;
+        p.epoch = ctx->epoch.as<uint32_t>();
 
         // graph key: everything the captured launches depend on
         uint64_t key = 1469598103934665603ull;
@@ -515,7 +517,7 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
             FIM_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
             cudaMemsetAsync(d_ctr, 0, sizeof(MineCounters), st);
             cudaMemsetAsync(ctx->dev_flag.p, 0, sizeof(int), st);
-            cudaMemsetAsync(ctx->tasks.p, 0, sizeof(Task) * kTaskCap, st);
+            launch_epoch_bump(ctx);
             const int64_t units = L.unit_prefix[n_db], items = L.item_prefix[n_db], tiles = L.tile_prefix[n_db];
             if (units > 0)
                 batch_build_kernel<<<(unsigned)units, 256, smem_build, st>>>(d_dbs, n_db, d_unit, L.ib,

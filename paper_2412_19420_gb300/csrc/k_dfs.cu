@@ -64,10 +64,21 @@ struct Smem {
     float mlp_w[FIM_MLP_PARAMS];         // scheduling MLP (bf16 values held as float)
     float h1[64], h2[64], y[2];
     uint32_t scan[33];                   // block scan scratch (<= 32 warps)
-    unsigned int sec_dense, sec_diff;    // nonzero 32-byte sectors of b_Y and d_Y
+    unsigned int sec_dense, sec_diff;    // nonzero 32-byte sectors (sparse parent: words) of b_Y and d_Y
     int nsrc;
     int diff;                            // 1: count through the diffset
     uint32_t *store;
+    int store_sparse;                    // 1: store b_Y as its non-zero words (index, word)
+    unsigned int zcount;                 // entries written by a sparse store
+    int psparse;                         // 1: the parent b_X is stored sparse ...
+    int pz;                              // ... as pz entries
+    const uint32_t *pidx, *pval;         // ... word indices and words
+    int lz[MAXPATH];                     // entries of each level's stored bitmap; -1 = dense
+    unsigned long long n_roots;          // root count (fixed once the DFS runs)
+    unsigned long long busy, root_busy, t_task;  // thread 0's worker timing
+    int err_seen;                        // last error flag read
+    uint32_t epoch;                      // this mine's task epoch
+    unsigned int iter;                   // classes since the worker started
     unsigned long long ticket;
     unsigned long long rbase, ibase;
     int flag;
@@ -129,6 +140,71 @@ __device__ __forceinline__ uint32_t warp_sectors(bool nz) {
     return __popc((b | (b >> 1)) & 0x55555555u);
 }
 
+// Sparse store of b_Y: a level of the worker's stack holds word indices in
+// its first half and the words in its second half.  Entries of one class
+// are appended in any order (supports are order-free sums).
+__device__ __forceinline__ void sparse_put4(const DfsParams &p, Smem &s, uint32_t *lv, int64_t half, uint4 y,
+                                            int64_t pos, int lane) {
+    const uint32_t w[4] = {y.x, y.y, y.z, y.w};
+    const uint32_t c = (w[0] != 0u) + (w[1] != 0u) + (w[2] != 0u) + (w[3] != 0u);
+    uint32_t x = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += t;
+    }
+    uint32_t base = 0;
+    if (lane == 31 && x) base = atomicAdd(&s.zcount, x);
+    base = __shfl_sync(0xffffffffu, base, 31);
+    uint32_t at = base + x - c;
+#pragma unroll
+    for (int q = 0; q < 4; q++)
+        if (w[q]) {
+            if (at < half) {
+                lv[at] = (uint32_t)(pos + q);
+                lv[half + at] = w[q];
+            } else {
+                set_err(p, FIM_E_STACK);
+            }
+            at++;
+        }
+}
+
+template <int U>
+__device__ __forceinline__ void sparse_put(const DfsParams &p, Smem &s, uint32_t *lv, int64_t half,
+                                           const uint32_t *ix, const uint32_t *y, int lane) {
+    uint32_t bal[U], cnt = 0;
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+        bal[u] = __ballot_sync(0xffffffffu, y[u] != 0u);
+        cnt += __popc(bal[u]);
+    }
+    uint32_t base = 0;
+    if (lane == 0 && cnt) base = atomicAdd(&s.zcount, cnt);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    const uint32_t lt = (1u << lane) - 1u;
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+        if (y[u]) {
+            const uint32_t at = base + __popc(bal[u] & lt);
+            if (at < half) {
+                lv[at] = ix[u];
+                lv[half + at] = y[u];
+            } else {
+                set_err(p, FIM_E_STACK);
+            }
+        }
+        base += __popc(bal[u]);
+    }
+}
+
+// b_Y of support supY is stored sparse when its non-zero words (at most
+// supY of them) are few: supY * sparse_div <= nw, and they fit half a level.
+__device__ __forceinline__ int sparse_ok(const DfsParams &p, const DbView &db, uint32_t supY) {
+    return p.sparse_div > 0 && (unsigned long long)supY * (unsigned)p.sparse_div <= (unsigned long long)db.nw &&
+           (int64_t)supY <= p.nwp_max / 2;
+}
+
 // Thread 0: the view of database `db` from the mine-wide arrays.
 __device__ void load_db(const DfsParams &p, Smem &s, uint32_t db) {
     const DbDesc &d = p.dbs[db];
@@ -152,15 +228,14 @@ __device__ void load_db(const DfsParams &p, Smem &s, uint32_t db) {
 // optional store of b_Y, s.diff selects the diffset count (nsrc == 2).
 // Frequent candidates are written compacted (item, support) to fi/fs and
 // emitted as records with prefix s.path[0..plen).  Returns |F| (uniform).
+// Dense pass over one candidate batch: the sources are whole bit columns or
+// a dense b_X.  Warps = G candidate groups x (NWARP / G) chunk workers.
 template <int NT>
-__device__ int class_pass(const DfsParams &p, Smem &s, const uint32_t *cand, const uint32_t *psup,
-                          int k, int plen, uint32_t *fi, uint32_t *fs) {
+__device__ __forceinline__ void dense_sweep(const DfsParams &p, Smem &s, int kb, bool first) {
     constexpr int NWARP = NT / 32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const DbView &db = s.db;
-    const int64_t nwp = db.nwp;
+    const int64_t nwp = s.db.nwp;
     const int nchunks = (int)((nwp + CHUNK - 1) / CHUNK);
-    // warps = G candidate groups x (NWARP / G) chunk workers
     const int G = nchunks >= NWARP ? 1 : NWARP / nchunks;
     const int CW = NWARP / G;
     const int g = warp % G, cw = warp / G;
@@ -168,18 +243,11 @@ __device__ int class_pass(const DfsParams &p, Smem &s, const uint32_t *cand, con
     const int nsrc = s.nsrc;
     const bool diff = s.diff != 0;
     const bool two = nsrc == 2;
-    uint32_t *store = s.store;
-    int nF = 0;
-    if (threadIdx.x == 0) { s.sec_dense = 0; s.sec_diff = 0; }
-
-    for (int b0 = 0; b0 < k; b0 += CB) {
-        const int kb = min(CB, k - b0);
-        for (int c = threadIdx.x; c < kb; c += NT) {
-            s.cptr[c] = column(db, cand[b0 + c]);
-            s.sup[c] = 0;
-        }
-        __syncthreads();
-        if (active) {
+    uint32_t *store = first && g == 0 ? s.store : nullptr;
+    const bool store_sparse = s.store_sparse != 0;
+    const int64_t half = p.nwp_max / 2;
+    const int b0 = first ? 0 : 1;
+    if (active) {
             for (int q = cw; q < nchunks; q += CW) {
                 const int64_t base = (int64_t)q * CHUNK + lane * 4;
                 uint4 x[V];
@@ -200,7 +268,10 @@ __device__ int class_pass(const DfsParams &p, Smem &s, const uint32_t *cand, con
                         }
                         // a popped task ANDs all of its prefix columns
                         for (int r = two ? 2 : 1; r < nsrc; r++) y = and4(y, ld_cg_u4(s.src[r] + pos));
-                        if (store && b0 == 0 && g == 0) *reinterpret_cast<uint4 *>(store + pos) = y;
+                        if (store && b0 == 0 && g == 0) {
+                            if (store_sparse) sparse_put4(p, s, store, half, y, pos, lane);
+                            else *reinterpret_cast<uint4 *>(store + pos) = y;
+                        }
                     }
                     x[v] = diff ? f : y;
                     if (ok[v] && b0 == 0 && g == 0) {
@@ -248,6 +319,110 @@ __device__ int class_pass(const DfsParams &p, Smem &s, const uint32_t *cand, con
                 }
             }
         }
+}
+
+// Pass over one candidate batch when b_X is stored as its pz non-zero words
+// (index, word): b_Y and d_Y exist only there, so the pass gathers col(c) and
+// col(e) at those word indices alone.  Warps = SG candidate groups x SCW
+// entry workers; each lane takes U entries per step.
+template <int NT>
+__device__ __forceinline__ void sparse_sweep(const DfsParams &p, Smem &s, int kb, bool first) {
+    constexpr int NWARP = NT / 32;
+    constexpr int U = 4;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int pz = s.pz;
+    const uint32_t *pidx = s.pidx, *pval = s.pval, *ext = s.src[1];
+    const int wsteps = (pz + 32 * U - 1) / (32 * U);
+    const int SG = wsteps >= NWARP ? 1 : NWARP / (wsteps > 0 ? wsteps : 1);
+    const int SCW = NWARP / SG;
+    const int sg = warp % SG, scw = warp / SG;
+    const bool sactive = warp < SG * SCW;
+    const bool diff = s.diff != 0;
+    uint32_t *store = s.store;
+    const int64_t half = p.nwp_max / 2;
+    const int b0 = first ? 0 : 1;
+    if (sactive) {
+            // b_X is its pz non-zero words: b_Y and d_Y exist only there, so
+            // the pass gathers col(c) and col(e) at those word indices alone
+            for (int e0 = scw * 32 * U; e0 < pz; e0 += SCW * 32 * U) {
+                uint32_t ix[U], pv[U], x[U], yv[U];
+#pragma unroll
+                for (int u = 0; u < U; u++) {
+                    const int t = e0 + u * 32 + lane;
+                    ix[u] = t < pz ? __ldcg(pidx + t) : 0u;
+                    pv[u] = t < pz ? __ldcg(pval + t) : 0u;
+                }
+                uint32_t secd = 0, secf = 0;
+#pragma unroll
+                for (int u = 0; u < U; u++) {
+                    const uint32_t cc = pv[u] ? __ldg(ext + ix[u]) : 0u;
+                    yv[u] = pv[u] & cc;
+                    const uint32_t fv = pv[u] & ~cc;
+                    x[u] = diff ? fv : yv[u];
+                    secd += __popc(__ballot_sync(0xffffffffu, yv[u] != 0u));
+                    secf += __popc(__ballot_sync(0xffffffffu, fv != 0u));
+                }
+                if (b0 == 0 && sg == 0) {
+                    if (lane == 0 && (secd | secf)) {
+                        atomicAdd(&s.sec_dense, secd);
+                        atomicAdd(&s.sec_diff, secf);
+                    }
+                    if (store) sparse_put<U>(p, s, store, half, ix, yv, lane);
+                }
+                int c = sg;
+                for (; c + SG < kb; c += 2 * SG) {
+                    const uint32_t *c0 = s.cptr[c], *c1 = s.cptr[c + SG];
+                    uint32_t n0 = 0, n1 = 0;
+#pragma unroll
+                    for (int u = 0; u < U; u++)
+                        if (x[u]) {
+                            n0 += __popc(x[u] & __ldg(c0 + ix[u]));
+                            n1 += __popc(x[u] & __ldg(c1 + ix[u]));
+                        }
+                    n0 = warp_sum_u32(n0);
+                    n1 = warp_sum_u32(n1);
+                    if (lane == 0) {
+                        if (n0) atomicAdd(&s.sup[c], n0);
+                        if (n1) atomicAdd(&s.sup[c + SG], n1);
+                    }
+                }
+                for (; c < kb; c += SG) {
+                    const uint32_t *c0 = s.cptr[c];
+                    uint32_t n0 = 0;
+#pragma unroll
+                    for (int u = 0; u < U; u++)
+                        if (x[u]) n0 += __popc(x[u] & __ldg(c0 + ix[u]));
+                    n0 = warp_sum_u32(n0);
+                    if (lane == 0 && n0) atomicAdd(&s.sup[c], n0);
+                }
+            }
+        }
+}
+
+template <int NT>
+__device__ int class_pass(const DfsParams &p, Smem &s, const uint32_t *cand, const uint32_t *psup,
+                          int k, int plen, uint32_t *fi, uint32_t *fs) {
+    constexpr int NWARP = NT / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const DbView &db = s.db;
+    const int nsrc = s.nsrc;
+    const bool diff = s.diff != 0;
+    uint32_t *store = s.store;
+    const bool store_sparse = s.store_sparse != 0;
+    const bool sparse_parent = s.psparse != 0;
+    const int pz = sparse_parent ? s.pz : 0;
+    int nF = 0;
+    if (threadIdx.x == 0) { s.sec_dense = 0; s.sec_diff = 0; s.zcount = 0; }
+
+    for (int b0 = 0; b0 < k; b0 += CB) {
+        const int kb = min(CB, k - b0);
+        for (int c = threadIdx.x; c < kb; c += NT) {
+            s.cptr[c] = column(db, cand[b0 + c]);
+            s.sup[c] = 0;
+        }
+        __syncthreads();
+        if (sparse_parent) sparse_sweep<NT>(p, s, kb, b0 == 0);
+        else dense_sweep<NT>(p, s, kb, b0 == 0);
         __syncthreads();
         // compact the frequent candidates of this batch, in order
         for (int c0 = 0; c0 < kb; c0 += NT) {
@@ -288,12 +463,19 @@ __device__ int class_pass(const DfsParams &p, Smem &s, const uint32_t *cand, con
         }
     }
     if (threadIdx.x == 0) {
+        // algorithmic bytes are the dense operands whatever the representation
         const unsigned long long src_bytes = 4ull * db.nw * ((unsigned long long)nsrc + (store ? 1 : 0));
         const unsigned long long secs = diff ? s.sec_diff : s.sec_dense;
+        // touched: a sparse parent reads (index, word) pairs and one sector of
+        // col(c) per entry; a sparse store writes 8 bytes per entry
+        const unsigned long long src_touched =
+            sparse_parent ? 40ull * (unsigned long long)pz + (store ? 8ull * s.zcount : 0ull)
+                          : 4ull * db.nw * ((unsigned long long)nsrc) +
+                                (store ? (store_sparse ? 8ull * s.zcount : 4ull * db.nw) : 0ull);
         atomicAdd(&p.ctr->supports_dfs, (unsigned long long)k);
         atomicAdd(&p.ctr->dfs_words, (unsigned long long)k * (unsigned long long)db.nw);
         atomicAdd(&p.ctr->dfs_bytes, 4ull * db.nw * (unsigned long long)k + src_bytes);
-        atomicAdd(&p.ctr->dfs_touched, 32ull * secs * (unsigned long long)k + src_bytes);
+        atomicAdd(&p.ctr->dfs_touched, 32ull * secs * (unsigned long long)k + src_touched);
         atomicAdd(&p.ctr->classes, 1ull);
         if (diff) atomicAdd(&p.ctr->diffset, 1ull);
         if (nF > 0) atomicMax(&p.ctr->max_len, plen + 1);
@@ -399,13 +581,6 @@ __device__ int root_candidates(const DfsParams &p, Smem &s, uint32_t a, uint32_t
     return n;
 }
 
-__device__ bool queue_hungry(const DfsParams &p) {
-    const unsigned long long t = *(volatile unsigned long long *)&p.ctr->ticket;
-    const unsigned long long q = *(volatile unsigned long long *)&p.ctr->qtail;
-    const unsigned long long r = *(volatile unsigned long long *)&p.ctr->n_roots;
-    return t > r + q;
-}
-
 // Try to hand the child class (prefix s.path[0..plen) + item, candidates
 // cand[0..k)) to the queue.  Returns true if it was published.
 template <int NT>
@@ -441,7 +616,7 @@ __device__ bool try_push(const DfsParams &p, Smem &s, int plen, uint32_t item, u
         atomicAdd((unsigned long long *)&p.ctr->pending, 1ull);
         atomicAdd(&p.ctr->pushed, 1ull);
         __threadfence();
-        atomicExch(&t->ready, 1u);
+        atomicExch(&t->ready, s.epoch);
     }
     __syncthreads();
     return true;
@@ -476,8 +651,16 @@ dfs_kernel(const DfsParams p) {
     if (p.learned)
         for (int i = threadIdx.x; i < FIM_MLP_PARAMS; i += NT) s.mlp_w[i] = __bfloat162float(p.mlp_w[i]);
     const bool want_feat = p.learned || p.trace;
-    unsigned long long busy = 0, t_task = 0, root_busy = 0;
-    if (threadIdx.x == 0) atomicCAS(&p.ctr->t_first, 0ull, globaltimer_ns());
+    // thread 0's timing state lives in shared memory, not in every thread's registers
+    if (threadIdx.x == 0) {
+        s.busy = 0;
+        s.root_busy = 0;
+        atomicCAS(&p.ctr->t_first, 0ull, globaltimer_ns());
+        s.n_roots = *(volatile unsigned long long *)&p.ctr->n_roots;  // final before the DFS starts
+        s.epoch = *(volatile const uint32_t *)p.epoch;
+        s.err_seen = 0;
+        s.iter = 0;
+    }
 
     while (true) {
         // ---- get the next task ---------------------------------------
@@ -501,7 +684,7 @@ dfs_kernel(const DfsParams p) {
                 unsigned long long spins = 0;
                 const unsigned long long t_wait = globaltimer_ns();
                 while (true) {
-                    if (*(volatile uint32_t *)&tk->ready) {
+                    if (*(volatile uint32_t *)&tk->ready == s.epoch) {
                         __threadfence();
                         const int len = (int)*(volatile uint32_t *)&tk->len;
                         for (int q = 0; q < len; q++) s.path[q] = ((volatile uint32_t *)tk->items)[q];
@@ -536,7 +719,7 @@ dfs_kernel(const DfsParams p) {
             }
             if (s.flag) {
                 load_db(p, s, s.task_db);
-                t_task = globaltimer_ns();
+                s.t_task = globaltimer_ns();
             }
         }
         __syncthreads();
@@ -566,7 +749,9 @@ dfs_kernel(const DfsParams p) {
                 for (int r = 0; r < tlen; r++) s.src[r] = column(s.db, s.path[r]);
                 s.nsrc = tlen;
                 s.diff = diff;
+                s.psparse = 0;
                 s.store = k >= 2 ? stk : nullptr;
+                s.store_sparse = sparse_ok(p, s.db, s.task_sup);
                 s.base[0] = 0;
                 s.supY[0] = s.task_sup;
                 s.work[0] = (unsigned long long)k * (unsigned long long)s.db.nw;
@@ -576,7 +761,8 @@ dfs_kernel(const DfsParams p) {
             // overwrites both in order
             int nF = class_pass<NT>(p, s, fi, fs, k, tlen, fi, fs);
             if (threadIdx.x == 0) {
-                if (root) root_busy += globaltimer_ns() - t_task;
+                if (root) s.root_busy += globaltimer_ns() - s.t_task;
+                s.lz[0] = (s.store && s.store_sparse) ? (int)s.zcount : -1;
                 s.nF[0] = nF;
                 s.cur[0] = 0;
                 s.base[1] = nF;
@@ -585,7 +771,12 @@ dfs_kernel(const DfsParams p) {
             __syncthreads();
             int L = 0;
             while (L >= 0) {
-                if (threadIdx.x == 0) s.stop = *(volatile int *)&p.ctr->err != 0;
+                // the error flag is read with the queue counters at each push
+                // decision; a class without one re-reads it every 16 classes
+                if (threadIdx.x == 0) {
+                    if ((++s.iter & 15u) == 0u) s.err_seen = *(volatile int *)&p.ctr->err;
+                    s.stop = s.err_seen != 0;
+                }
                 __syncthreads();
                 if (s.stop) break;
                 if (s.cur[L] >= s.nF[L]) {
@@ -623,7 +814,14 @@ dfs_kernel(const DfsParams p) {
                 if (plen + 1 <= p.split_depth && plen + 1 <= FIM_TASK_MAXR) {
                     // s.hungry, not s.flag: thread 0 rewrites s.flag inside
                     // try_push while other warps may still be reading this
-                    if (threadIdx.x == 0) s.hungry = queue_hungry(p);
+                    if (threadIdx.x == 0) {
+                        // three loads, one round trip
+                        const int e = *(volatile int *)&p.ctr->err;
+                        const unsigned long long t = *(volatile unsigned long long *)&p.ctr->ticket;
+                        const unsigned long long q = *(volatile unsigned long long *)&p.ctr->qtail;
+                        s.hungry = t > s.n_roots + q;
+                        s.err_seen = e;
+                    }
                     __syncthreads();
                     if (s.hungry && try_push<NT>(p, s, plen, citem, csup, fi + bC, kc)) continue;
                 }
@@ -636,18 +834,25 @@ dfs_kernel(const DfsParams p) {
                 if (want_feat) class_features(s, plen + 1, csup, supX, fs + bC, kc, s.feat[L + 1]);
                 const int diff = choose_diff(p, s, s.feat[L + 1], csup, supX);
                 if (threadIdx.x == 0) {
+                    uint32_t *lv = stk + (int64_t)L * p.nwp_max;  // b_X, the class at level L
                     s.path[plen] = citem;
-                    s.src[0] = stk + (int64_t)L * p.nwp_max;
+                    s.src[0] = lv;
                     s.src[1] = column(s.db, citem);
                     s.nsrc = 2;
+                    s.psparse = s.lz[L] >= 0;
+                    s.pz = s.lz[L];
+                    s.pidx = lv;
+                    s.pval = lv + p.nwp_max / 2;
                     s.diff = diff;
                     s.store = kc >= 2 ? stk + (int64_t)(L + 1) * p.nwp_max : nullptr;
+                    s.store_sparse = s.psparse || sparse_ok(p, s.db, csup);
                     s.supY[L + 1] = csup;
                     s.work[L + 1] = (unsigned long long)kc * (unsigned long long)s.db.nw;
                 }
                 __syncthreads();
                 nF = class_pass<NT>(p, s, fi + bC, fs + bC, kc, plen + 1, fi + bC, fs + bC);
                 if (threadIdx.x == 0) {
+                    s.lz[L + 1] = (s.store && s.store_sparse) ? (int)s.zcount : -1;
                     s.nF[L + 1] = nF;
                     s.cur[L + 1] = 0;
                     s.base[L + 2] = bC + nF;
@@ -661,17 +866,36 @@ dfs_kernel(const DfsParams p) {
         if (threadIdx.x == 0) {
             __threadfence();
             atomicAdd((unsigned long long *)&p.ctr->pending, (unsigned long long)(-1ll));
-            busy += globaltimer_ns() - t_task;
+            s.busy += globaltimer_ns() - s.t_task;
         }
     }
     if (threadIdx.x == 0) {
-        atomicAdd(&p.ctr->busy_ns, busy);
-        atomicAdd(&p.ctr->root_ns, root_busy);
+        atomicAdd(&p.ctr->busy_ns, s.busy);
+        atomicAdd(&p.ctr->root_ns, s.root_busy);
         atomicMax(&p.ctr->t_last, globaltimer_ns());
     }
 }
 
+__global__ void epoch_bump_kernel(uint32_t *e) {
+    const uint32_t v = *e + 1u;
+    *e = v ? v : 1u;  // 0 marks a slot that was never published
+}
+
 }  // namespace
+
+int prepare_task_queue(fim_ctx *ctx, size_t bytes) {
+    void *old = ctx->tasks.p;
+    FIM_TRY(fim_reserve(ctx, ctx->tasks, bytes));
+    if (ctx->tasks.p != old) FIM_CUDA_TRY(cudaMemsetAsync(ctx->tasks.p, 0, ctx->tasks.bytes, ctx->stream));
+    return FIM_OK;
+}
+
+int launch_epoch_bump(fim_ctx *ctx) {
+    ctx->launches++;
+    epoch_bump_kernel<<<1, 1, 0, ctx->stream>>>(ctx->epoch.as<uint32_t>());
+    FIM_CUDA_TRY(cudaGetLastError());
+    return FIM_OK;
+}
 
 int launch_dfs(fim_ctx *ctx, const DfsParams &p, int grid, int block) {
     if (grid <= 0) return FIM_OK;

@@ -80,3 +80,28 @@ def test_autotune_picks_a_valid_shape_and_caches_it(ctx, case, tmp_path):
     fim.fim_mine(ctx, minsup)
     assert fim.fim_fetch_results(ctx).sha256() == want
     autotune.apply(ctx, autotune.DEFAULT)
+
+
+SPARSE_CASES = [
+    ("planted", lambda: datagen.planted(n=20_000, m=600, n_patterns=40, seed=9), 120),
+    ("zipf_deep", lambda: datagen.zipf_baskets(3000, 50, 0.8, 6.0, 9), 2),
+    ("quest", lambda: datagen.quest(100_000, 300, 10.0, 4.0, 400, 5), 100),
+]
+
+
+@pytest.mark.parametrize("div", [0, 1, 2, 4, 64])
+@pytest.mark.parametrize("name,gen,minsup", SPARSE_CASES, ids=[c[0] for c in SPARSE_CASES])
+def test_sparse_classes_are_exact(ctx, name, gen, minsup, div):
+    # sparse_div decides which class bitmaps are kept as their non-zero words;
+    # dense, sparse and mixed stacks, counted dense or through diffsets, must
+    # all give the oracle's itemsets
+    c = gen()
+    want = oracle.apriori(c.indptr, c.indices, c.m, minsup).sha256()
+    fim.fim_set_tuning(ctx, "sparse_div", div)
+    try:
+        fim.fim_build_bitmaps(ctx, c.indptr, c.indices, c.m)
+        for flags in (0, fim.FIM_DIFFSET_RULE, fim.FIM_NO_SPLIT):
+            fim.fim_mine(ctx, minsup, flags)
+            assert fim.fim_fetch_results(ctx).sha256() == want, flags
+    finally:
+        fim.fim_set_tuning(ctx, "sparse_div", 8)

@@ -162,8 +162,10 @@ int fim_get_stats(const fim_ctx *ctx, fim_stats *out);
  *   "dfs_ctas_per_sm"  1..4      DFS workers per SM; dfs_threads x dfs_ctas_per_sm
  *                                must not exceed 1024 (FIM_E_INVAL otherwise)
  *   "split_depth"      0..8      longest prefix a worker may hand to the queue
- *   "sparse_div"       0..64     a class bitmap b_Y is kept as its non-zero words
- *                                when S(Y) x sparse_div <= nw (0 = always dense)
+ *   "sparse_div"       -1..64    a class bitmap b_Y is kept as its non-zero words
+ *                                when S(Y) x sparse_div <= nw (0 = always dense;
+ *                                -1 = automatic, the default: 4 when the frequent
+ *                                item columns exceed half of L2, else dense)
  *   "pairs_split"      0..4096   CTAs of the tensor-core pair pass, each taking an
  *                                equal share of the (tile, stage) space (0 = one per SM)
  *   "pairs_kdrain"     0..32768  128-transaction stages one accumulator sums before

@@ -19,11 +19,12 @@ from . import fim
 
 SPACE = {
     "dfs_threads": [256, 512],
-    "dfs_ctas_per_sm": [1, 2, 4],
-    "split_depth": [4, 6, 8],
-    "pairs_kdrain": [64, 256, 1024],
+    "dfs_ctas_per_sm": [2, 4],
+    "split_depth": [4, 8],
+    "sparse_div": [-1, 0, 4],
 }
-DEFAULT = {"dfs_threads": 256, "dfs_ctas_per_sm": 4, "split_depth": 8, "pairs_kdrain": 64, "pairs_split": 0}
+DEFAULT = {"dfs_threads": 256, "dfs_ctas_per_sm": 4, "split_depth": 8, "sparse_div": -1,
+           "pairs_kdrain": 0, "pairs_split": 0}
 
 
 def valid(cfg: dict) -> bool:

@@ -118,6 +118,7 @@ int fim_create(fim_ctx **out, int device, void *cuda_stream) {
     if (!ctx) return FIM_E_NOMEM;
     ctx->device = device;
     cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+    cudaDeviceGetAttribute(&ctx->l2_bytes, cudaDevAttrL2CacheSize, device);
     if (cuda_stream) {
         ctx->stream = (cudaStream_t)cuda_stream;
     } else {
@@ -152,7 +153,8 @@ void fim_destroy(fim_ctx *ctx) {
                      &ctx->scan_part, &ctx->out_off,
                      &ctx->out_items, &ctx->out_sup, &ctx->mlp_w32, &ctx->mlp_wbf, &ctx->trace_x,
                      &ctx->trace_y, &ctx->mlp_scratch, &ctx->root_order, &ctx->root_bucket,
-                     &ctx->root_hist, &ctx->rec_db, &ctx->dbdesc, &ctx->epoch};
+                     &ctx->root_hist, &ctx->rec_db, &ctx->dbdesc, &ctx->epoch, &ctx->sp_idx,
+                     &ctx->sp_val, &ctx->sp_z};
     for (DevBuf *b : all) fim_release(ctx, *b);
     fim_release(ctx, ctx->batch_prefix);
     fim_release(ctx, ctx->batch_slices);
@@ -329,8 +331,25 @@ int mine_once(fim_ctx *ctx, uint32_t thr, uint32_t flags, MineState &ms, bool *r
         p.rec_items_cap = ctx->rec_items_cap;
         p.ctr = d_ctr;
         p.spin_limit = kSpinLimitNs;
-        p.sparse_div = ctx->sparse_div;
+        // automatic: keep low-support classes sparse when the frequent item
+        // columns do not fit in half of L2 (streaming whole columns from HBM
+        // is latency-bound; from L2 the dense pass is as fast)
+        p.sparse_div = ctx->sparse_div >= 0 ? ctx->sparse_div
+                       : ((double)mf * (double)ctx->nwp * 4.0 > 0.5 * (double)ctx->l2_bytes ? 4 : 0);
         p.epoch = ctx->epoch.as<uint32_t>();
+        // sparse copies of the low-support item columns, for the root classes
+        // (bounded: at most 1 GiB of (index, word) pairs)
+        // (a child of a sparse parent is stored sparse: the copies must fit
+        // half a stack level, like every sparse class)
+        int64_t sp_cap = p.sparse_div > 0 ? ctx->nw / p.sparse_div : 0;
+        if (sp_cap > ctx->nwp / 2) sp_cap = ctx->nwp / 2;
+        if (sp_cap > 0 && (double)mf * (double)sp_cap * 8.0 <= (double)(1ull << 30)) {
+            FIM_TRY(launch_sparse_items(ctx, mf, sp_cap));
+            p.item_idx = ctx->sp_idx.as<uint32_t>();
+            p.item_val = ctx->sp_val.as<uint32_t>();
+            p.item_z = ctx->sp_z.as<int>();
+            p.item_cap = sp_cap;
+        }
         p.pair_cnt = ctx->pair_cnt.as<int>();
         p.item_sup = ctx->item_sup.as<uint32_t>();
         p.root_order = nullptr;
@@ -484,7 +503,7 @@ int fim_set_tuning(fim_ctx *ctx, const char *key, int64_t v) {
         {"dfs_ctas_per_sm", &ctx->dfs_ctas_per_sm, 1, 4},
         {"dfs_threads", &ctx->dfs_block, 256, 512},
         {"split_depth", &ctx->split_depth, 0, FIM_TASK_MAXR},
-        {"sparse_div", &ctx->sparse_div, 0, 64},
+        {"sparse_div", &ctx->sparse_div, -1, 64},
         {"pairs_split", &ctx->pairs_split, 0, 4096},
         {"pairs_kdrain", &ctx->pairs_kdrain, 0, 32768},
     };

@@ -152,6 +152,12 @@ struct DfsParams {
     // learned / traces
     const __nv_bfloat16 *mlp_w;  // bf16 weights or null
     const uint32_t *epoch;       // this mine's epoch (bumped on the stream before the DFS)
+    // sparse item columns (single database): item i's non-zero words at
+    // [i * item_cap, i * item_cap + item_z[i]) of item_idx / item_val, or
+    // item_z[i] < 0 when the column is kept dense only; null = none
+    const uint32_t *item_idx, *item_val;
+    const int *item_z;
+    int64_t item_cap;
     int learned;
     int diffset_rule;
     float *trace_x;          // [cap][8]
@@ -186,6 +192,7 @@ struct fim_ctx {
     DevBuf pair_cnt, pairbits, roots;
     DevBuf tasks, cand_pool, stack_bits, frame_items, frame_sups;
     DevBuf epoch;               // uint32: mine counter; a task slot is live when ready == epoch
+    DevBuf sp_idx, sp_val, sp_z; // sparse copies of low-support frequent item columns
     DevBuf rec_off, rec_len, rec_sup, rec_items, rec_db;
     DevBuf counters;            // MineCounters
     DevBuf dbdesc;              // DbDesc table of the mine
@@ -222,7 +229,8 @@ struct fim_ctx {
     int dfs_block = 256;
     int dfs_ctas_per_sm = 4;
     int split_depth = 8;
-    int sparse_div = 8;
+    int sparse_div = -1;        // -1: automatic (see sparse_div_for)
+    int l2_bytes = 0;
     int pairs_split = 0;        // split-K factor of the tensor-core pair pass (0 = auto)
     int pairs_kdrain = 0;       // stages (x128 transactions) per exact drain (0 = 64)
 
@@ -257,6 +265,8 @@ int launch_dfs(fim_ctx *ctx, const DfsParams &p, int grid, int block);
 // replayed graph bumps it too) and clear the slots only when the buffer is new.
 int prepare_task_queue(fim_ctx *ctx, size_t bytes);
 int launch_epoch_bump(fim_ctx *ctx);
+// Sparse copies of the frequent item columns with S <= cap (single database).
+int launch_sparse_items(fim_ctx *ctx, int mf, int64_t cap);
 
 // k_mlp.cu: learned root order (longest predicted subtree first)
 int launch_root_order(fim_ctx *ctx, MineCounters *d_ctr, size_t npairs);

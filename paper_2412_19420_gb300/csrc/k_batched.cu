@@ -490,7 +490,7 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
         p.mlp_w = ctx->mlp_wbf.as<__nv_bfloat16>();
         p.ctr = d_ctr;
         p.spin_limit = kSpinLimitNs;
-        p.sparse_div = ctx->sparse_div;
+        p.sparse_div = ctx->sparse_div > 0 ? ctx->sparse_div : 0;  // automatic: dense (small databases)
         p.epoch = ctx->epoch.as<uint32_t>();
 
         // graph key: everything the captured launches depend on

@@ -750,8 +750,21 @@ dfs_kernel(const DfsParams p) {
                 s.nsrc = tlen;
                 s.diff = diff;
                 s.psparse = 0;
+                // a root {a, b} whose parent column col(a) has a sparse copy
+                // gathers col(b) and the candidates at col(a)'s non-zero words
+                if (root && p.item_z) {
+                    const int za = __ldg(p.item_z + s.path[0]);
+                    if (za >= 0) {
+                        s.psparse = 1;
+                        s.pz = za;
+                        s.pidx = p.item_idx + (int64_t)s.path[0] * p.item_cap;
+                        s.pval = p.item_val + (int64_t)s.path[0] * p.item_cap;
+                    }
+                }
                 s.store = k >= 2 ? stk : nullptr;
-                s.store_sparse = sparse_ok(p, s.db, s.task_sup);
+                // a sparse parent's child has no more entries than the parent
+                // (item_cap <= half a stack level), so it is stored sparse too
+                s.store_sparse = s.psparse || sparse_ok(p, s.db, s.task_sup);
                 s.base[0] = 0;
                 s.supY[0] = s.task_sup;
                 s.work[0] = (unsigned long long)k * (unsigned long long)s.db.nw;
@@ -876,6 +889,53 @@ dfs_kernel(const DfsParams p) {
     }
 }
 
+// One CTA per frequent item i (internal id): if S(i) <= cap, its column's
+// non-zero words go to [i * cap, i * cap + z) as (index, word), in any order.
+__global__ void __launch_bounds__(256)
+sparse_items_kernel(const uint32_t *__restrict__ bm, const int32_t *__restrict__ perm,
+                    const uint32_t *__restrict__ item_sup, int64_t nwp, int64_t cap, uint32_t *__restrict__ idx,
+                    uint32_t *__restrict__ val, int *__restrict__ z) {
+    __shared__ unsigned int cnt;
+    const int i = blockIdx.x;
+    const int lane = threadIdx.x & 31;
+    const int32_t j = perm[i];
+    if (item_sup[j] > (uint64_t)cap) {
+        if (threadIdx.x == 0) z[i] = -1;
+        return;
+    }
+    if (threadIdx.x == 0) cnt = 0;
+    __syncthreads();
+    const uint32_t *col = bm + (int64_t)j * nwp;
+    uint32_t *oi = idx + (int64_t)i * cap, *ov = val + (int64_t)i * cap;
+    for (int64_t w0 = 0; w0 < nwp; w0 += 4 * 256) {  // nwp % 128 == 0: trips are warp-uniform
+        const int64_t pos = w0 + 4 * threadIdx.x;
+        const uint4 y = pos < nwp ? ldg_u4(col + pos) : make_uint4(0, 0, 0, 0);
+        const uint32_t w[4] = {y.x, y.y, y.z, y.w};
+        const uint32_t c = (w[0] != 0u) + (w[1] != 0u) + (w[2] != 0u) + (w[3] != 0u);
+        uint32_t x = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += t;
+        }
+        uint32_t base = 0;
+        if (lane == 31 && x) base = atomicAdd(&cnt, x);
+        base = __shfl_sync(0xffffffffu, base, 31);
+        uint32_t at = base + x - c;
+#pragma unroll
+        for (int q = 0; q < 4; q++)
+            if (w[q]) {
+                if (at < cap) {  // at most S(i) <= cap words are non-zero
+                    oi[at] = (uint32_t)(pos + q);
+                    ov[at] = w[q];
+                }
+                at++;
+            }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) z[i] = (int)cnt;
+}
+
 __global__ void epoch_bump_kernel(uint32_t *e) {
     const uint32_t v = *e + 1u;
     *e = v ? v : 1u;  // 0 marks a slot that was never published
@@ -887,6 +947,20 @@ int prepare_task_queue(fim_ctx *ctx, size_t bytes) {
     void *old = ctx->tasks.p;
     FIM_TRY(fim_reserve(ctx, ctx->tasks, bytes));
     if (ctx->tasks.p != old) FIM_CUDA_TRY(cudaMemsetAsync(ctx->tasks.p, 0, ctx->tasks.bytes, ctx->stream));
+    return FIM_OK;
+}
+
+int launch_sparse_items(fim_ctx *ctx, int mf, int64_t cap) {
+    if (mf <= 0) return FIM_OK;
+    FIM_TRY(fim_reserve(ctx, ctx->sp_idx, sizeof(uint32_t) * (size_t)mf * (size_t)cap));
+    FIM_TRY(fim_reserve(ctx, ctx->sp_val, sizeof(uint32_t) * (size_t)mf * (size_t)cap));
+    FIM_TRY(fim_reserve(ctx, ctx->sp_z, sizeof(int) * (size_t)mf));
+    ctx->launches++;
+    sparse_items_kernel<<<mf, 256, 0, ctx->stream>>>(ctx->bm.as<uint32_t>(), ctx->perm.as<int32_t>(),
+                                                     ctx->item_sup.as<uint32_t>(), ctx->nwp, cap,
+                                                     ctx->sp_idx.as<uint32_t>(), ctx->sp_val.as<uint32_t>(),
+                                                     ctx->sp_z.as<int>());
+    FIM_CUDA_TRY(cudaGetLastError());
     return FIM_OK;
 }
 

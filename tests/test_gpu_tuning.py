@@ -89,7 +89,7 @@ SPARSE_CASES = [
 ]
 
 
-@pytest.mark.parametrize("div", [0, 1, 2, 4, 64])
+@pytest.mark.parametrize("div", [-1, 0, 1, 2, 4, 64])
 @pytest.mark.parametrize("name,gen,minsup", SPARSE_CASES, ids=[c[0] for c in SPARSE_CASES])
 def test_sparse_classes_are_exact(ctx, name, gen, minsup, div):
     # sparse_div decides which class bitmaps are kept as their non-zero words;
@@ -104,4 +104,4 @@ def test_sparse_classes_are_exact(ctx, name, gen, minsup, div):
             fim.fim_mine(ctx, minsup, flags)
             assert fim.fim_fetch_results(ctx).sha256() == want, flags
     finally:
-        fim.fim_set_tuning(ctx, "sparse_div", 8)
+        fim.fim_set_tuning(ctx, "sparse_div", -1)

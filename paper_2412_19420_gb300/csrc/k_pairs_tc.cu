@@ -20,19 +20,24 @@
 // processed as segments that never cross a tile or a multiple of kdrain stages.
 //
 // CTA (672 threads):
-//   warps 0-11  producers, one operand row each (128 A rows, then 256 B
-//               rows): load the row's bits several stages ahead in registers,
-//               expand each bit to an e4m3 byte (0x40 = 2.0) and store the
-//               operand tiles in the SWIZZLE_128B K-major layout the MMA
-//               descriptors name.  When the A-block lies inside the B-block,
-//               A is read from B's tile and its producers only arrive;
-//   warps 12-19 epilogue: per segment, tcgen05.ld the f32 accumulator (two
-//               TMEM buffers, so draining one overlaps the MMAs into the
-//               other), convert to counts, transpose 32 x 16 blocks through
-//               shared memory and add them into pair_cnt[a][b] with coalesced
+//   warps 0-3   A producers, one row each: load the row's bits several
+//               stages ahead, expand each bit to an e4m3 byte (0x40 = 2.0)
+//               and write the 128-byte row straight into tensor memory
+//               (tcgen05.st; the MMA reads A from TMEM, so A costs no
+//               shared-memory bandwidth).  When the A-block lies inside the
+//               B-block, A is read from B's shared-memory tile instead and
+//               these warps only arrive;
+//   warps 4-11  B producers, one row each: the same expansion into the
+//               SWIZZLE_128B K-major shared-memory tile the B descriptor names;
+//   warps 12-19 epilogue: per segment, tcgen05.ld the f32 accumulator,
+//               convert to counts, transpose 32 x 16 blocks through shared
+//               memory and add them into pair_cnt[a][b] with coalesced
 //               atomics;
 //   warp 20     one elected thread issues 4 MMAs (128 x 256 x 32) per stage
 //               and commits stage release / accumulator-ready to mbarriers.
+// Tensor memory: the 256-column accumulator at column 0, then one 32-column
+// A slot per pipeline stage.  Shared-memory traffic per stage is the B tile
+// written once and read once (64 KB for 8.4 MFLOP).
 // Every mbarrier wait is bounded; on expiry the CTA records an error, lets
 // its MMAs finish, frees its tensor memory and returns.
 #include "fim_common.cuh"
@@ -42,25 +47,29 @@ namespace {
 constexpr int TM = 128;               // A rows (items a) per tile
 constexpr int TN = 256;               // B rows (items b) per tile
 constexpr int KB = 128;               // K elements (transactions) per stage = 128 bytes per row
-constexpr int STAGES = 4;
+constexpr int STAGES = 6;
 constexpr int NPROD = TM + TN;        // producer threads, one operand row each
 constexpr int NEPI = 256;             // epilogue threads
 constexpr int THREADS = NPROD + NEPI + 32;
-constexpr int A_BYTES = TM * KB;      // 16 KB per stage
+constexpr int A_BYTES = TM * KB;      // 16 KB: A inside B's tile starts this far in
 constexpr int B_BYTES = TN * KB;      // 32 KB per stage
 constexpr int PF = 4;                 // stages a producer loads ahead
-constexpr uint32_t TMEM_COLS = 2 * TN;  // two 256-column f32 accumulators
+constexpr int G = 2;                  // stages a producer publishes per fence
+constexpr uint32_t ACC_COL = 0;       // f32 accumulator: columns [0, 256)
+constexpr uint32_t A_COL = TN;        // A slot s: columns [A_COL + 32 s, A_COL + 32 s + 32)
+constexpr uint32_t A_SLOT_COLS = KB / 4;
+constexpr uint32_t TMEM_COLS = 512;   // power of two >= A_COL + STAGES * A_SLOT_COLS
+static_assert(A_COL + STAGES * A_SLOT_COLS <= TMEM_COLS, "tensor memory layout");
 constexpr int KDRAIN_MAX = 32768;     // 2^22 transactions: partials stay <= 2^24
 constexpr unsigned long long WAIT_NS = 2000000000ull;  // 2 s: far above any legitimate wait
 
 struct __align__(1024) TcSmem {
-    uint8_t a[STAGES][A_BYTES];
     uint8_t b[STAGES][B_BYTES];
     int xp[NEPI / 32][16][34];        // per epilogue warp: 16 columns x 32 rows (+2 pad)
     uint64_t full[STAGES];
     uint64_t empty[STAGES];
-    uint64_t acc_full[2];
-    uint64_t acc_empty[2];
+    uint64_t acc_full;
+    uint64_t acc_empty;
     uint64_t done;
     uint32_t tmem_base;
     int abort;
@@ -131,6 +140,20 @@ __device__ __forceinline__ void mma_f8(uint32_t tmem_d, uint64_t a, uint64_t b, 
         "l"(a), "l"(b), "r"(idesc), "r"(acc)
         : "memory");
 }
+// A from tensor memory (row m in lane m, K bytes packed 4 per 32-bit column).
+__device__ __forceinline__ void mma_f8_ts(uint32_t tmem_d, uint32_t tmem_a, uint64_t b, uint32_t idesc,
+                                          uint32_t acc) {
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], [%1], %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "r"(tmem_a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t *v) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr),
+                 "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+                 : "memory");
+}
 __device__ __forceinline__ void mma_commit(uint64_t *bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                      smem_addr(bar))
@@ -160,6 +183,20 @@ __device__ __forceinline__ void store_row(uint8_t *tile, int r, uint4 w) {
     for (int c = 0; c < 8; c++) {
         const uint32_t h = (words[c >> 1] >> ((c & 1) * 16)) & 0xFFFFu;
         *reinterpret_cast<uint4 *>(row + ((c ^ (r & 7)) << 4)) = bits16_to_e4m3(h);
+    }
+}
+
+// Row of A (this thread's TMEM lane) at columns [col, col + 32): word t of
+// the 128-byte row holds K elements 4t .. 4t + 3.
+__device__ __forceinline__ void store_row_tmem(uint32_t taddr, uint4 w) {
+    const uint32_t words[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+    for (int q = 0; q < 4; q++) {  // 32 bits = 32 elements = 8 columns per store
+        uint32_t v[8];
+        const uint4 lo = bits16_to_e4m3(words[q] & 0xFFFFu), hi = bits16_to_e4m3(words[q] >> 16);
+        v[0] = lo.x; v[1] = lo.y; v[2] = lo.z; v[3] = lo.w;
+        v[4] = hi.x; v[5] = hi.y; v[6] = hi.z; v[7] = hi.w;
+        tmem_st8(taddr + 8u * q, v);
     }
 }
 
@@ -208,7 +245,8 @@ pairs_tc_kernel(const uint32_t *__restrict__ bm, const int32_t *__restrict__ per
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < STAGES; i++) { mbar_init(&s.full[i], NPROD); mbar_init(&s.empty[i], 1); }
-        for (int i = 0; i < 2; i++) { mbar_init(&s.acc_full[i], 1); mbar_init(&s.acc_empty[i], NEPI); }
+        mbar_init(&s.acc_full, 1);
+        mbar_init(&s.acc_empty, NEPI);
         mbar_init(&s.done, 1);
         s.abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -249,17 +287,42 @@ pairs_tc_kernel(const uint32_t *__restrict__ bm, const int32_t *__restrict__ per
                 for (int u = 0; u < PF; u++)
                     nxt[u] = (col && k0 + PF + u < g.len) ? ldg_u4(col + (g.st + k0 + PF + u) * 4)
                                                           : make_uint4(0, 0, 0, 0);
+                // stages go out in pairs: both slots are filled, then one
+                // fence (proxy or tensor-memory) publishes both, so a
+                // producer pays that round trip once per two stages
 #pragma unroll
-                for (int u = 0; u < PF; u++) {
-                    if (k0 + u < g.len && ok) {
-                        const int slot = it % STAGES;
-                        const uint32_t ph = (uint32_t)(it / STAGES) & 1u;
-                        if (!(ok = mbar_wait(s, &s.empty[slot], ph ^ 1u))) break;
-                        if (store) store_row(is_a ? s.a[slot] : s.b[slot], r, cur[u]);
+                for (int u0 = 0; u0 < PF; u0 += G) {
+                    const int cnt = min(G, g.len - (k0 + u0));
+                    if (cnt <= 0 || !ok) break;
+#pragma unroll
+                    for (int v = 0; v < G; v++)
+                        if (v < cnt && ok) {
+                            const int sl = (it + v) % STAGES;
+                            ok = mbar_wait(s, &s.empty[sl], ((uint32_t)((it + v) / STAGES) & 1u) ^ 1u);
+                        }
+                    if (!ok) break;
+                    if (is_a) {
+                        if (store) {  // warp-uniform: a warp's 32 rows are all A or all B
+                            tc_fence_after();  // after the MMAs that read these slots
+#pragma unroll
+                            for (int v = 0; v < G; v++)
+                                if (v < cnt)
+                                    store_row_tmem(tmem + ((uint32_t)(warp * 32) << 16) +
+                                                       (A_COL + (uint32_t)((it + v) % STAGES) * A_SLOT_COLS),
+                                                   cur[u0 + v]);
+                            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+                            tc_fence_before();
+                        }
+                    } else {
+#pragma unroll
+                        for (int v = 0; v < G; v++)
+                            if (v < cnt) store_row(s.b[(it + v) % STAGES], r, cur[u0 + v]);
                         fence_proxy_async();
-                        mbar_arrive(&s.full[slot]);
-                        it++;
                     }
+#pragma unroll
+                    for (int v = 0; v < G; v++)
+                        if (v < cnt) mbar_arrive(&s.full[(it + v) % STAGES]);
+                    it += cnt;
                 }
 #pragma unroll
                 for (int u = 0; u < PF; u++) cur[u] = nxt[u];
@@ -277,15 +340,14 @@ pairs_tc_kernel(const uint32_t *__restrict__ bm, const int32_t *__restrict__ per
             w += g.len;
             int ta, tb;
             tile_coords(g.tile, mf, ntb, ta, tb);
-            const int buf = j & 1;
             // warp-uniform: tcgen05.ld below is a .sync.aligned warp instruction
-            if (!__all_sync(0xffffffffu, mbar_wait(s, &s.acc_full[buf], (uint32_t)(j >> 1) & 1u))) break;
+            if (!__all_sync(0xffffffffu, mbar_wait(s, &s.acc_full, (uint32_t)j & 1u))) break;
             tc_fence_after();
 #pragma unroll 1
             for (int x = 0; x < 8; x++) {
                 uint32_t v[16];
                 const uint32_t taddr =
-                    tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * TN + half * 128 + x * 16);
+                    tmem + ((uint32_t)(q * 32) << 16) + (ACC_COL + (uint32_t)(half * 128 + x * 16));
                 asm volatile(
                     "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
                     : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
@@ -310,7 +372,7 @@ pairs_tc_kernel(const uint32_t *__restrict__ bm, const int32_t *__restrict__ per
                 __syncwarp();
             }
             tc_fence_before();
-            mbar_arrive(&s.acc_empty[buf]);
+            mbar_arrive(&s.acc_empty);
         }
     } else if (lane == 0) {
         // ---------------- MMA issuer ----------------
@@ -323,8 +385,8 @@ pairs_tc_kernel(const uint32_t *__restrict__ bm, const int32_t *__restrict__ per
             int ta, tb;
             tile_coords(g.tile, mf, ntb, ta, tb);
             const bool a_in_b = tb == (ta >> 1);
-            const int buf = j & 1;
-            if (!(ok = mbar_wait(s, &s.acc_empty[buf], ((uint32_t)(j >> 1) & 1u) ^ 1u))) break;
+            // one accumulator: segment j starts once segment j - 1 is drained
+            if (!(ok = mbar_wait(s, &s.acc_empty, ((uint32_t)j & 1u) ^ 1u))) break;
             tc_fence_after();
             for (int k = 0; k < g.len; k++, it++) {
                 const int slot = it % STAGES;
@@ -332,14 +394,22 @@ pairs_tc_kernel(const uint32_t *__restrict__ bm, const int32_t *__restrict__ per
                 if (!(ok = mbar_wait(s, &s.full[slot], ph))) break;
                 tc_fence_after();
                 const uint32_t b0 = smem_addr(s.b[slot]);
-                const uint32_t a0 = a_in_b ? b0 + (uint32_t)((ta & 1) * A_BYTES) : smem_addr(s.a[slot]);
+                if (a_in_b) {
+                    const uint32_t a0 = b0 + (uint32_t)((ta & 1) * A_BYTES);
 #pragma unroll
-                for (int kk = 0; kk < KB / 32; kk++)
-                    mma_f8(tmem + (uint32_t)(buf * TN), sdesc(a0 + kk * 32), sdesc(b0 + kk * 32), IDESC,
-                           (k == 0 && kk == 0) ? 0u : 1u);
+                    for (int kk = 0; kk < KB / 32; kk++)
+                        mma_f8(tmem + ACC_COL, sdesc(a0 + kk * 32), sdesc(b0 + kk * 32), IDESC,
+                               (k == 0 && kk == 0) ? 0u : 1u);
+                } else {
+                    const uint32_t a0 = tmem + A_COL + (uint32_t)slot * A_SLOT_COLS;
+#pragma unroll
+                    for (int kk = 0; kk < KB / 32; kk++)  // 32 fp8 elements = 8 columns per MMA
+                        mma_f8_ts(tmem + ACC_COL, a0 + 8u * kk, sdesc(b0 + kk * 32), IDESC,
+                                  (k == 0 && kk == 0) ? 0u : 1u);
+                }
                 mma_commit(&s.empty[slot]);
             }
-            if (ok) mma_commit(&s.acc_full[buf]);
+            if (ok) mma_commit(&s.acc_full);
         }
         // make sure no MMA is in flight before the tensor memory is freed
         mma_commit(&s.done);

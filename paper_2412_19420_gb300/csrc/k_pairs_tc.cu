@@ -244,7 +244,8 @@ pairs_tc_kernel(const uint32_t *__restrict__ bm, const int32_t *__restrict__ per
     const int64_t w1 = (int64_t)(blockIdx.x + 1) * W / gridDim.x;
 
     if (threadIdx.x == 0) {
-        for (int i = 0; i < STAGES; i++) { mbar_init(&s.full[i], NPROD); mbar_init(&s.empty[i], 1); }
+        // one arrival per producer warp and stage
+        for (int i = 0; i < STAGES; i++) { mbar_init(&s.full[i], NPROD / 32); mbar_init(&s.empty[i], 1); }
         mbar_init(&s.acc_full, 1);
         mbar_init(&s.acc_empty, NEPI);
         mbar_init(&s.done, 1);
@@ -294,12 +295,16 @@ pairs_tc_kernel(const uint32_t *__restrict__ bm, const int32_t *__restrict__ per
                 for (int u0 = 0; u0 < PF; u0 += G) {
                     const int cnt = min(G, g.len - (k0 + u0));
                     if (cnt <= 0 || !ok) break;
+                    bool wok = true;  // lane 0 waits for the warp
+                    if (lane == 0) {
 #pragma unroll
-                    for (int v = 0; v < G; v++)
-                        if (v < cnt && ok) {
-                            const int sl = (it + v) % STAGES;
-                            ok = mbar_wait(s, &s.empty[sl], ((uint32_t)((it + v) / STAGES) & 1u) ^ 1u);
-                        }
+                        for (int v = 0; v < G; v++)
+                            if (v < cnt && wok) {
+                                const int sl = (it + v) % STAGES;
+                                wok = mbar_wait(s, &s.empty[sl], ((uint32_t)((it + v) / STAGES) & 1u) ^ 1u);
+                            }
+                    }
+                    ok = __shfl_sync(0xffffffffu, wok, 0);
                     if (!ok) break;
                     if (is_a) {
                         if (store) {  // warp-uniform: a warp's 32 rows are all A or all B
@@ -319,9 +324,10 @@ pairs_tc_kernel(const uint32_t *__restrict__ bm, const int32_t *__restrict__ per
                             if (v < cnt) store_row(s.b[(it + v) % STAGES], r, cur[u0 + v]);
                         fence_proxy_async();
                     }
+                    __syncwarp();  // the warp's stores are fenced: lane 0 arrives for it
 #pragma unroll
                     for (int v = 0; v < G; v++)
-                        if (v < cnt) mbar_arrive(&s.full[(it + v) % STAGES]);
+                        if (v < cnt && lane == 0) mbar_arrive(&s.full[(it + v) % STAGES]);
                     it += cnt;
                 }
 #pragma unroll

@@ -20,8 +20,8 @@
 // processed as segments that never cross a tile or a multiple of kdrain stages.
 //
 // CTA (672 threads):
-//   warps 0-3   A producers, one row each: load the row's bits several
-//               stages ahead, expand each bit to an e4m3 byte (0x40 = 2.0)
+//   warps 0-3   A producers, one row each: copy the row's bits D stages
+//               ahead into shared memory (cp.async), expand each bit to an e4m3 byte (0x40 = 2.0)
 //               and write the 128-byte row straight into tensor memory
 //               (tcgen05.st; the MMA reads A from TMEM, so A costs no
 //               shared-memory bandwidth).  When the A-block lies inside the
@@ -47,13 +47,13 @@ namespace {
 constexpr int TM = 128;               // A rows (items a) per tile
 constexpr int TN = 256;               // B rows (items b) per tile
 constexpr int KB = 128;               // K elements (transactions) per stage = 128 bytes per row
-constexpr int STAGES = 6;
+constexpr int STAGES = 5;
 constexpr int NPROD = TM + TN;        // producer threads, one operand row each
 constexpr int NEPI = 256;             // epilogue threads
 constexpr int THREADS = NPROD + NEPI + 32;
 constexpr int A_BYTES = TM * KB;      // 16 KB: A inside B's tile starts this far in
 constexpr int B_BYTES = TN * KB;      // 32 KB per stage
-constexpr int PF = 4;                 // stages a producer loads ahead
+constexpr int D = 8;                  // stages a producer's raw bits are copied ahead (cp.async)
 constexpr int G = 2;                  // stages a producer publishes per fence
 constexpr uint32_t ACC_COL = 0;       // f32 accumulator: columns [0, 256)
 constexpr uint32_t A_COL = TN;        // A slot s: columns [A_COL + 32 s, A_COL + 32 s + 32)
@@ -65,6 +65,7 @@ constexpr unsigned long long WAIT_NS = 2000000000ull;  // 2 s: far above any leg
 
 struct __align__(1024) TcSmem {
     uint8_t b[STAGES][B_BYTES];
+    uint4 stg[D][NPROD];              // raw bits: producer t's row, stage k at stg[k % D][t]
     int xp[NEPI / 32][16][34];        // per epilogue warp: 16 columns x 32 rows (+2 pad)
     uint64_t full[STAGES];
     uint64_t empty[STAGES];
@@ -74,6 +75,8 @@ struct __align__(1024) TcSmem {
     uint32_t tmem_base;
     int abort;
 };
+
+static_assert(sizeof(TcSmem) + 1024 <= 232448, "shared memory per CTA");
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -108,6 +111,14 @@ __device__ __forceinline__ bool mbar_wait(TcSmem &s, uint64_t *b, uint32_t parit
             }
         }
     }
+}
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 __device__ __forceinline__ void fence_proxy_async() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -279,60 +290,70 @@ pairs_tc_kernel(const uint32_t *__restrict__ bm, const int32_t *__restrict__ per
             const bool store = !(is_a && a_in_b);
             const int item = is_a ? ta * TM + r : tb * TN + r;
             const uint32_t *col = (store && item < mf) ? bm + (int64_t)perm[item] * nwp : nullptr;
-            uint4 cur[PF], nxt[PF];
+            // stage k of the segment is copied into stg[k % D] D stages ahead;
+            // every step commits exactly G copy groups (empty past the end),
+            // so "stages up to k0 + G - 1 have landed" is wait_group(D - G)
+            uint4 *const my = &s.stg[0][threadIdx.x];
 #pragma unroll
-            for (int u = 0; u < PF; u++)
-                cur[u] = (col && u < g.len) ? ldg_u4(col + (g.st + u) * 4) : make_uint4(0, 0, 0, 0);
-            for (int k0 = 0; k0 < g.len && ok; k0 += PF) {
+            for (int k = 0; k < D; k++) {
+                if (col && k < g.len) cp_async16(smem_addr(my + (k % D) * NPROD), col + (g.st + k) * 4);
+                cp_async_commit();
+            }
+            // stages go out in pairs: both slots are filled, then one fence
+            // (proxy or tensor-memory) publishes both, so a producer pays that
+            // round trip once per two stages
+            for (int k0 = 0; k0 < g.len && ok; k0 += G) {
+                const int cnt = min(G, g.len - k0);
+                if (cnt == G) cp_async_wait<D - G>();
+                else cp_async_wait<0>();
+                uint4 x[G];
 #pragma unroll
-                for (int u = 0; u < PF; u++)
-                    nxt[u] = (col && k0 + PF + u < g.len) ? ldg_u4(col + (g.st + k0 + PF + u) * 4)
-                                                          : make_uint4(0, 0, 0, 0);
-                // stages go out in pairs: both slots are filled, then one
-                // fence (proxy or tensor-memory) publishes both, so a
-                // producer pays that round trip once per two stages
-#pragma unroll
-                for (int u0 = 0; u0 < PF; u0 += G) {
-                    const int cnt = min(G, g.len - (k0 + u0));
-                    if (cnt <= 0 || !ok) break;
-                    bool wok = true;  // lane 0 waits for the warp
-                    if (lane == 0) {
-#pragma unroll
-                        for (int v = 0; v < G; v++)
-                            if (v < cnt && wok) {
-                                const int sl = (it + v) % STAGES;
-                                wok = mbar_wait(s, &s.empty[sl], ((uint32_t)((it + v) / STAGES) & 1u) ^ 1u);
-                            }
-                    }
-                    ok = __shfl_sync(0xffffffffu, wok, 0);
-                    if (!ok) break;
-                    if (is_a) {
-                        if (store) {  // warp-uniform: a warp's 32 rows are all A or all B
-                            tc_fence_after();  // after the MMAs that read these slots
-#pragma unroll
-                            for (int v = 0; v < G; v++)
-                                if (v < cnt)
-                                    store_row_tmem(tmem + ((uint32_t)(warp * 32) << 16) +
-                                                       (A_COL + (uint32_t)((it + v) % STAGES) * A_SLOT_COLS),
-                                                   cur[u0 + v]);
-                            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-                            tc_fence_before();
-                        }
-                    } else {
-#pragma unroll
-                        for (int v = 0; v < G; v++)
-                            if (v < cnt) store_row(s.b[(it + v) % STAGES], r, cur[u0 + v]);
-                        fence_proxy_async();
-                    }
-                    __syncwarp();  // the warp's stores are fenced: lane 0 arrives for it
+                for (int v = 0; v < G; v++)
+                    x[v] = (col && v < cnt) ? my[((k0 + v) % D) * NPROD] : make_uint4(0, 0, 0, 0);
+                bool wok = true;  // lane 0 waits for the warp
+                if (lane == 0) {
 #pragma unroll
                     for (int v = 0; v < G; v++)
-                        if (v < cnt && lane == 0) mbar_arrive(&s.full[(it + v) % STAGES]);
-                    it += cnt;
+                        if (v < cnt && wok) {
+                            const int sl = (it + v) % STAGES;
+                            wok = mbar_wait(s, &s.empty[sl], ((uint32_t)((it + v) / STAGES) & 1u) ^ 1u);
+                        }
                 }
+                ok = __shfl_sync(0xffffffffu, wok, 0);
+                if (!ok) break;
+                if (is_a) {
+                    if (store) {  // warp-uniform: a warp's 32 rows are all A or all B
+                        tc_fence_after();  // after the MMAs that read these slots
 #pragma unroll
-                for (int u = 0; u < PF; u++) cur[u] = nxt[u];
+                        for (int v = 0; v < G; v++)
+                            if (v < cnt)
+                                store_row_tmem(tmem + ((uint32_t)(warp * 32) << 16) +
+                                                   (A_COL + (uint32_t)((it + v) % STAGES) * A_SLOT_COLS),
+                                               x[v]);
+                        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+                        tc_fence_before();
+                    }
+                } else {
+#pragma unroll
+                    for (int v = 0; v < G; v++)
+                        if (v < cnt) store_row(s.b[(it + v) % STAGES], r, x[v]);
+                    fence_proxy_async();
+                }
+                __syncwarp();  // the warp's stores are fenced: lane 0 arrives for it
+#pragma unroll
+                for (int v = 0; v < G; v++)
+                    if (v < cnt && lane == 0) mbar_arrive(&s.full[(it + v) % STAGES]);
+                it += cnt;
+                // refill the staging slots just read (x[] has been consumed by
+                // the stores above, so the copies cannot overtake the reads)
+#pragma unroll
+                for (int v = 0; v < G; v++) {
+                    const int k = k0 + D + v;
+                    if (col && k < g.len) cp_async16(smem_addr(my + (k % D) * NPROD), col + (g.st + k) * 4);
+                    cp_async_commit();
+                }
             }
+            cp_async_wait<0>();  // the staging slots serve the next segment
         }
     } else if (warp < (NPROD + NEPI) / 32) {
         // ---------------- epilogue ----------------

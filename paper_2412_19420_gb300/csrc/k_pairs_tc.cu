@@ -290,68 +290,80 @@ pairs_tc_kernel(const uint32_t *__restrict__ bm, const int32_t *__restrict__ per
             const bool store = !(is_a && a_in_b);
             const int item = is_a ? ta * TM + r : tb * TN + r;
             const uint32_t *col = (store && item < mf) ? bm + (int64_t)perm[item] * nwp : nullptr;
-            // stage k of the segment is copied into stg[k % D] D stages ahead;
-            // every step commits exactly G copy groups (empty past the end),
-            // so "stages up to k0 + G - 1 have landed" is wait_group(D - G)
+            // Raw bits are staged in shared memory D = 8 stages ahead, refilled
+            // a quad of 4 stages at a time: the warp copies its 32 rows x 64
+            // contiguous bytes (4 lanes per row, 16 B each), so DRAM sees
+            // 64-byte runs however the rows are scattered.  Stage k of the
+            // segment lives in stg[k % D]; one copy group per quad.
             uint4 *const my = &s.stg[0][threadIdx.x];
+            const int row0 = threadIdx.x - lane;  // the warp's first producer thread
+            auto refill = [&](int q0) {  // stages [q0, q0 + 4) of the segment
 #pragma unroll
-            for (int k = 0; k < D; k++) {
-                if (col && k < g.len) cp_async16(smem_addr(my + (k % D) * NPROD), col + (g.st + k) * 4);
+                for (int i = 0; i < 4; i++) {
+                    const int piece = i * 32 + lane, rw = piece >> 2, k = q0 + (piece & 3);
+                    const uint32_t *c = reinterpret_cast<const uint32_t *>(
+                        __shfl_sync(0xffffffffu, reinterpret_cast<uintptr_t>(col), rw));
+                    if (c && k < g.len)
+                        cp_async16(smem_addr(&s.stg[k % D][row0 + rw]), c + (g.st + k) * 4);
+                }
                 cp_async_commit();
-            }
-            // stages go out in pairs: both slots are filled, then one fence
-            // (proxy or tensor-memory) publishes both, so a producer pays that
-            // round trip once per two stages
-            for (int k0 = 0; k0 < g.len && ok; k0 += G) {
-                const int cnt = min(G, g.len - k0);
-                if (cnt == G) cp_async_wait<D - G>();
-                else cp_async_wait<0>();
-                uint4 x[G];
+            };
+            refill(0);
+            refill(4);
+            for (int q0 = 0; q0 < g.len && ok; q0 += 4) {
+                cp_async_wait<1>();  // this lane's copies of quad q0 have landed ...
+                __syncwarp();        // ... and so have the other lanes' (they filled my row)
+                // stages go out in pairs: both slots are filled, then one fence
+                // (proxy or tensor-memory) publishes both, so a producer pays
+                // that round trip once per two stages
 #pragma unroll
-                for (int v = 0; v < G; v++)
-                    x[v] = (col && v < cnt) ? my[((k0 + v) % D) * NPROD] : make_uint4(0, 0, 0, 0);
-                bool wok = true;  // lane 0 waits for the warp
-                if (lane == 0) {
+                for (int k0 = q0; k0 < q0 + 4; k0 += G) {
+                    const int cnt = min(G, g.len - k0);
+                    if (cnt <= 0 || !ok) break;
+                    uint4 x[G];
 #pragma unroll
                     for (int v = 0; v < G; v++)
-                        if (v < cnt && wok) {
-                            const int sl = (it + v) % STAGES;
-                            wok = mbar_wait(s, &s.empty[sl], ((uint32_t)((it + v) / STAGES) & 1u) ^ 1u);
-                        }
-                }
-                ok = __shfl_sync(0xffffffffu, wok, 0);
-                if (!ok) break;
-                if (is_a) {
-                    if (store) {  // warp-uniform: a warp's 32 rows are all A or all B
-                        tc_fence_after();  // after the MMAs that read these slots
+                        x[v] = (col && v < cnt) ? my[((k0 + v) % D) * NPROD] : make_uint4(0, 0, 0, 0);
+                    bool wok = true;  // lane 0 waits for the warp
+                    if (lane == 0) {
 #pragma unroll
                         for (int v = 0; v < G; v++)
-                            if (v < cnt)
-                                store_row_tmem(tmem + ((uint32_t)(warp * 32) << 16) +
-                                                   (A_COL + (uint32_t)((it + v) % STAGES) * A_SLOT_COLS),
-                                               x[v]);
-                        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-                        tc_fence_before();
+                            if (v < cnt && wok) {
+                                const int sl = (it + v) % STAGES;
+                                wok = mbar_wait(s, &s.empty[sl], ((uint32_t)((it + v) / STAGES) & 1u) ^ 1u);
+                            }
                     }
-                } else {
+                    ok = __shfl_sync(0xffffffffu, wok, 0);
+                    if (!ok) break;
+                    if (is_a) {
+                        if (store) {  // warp-uniform: a warp's 32 rows are all A or all B
+                            tc_fence_after();  // after the MMAs that read these slots
+#pragma unroll
+                            for (int v = 0; v < G; v++)
+                                if (v < cnt)
+                                    store_row_tmem(tmem + ((uint32_t)(warp * 32) << 16) +
+                                                       (A_COL + (uint32_t)((it + v) % STAGES) * A_SLOT_COLS),
+                                                   x[v]);
+                            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+                            tc_fence_before();
+                        }
+                    } else {
+#pragma unroll
+                        for (int v = 0; v < G; v++)
+                            if (v < cnt) store_row(s.b[(it + v) % STAGES], r, x[v]);
+                        fence_proxy_async();
+                    }
+                    __syncwarp();  // the warp's stores are fenced: lane 0 arrives for it
 #pragma unroll
                     for (int v = 0; v < G; v++)
-                        if (v < cnt) store_row(s.b[(it + v) % STAGES], r, x[v]);
-                    fence_proxy_async();
+                        if (v < cnt && lane == 0) mbar_arrive(&s.full[(it + v) % STAGES]);
+                    it += cnt;
                 }
-                __syncwarp();  // the warp's stores are fenced: lane 0 arrives for it
-#pragma unroll
-                for (int v = 0; v < G; v++)
-                    if (v < cnt && lane == 0) mbar_arrive(&s.full[(it + v) % STAGES]);
-                it += cnt;
-                // refill the staging slots just read (x[] has been consumed by
-                // the stores above, so the copies cannot overtake the reads)
-#pragma unroll
-                for (int v = 0; v < G; v++) {
-                    const int k = k0 + D + v;
-                    if (col && k < g.len) cp_async16(smem_addr(my + (k % D) * NPROD), col + (g.st + k) * 4);
-                    cp_async_commit();
-                }
+                if (!ok) break;
+                // every lane has consumed its row of quad q0 (the stores above
+                // used the values), so the quad's slots can take stages q0 + 8
+                __syncwarp();
+                refill(q0 + D);
             }
             cp_async_wait<0>();  // the staging slots serve the next segment
         }

@@ -337,6 +337,7 @@ int mine_once(fim_ctx *ctx, uint32_t thr, uint32_t flags, MineState &ms, bool *r
         p.sparse_div = ctx->sparse_div >= 0 ? ctx->sparse_div
                        : ((double)mf * (double)ctx->nwp * 4.0 > 0.5 * (double)ctx->l2_bytes ? 4 : 0);
         p.epoch = ctx->epoch.as<uint32_t>();
+        p.learned_kmin = ctx->learned_kmin;
         // sparse copies of the low-support item columns, for the root classes
         // (bounded: at most 1 GiB of (index, word) pairs)
         // (a child of a sparse parent is stored sparse: the copies must fit
@@ -356,7 +357,7 @@ int mine_once(fim_ctx *ctx, uint32_t thr, uint32_t flags, MineState &ms, bool *r
         p.learned = (flags & FIM_LEARNED) ? 1 : 0;
         p.diffset_rule = (flags & FIM_DIFFSET_RULE) ? 1 : 0;
         p.mlp_w = ctx->mlp_wbf.as<__nv_bfloat16>();
-        if (p.learned) {
+        if (p.learned && ctx->learned_order) {
             FIM_TRY(launch_root_order(ctx, d_ctr, npairs));
             p.root_order = ctx->root_order.as<uint32_t>();
         }
@@ -504,6 +505,8 @@ int fim_set_tuning(fim_ctx *ctx, const char *key, int64_t v) {
         {"dfs_threads", &ctx->dfs_block, 256, 512},
         {"split_depth", &ctx->split_depth, 0, FIM_TASK_MAXR},
         {"sparse_div", &ctx->sparse_div, -1, 64},
+        {"learned_kmin", &ctx->learned_kmin, 1, 1 << 20},
+        {"learned_order", &ctx->learned_order, 0, 1},
         {"pairs_split", &ctx->pairs_split, 0, 4096},
         {"pairs_kdrain", &ctx->pairs_kdrain, 0, 32768},
     };

@@ -492,6 +492,7 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
         p.spin_limit = kSpinLimitNs;
         p.sparse_div = ctx->sparse_div > 0 ? ctx->sparse_div : 0;  // automatic: dense (small databases)
         p.epoch = ctx->epoch.as<uint32_t>();
+        p.learned_kmin = ctx->learned_kmin;
 
         // graph key: everything the captured launches depend on
         uint64_t key = 1469598103934665603ull;

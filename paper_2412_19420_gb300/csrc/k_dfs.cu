@@ -62,7 +62,7 @@ struct Smem {
     float feat[MAXPATH][NF];             // trace features of the class at each level
     float label[MAXPATH];                // measured representation label
     float mlp_w[FIM_MLP_PARAMS];         // scheduling MLP (bf16 values held as float)
-    float h1[64], h2[64], y[2];
+    float y[2];                          // scheduling MLP output
     uint32_t scan[33];                   // block scan scratch (<= 32 warps)
     unsigned int sec_dense, sec_diff;    // nonzero 32-byte sectors (sparse parent: words) of b_Y and d_Y
     int nsrc;
@@ -511,34 +511,53 @@ __device__ void class_features(Smem &s, int ylen, uint32_t supY, uint32_t supX, 
 // y = MLP(x) with bf16 weights and bf16-rounded activations, fp32 sums
 // (the same arithmetic as the bf16 mode of fim_mlp_forward).  Result in s.y.
 __device__ void mlp_infer(Smem &s, const float *x) {
-    const float *W1 = s.mlp_w, *b1 = W1 + 64 * 8, *W2 = b1 + 64, *b2 = W2 + 64 * 64, *W3 = b2 + 64,
+    // shared-memory copy: W1 and W2 transposed ([in][out]) so that the lanes
+    // of one warp read consecutive words; b1, b2, W3, b3 as stored
+    const float *W1t = s.mlp_w, *b1 = W1t + 64 * 8, *W2t = b1 + 64, *b2 = W2t + 64 * 64, *W3 = b2 + 64,
                 *b3 = W3 + 2 * 64;
-    const int t = threadIdx.x;
-    if (t < 64) {
-        float a = b1[t];
+    if (threadIdx.x < 32) {  // one warp; lane l owns hidden units l and l + 32
+        const int l = threadIdx.x;
+        float a0 = b1[l], a1 = b1[l + 32];
 #pragma unroll
-        for (int i = 0; i < 8; i++) a = fmaf(W1[t * 8 + i], bf16r(x[i]), a);
-        s.h1[t] = bf16r(fmaxf(a, 0.f));
-    }
-    __syncthreads();
-    if (t < 64) {
-        float a = b2[t];
-        for (int i = 0; i < 64; i++) a = fmaf(W2[t * 64 + i], s.h1[i], a);
-        s.h2[t] = bf16r(fmaxf(a, 0.f));
-    }
-    __syncthreads();
-    if (t < 64) {
-        const int o = t >> 5, l = t & 31;
-        float a = W3[o * 64 + l] * s.h2[l] + W3[o * 64 + l + 32] * s.h2[l + 32];
-        for (int d = 16; d > 0; d >>= 1) a += __shfl_xor_sync(0xffffffffu, a, d);
-        if (l == 0) s.y[o] = a + b3[o];
+        for (int i = 0; i < 8; i++) {
+            const float xi = bf16r(x[i]);
+            a0 = fmaf(W1t[i * 64 + l], xi, a0);
+            a1 = fmaf(W1t[i * 64 + l + 32], xi, a1);
+        }
+        const float h1a = bf16r(fmaxf(a0, 0.f)), h1b = bf16r(fmaxf(a1, 0.f));
+        float c0 = b2[l], c1 = b2[l + 32];
+#pragma unroll 8
+        for (int i = 0; i < 32; i++) {  // inputs 0..31 (lane i's first unit), in order
+            const float hi = __shfl_sync(0xffffffffu, h1a, i);
+            c0 = fmaf(W2t[i * 64 + l], hi, c0);
+            c1 = fmaf(W2t[i * 64 + l + 32], hi, c1);
+        }
+#pragma unroll 8
+        for (int i = 0; i < 32; i++) {  // inputs 32..63
+            const float hi = __shfl_sync(0xffffffffu, h1b, i);
+            c0 = fmaf(W2t[(32 + i) * 64 + l], hi, c0);
+            c1 = fmaf(W2t[(32 + i) * 64 + l + 32], hi, c1);
+        }
+        const float h2a = bf16r(fmaxf(c0, 0.f)), h2b = bf16r(fmaxf(c1, 0.f));
+        float y0 = W3[l] * h2a + W3[l + 32] * h2b;
+        float y1 = W3[64 + l] * h2a + W3[64 + l + 32] * h2b;
+        for (int d = 16; d > 0; d >>= 1) {
+            y0 += __shfl_xor_sync(0xffffffffu, y0, d);
+            y1 += __shfl_xor_sync(0xffffffffu, y1, d);
+        }
+        if (l == 0) {
+            s.y[0] = y0 + b3[0];
+            s.y[1] = y1 + b3[1];
+        }
     }
     __syncthreads();
 }
 
 // Representation of class Y before its pass: 1 = count through the diffset.
-__device__ int choose_diff(const DfsParams &p, Smem &s, const float *feat, uint32_t supY, uint32_t supX) {
+__device__ int choose_diff(const DfsParams &p, Smem &s, const float *feat, uint32_t supY, uint32_t supX,
+                           bool infer) {
     if (p.learned) {
+        if (!infer) return 0;  // too few candidates for the choice to matter: dense
         mlp_infer(s, feat);
         return s.y[1] > 0.f;
     }
@@ -649,8 +668,16 @@ dfs_kernel(const DfsParams p) {
     uint32_t *fs = p.frame_sups + (int64_t)wid * p.frame_pool;
     uint32_t *stk = p.stack_bits + (int64_t)wid * p.depth_cap * p.nwp_max;
     if (p.learned)
-        for (int i = threadIdx.x; i < FIM_MLP_PARAMS; i += NT) s.mlp_w[i] = __bfloat162float(p.mlp_w[i]);
-    const bool want_feat = p.learned || p.trace;
+        for (int i = threadIdx.x; i < FIM_MLP_PARAMS; i += NT) {
+            // W1 [64][8] and W2 [64][64] are stored [out][in]; keep them [in][out]
+            int d = i;
+            if (i < 64 * 8) d = (i % 8) * 64 + i / 8;
+            else if (i >= 64 * 8 + 64 && i < 64 * 8 + 64 + 64 * 64) {
+                const int k = i - (64 * 8 + 64);
+                d = 64 * 8 + 64 + (k % 64) * 64 + k / 64;
+            }
+            s.mlp_w[d] = __bfloat162float(p.mlp_w[i]);
+        }
     // thread 0's timing state lives in shared memory, not in every thread's registers
     if (threadIdx.x == 0) {
         s.busy = 0;
@@ -743,8 +770,11 @@ dfs_kernel(const DfsParams p) {
             // a root {a, b} has parent {a}: b_X = col(a), S(X) = S({a})
             const uint32_t supX =
                 root ? (uint32_t)__ldg(s.db.item_sup + __ldg(s.db.perm + s.path[0])) : s.task_sup;
-            if (want_feat) class_features(s, tlen, s.task_sup, supX, fs, root ? k : 0, s.feat[0]);
-            const int diff = root ? choose_diff(p, s, s.feat[0], s.task_sup, supX) : 0;
+            // the network is consulted only where its choice can pay for the
+            // inference: classes with at least learned_kmin candidates
+            const bool infer = p.learned && root && k >= p.learned_kmin;
+            if (p.trace || infer) class_features(s, tlen, s.task_sup, supX, fs, root ? k : 0, s.feat[0]);
+            const int diff = root ? choose_diff(p, s, s.feat[0], s.task_sup, supX, infer) : 0;
             if (threadIdx.x == 0) {
                 for (int r = 0; r < tlen; r++) s.src[r] = column(s.db, s.path[r]);
                 s.nsrc = tlen;
@@ -844,8 +874,9 @@ dfs_kernel(const DfsParams p) {
                 }
                 // descend: b_child = b_parent AND col(citem)
                 const uint32_t supX = s.supY[L];
-                if (want_feat) class_features(s, plen + 1, csup, supX, fs + bC, kc, s.feat[L + 1]);
-                const int diff = choose_diff(p, s, s.feat[L + 1], csup, supX);
+                const bool infer = p.learned && kc >= p.learned_kmin;
+                if (p.trace || infer) class_features(s, plen + 1, csup, supX, fs + bC, kc, s.feat[L + 1]);
+                const int diff = choose_diff(p, s, s.feat[L + 1], csup, supX, infer);
                 if (threadIdx.x == 0) {
                     uint32_t *lv = stk + (int64_t)L * p.nwp_max;  // b_X, the class at level L
                     s.path[plen] = citem;

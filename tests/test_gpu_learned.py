@@ -6,7 +6,8 @@ miner's traces of one planted database and judged on a held-out one:
   * its work and representation predictions beat the trivial predictors,
     scored against the plain miner's measured traces;
   * the learned miner streams fewer bytes than the plain miner (diffset
-    classes skip the sectors a dense bitmap would read).
+    classes skip the sectors a dense bitmap would read);
+  * the root order from the network's work prediction is exact too.
 """
 import numpy as np
 import pytest
@@ -56,8 +57,17 @@ def test_learned_miner_is_exact_and_streams_fewer_bytes(trained):
     held = datagen.planted(n=20_000, m=800, n_patterns=60, seed=5)
     want = oracle.apriori(held.indptr, held.indices, held.m, 100)
     plain, sp = _mine(ctx, held, 100, fim.FIM_NO_SPLIT)
-    learned, sl = _mine(ctx, held, 100, fim.FIM_LEARNED | fim.FIM_NO_SPLIT)
+    # every class consults the network (by default only classes with >= 8
+    # candidates do, where the choice can pay for the inference)
+    fim.fim_set_tuning(ctx, "learned_kmin", 1)
+    try:
+        learned, sl = _mine(ctx, held, 100, fim.FIM_LEARNED | fim.FIM_NO_SPLIT)
+    finally:
+        fim.fim_set_tuning(ctx, "learned_kmin", 8)
     rule, sr = _mine(ctx, held, 100, fim.FIM_DIFFSET_RULE | fim.FIM_NO_SPLIT)
+    default, sd = _mine(ctx, held, 100, fim.FIM_LEARNED | fim.FIM_NO_SPLIT)
+    assert default.sha256() == want.sha256()
+    assert sd["dfs_touched_bytes"] <= sp["dfs_touched_bytes"]
     assert plain.sha256() == want.sha256()
     assert learned.sha256() == want.sha256()
     assert rule.sha256() == want.sha256()
@@ -66,3 +76,16 @@ def test_learned_miner_is_exact_and_streams_fewer_bytes(trained):
     # miner, and about as few as the closed-form size rule
     assert sl["dfs_touched_bytes"] < 0.9 * sp["dfs_touched_bytes"], (sl, sp)
     assert sl["dfs_touched_bytes"] < 1.05 * sr["dfs_touched_bytes"], (sl, sr)
+
+
+def test_learned_root_order_is_exact(trained):
+    ctx, w, _ = trained
+    fim.fim_sched_load_weights(ctx, w)
+    held = datagen.planted(n=20_000, m=800, n_patterns=60, seed=5)
+    want = oracle.apriori(held.indptr, held.indices, held.m, 100)
+    fim.fim_set_tuning(ctx, "learned_order", 1)
+    try:
+        got, _ = _mine(ctx, held, 100, fim.FIM_LEARNED)
+    finally:
+        fim.fim_set_tuning(ctx, "learned_order", 0)
+    assert got.sha256() == want.sha256()

@@ -52,6 +52,9 @@ def _args():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOAD_DESC))
     ap.add_argument("--flags", type=int, default=0, help="extra fim_mine flags")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--learned", action="store_true",
+                    help="single database: mine with FIM_LEARNED, the network trained on the GPU "
+                         "from plain-miner traces of the same generator at another seed")
     return ap.parse_args()
 
 
@@ -351,10 +354,15 @@ def main():
     csr, minsup = _load_workload(args.workload)
     stream = torch.cuda.Stream()
     ctx = fim.fim_create(local, stream)
+    training = None
+    if args.learned:
+        from paper_2412_19420_gb300 import datagen, sched
+        fn, _ = datagen.WORKLOADS[args.workload]
+        training = _train_scheduler(ctx, fim, sched, datagen, [(fn(seed=1), minsup)])
     ip_d = torch.from_numpy(csr.indptr).cuda()
     ix_d = torch.from_numpy(csr.indices).cuda()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
-    flags = args.flags
+    flags = args.flags | (fim.FIM_LEARNED if args.learned else 0)
 
     def mine_device(out):
         fim.fim_build_bitmaps(ctx, ip_d, ix_d, csr.m)
@@ -464,6 +472,7 @@ def main():
         "data": "synthetic (seeded generator, paper_2412_19420_gb300.datagen)",
         "config": {"workload": args.workload, "desc": WORKLOAD_DESC[args.workload],
                    "n_trans": csr.n, "n_items": csr.m, "minsup": minsup, "flags": flags,
+                   "scheduler_training": training,
                    "parallelism": f"replicas x{world}",
                    "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write)",
                    "frequent_itemsets": int(st["n_sets"]), "max_len": int(st["max_len"]),

@@ -83,6 +83,8 @@ struct Smem {
     unsigned long long rbase, ibase;
     int flag;
     int hungry;
+    int kc;                              // candidates of the child being set up (-1: overflow)
+    int ftot;                            // frequent candidates of a small batch
     int stop;
     int task_len;
     uint32_t task_sup;
@@ -402,7 +404,6 @@ __device__ __forceinline__ void sparse_sweep(const DfsParams &p, Smem &s, int kb
 template <int NT>
 __device__ int class_pass(const DfsParams &p, Smem &s, const uint32_t *cand, const uint32_t *psup,
                           int k, int plen, uint32_t *fi, uint32_t *fs) {
-    constexpr int NWARP = NT / 32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const DbView &db = s.db;
     const int nsrc = s.nsrc;
@@ -424,6 +425,51 @@ __device__ int class_pass(const DfsParams &p, Smem &s, const uint32_t *cand, con
         if (sparse_parent) sparse_sweep<NT>(p, s, kb, b0 == 0);
         else dense_sweep<NT>(p, s, kb, b0 == 0);
         __syncthreads();
+        if (kb <= 32) {
+            // few candidates (the common case): warp 0 alone, one ballot, no
+            // block-wide scan
+            if (warp == 0) {
+                uint32_t item = 0, sup = 0;
+                bool f = false;
+                if (lane < kb) {
+                    item = cand[b0 + lane];
+                    sup = diff ? psup[b0 + lane] - s.sup[lane] : s.sup[lane];
+                    f = sup >= db.thr;
+                }
+                const uint32_t bal = __ballot_sync(0xffffffffu, f);
+                const uint32_t tot = __popc(bal);
+                if (tot) {
+                    unsigned long long rb = 0, ib = 0;
+                    if (lane == 0) {
+                        rb = atomicAdd(&p.ctr->n_records, (unsigned long long)tot);
+                        ib = atomicAdd(&p.ctr->n_rec_items, (unsigned long long)tot * (plen + 1));
+                    }
+                    rb = __shfl_sync(0xffffffffu, rb, 0);
+                    ib = __shfl_sync(0xffffffffu, ib, 0);
+                    if (f) {
+                        const uint32_t pos = __popc(bal & ((1u << lane) - 1u));
+                        fi[nF + pos] = item;
+                        fs[nF + pos] = sup;
+                        const unsigned long long r = rb + pos;
+                        const unsigned long long it = ib + (unsigned long long)pos * (plen + 1);
+                        if (r < p.rec_cap && it + plen + 1 <= p.rec_items_cap) {
+                            p.rec_off[r] = it;
+                            p.rec_len[r] = (uint32_t)(plen + 1);
+                            p.rec_sup[r] = sup;
+                            p.rec_db[r] = db.id;
+                            for (int q = 0; q < plen; q++) p.rec_items[it + q] = s.path[q];
+                            p.rec_items[it + plen] = item;
+                        } else {
+                            atomicOr(&p.ctr->overflow, r < p.rec_cap ? 2 : 1);
+                        }
+                    }
+                }
+                if (lane == 0) s.ftot = (int)tot;
+            }
+            __syncthreads();
+            nF += s.ftot;
+            continue;  // kb <= 32 < CB: this was the class's only batch
+        }
         // compact the frequent candidates of this batch, in order
         for (int c0 = 0; c0 < kb; c0 += NT) {
             const int c = c0 + threadIdx.x;
@@ -664,6 +710,7 @@ dfs_kernel(const DfsParams p) {
     extern __shared__ __align__(16) uint8_t dyn_smem[];
     Smem &s = *reinterpret_cast<Smem *>(dyn_smem);
     const int wid = blockIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t *fi = p.frame_items + (int64_t)wid * p.frame_pool;
     uint32_t *fs = p.frame_sups + (int64_t)wid * p.frame_pool;
     uint32_t *stk = p.stack_bits + (int64_t)wid * p.depth_cap * p.nwp_max;
@@ -827,9 +874,7 @@ dfs_kernel(const DfsParams p) {
                     L--;
                     continue;
                 }
-                const int j = s.cur[L];
-                __syncthreads();
-                if (threadIdx.x == 0) s.cur[L] = j + 1;
+                const int j = s.cur[L];  // thread 0 advances cur[L] after the barrier below
                 const int plen = tlen + L;          // prefix length at level L
                 const long long bL = s.base[L];
                 const long long bC = s.base[L + 1]; // child's candidates go here
@@ -839,35 +884,61 @@ dfs_kernel(const DfsParams p) {
                 // each with its support in this class (the child's parent)
                 int kc = 0;
                 const int nFL = s.nF[L];
-                bool overflow = false;
-                for (int l0 = j + 1; l0 < nFL; l0 += NT) {
-                    const int l = l0 + threadIdx.x;
-                    uint32_t d = 0, ds = 0, f = 0;
-                    if (l < nFL) { d = fi[bL + l]; ds = fs[bL + l]; f = pairbit(s.db, citem, d); }
-                    uint32_t tot;
-                    const uint32_t pos = block_scan<NT>(s, f, &tot);
-                    if (bC + kc + (long long)tot > p.frame_pool) { overflow = true; break; }
-                    if (f) { fi[bC + kc + pos] = d; fs[bC + kc + pos] = ds; }
-                    kc += (int)tot;
+                const bool may_push = plen + 1 <= p.split_depth && plen + 1 <= FIM_TASK_MAXR;
+                if (nFL - (j + 1) <= 32) {
+                    // few siblings: warp 0 alone, compacted with a ballot
+                    if (warp == 0) {
+                        const int l = j + 1 + lane;
+                        uint32_t d = 0, ds = 0;
+                        bool f = false;
+                        if (l < nFL) { d = fi[bL + l]; ds = fs[bL + l]; f = pairbit(s.db, citem, d); }
+                        const uint32_t bal = __ballot_sync(0xffffffffu, f);
+                        const int tot = __popc(bal);
+                        if (bC + (long long)tot > p.frame_pool) {
+                            if (lane == 0) { set_err(p, FIM_E_STACK); s.kc = -1; }
+                        } else {
+                            if (f) {
+                                const int pos = __popc(bal & ((1u << lane) - 1u));
+                                fi[bC + pos] = d;
+                                fs[bC + pos] = ds;
+                            }
+                            if (lane == 0) s.kc = tot;
+                        }
+                    }
+                } else {
+                    bool overflow = false;
+                    for (int l0 = j + 1; l0 < nFL; l0 += NT) {
+                        const int l = l0 + threadIdx.x;
+                        uint32_t d = 0, ds = 0, f = 0;
+                        if (l < nFL) { d = fi[bL + l]; ds = fs[bL + l]; f = pairbit(s.db, citem, d); }
+                        uint32_t tot;
+                        const uint32_t pos = block_scan<NT>(s, f, &tot);
+                        if (bC + kc + (long long)tot > p.frame_pool) { overflow = true; break; }
+                        if (f) { fi[bC + kc + pos] = d; fs[bC + kc + pos] = ds; }
+                        kc += (int)tot;
+                    }
+                    if (threadIdx.x == 0) {
+                        if (overflow) set_err(p, FIM_E_STACK);
+                        s.kc = overflow ? -1 : kc;
+                    }
                 }
-                if (overflow) { if (threadIdx.x == 0) set_err(p, FIM_E_STACK); break; }
+                if (threadIdx.x == 0 && may_push) {
+                    // the queue's hunger and the error flag: three loads, one
+                    // round trip, published by the barrier below (s.hungry,
+                    // not s.flag: thread 0 rewrites s.flag inside try_push)
+                    const int e = *(volatile int *)&p.ctr->err;
+                    const unsigned long long t = *(volatile unsigned long long *)&p.ctr->ticket;
+                    const unsigned long long q = *(volatile unsigned long long *)&p.ctr->qtail;
+                    s.hungry = t > s.n_roots + q;
+                    s.err_seen = e;
+                }
                 __syncthreads();
+                kc = s.kc;
+                if (threadIdx.x == 0) s.cur[L] = j + 1;  // every thread has read cur[L]
+                if (kc < 0) break;
                 if (kc == 0) continue;
                 if (maxlen && (uint32_t)plen + 2 > maxlen) continue;
-                if (plen + 1 <= p.split_depth && plen + 1 <= FIM_TASK_MAXR) {
-                    // s.hungry, not s.flag: thread 0 rewrites s.flag inside
-                    // try_push while other warps may still be reading this
-                    if (threadIdx.x == 0) {
-                        // three loads, one round trip
-                        const int e = *(volatile int *)&p.ctr->err;
-                        const unsigned long long t = *(volatile unsigned long long *)&p.ctr->ticket;
-                        const unsigned long long q = *(volatile unsigned long long *)&p.ctr->qtail;
-                        s.hungry = t > s.n_roots + q;
-                        s.err_seen = e;
-                    }
-                    __syncthreads();
-                    if (s.hungry && try_push<NT>(p, s, plen, citem, csup, fi + bC, kc)) continue;
-                }
+                if (may_push && s.hungry && try_push<NT>(p, s, plen, citem, csup, fi + bC, kc)) continue;
                 if (L + 1 >= p.depth_cap || plen + 1 >= MAXPATH) {
                     if (threadIdx.x == 0) set_err(p, FIM_E_STACK);
                     break;
@@ -902,7 +973,7 @@ dfs_kernel(const DfsParams p) {
                     s.base[L + 2] = bC + nF;
                     s.label[L + 1] = s.sec_diff < s.sec_dense ? 1.f : 0.f;
                 }
-                __syncthreads();
+                // (the barrier at the top of the loop publishes these)
                 L++;
             }
         }

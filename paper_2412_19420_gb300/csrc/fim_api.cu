@@ -338,6 +338,7 @@ int mine_once(fim_ctx *ctx, uint32_t thr, uint32_t flags, MineState &ms, bool *r
                        : ((double)mf * (double)ctx->nwp * 4.0 > 0.5 * (double)ctx->l2_bytes ? 4 : 0);
         p.epoch = ctx->epoch.as<uint32_t>();
         p.learned_kmin = ctx->learned_kmin;
+        p.root_reverse = ctx->root_reverse;
         // sparse copies of the low-support item columns, for the root classes
         // (bounded: at most 1 GiB of (index, word) pairs)
         // (a child of a sparse parent is stored sparse: the copies must fit
@@ -507,6 +508,7 @@ int fim_set_tuning(fim_ctx *ctx, const char *key, int64_t v) {
         {"sparse_div", &ctx->sparse_div, -1, 64},
         {"learned_kmin", &ctx->learned_kmin, 1, 1 << 20},
         {"learned_order", &ctx->learned_order, 0, 1},
+        {"root_reverse", &ctx->root_reverse, 0, 1},
         {"pairs_split", &ctx->pairs_split, 0, 4096},
         {"pairs_kdrain", &ctx->pairs_kdrain, 0, 32768},
     };

@@ -168,6 +168,7 @@ struct DfsParams {
     unsigned long long spin_limit;  // bounded waits (iterations)
     int sparse_div;                 // store b_Y sparse when S(Y) * sparse_div <= nw (0: never)
     int learned_kmin;               // FIM_LEARNED consults the network for classes with >= this many candidates
+    int root_reverse;               // hand out the root classes in reverse emission order
 };
 
 // ---------------------------------------------------------------- the ctx
@@ -233,6 +234,7 @@ struct fim_ctx {
     int sparse_div = -1;        // -1: automatic (frequent columns vs L2)
     int learned_kmin = 8;
     int learned_order = 0;      // 1: FIM_LEARNED also orders roots longest-predicted-first
+    int root_reverse = 0;
     int l2_bytes = 0;
     int pairs_split = 0;        // split-K factor of the tensor-core pair pass (0 = auto)
     int pairs_kdrain = 0;       // stages (x128 transactions) per exact drain (0 = 64)

@@ -86,6 +86,70 @@ batch_build_kernel(const DbDesc *__restrict__ dbs, int n_db, const int64_t *__re
         col0[(int64_t)(i0 + k / WB) * D.nwp + w0 + k % WB] = tile[k];
 }
 
+// Databases with at most 1,024 items: one CTA per 1,024-transaction block of
+// one database holds the block's 32 words of every item column in shared
+// memory.  Each thread takes whole rows (no search for a row's position),
+// sets its rows' bits with shared atomics, then the block is written out
+// coalesced (128 bytes per column) and each column's popcount over the block
+// is added into S(I_j) (Eq. 3): no second pass reads the columns.
+__global__ void __launch_bounds__(256)
+batch_build_rows_kernel(const DbDesc *__restrict__ dbs, int n_db, const int64_t *__restrict__ unit_prefix,
+                        uint32_t *__restrict__ bm, uint32_t *__restrict__ sup, int *__restrict__ flag) {
+    // [WB][m + 1]: a warp's 32 consecutive rows share their word, so the
+    // word-major layout (padded) spreads their items' bits over the banks
+    extern __shared__ uint32_t tile[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int d = find_db(unit_prefix, n_db, blockIdx.x);
+    const DbDesc &D = dbs[d];
+    const int m = D.m, ms = m + 1;
+    const int64_t w0 = (int64_t)(blockIdx.x - unit_prefix[d]) * WB;
+    const int64_t n = D.n;
+    const int64_t nnz = n > 0 ? D.indptr[n] : 0;
+    const int64_t t0 = w0 * 32, t1 = min64(n, t0 + WB * 32);
+    for (int k = threadIdx.x; k < ms * WB; k += blockDim.x) tile[k] = 0u;
+    __syncthreads();
+    int bad = 0;
+    // warp w takes rows in groups of 32 (one tile word): lane i holds the
+    // group's row start i, the warp streams the group's elements 32 at a
+    // time (coalesced), and each element finds its row by a binary search
+    // over the lanes' starts
+    for (int64_t rb = t0 + 32 * warp; rb < t1; rb += 32 * (int64_t)(blockDim.x >> 5)) {
+        const int nr = (int)min64(32, t1 - rb);
+        const int64_t off = D.indptr[rb + (lane < nr ? lane : nr)];  // lane i < nr: start of row i
+        const int64_t e_end = D.indptr[rb + nr];                       // the group's end (broadcast)
+        int64_t off_next = __shfl_down_sync(0xffffffffu, off, 1);
+        if (lane == nr - 1) off_next = e_end;
+        if (lane < nr && (off_next < off || off < 0 || off_next > nnz)) bad = 1;
+        const int64_t e_begin = __shfl_sync(0xffffffffu, off, 0);
+        if (__any_sync(0xffffffffu, bad)) continue;  // a malformed group: flagged, not read
+        const uint32_t wl = (uint32_t)((rb - t0) >> 5);
+        for (int64_t e0 = max64(0, e_begin); e0 < min64(nnz, e_end); e0 += 32) {
+            const int64_t e = e0 + lane;
+            const bool v = e < min64(nnz, e_end);
+            const int32_t it = v ? D.indices[e] : 0;
+            int r = 0;  // largest r < nr with start(r) <= e
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1) {
+                const int c = r + step;
+                const int64_t oc = __shfl_sync(0xffffffffu, off, c < 32 ? c : 31);
+                if (c < nr && oc <= e) r = c;
+            }
+            if (!v) continue;
+            if (it < 0 || it >= m) { bad = 1; continue; }
+            atomicOr(&tile[wl * ms + it], 1u << r);
+        }
+    }
+    if (bad) atomicExch(flag, 1);
+    __syncthreads();
+    uint32_t *col0 = bm + D.bm_off;
+    for (int k = threadIdx.x; k < m * WB; k += blockDim.x)
+        col0[(int64_t)(k / WB) * D.nwp + w0 + k % WB] = tile[(k % WB) * ms + k / WB];
+    for (int j = warp; j < m; j += (int)(blockDim.x >> 5)) {  // WB == 32: one word per lane
+        const uint32_t c = warp_sum_u32(__popc(tile[lane * ms + j]));
+        if (lane == 0 && c) atomicAdd(&sup[D.item_off + j], c);
+    }
+}
+
 // One CTA per item column of the batch: S(I_j) by popcount.
 __global__ void __launch_bounds__(256)
 batch_support_kernel(const DbDesc *__restrict__ dbs, int n_db, const int64_t *__restrict__ item_prefix,
@@ -204,23 +268,26 @@ batch_pairs_kernel(const DbDesc *__restrict__ dbs, int n_db, const int64_t *__re
         }
 }
 
-// One CTA per (database, row a): threshold, pair bitset, pair records, roots.
+// One warp per (database, row a): threshold, pair bitset, pair records, roots.
 __global__ void __launch_bounds__(256)
 batch_finalize_kernel(const DbDesc *__restrict__ dbs, int n_db, const int64_t *__restrict__ item_prefix,
+                      int64_t n_items,
                       const int *__restrict__ pair_cnt, uint32_t *__restrict__ pairbits, MineCounters *ctr,
                       unsigned long long *rec_off, uint32_t *rec_len, uint32_t *rec_sup, uint32_t *rec_items,
                       uint32_t *rec_db, unsigned long long rec_cap, unsigned long long items_cap,
                       uint32_t *root_a, uint32_t *root_b, uint32_t *root_sup, uint32_t *root_db) {
-    const int d = find_db(item_prefix, n_db, blockIdx.x);
+    const int lane = threadIdx.x & 31;
+    const int64_t gi = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (gi >= n_items) return;
+    const int d = find_db(item_prefix, n_db, gi);
     const DbDesc &D = dbs[d];
-    const int a = (int)(blockIdx.x - item_prefix[d]);
+    const int a = (int)(gi - item_prefix[d]);
     const int mf = *(volatile const int32_t *)&D.mfreq;
     if (a >= mf) return;
     const int mpw = (mf + 31) / 32;
     const int *row = pair_cnt + D.pair_off + (int64_t)a * mf;
     const bool emit = D.maxlen == 0 || D.maxlen >= 2;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-    for (int w = warp; w < mpw; w += nwarp) {
+    for (int w = 0; w < mpw; w++) {
         const int b = w * 32 + lane;
         const uint32_t s = (b > a && b < mf) ? (uint32_t)row[b] : 0u;
         const bool f = emit && b > a && b < mf && s >= D.thr;
@@ -493,6 +560,7 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
         p.sparse_div = ctx->sparse_div > 0 ? ctx->sparse_div : 0;  // automatic: dense (small databases)
         p.epoch = ctx->epoch.as<uint32_t>();
         p.learned_kmin = ctx->learned_kmin;
+        p.root_reverse = ctx->root_reverse;
 
         // graph key: everything the captured launches depend on
         uint64_t key = 1469598103934665603ull;
@@ -508,6 +576,8 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
         const size_t smem_build = (size_t)L.ib * WB * sizeof(uint32_t);
         FIM_CUDA_TRY(cudaFuncSetAttribute(batch_build_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)smem_build));
+        FIM_CUDA_TRY(cudaFuncSetAttribute(batch_build_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)((size_t)(L.m_max + 1) * WB * sizeof(uint32_t))));
         const bool reuse = ctx->batch_graph_exec && ctx->batch_graph_key == key;
         if (!reuse) {
             if (ctx->batch_graph_exec) {
@@ -520,13 +590,26 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
             cudaMemsetAsync(ctx->dev_flag.p, 0, sizeof(int), st);
             launch_epoch_bump(ctx);
             const int64_t units = L.unit_prefix[n_db], items = L.item_prefix[n_db], tiles = L.tile_prefix[n_db];
-            if (units > 0)
-                batch_build_kernel<<<(unsigned)units, 256, smem_build, st>>>(d_dbs, n_db, d_unit, L.ib,
-                                                                             ctx->bm.as<uint32_t>(),
-                                                                             ctx->dev_flag.as<int>());
+            // rows-per-thread build with fused supports when every database's
+            // block of columns fits shared memory (ib == m_max <= 1,024)
+            const bool rows_build = L.ib == L.m_max;
+            const size_t smem_rows = (size_t)(L.m_max + 1) * WB * sizeof(uint32_t);
+            if (rows_build && items > 0)
+                cudaMemsetAsync(ctx->item_sup.p, 0, sizeof(uint32_t) * (size_t)items, st);
+            if (units > 0) {
+                if (rows_build)
+                    batch_build_rows_kernel<<<(unsigned)units, 256, smem_rows, st>>>(
+                        d_dbs, n_db, d_unit, ctx->bm.as<uint32_t>(), ctx->item_sup.as<uint32_t>(),
+                        ctx->dev_flag.as<int>());
+                else
+                    batch_build_kernel<<<(unsigned)units, 256, smem_build, st>>>(
+                        d_dbs, n_db, d_unit, L.ib, ctx->bm.as<uint32_t>(), ctx->dev_flag.as<int>());
+            }
             if (items > 0) {
-                batch_support_kernel<<<(unsigned)items, 256, 0, st>>>(d_dbs, n_db, d_item, ctx->bm.as<uint32_t>(),
-                                                                      ctx->item_sup.as<uint32_t>());
+                if (!rows_build)
+                    batch_support_kernel<<<(unsigned)items, 256, 0, st>>>(d_dbs, n_db, d_item,
+                                                                          ctx->bm.as<uint32_t>(),
+                                                                          ctx->item_sup.as<uint32_t>());
                 batch_rank_kernel<<<(unsigned)ceil_div64(items * 32, 256), 256, 0, st>>>(
                     d_dbs, n_db, d_item, items, ctx->item_sup.as<uint32_t>(), ctx->perm.as<int32_t>(), d_ctr,
                     p.rec_off, p.rec_len, p.rec_sup, p.rec_items, p.rec_db, p.rec_cap, p.rec_items_cap);
@@ -534,8 +617,8 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
             if (tiles > 0 && maxlen != 1) {
                 batch_pairs_kernel<<<(unsigned)tiles, 256, 0, st>>>(d_dbs, n_db, d_tile, ctx->bm.as<uint32_t>(),
                                                                     ctx->perm.as<int32_t>(), ctx->pair_cnt.as<int>());
-                batch_finalize_kernel<<<(unsigned)items, 256, 0, st>>>(
-                    d_dbs, n_db, d_item, ctx->pair_cnt.as<int>(), ctx->pairbits.as<uint32_t>(), d_ctr, p.rec_off,
+                batch_finalize_kernel<<<(unsigned)ceil_div64(items * 32, 256), 256, 0, st>>>(
+                    d_dbs, n_db, d_item, items, ctx->pair_cnt.as<int>(), ctx->pairbits.as<uint32_t>(), d_ctr, p.rec_off,
                     p.rec_len, p.rec_sup, p.rec_items, p.rec_db, p.rec_cap, p.rec_items_cap, roots, roots + rc,
                     roots + 2 * rc, roots + 3 * rc);
             }
@@ -607,6 +690,10 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
         s.classes = c.classes;
         s.tasks_pushed = c.pushed;
         s.diffset_classes = c.diffset;
+        s.dfs_busy_ns = c.busy_ns;
+        s.dfs_root_ns = c.root_ns;
+        s.dfs_span_ns = c.t_last > c.t_first && c.t_first != 0 ? c.t_last - c.t_first : 0;
+        s.dfs_workers = (uint64_t)ctx->num_sms * (uint64_t)ctx->dfs_ctas_per_sm;
         s.launches_build = 0;
         s.launches_mine = ctx->launches - launches0;
         s.pair_path = 0;

@@ -745,7 +745,10 @@ dfs_kernel(const DfsParams p) {
             if (*(volatile int *)&p.ctr->err != 0) {
                 // an error ends the mine: take no more work
             } else if (t < nr) {
-                const unsigned long long rt = p.root_order ? p.root_order[t] : t;
+                // roots come out of the pair pass by ascending first item, i.e.
+                // ascending item support; root_reverse hands out the pairs of
+                // the most frequent items (the largest subtrees) first
+                const unsigned long long rt = p.root_order ? p.root_order[t] : (p.root_reverse ? nr - 1 - t : t);
                 s.path[0] = p.root_a[rt];
                 s.path[1] = p.root_b[rt];
                 s.task_len = 2;

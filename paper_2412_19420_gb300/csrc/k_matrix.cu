@@ -1,13 +1,13 @@
 // k_matrix.cu -- matrix construction (Eq. 1) and singleton support (Eq. 3).
 //
 // build_bitmaps_kernel: one CTA owns a block of WB words (32*WB transactions)
-// and a range of IB items.  It ORs every (transaction, item) pair of its
-// transactions into a shared-memory tile with atomicOr -- OR makes repeated
-// items idempotent, which is the set membership of Eq. 1 -- and then writes
-// the tile out as WB-word (64-byte) runs of each item column with 16-byte
-// stores.  A 64-byte row keeps the tile at 64 KB for 1,024 items, so several
-// CTAs share an SM and their zero / scatter / write phases overlap.  The CTA
-// also validates its slice of the CSR (monotone indptr, items in [0, m)).
+// and a range of IB items.  Each warp streams a 32-row group's elements
+// (coalesced) and ORs every (transaction, item) pair into a shared-memory
+// tile with atomicOr -- OR makes repeated items idempotent, which is the set
+// membership of Eq. 1 -- and the tile goes out as WB-word (64-byte) runs of
+// each item column with 16-byte stores.  A 64-byte run keeps the tile at
+// 64 KB for 1,024 items, so several CTAs share an SM.  The CTA also validates
+// its slice of the CSR (monotone indptr, items in [0, m)).
 #include "fim_common.cuh"
 
 namespace {
@@ -19,40 +19,51 @@ __global__ void __launch_bounds__(BUILD_THREADS)
 build_bitmaps_kernel(const int64_t *__restrict__ indptr, const int32_t *__restrict__ indices,
                      int64_t n, int32_t m, int64_t nnz, int64_t nwp, int ib,
                      uint32_t *__restrict__ bm, int *__restrict__ flag, int *__restrict__ max_len) {
-    extern __shared__ __align__(16) uint32_t tile[];  // [ib][WB]
-    __shared__ int64_t s_ptr[WB * 32 + 1];
+    // [WB][ib + 1], word-major and padded: the 32 rows of a warp's group share
+    // their word, so their items' bits spread over the banks
+    extern __shared__ __align__(16) uint32_t tile[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int ms = ib + 1;
     const int64_t w0 = (int64_t)blockIdx.x * WB;
     const int i0 = blockIdx.y * ib;
     const int icount = min(ib, m - i0);
     const int64_t t0 = w0 * 32;
     const int64_t t1 = min(n, t0 + WB * 32);
 
-    uint4 *tile4 = reinterpret_cast<uint4 *>(tile);  // a row is WB / 4 = 4 uint4
-    for (int k = threadIdx.x; k < icount * (WB / 4); k += blockDim.x) tile4[k] = make_uint4(0, 0, 0, 0);
-    const int rows = t1 > t0 ? (int)(t1 - t0) : 0;
-    int bad = 0, my_max = 0;
-    if (rows > 0)  // rows == 0: a padding block past the last transaction
-        for (int k = threadIdx.x; k <= rows; k += blockDim.x) s_ptr[k] = indptr[t0 + k];
+    for (int k = threadIdx.x; k < WB * ms; k += blockDim.x) tile[k] = 0u;
     __syncthreads();
-    if (rows > 0) {
-        for (int k = threadIdx.x; k < rows; k += blockDim.x) {
-            int64_t a = s_ptr[k], b = s_ptr[k + 1];
-            if (b < a || a < 0 || b > nnz) bad = 1;
-            else my_max = max(my_max, (int)min64(b - a, 1 << 30));
+    int bad = 0, my_max = 0;
+    // warp w takes 32-row groups: lane i holds the group's start of row i, the
+    // warp streams the group's elements 32 at a time (coalesced) and each
+    // element finds its row by a binary search over the lanes' starts
+    for (int64_t rb = t0 + 32 * warp; rb < t1; rb += 32 * (int64_t)(blockDim.x >> 5)) {
+        const int nr = (int)min64(32, t1 - rb);
+        const int64_t off = indptr[rb + (lane < nr ? lane : nr)];
+        const int64_t e_end = indptr[rb + nr];
+        int64_t off_next = __shfl_down_sync(0xffffffffu, off, 1);
+        if (lane == nr - 1) off_next = e_end;
+        if (lane < nr) {
+            if (off_next < off || off < 0 || off_next > nnz) bad = 1;
+            else my_max = max(my_max, (int)min64(off_next - off, 1 << 30));
         }
-        const int64_t e0 = max64(0, s_ptr[0]);
-        const int64_t e1 = min64(nnz, s_ptr[rows]);
-        for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-            int32_t it = indices[e];
+        if (__any_sync(0xffffffffu, bad)) continue;  // malformed: flagged, not read
+        const int64_t e_begin = __shfl_sync(0xffffffffu, off, 0);
+        const uint32_t wl = (uint32_t)((rb - t0) >> 5);
+        for (int64_t e0 = e_begin; e0 < e_end; e0 += 32) {
+            const int64_t e = e0 + lane;
+            const bool v = e < e_end;
+            const int32_t it = v ? indices[e] : 0;
+            int r = 0;  // largest r < nr with start(r) <= e
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1) {
+                const int c = r + step;
+                const int64_t oc = __shfl_sync(0xffffffffu, off, c < 32 ? c : 31);
+                if (c < nr && oc <= e) r = c;
+            }
+            if (!v) continue;
             if (it < 0 || it >= m) { bad = 1; continue; }
             if (it < i0 || it >= i0 + icount) continue;
-            // row r with s_ptr[r] <= e < s_ptr[r+1] (last such r for empty rows)
-            int lo = 0, hi = rows;  // invariant: s_ptr[lo] <= e < s_ptr[hi]
-            while (hi - lo > 1) {
-                int mid = (lo + hi) >> 1;
-                if (s_ptr[mid] <= e) lo = mid; else hi = mid;
-            }
-            atomicOr(&tile[(it - i0) * WB + (lo >> 5)], 1u << (lo & 31));
+            atomicOr(&tile[wl * ms + (it - i0)], 1u << r);
         }
     }
     if (bad) atomicExch(flag, 1);
@@ -61,7 +72,9 @@ build_bitmaps_kernel(const int64_t *__restrict__ indptr, const int32_t *__restri
     // write-out: 16-byte stores, four consecutive threads per 64-byte row
     for (int k = threadIdx.x; k < icount * (WB / 4); k += blockDim.x) {
         const int r = k / (WB / 4), c = k % (WB / 4);
-        *reinterpret_cast<uint4 *>(bm + (int64_t)(i0 + r) * nwp + w0 + 4 * c) = tile4[k];
+        const uint4 v = make_uint4(tile[(4 * c + 0) * ms + r], tile[(4 * c + 1) * ms + r],
+                                   tile[(4 * c + 2) * ms + r], tile[(4 * c + 3) * ms + r]);
+        *reinterpret_cast<uint4 *>(bm + (int64_t)(i0 + r) * nwp + w0 + 4 * c) = v;
     }
 }
 
@@ -143,7 +156,7 @@ int launch_build_bitmaps(fim_ctx *ctx, const int64_t *d_indptr, const int32_t *d
     int ib = ctx->m < 1024 ? ctx->m : 1024;
     if (ib < 1) ib = 1;
     const int niblk = (int)ceil_div64(ctx->m > 0 ? ctx->m : 1, ib);
-    const size_t smem = (size_t)ib * WB * sizeof(uint32_t);
+    const size_t smem = (size_t)(ib + 1) * WB * sizeof(uint32_t);
     FIM_CUDA_TRY(cudaFuncSetAttribute(build_bitmaps_kernel,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int *flag = ctx->dev_flag.as<int>();

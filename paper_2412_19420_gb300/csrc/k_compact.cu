@@ -13,6 +13,9 @@
 //      scan of the [digit][tile] counts, a stable scatter ranked with
 //      __match_any_sync that moves the word with its record index);
 //   4. writes offsets (exclusive scan of the sizes), items and supports.
+#include <utility>
+#include <vector>
+
 #include "fim_common.cuh"
 
 namespace {
@@ -150,8 +153,10 @@ scan_apply_kernel(uint32_t *__restrict__ a, unsigned long long n, const uint32_t
 
 // Exclusive scan of a uint32 array (length <= a few million) in one CTA.
 __global__ void __launch_bounds__(1024)
-scan_single_kernel(uint32_t *__restrict__ a, unsigned long long n) {
+scan_single_kernel(uint32_t *__restrict__ a, unsigned long long n, uint32_t *__restrict__ zero,
+                   unsigned long long nzero) {
     __shared__ uint32_t s[1024];
+    for (unsigned long long i = threadIdx.x; i < nzero; i += 1024) zero[i] = 0u;  // next pass's histogram
     const unsigned long long seg = (n + 1023) / 1024;
     const unsigned long long b = threadIdx.x * seg, e = b + seg < n ? b + seg : n;
     uint32_t sum = 0;
@@ -175,7 +180,8 @@ scan_single_kernel(uint32_t *__restrict__ a, unsigned long long n) {
 __global__ void __launch_bounds__(RT)
 rs_scatter_kernel(const unsigned long long *__restrict__ key_in, const uint32_t *__restrict__ idx_in,
                   unsigned long long *__restrict__ key_out, uint32_t *__restrict__ idx_out, unsigned long long n,
-                  int shift, const uint32_t *__restrict__ hist, int ntiles) {
+                  int shift, const uint32_t *__restrict__ hist, int ntiles, uint32_t *__restrict__ next_hist,
+                  int next_shift) {
     __shared__ uint32_t base[256];
     __shared__ uint32_t wc[RT / 32][257];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -193,11 +199,20 @@ rs_scatter_kernel(const unsigned long long *__restrict__ key_in, const uint32_t 
         const uint32_t rank = __popc(peers & ((1u << lane) - 1u));
         if (valid && rank == 0) wc[warp][d] = __popc(peers);
         __syncthreads();
+        uint32_t off = 0;
         if (valid) {
-            uint32_t off = base[d] + rank;
+            off = base[d] + rank;
             for (int w = 0; w < warp; w++) off += wc[w][d];
             key_out[off] = k;
             idx_out[off] = v;
+        }
+        if (next_hist) {
+            // the next digit's [digit][tile] count, by destination tile: one
+            // atomic per distinct (digit, tile) of the warp
+            const uint32_t key2 = valid ? ((uint32_t)((k >> next_shift) & 255u) << 20) | (off / TILE) : 0xFFFFFFFFu;
+            const uint32_t peers2 = __match_any_sync(0xffffffffu, key2);
+            if (valid && lane == __ffs(peers2) - 1)
+                atomicAdd(&next_hist[(size_t)(key2 >> 20) * ntiles + (key2 & 0xFFFFFu)], (uint32_t)__popc(peers2));
         }
         __syncthreads();
         uint32_t add = 0;
@@ -316,7 +331,10 @@ int launch_compact(fim_ctx *ctx, uint64_t R, int n_db, int m_max) {
     const int ntiles = (int)ceil_div64((int64_t)R, TILE);
     const unsigned long long nhist = 256ull * (unsigned long long)ntiles;
     const int nchunks = (int)ceil_div64((int64_t)nhist, SC_CHUNK);
-    FIM_TRY(fim_reserve(ctx, ctx->hist, sizeof(uint32_t) * nhist));
+    // small sorts (one-CTA scans) fold each digit's histogram into the
+    // previous digit's scatter: two histogram buffers, used in turn
+    const bool fuse = nchunks <= 1;
+    FIM_TRY(fim_reserve(ctx, ctx->hist, sizeof(uint32_t) * nhist * (fuse ? 2 : 1)));
     FIM_TRY(fim_reserve(ctx, ctx->scan_part, sizeof(uint32_t) * (size_t)nchunks));
     const int nblk = (int)ceil_div64((int64_t)R, ST);
     FIM_TRY(fim_reserve(ctx, ctx->scan_tmp, sizeof(unsigned long long) * (size_t)nblk));
@@ -337,37 +355,53 @@ int launch_compact(fim_ctx *ctx, uint64_t R, int n_db, int m_max) {
         // order and is read straight from the key array.
         unsigned long long *ka = ctx->kv_a.as<unsigned long long>(), *kb = ctx->kv_b.as<unsigned long long>();
         uint32_t *hist = ctx->hist.as<uint32_t>();
+        uint32_t *hist_nxt = fuse ? hist + nhist : nullptr;
         const int key_pad = kw * 64 - total_bits;  // zero bits at the key's LSB end
-        bool first_word = true;
+        // the digit passes, least significant first: (word, shift)
+        std::vector<std::pair<int, int>> passes;
         for (int w = kw - 1; w >= 0; w--) {
             const int word_lo_bit = (kw - 1 - w) * 64;  // bit index (from the key's LSB) of this word's bit 0
-            const unsigned long long *kin = keys + (size_t)w * R;
-            if (!first_word) {
-                gather_word_kernel<<<(unsigned)ceil_div64((int64_t)R, 256), 256, 0, st>>>(kin, ia, R, ka);
-                nk++;
-                kin = ka;
-            }
-            first_word = false;
-            for (int d = 0; d < 8; d++) {
-                const int lo = word_lo_bit + d * 8;
-                if (lo + 8 <= key_pad) continue;          // digit holds only padding
-                rs_hist_kernel<<<ntiles, RT, 0, st>>>(kin, R, d * 8, hist, ntiles);
-                if (nchunks <= 1) {
-                    scan_single_kernel<<<1, 1024, 0, st>>>(hist, nhist);
-                    nk += 1;
+            for (int d = 0; d < 8; d++)
+                if (word_lo_bit + d * 8 + 8 > key_pad) passes.push_back({w, d * 8});  // skip pure padding
+        }
+        const unsigned long long *kin = nullptr;
+        for (size_t i = 0; i < passes.size(); i++) {
+            const int w = passes[i].first, shift = passes[i].second;
+            const bool new_word = i == 0 || passes[i - 1].first != w;
+            if (new_word) {
+                if (i == 0) {
+                    kin = keys + (size_t)w * R;  // record order: read the key array itself
                 } else {
-                    uint32_t *part = ctx->scan_part.as<uint32_t>();
-                    scan_reduce_kernel<<<nchunks, SC_T, 0, st>>>(hist, nhist, part);
-                    scan_single_kernel<<<1, 1024, 0, st>>>(part, (unsigned long long)nchunks);
-                    scan_apply_kernel<<<nchunks, SC_T, 0, st>>>(hist, nhist, part);
-                    nk += 3;
+                    gather_word_kernel<<<(unsigned)ceil_div64((int64_t)R, 256), 256, 0, st>>>(
+                        keys + (size_t)w * R, ia, R, ka);
+                    nk++;
+                    kin = ka;
                 }
-                unsigned long long *kout = (kin == ka) ? kb : ka;
-                rs_scatter_kernel<<<ntiles, RT, 0, st>>>(kin, ia, kout, ib, R, d * 8, hist, ntiles);
-                nk += 2;
-                uint32_t *t = ia; ia = ib; ib = t;
-                kin = kout;
             }
+            const bool next_fused = fuse && i + 1 < passes.size() && passes[i + 1].first == w;
+            if (new_word || !fuse) {
+                rs_hist_kernel<<<ntiles, RT, 0, st>>>(kin, R, shift, hist, ntiles);
+                nk++;
+            }  // else: the previous scatter has counted this digit into hist
+            if (nchunks <= 1) {
+                scan_single_kernel<<<1, 1024, 0, st>>>(hist, nhist, next_fused ? hist_nxt : nullptr,
+                                                       next_fused ? nhist : 0ull);
+                nk += 1;
+            } else {
+                uint32_t *part = ctx->scan_part.as<uint32_t>();
+                scan_reduce_kernel<<<nchunks, SC_T, 0, st>>>(hist, nhist, part);
+                scan_single_kernel<<<1, 1024, 0, st>>>(part, (unsigned long long)nchunks, nullptr, 0ull);
+                scan_apply_kernel<<<nchunks, SC_T, 0, st>>>(hist, nhist, part);
+                nk += 3;
+            }
+            unsigned long long *kout = (kin == ka) ? kb : ka;
+            rs_scatter_kernel<<<ntiles, RT, 0, st>>>(kin, ia, kout, ib, R, shift, hist, ntiles,
+                                                     next_fused ? hist_nxt : nullptr,
+                                                     next_fused ? passes[i + 1].second : 0);
+            nk++;
+            uint32_t *t = ia; ia = ib; ib = t;
+            kin = kout;
+            if (fuse) { uint32_t *h = hist; hist = hist_nxt; hist_nxt = h; }
         }
         unsigned long long *bsum = ctx->scan_tmp.as<unsigned long long>();
         len_block_sums_kernel<<<nblk, ST, 0, st>>>(ia, ctx->rec_len.as<uint32_t>(), R, bsum);

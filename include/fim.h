@@ -162,6 +162,9 @@ int fim_get_stats(const fim_ctx *ctx, fim_stats *out);
  *   "dfs_ctas_per_sm"  1..4      DFS workers per SM; dfs_threads x dfs_ctas_per_sm
  *                                must not exceed 1024 (FIM_E_INVAL otherwise)
  *   "split_depth"      0..8      longest prefix a worker may hand to the queue
+ *   "root_reverse"     0, 1      hand out the root classes (frequent pairs) in
+ *                                reverse order: pairs of the most frequent items
+ *                                first (default 0)
  *   "learned_order"    0, 1      FIM_LEARNED also hands out the roots longest-
  *                                predicted-subtree first (default 0)
  *   "learned_kmin"     1..2^20   FIM_LEARNED consults the network only for classes

@@ -24,7 +24,7 @@ SPACE = {
     "sparse_div": [-1, 0, 4],
 }
 DEFAULT = {"dfs_threads": 256, "dfs_ctas_per_sm": 4, "split_depth": 8, "sparse_div": -1,
-           "pairs_kdrain": 0, "pairs_split": 0}
+           "root_reverse": 0, "pairs_kdrain": 0, "pairs_split": 0}
 
 
 def valid(cfg: dict) -> bool:

@@ -30,13 +30,14 @@ def case():
     return c, minsup, oracle.apriori(c.indptr, c.indices, c.m, minsup).sha256()
 
 
-SHAPES = [(256, 1, 0), (256, 4, 8), (512, 1, 2), (512, 2, 6), (256, 2, 1)]
+SHAPES = [(256, 1, 0, 0), (256, 4, 8, 0), (512, 1, 2, 0), (512, 2, 6, 1), (256, 2, 1, 1), (256, 4, 8, 1)]
 
 
-@pytest.mark.parametrize("threads,per_sm,split", SHAPES)
-def test_every_shape_is_exact(ctx, case, threads, per_sm, split):
+@pytest.mark.parametrize("threads,per_sm,split,reverse", SHAPES)
+def test_every_shape_is_exact(ctx, case, threads, per_sm, split, reverse):
     c, minsup, want = case
-    autotune.apply(ctx, {"dfs_threads": threads, "dfs_ctas_per_sm": per_sm, "split_depth": split})
+    autotune.apply(ctx, {"dfs_threads": threads, "dfs_ctas_per_sm": per_sm, "split_depth": split,
+                         "root_reverse": reverse})
     try:
         fim.fim_build_bitmaps(ctx, c.indptr, c.indices, c.m)
         fim.fim_mine(ctx, minsup)

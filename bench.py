@@ -275,8 +275,22 @@ def run_batched(args):
     out_h = (torch.empty(R + 1, dtype=torch.int64).pin_memory(), torch.empty(max(T, 1), dtype=torch.int32).pin_memory(),
              torch.empty(max(R, 1), dtype=torch.int32).pin_memory())
 
+    # the CSRs in pinned host memory, packed back to back (the library uploads
+    # contiguous databases in one copy per array)
+    n_ptr = sum(c.n + 1 for c in dbs)
+    n_idx = sum(c.nnz for c in dbs)
+    ptr_h = torch.empty(n_ptr, dtype=torch.int64).pin_memory().numpy()
+    idx_h = torch.empty(max(n_idx, 1), dtype=torch.int32).pin_memory().numpy()
+    hdbs, po, io = [], 0, 0
+    for c in dbs:
+        ptr_h[po:po + c.n + 1] = c.indptr
+        idx_h[io:io + c.nnz] = c.indices
+        hdbs.append(datagen.Csr(indptr=ptr_h[po:po + c.n + 1], indices=idx_h[io:io + c.nnz], m=c.m))
+        po += c.n + 1
+        io += c.nnz
+
     def e2e_step():
-        fim.fim_mine_batched(ctx, dbs, ms, flags)
+        fim.fim_mine_batched(ctx, hdbs, ms, flags)
         fim.fim_fetch_batched(ctx, fim.FIM_ALL_DBS, tuple(x.numpy() for x in out_h))
     e2e_step()
     e2e = timed(e2e_step, args.steps)

@@ -450,20 +450,40 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
     if (!on_device) {
         FIM_TRY(fim_reserve(ctx, ctx->csr_ptr, sizeof(int64_t) * (size_t)(host_ptr_total ? host_ptr_total : 1)));
         FIM_TRY(fim_reserve(ctx, ctx->csr_idx, sizeof(int32_t) * (size_t)(host_nnz_total ? host_nnz_total : 1)));
+        // databases whose arrays follow each other in host memory (one packed
+        // buffer) go up in one copy per run instead of one per database
+        struct Run { const char *src = nullptr; char *dst = nullptr; size_t bytes = 0; };
+        Run rp, ri;
+        auto flush = [&](Run &r) -> int {
+            if (r.bytes) FIM_CUDA_TRY(cudaMemcpyAsync(r.dst, r.src, r.bytes, cudaMemcpyHostToDevice, st));
+            r = Run{};
+            return FIM_OK;
+        };
+        auto add = [&](Run &r, const void *src, void *dst, size_t bytes) -> int {
+            if (!bytes) return FIM_OK;
+            if (r.bytes && r.src + r.bytes == (const char *)src && r.dst + r.bytes == (char *)dst) {
+                r.bytes += bytes;
+                return FIM_OK;
+            }
+            FIM_TRY(flush(r));
+            r.src = (const char *)src;
+            r.dst = (char *)dst;
+            r.bytes = bytes;
+            return FIM_OK;
+        };
         int64_t po = 0, io = 0;
         for (int d = 0; d < n_db; d++) {
             const fim_db_desc &x = in[d];
             const int64_t nnz = x.indptr[x.n_trans];
-            FIM_CUDA_TRY(cudaMemcpyAsync(ctx->csr_ptr.as<int64_t>() + po, x.indptr,
-                                         sizeof(int64_t) * (size_t)(x.n_trans + 1), cudaMemcpyHostToDevice, st));
-            if (nnz > 0)
-                FIM_CUDA_TRY(cudaMemcpyAsync(ctx->csr_idx.as<int32_t>() + io, x.indices, sizeof(int32_t) * (size_t)nnz,
-                                             cudaMemcpyHostToDevice, st));
+            FIM_TRY(add(rp, x.indptr, ctx->csr_ptr.as<int64_t>() + po, sizeof(int64_t) * (size_t)(x.n_trans + 1)));
+            if (nnz > 0) FIM_TRY(add(ri, x.indices, ctx->csr_idx.as<int32_t>() + io, sizeof(int32_t) * (size_t)nnz));
             L.dbs[d].indptr = ctx->csr_ptr.as<int64_t>() + po;
             L.dbs[d].indices = ctx->csr_idx.as<int32_t>() + io;
             po += x.n_trans + 1;
             io += nnz;
         }
+        FIM_TRY(flush(rp));
+        FIM_TRY(flush(ri));
     } else {
         for (int d = 0; d < n_db; d++) {
             L.dbs[d].indptr = in[d].indptr;

@@ -141,16 +141,15 @@ def _load_workload(name):
     return fn(), minsup
 
 
-def cpu_baseline(csr, minsup, budget_s=20.0, threads=None):
+def cpu_baseline(csr, minsup, budget_s=20.0, threads=None, frac=1.0):
     """The oracle (plain Apriori, all host cores unless `threads` is given) on
     a bounded sample of the workload: the first n' transactions, with minsup
-    scaled by n'/n."""
+    scaled by n'/n, starting from the fraction `frac` of the workload."""
     import numpy as np
     import oracle
     from paper_2412_19420_gb300 import datagen
     cores = threads or _cores()
     n = csr.n
-    frac = 1.0
     while True:
         n_s = max(1, int(n * frac))
         ms = max(1, int(round(minsup * n_s / n)))
@@ -167,7 +166,7 @@ def cpu_baseline(csr, minsup, budget_s=20.0, threads=None):
               f"first {n_s:,} of {n:,} transactions, minsup {ms:,}") + \
         f"; {r.n_candidates:,} candidate supports counted, {len(r):,} frequent itemsets"
     return {"value": r.n_candidates / dt, "unit": "supports/s", "cores": cores, "kind": "oracle",
-            "sample": sample, "seconds": round(dt, 3)}
+            "sample": sample, "seconds": round(dt, 3), "frac": n_s / max(1, n)}
 
 
 def run_reference(args):
@@ -500,7 +499,11 @@ def main():
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(csr, minsup)
-        one = cpu_baseline(csr, minsup, budget_s=8.0, threads=1)
+        # one thread: start from the sample the all-core run's time suggests
+        nt = line["cpu_baseline"]
+        guess = nt.pop("frac") * min(1.0, 8.0 / max(1e-3, nt["seconds"] * nt["cores"]))
+        one = cpu_baseline(csr, minsup, budget_s=8.0, threads=1, frac=max(guess, 1 / 64))
+        one.pop("frac")
         line["cpu_baseline"]["single_thread"] = {k: one[k] for k in ("value", "sample", "seconds")}
     if rank == 0:
         print(json.dumps(line))

@@ -144,9 +144,11 @@ batch_build_rows_kernel(const DbDesc *__restrict__ dbs, int n_db, const int64_t 
     uint32_t *col0 = bm + D.bm_off;
     for (int k = threadIdx.x; k < m * WB; k += blockDim.x)
         col0[(int64_t)(k / WB) * D.nwp + w0 + k % WB] = tile[(k % WB) * ms + k / WB];
-    for (int j = warp; j < m; j += (int)(blockDim.x >> 5)) {  // WB == 32: one word per lane
-        const uint32_t c = warp_sum_u32(__popc(tile[lane * ms + j]));
-        if (lane == 0 && c) atomicAdd(&sup[D.item_off + j], c);
+    for (int j = threadIdx.x; j < m; j += blockDim.x) {  // a thread per item: 32 words
+        uint32_t c = 0;
+#pragma unroll 8
+        for (int w = 0; w < WB; w++) c += __popc(tile[w * ms + j]);
+        if (c) atomicAdd(&sup[D.item_off + j], c);
     }
 }
 
@@ -214,13 +216,84 @@ __global__ void batch_rank_kernel(DbDesc *__restrict__ dbs, int n_db, const int6
     }
 }
 
+// Pair supports of a database with at most 64 frequent items, in one CTA:
+// the threads cover only the upper-triangle 4 x 4 blocks of the m' x m'
+// pair matrix (nb (nb + 1) / 2 of them, nb = ceil(m' / 4)), and the CTA's
+// spare threads split the transactions into KG groups whose partial counts
+// meet in shared memory.  Every 4 x 4 block holds at least one pair a < b.
+__device__ void small_pairs(const DbDesc &D, int mf, const uint32_t *__restrict__ col0,
+                            const int32_t *__restrict__ perm, int *__restrict__ out, uint32_t *smem) {
+    __shared__ int64_t s_col[TI];
+    const int nb = (mf + 3) >> 2;
+    const int nblk = nb * (nb + 1) / 2;
+    const int KG = 256 / nblk >= 4 ? 4 : (256 / nblk >= 2 ? 2 : 1);
+    const int t = threadIdx.x;
+    const bool act = t < nblk * KG;
+    const int blk = t % nblk, kg = t / nblk;
+    int bi = 0, r = blk;
+    while (r >= nb - bi) { r -= nb - bi; bi++; }
+    const int bj = bi + r;
+    if (t < TI) s_col[t] = t < mf ? (int64_t)perm[t] * D.nwp : -1;
+    uint32_t (*S)[KW][TI] = reinterpret_cast<uint32_t (*)[KW][TI]>(smem);  // [KG][KW][TI]
+    uint32_t acc[4][4] = {};
+    const int64_t step = (int64_t)KW * KG;  // divides the 128-word column padding
+    for (int64_t k = 0; k < D.nw; k += step) {
+        __syncthreads();
+        // a thread copies 8 words (one 32-byte sector) of one row; consecutive
+        // threads take consecutive rows, so the transposed stores are
+        // conflict-free
+        for (int e = t; e < KG * TI * (KW / 8); e += blockDim.x) {
+            const int row = e % TI, q = (e / TI) % (KW / 8), g = e / (TI * (KW / 8));
+            uint4 v0 = make_uint4(0, 0, 0, 0), v1 = v0;
+            if (s_col[row] >= 0) {
+                const uint32_t *src = col0 + s_col[row] + k + (int64_t)g * KW + 8 * q;
+                v0 = ldg_u4(src);
+                v1 = ldg_u4(src + 4);
+            }
+            const uint32_t w[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+#pragma unroll
+            for (int c = 0; c < 8; c++) S[g][8 * q + c][row] = w[c];
+        }
+        __syncthreads();
+        if (act) {
+#pragma unroll 8
+            for (int kk = 0; kk < KW; kk++) {
+                const uint4 a = *reinterpret_cast<const uint4 *>(&S[kg][kk][bi * 4]);
+                const uint4 b = *reinterpret_cast<const uint4 *>(&S[kg][kk][bj * 4]);
+                const uint32_t x[4] = {a.x, a.y, a.z, a.w}, y[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+                for (int i = 0; i < 4; i++)
+#pragma unroll
+                    for (int j = 0; j < 4; j++) acc[i][j] += __popc(x[i] & y[j]);
+            }
+        }
+    }
+    // the KG partial counts meet in shared memory (the staging area, reused)
+    int (*R)[TI] = reinterpret_cast<int (*)[TI]>(smem);
+    __syncthreads();
+    for (int e = t; e < TI * TI; e += blockDim.x) R[e / TI][e % TI] = 0;
+    __syncthreads();
+    if (act)
+#pragma unroll
+        for (int i = 0; i < 4; i++)
+#pragma unroll
+            for (int j = 0; j < 4; j++)
+                if (acc[i][j]) atomicAdd(&R[bi * 4 + i][bj * 4 + j], (int)acc[i][j]);
+    __syncthreads();
+    for (int e = t; e < mf * mf; e += blockDim.x) {
+        const int a = e / mf, b = e % mf;
+        if (a < b) out[e] = R[a][b];
+    }
+}
+
 // Pair supports of one 64 x 64 tile of one database (CUDA cores, exact).
 __global__ void __launch_bounds__(256)
 batch_pairs_kernel(const DbDesc *__restrict__ dbs, int n_db, const int64_t *__restrict__ tile_prefix,
                    const uint32_t *__restrict__ bm, const int32_t *__restrict__ perm_base,
                    int *__restrict__ pair_cnt) {
-    __shared__ __align__(16) uint32_t As[KW][TI];
-    __shared__ __align__(16) uint32_t Bs[KW][TI];
+    __shared__ __align__(16) uint32_t smem[4 * KW * TI];  // 32 KB
+    uint32_t (*As)[TI] = reinterpret_cast<uint32_t (*)[TI]>(smem);
+    uint32_t (*Bs)[TI] = reinterpret_cast<uint32_t (*)[TI]>(smem + KW * TI);
     const int d = find_db(tile_prefix, n_db, blockIdx.x);
     const DbDesc &D = dbs[d];
     const int mf = *(volatile const int32_t *)&D.mfreq;
@@ -231,6 +304,10 @@ batch_pairs_kernel(const DbDesc *__restrict__ dbs, int n_db, const int64_t *__re
     if (tb * TI >= mf || D.maxlen == 1) return;
     const int32_t *perm = perm_base + D.item_off;
     const uint32_t *col0 = bm + D.bm_off;
+    if (mf <= TI) {  // one tile: only its upper triangle, with the spare threads on K
+        small_pairs(D, mf, col0, perm, pair_cnt + D.pair_off, smem);
+        return;
+    }
     const int t = threadIdx.x, lr = t & 63, lc = (t >> 6) * 8;
     const int ra = ta * TI + lr, rb = tb * TI + lr;
     const uint32_t *pa = ra < mf ? col0 + (int64_t)perm[ra] * D.nwp : nullptr;
@@ -370,12 +447,6 @@ struct Layout {
     int64_t words = 0, items = 0, pairs = 0, pb = 0, root_cap = 0, nwp_max = 0, max_row_bound = 0;
     int m_max = 0, ib = 1;
 };
-
-int bits_needed(int64_t v) {
-    int b = 1;
-    while ((1LL << b) < v) b++;
-    return b;
-}
 
 }  // namespace
 

@@ -92,7 +92,8 @@ batch_build_kernel(const DbDesc *__restrict__ dbs, int n_db, const int64_t *__re
 // sets its rows' bits with shared atomics, then the block is written out
 // coalesced (128 bytes per column) and each column's popcount over the block
 // is added into S(I_j) (Eq. 3): no second pass reads the columns.
-__global__ void __launch_bounds__(256)
+constexpr int BUILD_ROWS_THREADS = 512;
+__global__ void __launch_bounds__(BUILD_ROWS_THREADS)
 batch_build_rows_kernel(const DbDesc *__restrict__ dbs, int n_db, const int64_t *__restrict__ unit_prefix,
                         uint32_t *__restrict__ bm, uint32_t *__restrict__ sup, int *__restrict__ flag) {
     // [WB][m + 1]: a warp's 32 consecutive rows share their word, so the
@@ -689,7 +690,7 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
                 cudaMemsetAsync(ctx->item_sup.p, 0, sizeof(uint32_t) * (size_t)items, st);
             if (units > 0) {
                 if (rows_build)
-                    batch_build_rows_kernel<<<(unsigned)units, 256, smem_rows, st>>>(
+                    batch_build_rows_kernel<<<(unsigned)units, BUILD_ROWS_THREADS, smem_rows, st>>>(
                         d_dbs, n_db, d_unit, ctx->bm.as<uint32_t>(), ctx->item_sup.as<uint32_t>(),
                         ctx->dev_flag.as<int>());
                 else

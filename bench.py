@@ -52,6 +52,8 @@ def _args():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOAD_DESC))
     ap.add_argument("--flags", type=int, default=0, help="extra fim_mine flags")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--rules-ppm", type=int, default=500_000,
+                    help="also time association rules at this confidence (ppm); -1 skips")
     ap.add_argument("--learned", action="store_true",
                     help="single database: mine with FIM_LEARNED, the network trained on the GPU "
                          "from plain-miner traces of the same generator at another seed")
@@ -452,6 +454,25 @@ def main():
     h2d = csr.indptr.nbytes + csr.indices.nbytes
     d2h = 8 * (R + 1) + 4 * T + 4 * R
 
+    # ---- association rules of the last mine (a post-pass, not in the step)
+    rules = None
+    if args.rules_ppm >= 0:
+        fim.fim_rules(ctx, args.rules_ppm)  # sizes the rule buffers
+        rule_ms = []
+        for _ in range(max(3, args.steps)):
+            stream.synchronize()
+            t0 = time.perf_counter()
+            n_rules = fim.fim_rules(ctx, args.rules_ppm)
+            rule_ms.append(1000 * (time.perf_counter() - t0))
+        lens = np.diff(got.offsets.astype(np.int64))
+        lens = lens[(lens >= 2) & (lens <= fim.FIM_RULES_MAX_LEN)]
+        evaluated = int(((np.int64(1) << lens) - 2).sum())
+        ms_r = statistics.median(rule_ms)
+        rules = {"min_conf_ppm": args.rules_ppm, "n_rules": int(n_rules), "antecedents_evaluated": evaluated,
+                 "ms": round(ms_r, 4), "rules_per_s": n_rules / (ms_r / 1000),
+                 "antecedents_per_s": evaluated / (ms_r / 1000),
+                 "timing": "host wall clock around fim_rules (two passes, a scan, one sync), median"}
+
     # ---- roofline of the dominant phase ---------------------------------
     hbm, bf16, bf16_s, src = _peaks()
     avg = {p: phase[p] / args.steps for p in phase}
@@ -506,6 +527,8 @@ def main():
         "roofline": roof,
         "clocks": clk.summary(),
     }
+    if rules is not None:
+        line["rules"] = rules
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(csr, minsup)
         # one thread: start from the sample the all-core run's time suggests

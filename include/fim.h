@@ -248,6 +248,42 @@ int fim_mlp_backward(fim_ctx *ctx, const float *params, const float *x, const fl
 int fim_mlp_adam(fim_ctx *ctx, float *params, const float *grad, float *m, float *v,
                  int step, float lr, float beta1, float beta2, float eps);
 
+/* ---- association rules -------------------------------------------------
+ * Section IV.A names confidence and lift beside support as the measures the
+ * mined itemsets are evaluated with; the paper prints no formula, so these
+ * are the textbook ones.  For a frequent set Z, a nonempty proper subset X of
+ * Z and Y = Z \ X, the rule X -> Y has
+ *     conf(X -> Y) = S(Z) / S(X)
+ *     lift(X -> Y) = conf(X -> Y) / (S(Y) / n) = S(Z) n / (S(X) S(Y))
+ * with S the supports of Eq. 3 and n the transactions.
+ *
+ * fim_rules: from the itemsets held by the last fim_mine, builds on the device
+ * every rule X -> Y with 2 <= |Z| <= max_len (0 = FIM_RULES_MAX_LEN) and
+ * conf >= min_conf_ppm / 10^6, decided in integers: S(Z) * 10^6 >= min_conf_ppm
+ * * S(X).  Rules are ordered by the index of Z in the canonical output, then by
+ * ante_mask ascending; ante_mask bit i set means the i-th item of Z (its items
+ * ascending) is in X, the others form Y.  conf is the double S(Z) / S(X); lift
+ * is the double (S(Z) n) / (S(X) S(Y)) of the two exact integer products, each
+ * rounded once to double, so results are reproducible bit for bit.  Sets
+ * longer than max_len yield no rules (a set of size L has 2^L - 2 of them).
+ * The rules stay in device memory of the ctx until the next fim_rules or
+ * fim_mine; *n_rules gets their number.
+ * Errors: FIM_E_STATE (no fim_mine result held, or the held sets are not
+ * downward closed), FIM_E_INVAL (min_conf_ppm > 10^6, max_len outside
+ * {0} u [2, FIM_RULES_MAX_LEN], n_rules NULL), FIM_E_NOMEM, FIM_E_CUDA. */
+#define FIM_RULES_MAX_LEN 20
+int fim_rules(fim_ctx *ctx, uint32_t min_conf_ppm, int max_len, uint64_t *n_rules);
+
+/* fim_fetch_rules: copies the rules of the last fim_rules (for the itemsets
+ * still held) into caller buffers of cap entries each: set_index (uint64, the
+ * index of Z in fim_fetch_results' order), ante_mask, conf, lift.  With all
+ * four NULL it only writes *n_rules.  flags: FIM_OUTPUT_HOST or
+ * FIM_OUTPUT_DEVICE.  Errors: FIM_E_STATE (no rules for the held itemsets),
+ * FIM_E_TOO_SMALL (cap < *n_rules, which is still written), FIM_E_INVAL (some
+ * but not all buffers NULL), FIM_E_CUDA. */
+int fim_fetch_rules(fim_ctx *ctx, uint64_t *n_rules, uint64_t *set_index, uint32_t *ante_mask,
+                    double *conf, double *lift, uint64_t cap, uint32_t flags);
+
 /* ---- allocation-free entry point ---------------------------------------
  * The paper has no counterpart to this call.  It serves callers that cannot
  * allocate device memory while they use the library: processes whose own

@@ -206,6 +206,11 @@ struct fim_ctx {
     DevBuf keys, idx_a, idx_b, hist, scan_tmp, kv_a, kv_b, scan_part;
     DevBuf out_off, out_items, out_sup;
     uint64_t out_sets = 0, out_items_total = 0;
+    uint64_t mine_serial = 0;   // completed fim_mine calls; names the output held
+
+    // association rules of the held output
+    DevBuf rule_cnt, rule_set, rule_mask, rule_conf, rule_lift;
+    uint64_t rules_n = 0, rules_of = 0;  // rules_of: mine_serial the rules belong to
 
     // learned scheduler
     DevBuf mlp_w32, mlp_wbf, mlp_scratch;

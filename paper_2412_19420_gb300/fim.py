@@ -84,6 +84,8 @@ def _load():
         "fim_mlp_adam": (ctypes.c_int, [P, P, P, P, P, ctypes.c_int, ctypes.c_float, ctypes.c_float,
                                         ctypes.c_float, ctypes.c_float]),
         "fim_set_tuning": (ctypes.c_int, [P, ctypes.c_char_p, I64]),
+        "fim_rules": (ctypes.c_int, [P, U32, ctypes.c_int, ctypes.POINTER(U64)]),
+        "fim_fetch_rules": (ctypes.c_int, [P, ctypes.POINTER(U64), P, P, P, P, U64, U32]),
         "fim_batch_slices": (ctypes.c_int, [P, P, U64]),
         "fim_pair_supports_noalloc": (ctypes.c_int, [P, P, I64, I32, P, P]),
         "fim_minsup_from_ppm": (U64, [I64, U32]),
@@ -224,6 +226,55 @@ def fim_fetch_results(ctx, out=None) -> Itemsets:
     if dev:
         return Itemsets(off[: R + 1], it[:T], sup[:R])
     return Itemsets(off[: R + 1].copy(), it[:T].copy(), sup[:R].copy())
+
+
+FIM_RULES_MAX_LEN = 20
+
+
+@dataclasses.dataclass
+class Rules:
+    """Association rules X -> Z \\ X of the held itemsets (include/fim.h):
+    set_index = index of Z in fim_fetch_results' order, ante_mask bit i = the
+    i-th item of Z is in X."""
+    set_index: np.ndarray  # uint64[N]
+    ante_mask: np.ndarray  # uint32[N]
+    conf: np.ndarray       # float64[N]
+    lift: np.ndarray       # float64[N]
+
+    def __len__(self) -> int:
+        return int(self.set_index.shape[0])
+
+
+def fim_rules(ctx, min_conf_ppm: int, max_len: int = 0) -> int:
+    """Build the rules with confidence >= min_conf_ppm / 10^6 on the device;
+    returns their number."""
+    n = ctypes.c_uint64()
+    _check(_lib.fim_rules(ctx, int(min_conf_ppm), int(max_len), ctypes.byref(n)), "fim_rules")
+    return int(n.value)
+
+
+def fim_fetch_rules(ctx, out=None) -> Rules:
+    """The rules of the last fim_rules into new host arrays, or into `out` =
+    (set_index, ante_mask, conf, lift) buffers (numpy, pinned host or torch
+    CUDA tensors)."""
+    n = ctypes.c_uint64()
+    _check(_lib.fim_fetch_rules(ctx, ctypes.byref(n), None, None, None, None, 0, 0), "fim_fetch_rules")
+    N = int(n.value)
+    if out is None:
+        out = (np.empty(max(N, 1), np.uint64), np.empty(max(N, 1), np.uint32),
+               np.empty(max(N, 1), np.float64), np.empty(max(N, 1), np.float64))
+    si, am, cf, lf = out
+    _sync_torch(si, am, cf, lf)
+    ptrs = [_ptr(a) for a in out]
+    dev = ptrs[0][1]
+    if any(d != dev for _, d in ptrs):
+        raise ValueError("fim_fetch_rules: buffers must all be host or all device")
+    cap = min(int(a.shape[0]) for a in out)
+    _check(_lib.fim_fetch_rules(ctx, ctypes.byref(n), *[p for p, _ in ptrs], cap,
+                                FIM_OUTPUT_DEVICE if dev else FIM_OUTPUT_HOST), "fim_fetch_rules")
+    if dev:
+        return Rules(si[:N], am[:N], cf[:N], lf[:N])
+    return Rules(si[:N].copy(), am[:N].copy(), cf[:N].copy(), lf[:N].copy())
 
 
 def fim_set_tuning(ctx, key: str, value: int) -> None:

@@ -267,12 +267,18 @@ int fim_mlp_adam(fim_ctx *ctx, float *params, const float *grad, float *m, float
  * rounded once to double, so results are reproducible bit for bit.  Sets
  * longer than max_len yield no rules (a set of size L has 2^L - 2 of them).
  * The rules stay in device memory of the ctx until the next fim_rules or
- * fim_mine; *n_rules gets their number.
+ * fim_mine; *n_rules gets their number.  Scratch: 8 bytes per held set and
+ * one bit plus 2 bytes per candidate rule (sum of 2^|Z| - 2).
  * Errors: FIM_E_STATE (no fim_mine result held, or the held sets are not
  * downward closed), FIM_E_INVAL (min_conf_ppm > 10^6, max_len outside
- * {0} u [2, FIM_RULES_MAX_LEN], n_rules NULL), FIM_E_NOMEM, FIM_E_CUDA. */
+ * {0} u [2, FIM_RULES_MAX_LEN], n_rules NULL), FIM_E_NOMEM (also when the
+ * candidate rules' scratch does not fit), FIM_E_CUDA. */
 #define FIM_RULES_MAX_LEN 20
 int fim_rules(fim_ctx *ctx, uint32_t min_conf_ppm, int max_len, uint64_t *n_rules);
+
+/* fim_rules_evaluated: the candidate rules the last fim_rules tested,
+ * sum over the sets Z it covered of 2^|Z| - 2.  Errors as fim_fetch_rules. */
+int fim_rules_evaluated(const fim_ctx *ctx, uint64_t *n_evaluated);
 
 /* fim_fetch_rules: copies the rules of the last fim_rules (for the itemsets
  * still held) into caller buffers of cap entries each: set_index (uint64, the

@@ -151,7 +151,8 @@ void fim_destroy(fim_ctx *ctx) {
                      &ctx->rec_off, &ctx->rec_len, &ctx->rec_sup, &ctx->rec_items, &ctx->counters,
                      &ctx->keys, &ctx->idx_a, &ctx->idx_b, &ctx->hist, &ctx->scan_tmp, &ctx->kv_a, &ctx->kv_b,
                      &ctx->scan_part, &ctx->out_off,
-                     &ctx->out_items, &ctx->out_sup, &ctx->rule_cnt, &ctx->rule_set, &ctx->rule_mask,
+                     &ctx->out_items, &ctx->out_sup, &ctx->rule_base, &ctx->rule_part, &ctx->rule_bits,
+                     &ctx->rule_kbase, &ctx->rule_set, &ctx->rule_mask,
                      &ctx->rule_conf, &ctx->rule_lift, &ctx->mlp_w32, &ctx->mlp_wbf, &ctx->trace_x,
                      &ctx->trace_y, &ctx->mlp_scratch, &ctx->root_order, &ctx->root_bucket,
                      &ctx->root_hist, &ctx->rec_db, &ctx->dbdesc, &ctx->epoch, &ctx->sp_idx,

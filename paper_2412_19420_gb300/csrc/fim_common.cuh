@@ -209,8 +209,10 @@ struct fim_ctx {
     uint64_t mine_serial = 0;   // completed fim_mine calls; names the output held
 
     // association rules of the held output
-    DevBuf rule_cnt, rule_set, rule_mask, rule_conf, rule_lift;
-    uint64_t rules_n = 0, rules_of = 0;  // rules_of: mine_serial the rules belong to
+    DevBuf rule_base, rule_part, rule_bits, rule_kbase;  // evaluation space, scans, keep words
+    DevBuf rule_set, rule_mask, rule_conf, rule_lift;
+    uint64_t rules_n = 0, rules_evaluated = 0;
+    uint64_t rules_of = 0;      // mine_serial the rules belong to
 
     // learned scheduler
     DevBuf mlp_w32, mlp_wbf, mlp_scratch;

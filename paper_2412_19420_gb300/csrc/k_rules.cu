@@ -1,127 +1,178 @@
 // k_rules.cu -- association rules from the frequent itemsets: a post-pass over
 // the canonical output of the extraction (Eq. 3), for the confidence and lift
-// measures the paper names beside support.
+// measures the paper names beside support (Section IV.A).
 //
-// For every frequent Z with 2 <= |Z| <= FIM_RULES_MAX_LEN and every nonempty
-// proper subset X of Z (Y = Z \ X), the rule X -> Y has
+// For every frequent Z with 2 <= |Z| <= max_len and every nonempty proper
+// subset X of Z (Y = Z \ X), the rule X -> Y has
 //     conf = S(Z) / S(X),     lift = S(Z) n / (S(X) S(Y)),
 // and is kept when S(Z) * 10^6 >= min_conf_ppm * S(X) (exact integers).
-// S(X) and S(Y) are looked up in the canonical output itself, which is sorted
-// by (size, items): every subset of a frequent set is frequent (downward
-// closure), so a binary search always finds it.
 //
-// One warp per Z: lane l takes the antecedent masks l + 1, l + 33, ... in
-// rounds of 32, so each round's kept rules are compacted with one ballot and
-// stay in mask order.  Pass 1 counts the kept rules of every Z, a scan gives
-// each Z its slice, pass 2 writes (set index, mask, conf, lift).
+// Work layout.  The candidate rules of all sets form one flat space of
+// E = sum_Z (2^|Z| - 2) evaluations in (set index, antecedent mask) order, so
+// a set of 11 items spreads its 2,046 antecedents over 2,046 threads instead
+// of serialising them in one warp.  Evaluation e belongs to the set z with
+// ebase[z] <= e < ebase[z+1] (ebase = exclusive scan of the per-set counts)
+// and has mask e - ebase[z] + 1.
+//   1. size_bounds: first set index of every size (the output is ordered by
+//      size, then lexicographically), so a subset lookup searches only the
+//      sets of its own size;
+//   2. scan of the per-set counts -> ebase, E;
+//   3. keep: one thread per evaluation looks up S(X) and S(Y) by binary search
+//      (every subset of a frequent set is frequent: downward closure), decides
+//      the threshold, and one ballot per 32 evaluations stores a keep word;
+//   4. scan of the keep words' popcounts -> each word's first output slot;
+//   5. write: the kept evaluations redo their two lookups and write (set index,
+//      mask, conf, lift) at their slot, so the output keeps evaluation order.
+// The itemsets (offsets, items, supports) stay resident from the mine and the
+// lookups hit L2 for outputs up to tens of MB: the kernels are bound by
+// dependent-load latency, not by HBM bandwidth.
 #include "fim_common.cuh"
 
 namespace {
 
 constexpr int RMAX = FIM_RULES_MAX_LEN;
-constexpr int RULE_WARPS = 8;  // warps (sets) per 256-thread CTA
+constexpr int RT = 256;                    // threads per CTA of the evaluation kernels
+constexpr int SCAN_T = 1024, SCAN_I = 8;   // scan: 1024 threads x 8 elements per CTA
+constexpr int SCAN_CHUNK = SCAN_T * SCAN_I;
+constexpr int NSIZE = 32;                  // size_start entries (sizes 0 .. 31)
 
-// Index in the canonical order of the subset of z (|z| = L, items ascending)
-// picked by the bits of mask, or -1 if it is not in the output.  The canonical
-// order is (size, items lexicographic), so a binary search over the sets finds
-// it; the subset's k-th item is z[k-th set bit of mask].
-__device__ int64_t find_subset(const unsigned long long *__restrict__ off, const uint32_t *__restrict__ items,
-                               int64_t R, const uint32_t *z, int L, uint32_t mask) {
-    const int ls = __popc(mask);
-    int64_t lo = 0, hi = R;  // first r with key(r) >= key(subset)
+struct SetsView {
+    const unsigned long long *off;         // [R + 1]
+    const uint32_t *items;
+    const uint32_t *sup;                   // [R]
+    const unsigned long long *size_start;  // [NSIZE]: first set with |set| >= l
+    int64_t R;
+};
+
+// Set sizes do not decrease along the canonical order: size_start[l] is the
+// first set index with size >= l (R if none).
+__global__ void size_bounds_kernel(const unsigned long long *__restrict__ off, int64_t R,
+                                   unsigned long long *__restrict__ size_start) {
+    const int l = threadIdx.x;
+    if (l >= NSIZE) return;
+    int64_t lo = 0, hi = R;
     while (lo < hi) {
         const int64_t mid = (lo + hi) >> 1;
-        const unsigned long long o = off[mid];
-        const int lm = (int)(off[mid + 1] - o);
-        int c = lm < ls ? -1 : (lm > ls ? 1 : 0);
-        if (c == 0) {
-            int k = 0;
-            for (int i = 0; i < L; i++) {
-                if (!((mask >> i) & 1u)) continue;
-                const uint32_t a = items[o + k++], b = z[i];
-                if (a != b) {
-                    c = a < b ? -1 : 1;
-                    break;
-                }
-            }
-        }
+        if ((int64_t)(off[mid + 1] - off[mid]) < l) lo = mid + 1;
+        else hi = mid;
+    }
+    size_start[l] = (unsigned long long)lo;
+}
+
+// Compares a stored set of size |mask| with the subset of z picked by mask.
+__device__ __forceinline__ int cmp_subset(const uint32_t *__restrict__ it, const uint32_t *__restrict__ zp,
+                                          uint32_t mask) {
+    int k = 0;
+    for (uint32_t mm = mask; mm; mm &= mm - 1) {
+        const uint32_t a = it[k++], b = __ldg(zp + (__ffs(mm) - 1));
+        if (a != b) return a < b ? -1 : 1;
+    }
+    return 0;
+}
+
+// Index of the subset of z (items at zp, ascending) picked by mask, or -1.
+__device__ __forceinline__ int64_t find_subset(const SetsView &v, const uint32_t *zp, uint32_t mask) {
+    const int ls = __popc(mask);
+    int64_t lo = (int64_t)v.size_start[ls], hi = (int64_t)v.size_start[ls + 1];
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        const int c = cmp_subset(v.items + v.off[mid], zp, mask);
+        if (c == 0) return mid;
         if (c < 0) lo = mid + 1;
         else hi = mid;
     }
-    if (lo >= R) return -1;
-    const unsigned long long o = off[lo];
-    if ((int)(off[lo + 1] - o) != ls) return -1;
-    int k = 0;
-    for (int i = 0; i < L; i++)
-        if (((mask >> i) & 1u) && items[o + k++] != z[i]) return -1;
-    return lo;
+    return -1;
 }
 
-// One warp per frequent set z.  WRITE = false: cnt[z] = kept rules of z.
-// WRITE = true: the kept rules of z go to [base[z], base[z] + cnt[z]) in
-// antecedent-mask order.
-template <bool WRITE>
-__global__ void __launch_bounds__(RULE_WARPS * 32)
-rules_kernel(const unsigned long long *__restrict__ off, const uint32_t *__restrict__ items,
-             const uint32_t *__restrict__ sup, int64_t R, uint64_t n, uint32_t ppm, int max_len,
-             unsigned long long *__restrict__ cnt, const unsigned long long *__restrict__ base,
-             unsigned long long *__restrict__ set_index, uint32_t *__restrict__ ante_mask,
-             double *__restrict__ conf, double *__restrict__ lift, int *__restrict__ err) {
-    __shared__ uint32_t zs[RULE_WARPS][RMAX];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int64_t z = (int64_t)blockIdx.x * RULE_WARPS + wid;
-    if (z >= R) return;
-    const int L = (int)(off[z + 1] - off[z]);
-    if (L < 2 || L > max_len) {
-        if (!WRITE && lane == 0) cnt[z] = 0;
-        return;
+// The set of evaluation e < E = ebase[R]: the last z with ebase[z] <= e.
+__device__ __forceinline__ int64_t set_of_eval(const unsigned long long *__restrict__ ebase, int64_t R,
+                                               unsigned long long e) {
+    int64_t lo = 0, hi = R;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (ebase[mid] <= e) lo = mid + 1;
+        else hi = mid;
     }
-    uint32_t *zi = zs[wid];
-    if (lane < L) zi[lane] = items[off[z] + lane];
-    __syncwarp();
-    const uint64_t sz = sup[z];
-    const uint32_t full = (1u << L) - 1u;  // antecedent masks 1 .. full - 1
-    unsigned long long pos = WRITE ? base[z] : 0ull;
-    const uint32_t lt = (1u << lane) - 1u;
-    for (uint32_t m0 = 1; m0 < full; m0 += 32) {
-        const uint32_t m = m0 + lane;
-        bool keep = false;
-        double c = 0.0, l = 0.0;
-        if (m < full) {
-            const int64_t rx = find_subset(off, items, R, zi, L, m);
-            const int64_t ry = find_subset(off, items, R, zi, L, full & ~m);
-            if (rx < 0 || ry < 0) {
-                atomicExch(err, 1);  // a subset is missing: the sets are not downward closed
-            } else {
-                const uint64_t sx = sup[rx], sy = sup[ry];
-                keep = sz * 1000000ull >= (uint64_t)ppm * sx;
-                if (WRITE && keep) {
-                    c = (double)sz / (double)sx;
-                    l = (double)(sz * n) / (double)(sx * sy);
-                }
-            }
-        }
-        const uint32_t bal = __ballot_sync(0xffffffffu, keep);
-        if (WRITE && keep) {
-            const unsigned long long at = pos + __popc(bal & lt);
-            set_index[at] = (unsigned long long)z;
-            ante_mask[at] = m;
-            conf[at] = c;
-            lift[at] = l;
-        }
-        pos += __popc(bal);
-    }
-    if (!WRITE && lane == 0) cnt[z] = pos;
+    return lo - 1;
 }
 
-// Exclusive scan of cnt[0..R) into base[0..R), total into base[R] (one CTA).
+struct Eval {
+    int64_t z;
+    uint32_t mask;
+    uint64_t sz, sx, sy;
+    bool ok;  // both subsets found
+};
+
+__device__ __forceinline__ Eval evaluate(const SetsView &v, const unsigned long long *__restrict__ ebase,
+                                         unsigned long long e) {
+    Eval r;
+    r.z = set_of_eval(ebase, v.R, e);
+    const unsigned long long o = v.off[r.z];
+    const int L = (int)(v.off[r.z + 1] - o);
+    const uint32_t full = (1u << L) - 1u;
+    r.mask = (uint32_t)(e - ebase[r.z]) + 1u;
+    const uint32_t *zp = v.items + o;
+    const int64_t rx = find_subset(v, zp, r.mask);
+    const int64_t ry = find_subset(v, zp, full & ~r.mask);
+    r.ok = rx >= 0 && ry >= 0;
+    r.sz = v.sup[r.z];
+    r.sx = r.ok ? v.sup[rx] : 1;
+    r.sy = r.ok ? v.sup[ry] : 1;
+    return r;
+}
+
+// Candidate rules of a set: 2^L - 2 for 2 <= L <= max_len, else none.
+struct SetEvals {
+    const unsigned long long *off;
+    int max_len;
+    __device__ __forceinline__ unsigned long long operator()(unsigned long long i) const {
+        const int L = (int)(off[i + 1] - off[i]);
+        return (L >= 2 && L <= max_len) ? (1ull << L) - 2ull : 0ull;
+    }
+};
+
+struct WordPop {
+    const uint32_t *bits;
+    __device__ __forceinline__ unsigned long long operator()(unsigned long long i) const {
+        return (unsigned long long)__popc(bits[i]);
+    }
+};
+
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Exclusive scan of src(0 .. n-1) into out[0 .. n], out[n] = total, in three
+// launches: chunk sums, a scan of the chunk sums in one CTA, a rescan of every
+// chunk from its base.
+template <class Src>
+__global__ void __launch_bounds__(SCAN_T)
+scan_sum_kernel(Src src, unsigned long long n, unsigned long long *__restrict__ part) {
+    __shared__ unsigned long long s[SCAN_T / 32];
+    const unsigned long long b = (unsigned long long)blockIdx.x * SCAN_CHUNK + (unsigned long long)threadIdx.x * SCAN_I;
+    unsigned long long v = 0;
+#pragma unroll
+    for (int i = 0; i < SCAN_I; i++)
+        if (b + i < n) v += src(b + i);
+    v = warp_sum_u64(v);
+    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        unsigned long long t = s[threadIdx.x];
+        t = warp_sum_u64(t);
+        if (threadIdx.x == 0) part[blockIdx.x] = t;
+    }
+}
+
 __global__ void __launch_bounds__(1024)
-rules_scan_kernel(const unsigned long long *__restrict__ cnt, int64_t R, unsigned long long *__restrict__ base) {
+scan_part_kernel(unsigned long long *__restrict__ part, unsigned long long np) {
     __shared__ unsigned long long s[1024];
-    const int64_t seg = (R + 1023) / 1024;
-    const int64_t b = (int64_t)threadIdx.x * seg, e = b + seg < R ? b + seg : R;
+    const unsigned long long seg = (np + 1023) / 1024;
+    const unsigned long long b = threadIdx.x * seg, e = b + seg < np ? b + seg : np;
     unsigned long long sum = 0;
-    for (int64_t i = b; i < e; i++) sum += cnt[i];
+    for (unsigned long long i = b; i < e; i++) sum += part[i];
     s[threadIdx.x] = sum;
     __syncthreads();
     for (int o = 1; o < 1024; o <<= 1) {
@@ -131,11 +182,107 @@ rules_scan_kernel(const unsigned long long *__restrict__ cnt, int64_t R, unsigne
         __syncthreads();
     }
     unsigned long long run = s[threadIdx.x] - sum;
-    for (int64_t i = b; i < e; i++) {
-        base[i] = run;
-        run += cnt[i];
+    for (unsigned long long i = b; i < e; i++) {
+        const unsigned long long v = part[i];
+        part[i] = run;
+        run += v;
     }
-    if (threadIdx.x == 1023) base[R] = s[1023];
+    if (threadIdx.x == 1023) part[np] = s[1023];
+}
+
+template <class Src>
+__global__ void __launch_bounds__(SCAN_T)
+scan_out_kernel(Src src, unsigned long long n, const unsigned long long *__restrict__ part,
+                unsigned long long *__restrict__ out) {
+    __shared__ unsigned long long s[SCAN_T / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned long long b = (unsigned long long)blockIdx.x * SCAN_CHUNK + (unsigned long long)threadIdx.x * SCAN_I;
+    unsigned long long v[SCAN_I], sum = 0;
+#pragma unroll
+    for (int i = 0; i < SCAN_I; i++) {
+        v[i] = b + i < n ? src(b + i) : 0ull;
+        sum += v[i];
+    }
+    unsigned long long x = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s[warp] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long acc = part[blockIdx.x];
+        for (int w = 0; w < SCAN_T / 32; w++) {
+            const unsigned long long t = s[w];
+            s[w] = acc;
+            acc += t;
+        }
+    }
+    __syncthreads();
+    unsigned long long run = s[warp] + x - sum;
+#pragma unroll
+    for (int i = 0; i < SCAN_I; i++) {
+        if (b + i < n) out[b + i] = run;
+        run += v[i];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) out[n] = part[gridDim.x];
+}
+
+// One thread per evaluation; warp w of the grid-stride loop owns evaluations
+// [32w, 32w + 32) and stores their keep bits as one word.
+__global__ void __launch_bounds__(RT)
+rule_keep_kernel(SetsView v, const unsigned long long *__restrict__ ebase, unsigned long long E, uint32_t ppm,
+                 uint32_t *__restrict__ keep_bits, int *__restrict__ err) {
+    const int lane = threadIdx.x & 31;
+    const unsigned long long nw = (E + 31) / 32;
+    const unsigned long long tw = (unsigned long long)gridDim.x * (RT / 32);
+    for (unsigned long long w = ((unsigned long long)blockIdx.x * RT + threadIdx.x) >> 5; w < nw; w += tw) {
+        const unsigned long long e = w * 32 + lane;
+        bool keep = false;
+        if (e < E) {
+            const Eval r = evaluate(v, ebase, e);
+            if (!r.ok) atomicExch(err, 1);  // a subset is missing: not a mine's output
+            else keep = r.sz * 1000000ull >= (uint64_t)ppm * r.sx;
+        }
+        const uint32_t bal = __ballot_sync(0xffffffffu, keep);
+        if (lane == 0) keep_bits[w] = bal;
+    }
+}
+
+__global__ void __launch_bounds__(RT)
+rule_write_kernel(SetsView v, const unsigned long long *__restrict__ ebase, unsigned long long E, uint64_t n,
+                  const uint32_t *__restrict__ keep_bits, const unsigned long long *__restrict__ kbase,
+                  unsigned long long *__restrict__ set_index, uint32_t *__restrict__ ante_mask,
+                  double *__restrict__ conf, double *__restrict__ lift) {
+    const int lane = threadIdx.x & 31;
+    const unsigned long long nw = (E + 31) / 32;
+    const unsigned long long tw = (unsigned long long)gridDim.x * (RT / 32);
+    const uint32_t lt = (1u << lane) - 1u;
+    for (unsigned long long w = ((unsigned long long)blockIdx.x * RT + threadIdx.x) >> 5; w < nw; w += tw) {
+        const uint32_t bits = keep_bits[w];
+        if (!((bits >> lane) & 1u)) continue;
+        const Eval r = evaluate(v, ebase, w * 32 + lane);
+        const unsigned long long at = kbase[w] + __popc(bits & lt);
+        set_index[at] = (unsigned long long)r.z;
+        ante_mask[at] = r.mask;
+        conf[at] = (double)r.sz / (double)r.sx;
+        lift[at] = (double)(r.sz * n) / (double)(r.sx * r.sy);
+    }
+}
+
+template <class Src>
+int scan_into(fim_ctx *ctx, Src src, unsigned long long n, unsigned long long *out) {
+    const unsigned long long np = (n + SCAN_CHUNK - 1) / SCAN_CHUNK;
+    FIM_TRY(fim_reserve(ctx, ctx->rule_part, sizeof(unsigned long long) * (size_t)(np + 1)));
+    unsigned long long *part = ctx->rule_part.as<unsigned long long>();
+    cudaStream_t st = ctx->stream;
+    ctx->launches += 3;
+    scan_sum_kernel<<<(unsigned)np, SCAN_T, 0, st>>>(src, n, part);
+    scan_part_kernel<<<1, 1024, 0, st>>>(part, np);
+    scan_out_kernel<<<(unsigned)np, SCAN_T, 0, st>>>(src, n, part, out);
+    FIM_CUDA_TRY(cudaGetLastError());
+    return FIM_OK;
 }
 
 }  // namespace
@@ -156,44 +303,67 @@ int fim_rules(fim_ctx *ctx, uint32_t min_conf_ppm, int max_len, uint64_t *n_rule
     const int64_t R = (int64_t)ctx->out_sets;
     ctx->rules_n = 0;
     ctx->rules_of = 0;
+    ctx->rules_evaluated = 0;
     if (R > 0) {
-        FIM_TRY(fim_reserve(ctx, ctx->rule_cnt, sizeof(unsigned long long) * (size_t)(2 * R + 1)));
-        unsigned long long *cnt = ctx->rule_cnt.as<unsigned long long>(), *base = cnt + R;
-        int *err = ctx->dev_flag.as<int>() + 2;
-        FIM_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
-        const unsigned blocks = (unsigned)ceil_div64(R, RULE_WARPS);
-        const unsigned long long *off = ctx->out_off.as<unsigned long long>();
-        const uint32_t *items = ctx->out_items.as<uint32_t>(), *sup = ctx->out_sup.as<uint32_t>();
-        ctx->launches += 2;
-        rules_kernel<false><<<blocks, RULE_WARPS * 32, 0, st>>>(off, items, sup, R, (uint64_t)ctx->n, min_conf_ppm,
-                                                                max_len, cnt, nullptr, nullptr, nullptr, nullptr,
-                                                                nullptr, err);
-        rules_scan_kernel<<<1, 1024, 0, st>>>(cnt, R, base);
-        FIM_CUDA_TRY(cudaGetLastError());
-        unsigned long long total = 0;
-        int bad = 0;
-        FIM_CUDA_TRY(cudaMemcpyAsync(&total, base + R, sizeof(total), cudaMemcpyDeviceToHost, st));
-        FIM_CUDA_TRY(cudaMemcpyAsync(&bad, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+        // ebase [R + 1], then size_start [NSIZE]
+        FIM_TRY(fim_reserve(ctx, ctx->rule_base, sizeof(unsigned long long) * (size_t)(R + 1 + NSIZE)));
+        unsigned long long *ebase = ctx->rule_base.as<unsigned long long>(), *size_start = ebase + R + 1;
+        const SetsView v{ctx->out_off.as<unsigned long long>(), ctx->out_items.as<uint32_t>(),
+                         ctx->out_sup.as<uint32_t>(), size_start, R};
+        ctx->launches++;
+        size_bounds_kernel<<<1, NSIZE, 0, st>>>(v.off, R, size_start);
+        FIM_TRY(scan_into(ctx, SetEvals{v.off, max_len}, (unsigned long long)R, ebase));
+        unsigned long long E = 0;
+        FIM_CUDA_TRY(cudaMemcpyAsync(&E, ebase + R, sizeof(E), cudaMemcpyDeviceToHost, st));
         FIM_CUDA_TRY(cudaStreamSynchronize(st));
-        if (bad) return FIM_E_STATE;  // not the output of a mine
-        if (total) {
-            FIM_TRY(fim_reserve(ctx, ctx->rule_set, sizeof(unsigned long long) * (size_t)total));
-            FIM_TRY(fim_reserve(ctx, ctx->rule_mask, sizeof(uint32_t) * (size_t)total));
-            FIM_TRY(fim_reserve(ctx, ctx->rule_conf, sizeof(double) * (size_t)total));
-            FIM_TRY(fim_reserve(ctx, ctx->rule_lift, sizeof(double) * (size_t)total));
+        ctx->rules_evaluated = E;
+        if (E > 0) {
+            const unsigned long long nw = (E + 31) / 32;
+            FIM_TRY(fim_reserve(ctx, ctx->rule_bits, sizeof(uint32_t) * (size_t)nw));
+            FIM_TRY(fim_reserve(ctx, ctx->rule_kbase, sizeof(unsigned long long) * (size_t)(nw + 1)));
+            uint32_t *bits = ctx->rule_bits.as<uint32_t>();
+            unsigned long long *kbase = ctx->rule_kbase.as<unsigned long long>();
+            int *err = ctx->dev_flag.as<int>() + 2;
+            FIM_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
+            const unsigned long long want = (nw + RT / 32 - 1) / (RT / 32);
+            const unsigned long long cap = (unsigned long long)(ctx->num_sms > 0 ? ctx->num_sms : 1) * 8ull;  // 2,048 threads per SM
+            const unsigned grid = (unsigned)(want < cap ? want : cap);
             ctx->launches++;
-            rules_kernel<true><<<blocks, RULE_WARPS * 32, 0, st>>>(
-                off, items, sup, R, (uint64_t)ctx->n, min_conf_ppm, max_len, cnt, base,
-                ctx->rule_set.as<unsigned long long>(), ctx->rule_mask.as<uint32_t>(), ctx->rule_conf.as<double>(),
-                ctx->rule_lift.as<double>(), err);
+            rule_keep_kernel<<<grid, RT, 0, st>>>(v, ebase, E, min_conf_ppm, bits, err);
             FIM_CUDA_TRY(cudaGetLastError());
+            FIM_TRY(scan_into(ctx, WordPop{bits}, nw, kbase));
+            unsigned long long total = 0;
+            int bad = 0;
+            FIM_CUDA_TRY(cudaMemcpyAsync(&total, kbase + nw, sizeof(total), cudaMemcpyDeviceToHost, st));
+            FIM_CUDA_TRY(cudaMemcpyAsync(&bad, err, sizeof(int), cudaMemcpyDeviceToHost, st));
             FIM_CUDA_TRY(cudaStreamSynchronize(st));
+            if (bad) return FIM_E_STATE;  // the held sets are not downward closed
+            if (total) {
+                FIM_TRY(fim_reserve(ctx, ctx->rule_set, sizeof(unsigned long long) * (size_t)total));
+                FIM_TRY(fim_reserve(ctx, ctx->rule_mask, sizeof(uint32_t) * (size_t)total));
+                FIM_TRY(fim_reserve(ctx, ctx->rule_conf, sizeof(double) * (size_t)total));
+                FIM_TRY(fim_reserve(ctx, ctx->rule_lift, sizeof(double) * (size_t)total));
+                ctx->launches++;
+                rule_write_kernel<<<grid, RT, 0, st>>>(v, ebase, E, (uint64_t)ctx->n, bits, kbase,
+                                                       ctx->rule_set.as<unsigned long long>(),
+                                                       ctx->rule_mask.as<uint32_t>(), ctx->rule_conf.as<double>(),
+                                                       ctx->rule_lift.as<double>());
+                FIM_CUDA_TRY(cudaGetLastError());
+                FIM_CUDA_TRY(cudaStreamSynchronize(st));
+            }
+            ctx->rules_n = total;
         }
-        ctx->rules_n = total;
     }
     ctx->rules_of = ctx->mine_serial;
     if (ctx->bytes_held > ctx->stats.peak_device_bytes) ctx->stats.peak_device_bytes = ctx->bytes_held;
     *n_rules = ctx->rules_n;
+    return FIM_OK;
+}
+
+int fim_rules_evaluated(const fim_ctx *ctx, uint64_t *n_evaluated) {
+    if (!ctx || !n_evaluated) return FIM_E_INVAL;
+    if (!ctx->mined || ctx->rules_of != ctx->mine_serial) return FIM_E_STATE;
+    *n_evaluated = ctx->rules_evaluated;
     return FIM_OK;
 }
 

@@ -86,6 +86,7 @@ def _load():
         "fim_set_tuning": (ctypes.c_int, [P, ctypes.c_char_p, I64]),
         "fim_rules": (ctypes.c_int, [P, U32, ctypes.c_int, ctypes.POINTER(U64)]),
         "fim_fetch_rules": (ctypes.c_int, [P, ctypes.POINTER(U64), P, P, P, P, U64, U32]),
+        "fim_rules_evaluated": (ctypes.c_int, [P, ctypes.POINTER(U64)]),
         "fim_batch_slices": (ctypes.c_int, [P, P, U64]),
         "fim_pair_supports_noalloc": (ctypes.c_int, [P, P, I64, I32, P, P]),
         "fim_minsup_from_ppm": (U64, [I64, U32]),
@@ -250,6 +251,13 @@ def fim_rules(ctx, min_conf_ppm: int, max_len: int = 0) -> int:
     returns their number."""
     n = ctypes.c_uint64()
     _check(_lib.fim_rules(ctx, int(min_conf_ppm), int(max_len), ctypes.byref(n)), "fim_rules")
+    return int(n.value)
+
+
+def fim_rules_evaluated(ctx) -> int:
+    """Candidate rules the last fim_rules tested (sum of 2^|Z| - 2)."""
+    n = ctypes.c_uint64()
+    _check(_lib.fim_rules_evaluated(ctx, ctypes.byref(n)), "fim_rules_evaluated")
     return int(n.value)
 
 

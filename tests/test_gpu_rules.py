@@ -75,6 +75,25 @@ def test_long_sets_and_many_warps(ctx):
     _same(got, _want(c, n, 1_000_000))
 
 
+def test_many_sets_few_candidates(ctx):
+    # every subset of 14 items once: 16,383 frequent sets (two scan chunks of
+    # set counts); max_len 2 leaves 182 candidate rules, all with conf 1/2
+    m = 14
+    c = datagen.from_lists([[j for j in range(m) if i >> j & 1] for i in range(1 << m)], m)
+    got = _gpu_rules(ctx, c, 1, 0, max_len=2)
+    assert fim.fim_rules_evaluated(ctx) == 2 * 91
+    assert set(got.conf.tolist()) == {0.5} and set(got.lift.tolist()) == {1.0}
+    _same(got, _want(c, 1, 0, max_len=2))
+
+
+def test_evaluated_count(ctx):
+    c = datagen.random_dense(250, 11, 0.5, 21)
+    _gpu_rules(ctx, c, 15, 700_000)
+    its = oracle.apriori(c.indptr, c.indices, c.m, 15)
+    L = np.diff(its.offsets.astype(np.int64))
+    assert fim.fim_rules_evaluated(ctx) == int(((np.int64(1) << L[L >= 2]) - 2).sum())
+
+
 def test_zipf_tiles_and_ragged(ctx):
     for n, m, s in [(4097, 130, 2), (70_001, 200, 3)]:
         c = datagen.zipf_baskets(n, m, 0.9, 6.0, s)

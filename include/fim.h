@@ -248,6 +248,46 @@ int fim_mlp_backward(fim_ctx *ctx, const float *params, const float *x, const fl
 int fim_mlp_adam(fim_ctx *ctx, float *params, const float *grad, float *m, float *v,
                  int step, float lr, float beta1, float beta2, float eps);
 
+/* ---- one mine split over several GPUs ------------------------------------
+ * The paper's decomposition of the matrix into parts mined separately and
+ * merged (Section II), in the form that needs no communication during the
+ * mine: after the pair pass, every frequent pair {a, b} (a < b in the
+ * miner's internal item order) roots a prefix class holding the frequent sets
+ * whose two smallest items are a and b; these classes partition the sets of
+ * size >= 3.
+ *
+ * fim_mine_shard: fim_mine restricted to shard `shard` of n_shards (1 <=
+ * n_shards <= FIM_MAX_SHARDS).  Every shard builds the same matrix and runs
+ * the singleton and pair passes in full; the root classes in (a, b) order are
+ * cut into n_shards contiguous ranges of about equal estimated cost (1 + k +
+ * k(k-1)/2 for a class with k candidates), computed from integers every shard
+ * derives identically, and the shard mines only its range.  Shard 0 also
+ * reports the frequent singletons and pairs.  The held output (canonical,
+ * fetched with fim_fetch_results) is the shard's part: the parts of shards
+ * 0 .. n_shards-1 are disjoint and their union is fim_mine's answer.
+ * n_shards == 1 is fim_mine.  Errors: as fim_mine; FIM_E_INVAL for a shard
+ * outside [0, n_shards) or n_shards outside [1, FIM_MAX_SHARDS]. */
+#define FIM_MAX_SHARDS 1024
+int fim_mine_shard(fim_ctx *ctx, uint64_t minsup, uint32_t flags, int shard, int n_shards);
+
+/* fim_merge_results: replaces the ctx's held itemsets with the canonical
+ * union of n_parts disjoint canonical lists -- the fim_fetch_results outputs
+ * of the shards of one database.  Part p has n_sets[p] sets and
+ * n_items_total[p] items: offsets[p] (n_sets[p] + 1 entries, first 0, last
+ * n_items_total[p]), items[p] (the caller's ids, < n_items), supports[p].  All
+ * arrays are host pointers (FIM_INPUT_HOST) or device pointers of the ctx's
+ * GPU (FIM_INPUT_DEVICE); they are copied and may be freed on return.
+ * n_trans is the database's transaction count (the n of lift in fim_rules).
+ * The result is fetched with fim_fetch_results and feeds fim_rules, like a
+ * mine's.  Parts that overlap give duplicate sets: the call does not check.
+ * Errors: FIM_E_INVAL (a NULL array, malformed offsets, a set longer than 255
+ * items, an item >= n_items, n_trans or n_items out of range), FIM_E_NOMEM,
+ * FIM_E_CUDA. */
+int fim_merge_results(fim_ctx *ctx, int64_t n_trans, int32_t n_items, int n_parts,
+                      const uint64_t *n_sets, const uint64_t *n_items_total,
+                      const uint64_t *const *offsets, const uint32_t *const *items,
+                      const uint32_t *const *supports, uint32_t flags);
+
 /* ---- association rules -------------------------------------------------
  * Section IV.A names confidence and lift beside support as the measures the
  * mined itemsets are evaluated with; the paper prints no formula, so these

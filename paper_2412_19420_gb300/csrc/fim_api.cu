@@ -247,7 +247,7 @@ int mine_once(fim_ctx *ctx, uint32_t thr, uint32_t flags, MineState &ms, bool *r
     FIM_CUDA_TRY(cudaMemsetAsync(d_ctr, 0, sizeof(MineCounters), st));
     cudaEventRecord(ctx->ev[0], st);
     FIM_TRY(launch_rank_items(ctx, thr, d_ctr));
-    FIM_TRY(launch_emit_singletons(ctx, d_ctr));
+    if (ctx->shard == 0) FIM_TRY(launch_emit_singletons(ctx, d_ctr));
     FIM_CUDA_TRY(cudaMemcpyAsync(&ctx->host_ctr, d_ctr, sizeof(MineCounters), cudaMemcpyDeviceToHost, st));
     FIM_CUDA_TRY(cudaStreamSynchronize(st));
     ctx->mfreq = ctx->host_ctr.m_freq;
@@ -280,6 +280,8 @@ int mine_once(fim_ctx *ctx, uint32_t thr, uint32_t flags, MineState &ms, bool *r
         if (rc == FIM_OK) ctx->stats.pair_path = 1;
         else FIM_TRY(launch_pairs_popc(ctx));
         FIM_TRY(launch_pairs_finalize(ctx, thr, d_ctr));
+        // a shard of a split mine takes only the root classes it owns
+        if (ctx->n_shards > 1) FIM_TRY(launch_shard_roots(ctx, d_ctr, ctx->shard, ctx->n_shards));
     }
     cudaEventRecord(ctx->ev[2], st);
     const bool do_dfs = do_pairs && mf >= 3 && (maxlen == 0 || maxlen >= 3);
@@ -402,8 +404,8 @@ int mine_once(fim_ctx *ctx, uint32_t thr, uint32_t flags, MineState &ms, bool *r
         return FIM_OK;
     }
     int lmax = c.max_len;
-    if (mf >= 1 && lmax < 1) lmax = 1;
-    if (c.n_roots > 0 && lmax < 2) lmax = 2;
+    if (ctx->shard == 0 && mf >= 1 && lmax < 1) lmax = 1;
+    if (ctx->shard == 0 && c.n_records > (unsigned long long)mf && lmax < 2) lmax = 2;
     ctx->host_ctr.max_len = lmax;
     FIM_TRY(launch_compact(ctx, c.n_records, 1, ctx->m));
     cudaEventRecord(ctx->ev[4], st);
@@ -468,9 +470,20 @@ int fim_mine(fim_ctx *ctx, uint64_t minsup, uint32_t flags) {
     s.dfs_workers = (uint64_t)ctx->num_sms * (uint64_t)ctx->dfs_ctas_per_sm;
     s.dfs_root_ns = c.root_ns;
     if (ctx->bytes_held > s.peak_device_bytes) s.peak_device_bytes = ctx->bytes_held;
+    ctx->out_n = ctx->n;
     ctx->mined = true;
     ctx->mine_serial++;
     return FIM_OK;
+}
+
+int fim_mine_shard(fim_ctx *ctx, uint64_t minsup, uint32_t flags, int shard, int n_shards) {
+    if (!ctx || n_shards < 1 || n_shards > FIM_MAX_SHARDS || shard < 0 || shard >= n_shards) return FIM_E_INVAL;
+    ctx->shard = shard;
+    ctx->n_shards = n_shards;
+    const int rc = fim_mine(ctx, minsup, flags);
+    ctx->shard = 0;
+    ctx->n_shards = 1;
+    return rc;
 }
 
 int fim_fetch_results(fim_ctx *ctx, uint64_t *n_sets, uint64_t *n_items_total, uint64_t *offsets,

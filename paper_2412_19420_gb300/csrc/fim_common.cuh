@@ -207,6 +207,9 @@ struct fim_ctx {
     DevBuf out_off, out_items, out_sup;
     uint64_t out_sets = 0, out_items_total = 0;
     uint64_t mine_serial = 0;   // completed fim_mine calls; names the output held
+    int64_t out_n = 0;          // transactions behind the held output
+    int shard = 0, n_shards = 1; // prefix-class share of the mine in progress
+    DevBuf shard_cost, merge_off;
 
     // association rules of the held output
     DevBuf rule_base, rule_part, rule_bits, rule_kbase;  // evaluation space, scans, keep words
@@ -284,7 +287,11 @@ int launch_sparse_items(fim_ctx *ctx, int mf, int64_t cap);
 int launch_root_order(fim_ctx *ctx, MineCounters *d_ctr, size_t npairs);
 
 // k_compact.cu
-int launch_compact(fim_ctx *ctx, uint64_t n_records, int n_db, int m_max);
+// identity_items: the records already hold the caller's item ids (a merge)
+int launch_compact(fim_ctx *ctx, uint64_t n_records, int n_db, int m_max, bool identity_items = false);
+
+// k_shard.cu: append the root classes shard `shard` of n_shards owns
+int launch_shard_roots(fim_ctx *ctx, MineCounters *d_ctr, int shard, int n_shards);
 
 // ---------------------------------------------------------------- device helpers
 #ifdef __CUDACC__

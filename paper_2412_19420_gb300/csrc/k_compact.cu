@@ -37,9 +37,11 @@ __global__ void prep_keys_kernel(unsigned long long R, const unsigned long long 
     const unsigned long long off = rec_off[r];
     const int len = (int)rec_len[r];
     const uint32_t db = db_bits ? rec_db[r] : 0u;
-    const int32_t *perm = perm_base + dbs[db].item_off;
     uint32_t *it = items + off;
-    for (int q = 0; q < len; q++) it[q] = (uint32_t)perm[it[q]];
+    if (perm_base) {  // null: the items are already the caller's ids
+        const int32_t *perm = perm_base + dbs[db].item_off;
+        for (int q = 0; q < len; q++) it[q] = (uint32_t)perm[it[q]];
+    }
     for (int q = 1; q < len; q++) {  // insertion sort (sets are short)
         const uint32_t v = it[q];
         int z = q - 1;
@@ -306,7 +308,7 @@ int bits_for(int m) {
 
 }  // namespace
 
-int launch_compact(fim_ctx *ctx, uint64_t R, int n_db, int m_max) {
+int launch_compact(fim_ctx *ctx, uint64_t R, int n_db, int m_max, bool identity_items) {
     cudaStream_t st = ctx->stream;
     const int db_bits = n_db > 1 ? bits_for(n_db) : 0;
     const unsigned long long total_items = ctx->host_ctr.n_rec_items;
@@ -346,7 +348,7 @@ int launch_compact(fim_ctx *ctx, uint64_t R, int n_db, int m_max) {
         uint32_t *ia = ctx->idx_a.as<uint32_t>(), *ib = ctx->idx_b.as<uint32_t>();
         prep_keys_kernel<<<(unsigned)ceil_div64((int64_t)R, 256), 256, 0, st>>>(
             R, ctx->rec_off.as<unsigned long long>(), ctx->rec_len.as<uint32_t>(),
-            ctx->rec_items.as<uint32_t>(), ctx->perm.as<int32_t>(), ctx->dbdesc.as<DbDesc>(),
+            ctx->rec_items.as<uint32_t>(), identity_items ? nullptr : ctx->perm.as<int32_t>(), ctx->dbdesc.as<DbDesc>(),
             ctx->rec_db.as<uint32_t>(), db_bits, bits, kw, keys, ia);
         nk++;
         // LSD: least significant word first; within a word, low digits first.
@@ -424,7 +426,7 @@ int launch_compact(fim_ctx *ctx, uint64_t R, int n_db, int m_max) {
     mix((uint64_t)(uintptr_t)ctx->idx_b.p); mix((uint64_t)(uintptr_t)ctx->hist.p);
     mix((uint64_t)(uintptr_t)ctx->scan_tmp.p); mix((uint64_t)(uintptr_t)ctx->rec_off.p);
     mix((uint64_t)(uintptr_t)ctx->rec_items.p); mix((uint64_t)(uintptr_t)ctx->out_off.p);
-    mix((uint64_t)(uintptr_t)ctx->out_items.p); mix((uint64_t)(uintptr_t)ctx->perm.p);
+    mix((uint64_t)(uintptr_t)ctx->out_items.p); mix(identity_items ? 0ull : (uint64_t)(uintptr_t)ctx->perm.p);
     mix((uint64_t)(uintptr_t)ctx->dbdesc.p); mix((uint64_t)(uintptr_t)ctx->rec_db.p);
     mix((uint64_t)(uintptr_t)ctx->kv_a.p); mix((uint64_t)(uintptr_t)ctx->kv_b.p);
     mix((uint64_t)(uintptr_t)ctx->scan_part.p);

@@ -82,7 +82,7 @@ pairs_finalize_kernel(const int *__restrict__ pair_cnt, int mf, int mpw, uint32_
                       uint32_t *__restrict__ pairbits, MineCounters *ctr,
                       unsigned long long *rec_off, uint32_t *rec_len, uint32_t *rec_sup,
                       uint32_t *rec_items, unsigned long long rec_cap, unsigned long long items_cap,
-                      uint32_t *root_a, uint32_t *root_b, uint32_t *root_sup, int emit) {
+                      uint32_t *root_a, uint32_t *root_b, uint32_t *root_sup, int emit, int emit_roots) {
     const int a = blockIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     for (int w = warp; w < mpw; w += nwarp) {
@@ -98,8 +98,10 @@ pairs_finalize_kernel(const int *__restrict__ pair_cnt, int mf, int mpw, uint32_
         if (lane == 0) {
             rbase = atomicAdd(&ctr->n_records, (unsigned long long)cnt);
             ibase = atomicAdd(&ctr->n_rec_items, 2ull * cnt);
-            root = atomicAdd(&ctr->n_roots, (unsigned long long)cnt);
-            atomicAdd((unsigned long long *)&ctr->pending, (unsigned long long)cnt);
+            if (emit_roots) {
+                root = atomicAdd(&ctr->n_roots, (unsigned long long)cnt);
+                atomicAdd((unsigned long long *)&ctr->pending, (unsigned long long)cnt);
+            }
         }
         rbase = __shfl_sync(0xffffffffu, rbase, 0);
         ibase = __shfl_sync(0xffffffffu, ibase, 0);
@@ -116,9 +118,11 @@ pairs_finalize_kernel(const int *__restrict__ pair_cnt, int mf, int mpw, uint32_
             } else {
                 atomicOr(&ctr->overflow, r < rec_cap ? 2 : 1);
             }
-            root_a[root + pos] = (uint32_t)a;
-            root_b[root + pos] = (uint32_t)b;
-            root_sup[root + pos] = s;
+            if (emit_roots) {
+                root_a[root + pos] = (uint32_t)a;
+                root_b[root + pos] = (uint32_t)b;
+                root_sup[root + pos] = s;
+            }
         }
     }
 }
@@ -160,7 +164,8 @@ int launch_pairs_finalize(fim_ctx *ctx, uint32_t thr, MineCounters *d_ctr) {
         ctx->rec_off.as<unsigned long long>(), ctx->rec_len.as<uint32_t>(),
         ctx->rec_sup.as<uint32_t>(), ctx->rec_items.as<uint32_t>(), ctx->rec_cap,
         ctx->rec_items_cap, roots, roots + npairs, roots + 2 * npairs,
-        (ctx->mflags & FIM_MAXLEN(0xff)) == 0 || (ctx->mflags >> 24) >= 2);
+        ctx->shard == 0 && ((ctx->mflags & FIM_MAXLEN(0xff)) == 0 || (ctx->mflags >> 24) >= 2),
+        ctx->n_shards == 1);
     FIM_CUDA_TRY(cudaGetLastError());
     return FIM_OK;
 }

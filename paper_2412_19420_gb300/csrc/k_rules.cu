@@ -344,7 +344,7 @@ int fim_rules(fim_ctx *ctx, uint32_t min_conf_ppm, int max_len, uint64_t *n_rule
                 FIM_TRY(fim_reserve(ctx, ctx->rule_conf, sizeof(double) * (size_t)total));
                 FIM_TRY(fim_reserve(ctx, ctx->rule_lift, sizeof(double) * (size_t)total));
                 ctx->launches++;
-                rule_write_kernel<<<grid, RT, 0, st>>>(v, ebase, E, (uint64_t)ctx->n, bits, kbase,
+                rule_write_kernel<<<grid, RT, 0, st>>>(v, ebase, E, (uint64_t)ctx->out_n, bits, kbase,
                                                        ctx->rule_set.as<unsigned long long>(),
                                                        ctx->rule_mask.as<uint32_t>(), ctx->rule_conf.as<double>(),
                                                        ctx->rule_lift.as<double>());

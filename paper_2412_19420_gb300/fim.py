@@ -85,6 +85,8 @@ def _load():
                                         ctypes.c_float, ctypes.c_float]),
         "fim_set_tuning": (ctypes.c_int, [P, ctypes.c_char_p, I64]),
         "fim_rules": (ctypes.c_int, [P, U32, ctypes.c_int, ctypes.POINTER(U64)]),
+        "fim_mine_shard": (ctypes.c_int, [P, U64, U32, ctypes.c_int, ctypes.c_int]),
+        "fim_merge_results": (ctypes.c_int, [P, I64, I32, ctypes.c_int, P, P, P, P, P, U32]),
         "fim_fetch_rules": (ctypes.c_int, [P, ctypes.POINTER(U64), P, P, P, P, U64, U32]),
         "fim_rules_evaluated": (ctypes.c_int, [P, ctypes.POINTER(U64)]),
         "fim_batch_slices": (ctypes.c_int, [P, P, U64]),
@@ -227,6 +229,37 @@ def fim_fetch_results(ctx, out=None) -> Itemsets:
     if dev:
         return Itemsets(off[: R + 1], it[:T], sup[:R])
     return Itemsets(off[: R + 1].copy(), it[:T].copy(), sup[:R].copy())
+
+
+FIM_MAX_SHARDS = 1024
+
+
+def fim_mine_shard(ctx, minsup: int, flags: int, shard: int, n_shards: int) -> None:
+    """fim_mine restricted to one shard's root classes (include/fim.h)."""
+    _check(_lib.fim_mine_shard(ctx, int(minsup), int(flags), int(shard), int(n_shards)), "fim_mine_shard")
+
+
+def fim_merge_results(ctx, n_trans: int, n_items: int, parts) -> None:
+    """Replace the held itemsets with the canonical union of disjoint parts,
+    each an Itemsets or an (offsets, items, supports) triple -- all numpy
+    (host) or all torch CUDA tensors on the ctx's device."""
+    parts = [(p.offsets, p.items, p.supports) if hasattr(p, "offsets") else tuple(p) for p in parts]
+    if not parts:
+        raise ValueError("fim_merge_results needs at least one part")
+    flat = [a for p in parts for a in p]
+    _sync_torch(*flat)
+    ptrs = [_ptr(a) for a in flat]
+    dev = ptrs[0][1]
+    if any(d != dev for _, d in ptrs):
+        raise ValueError("fim_merge_results: parts must all be host or all device")
+    n = len(parts)
+    n_sets = (ctypes.c_uint64 * n)(*[int(p[0].shape[0]) - 1 for p in parts])
+    n_items_total = (ctypes.c_uint64 * n)(*[int(p[0][-1]) if int(p[0].shape[0]) > 1 else 0 for p in parts])
+    offs = (ctypes.c_void_p * n)(*[ptrs[3 * i][0] for i in range(n)])
+    its = (ctypes.c_void_p * n)(*[ptrs[3 * i + 1][0] for i in range(n)])
+    sups = (ctypes.c_void_p * n)(*[ptrs[3 * i + 2][0] for i in range(n)])
+    _check(_lib.fim_merge_results(ctx, int(n_trans), int(n_items), n, n_sets, n_items_total, offs, its, sups,
+                                  FIM_INPUT_DEVICE if dev else FIM_INPUT_HOST), "fim_merge_results")
 
 
 FIM_RULES_MAX_LEN = 20

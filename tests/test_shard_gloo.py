@@ -1,0 +1,115 @@
+"""The multi-rank path of a split mine, on CPU: two gloo ranks run
+``shard.mine_sharded`` end to end -- size exchange, point-to-point transfer of
+every rank's (offsets, items, supports), merge on rank 0 -- with the GPU calls
+replaced by a stand-in that mines with the oracle and splits the answer
+between the ranks.  The GPU kernels of the split (ownership of root classes,
+merge) are covered by tests/test_gpu_shard.py on one GPU.
+"""
+import os
+import socket
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+dist = pytest.importorskip("torch.distributed")
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+class _OracleApi:
+    """Stand-in for the library binding: every rank mines the whole database
+    with the oracle and keeps its share -- singletons and pairs on rank 0,
+    larger sets by their two smallest items, as the GPU split does."""
+
+    def __init__(self, skew=False):
+        self.skew = skew
+
+    def fim_build_bitmaps(self, ctx, indptr, indices, n_items):
+        ctx["db"] = (np.asarray(indptr), np.asarray(indices), n_items)
+
+    def fim_mine_shard(self, ctx, minsup, flags, shard, n_shards):
+        import oracle
+        ip, ix, m = ctx["db"]
+        full = oracle.apriori(ip, ix, m, minsup)
+        sets = []
+        for q in range(len(full)):
+            x = tuple(int(v) for v in full.items[full.offsets[q]:full.offsets[q + 1]])
+            if len(x) <= 2:
+                own = shard == 0
+            elif self.skew:  # every class on the last rank
+                own = shard == n_shards - 1
+            else:
+                own = (x[0] * 31 + x[1]) % n_shards == shard
+            if own:
+                sets.append((x, int(full.supports[q])))
+        ctx["part"] = sets
+
+    def fim_result_sizes(self, ctx):
+        sets = ctx.get("merged", ctx.get("part"))
+        return len(sets), sum(len(x) for x, _ in sets)
+
+    def fim_fetch_results(self, ctx, out):
+        off, it, sup = out
+        sets = ctx["part"]
+        off[0] = 0
+        k = 0
+        for q, (x, s) in enumerate(sets):
+            it[k:k + len(x)] = x
+            k += len(x)
+            off[q + 1] = k
+            sup[q] = s
+
+    def fim_merge_results(self, ctx, n_trans, n_items, parts):
+        got = []
+        for off, it, sup in parts:
+            assert off.dtype == np.int64 and it.dtype == np.int32 and sup.dtype == np.int32
+            for q in range(len(off) - 1):
+                got.append((tuple(int(v) for v in it[off[q]:off[q + 1]]), int(sup[q])))
+        got.sort(key=lambda e: (len(e[0]), e[0]))
+        ctx["merged"] = got
+        ctx["n_parts"] = len(parts)
+
+
+def _worker(rank, world, port, case, skew):
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    if root not in sys.path:
+        sys.path.insert(0, root)
+    import oracle
+    from paper_2412_19420_gb300 import datagen, shard
+
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
+    try:
+        c, minsup = case
+        ctx = {}
+        n = shard.mine_sharded(ctx, c.indptr, c.indices, c.m, minsup, api=_OracleApi(skew))
+        if rank == 0:
+            want = oracle.apriori(c.indptr, c.indices, c.m, minsup).as_dict()
+            got = dict(ctx["merged"])
+            assert n == len(want) and got == want and ctx["n_parts"] == world
+        else:
+            assert n is None
+    finally:
+        dist.destroy_process_group()
+
+
+def _cases():
+    from paper_2412_19420_gb300 import datagen
+    return {
+        "zipf": (datagen.zipf_baskets(3000, 40, 0.8, 5.0, 9), 30),
+        "dense": (datagen.random_dense(200, 10, 0.5, 4), 20),
+        "pairs_only": (datagen.random_dense(200, 10, 0.5, 4), 60),   # nothing of size 3: rank 1 sends nothing
+    }
+
+
+@pytest.mark.parametrize("name", ["zipf", "dense", "pairs_only"])
+@pytest.mark.parametrize("skew", [False, True])
+def test_two_rank_split_mine_over_gloo(name, skew):
+    import torch.multiprocessing as mp
+    mp.start_processes(_worker, args=(2, _free_port(), _cases()[name], skew), nprocs=2, join=True,
+                       start_method="spawn")

@@ -12,9 +12,12 @@ between steps.
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
     python bench.py --impl reference      # the CPU oracle on the host cores
 
-Under torchrun (N > 1) every rank mines its own replica of the workload
-(replicas only: the single-database path has no exchange step); the value is
-the supports of all ranks over the slowest rank's time.
+Under torchrun (N > 1) every rank mines its own replica of the workload;
+the value is the supports of all ranks over the slowest rank's time.  With
+--shard the ranks instead split one mine (prefix-class shards, the parts
+gathered and merged on rank 0; strong scaling, also runnable at N = 1).
+After the timed mines the association rules of the last one are timed once
+more (--rules-ppm), reported beside the step.
 """
 from __future__ import annotations
 
@@ -52,6 +55,9 @@ def _args():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOAD_DESC))
     ap.add_argument("--flags", type=int, default=0, help="extra fim_mine flags")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--shard", action="store_true",
+                    help="split one mine over the ranks (prefix-class shards, gather + merge on rank 0) "
+                         "instead of one replica per rank")
     ap.add_argument("--rules-ppm", type=int, default=500_000,
                     help="also time association rules at this confidence (ppm); -1 skips")
     ap.add_argument("--learned", action="store_true",
@@ -345,6 +351,178 @@ def run_batched(args):
     fim.fim_destroy(ctx)
 
 
+def run_sharded(args):
+    """One mine of the workload split over the ranks: every rank builds the
+    whole matrix and mines its prefix-class shard (fim_mine_shard), the parts
+    are gathered on rank 0 (torch.distributed over NCCL) and merged into the
+    canonical answer (fim_merge_results), which rank 0 fetches.  Strong
+    scaling: the job's work is one mine whatever the rank count."""
+    import socket
+
+    import torch
+    import torch.distributed as dist
+    from paper_2412_19420_gb300 import fim, shard
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    else:  # the gather still runs, over a one-rank group
+        with socket.socket() as sk:
+            sk.bind(("127.0.0.1", 0))
+            port = sk.getsockname()[1]
+        dist.init_process_group("nccl", init_method=f"tcp://127.0.0.1:{port}", rank=0, world_size=1)
+
+    def barrier():
+        dist.barrier()
+        torch.cuda.synchronize()
+
+    csr, minsup = _load_workload(args.workload)
+    stream = torch.cuda.Stream()
+    ctx = fim.fim_create(local, stream)
+    flags = args.flags
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+
+    def mine(ip, ix, out_final):
+        """One step; returns (stats of this rank's shard mine, merge stats or None)."""
+        fim.fim_build_bitmaps(ctx, ip, ix, csr.m)
+        fim.fim_mine_shard(ctx, minsup, flags, rank, world)
+        st_mine = fim.fim_get_stats(ctx)
+        R, T = fim.fim_result_sizes(ctx)
+        part = (torch.empty(R + 1, dtype=torch.int64, device="cuda"),
+                torch.empty(max(T, 1), dtype=torch.int32, device="cuda"),
+                torch.empty(max(R, 1), dtype=torch.int32, device="cuda"))
+        fim.fim_fetch_results(ctx, part)
+        parts = shard.gather_parts((part[0], part[1][:T], part[2][:R]))
+        if rank != 0:
+            torch.cuda.current_stream().synchronize()  # the sends have left
+            return st_mine, None
+        fim.fim_merge_results(ctx, csr.n, csr.m, parts)
+        st_merge = fim.fim_get_stats(ctx)
+        fim.fim_fetch_results(ctx, out_final)
+        return st_mine, st_merge
+
+    ip_d = torch.from_numpy(csr.indptr).cuda()
+    ix_d = torch.from_numpy(csr.indices).cuda()
+    fim.fim_build_bitmaps(ctx, ip_d, ix_d, csr.m)
+    fim.fim_mine(ctx, minsup, flags)
+    R, T = fim.fim_result_sizes(ctx)  # the merged answer's size
+    out_d = (torch.empty(R + 1, dtype=torch.int64, device="cuda"),
+             torch.empty(max(T, 1), dtype=torch.int32, device="cuda"),
+             torch.empty(max(R, 1), dtype=torch.int32, device="cuda"))
+    for _ in range(args.warmup):
+        mine(ip_d, ix_d, out_d)
+    barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    phase = {k: 0.0 for k in ("ms_build", "ms_singletons", "ms_pairs", "ms_dfs", "ms_compact")}
+    launches, merge_ms = 0, 0.0
+    with ClockSampler(local) as clk:
+        barrier()
+        for k in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(k)
+            ev[k][0].record(stream)
+            st_mine, st_merge = mine(ip_d, ix_d, out_d)
+            ev[k][1].record(stream)
+            for p in phase:
+                phase[p] += st_mine[p]
+            launches += st_mine["launches_build"] + st_mine["launches_mine"]
+            if st_merge is not None:
+                launches += st_merge["launches_mine"]
+                merge_ms += st_merge["ms_compact"]
+        barrier()
+    ms_step = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+    # the job's supports: singletons and pairs once (every rank computes them),
+    # the DFS supports of every shard
+    t = torch.tensor([ms_step], dtype=torch.float64, device="cuda")
+    dfs = torch.tensor([float(st_mine["supports_dfs"])], dtype=torch.float64, device="cuda")
+    lc = torch.tensor([float(launches)], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(dfs, op=dist.ReduceOp.SUM)
+    dist.all_reduce(lc, op=dist.ReduceOp.SUM)
+    supports = st_mine["supports_singletons"] + st_mine["supports_pairs"] + dfs.item()
+    ms_max = float(t.item())
+    value = supports / (ms_max / 1000.0)
+
+    # e2e: host CSR on every rank, the merged answer to pinned host memory on rank 0
+    ip_h = torch.from_numpy(csr.indptr).pin_memory()
+    ix_h = torch.from_numpy(csr.indices).pin_memory()
+    out_h = tuple(torch.empty(x.shape[0], dtype=x.dtype).pin_memory() for x in out_d)
+    e2e_ms = []
+    for k in range(args.warmup + args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(k)
+        barrier()
+        t0 = time.perf_counter()
+        mine(ip_h.numpy(), ix_h.numpy(), tuple(x.numpy() for x in out_h))
+        if k >= args.warmup:
+            e2e_ms.append(1000 * (time.perf_counter() - t0))
+    e2e_t = torch.tensor([statistics.mean(e2e_ms)], dtype=torch.float64, device="cuda")
+    dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+    e2e_value = supports / (float(e2e_t.item()) / 1000.0)
+
+    avg = {p: phase[p] / args.steps for p in phase}
+    roof = _roofline(st_mine, avg, csr, args.workload)
+    line = {
+        "metric": "itemset supports/sec", "value": value, "unit": "supports/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
+        "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic (seeded generator, paper_2412_19420_gb300.datagen)",
+        "config": {"workload": args.workload, "desc": WORKLOAD_DESC[args.workload],
+                   "n_trans": csr.n, "n_items": csr.m, "minsup": minsup, "flags": flags,
+                   "parallelism": f"prefix-class shards x{world}, gather + merge on rank 0",
+                   "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write)",
+                   "frequent_itemsets": int(R), "merge_ms": round(merge_ms / args.steps, 4),
+                   "supports_per_step": int(supports)},
+        "e2e": {"value": e2e_value, "unit": "supports/s",
+                "h2d_bytes_per_step": int(world * (csr.indptr.nbytes + csr.indices.nbytes)),
+                "d2h_bytes_per_step": int(8 * (R + 1) + 4 * T + 4 * R), "ms_per_step": float(e2e_t.item())},
+        "gpu_launches": int(lc.item()),
+        "roofline": roof,
+        "clocks": clk.summary(),
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    fim.fim_destroy(ctx)
+    dist.destroy_process_group()
+
+
+def _roofline(st, avg, csr, workload):
+    """Roofline of the dominant phase of a mine: st = fim_get_stats of a
+    timed mine, avg = mean CUDA-event phase times (ms)."""
+    hbm, bf16, bf16_s, src = _peaks()
+    dom = max(("ms_pairs", "ms_dfs", "ms_compact", "ms_build"), key=lambda p: avg[p])
+    if dom == "ms_dfs":
+        # bytes of the operands the chosen representations stream, at 32-byte
+        # sector granularity (zero sectors skipped, sparse classes as
+        # (index, word) pairs); the dense-column figure is reported beside it
+        ach = st["dfs_touched_bytes"] / (avg[dom] / 1000) / 1e9
+        roof = {"kernel": "dfs_kernel", "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                "frac": ach / hbm, "traffic": _kernel_traffic("dfs_kernel", workload),
+                "algorithmic_bytes_per_launch": st["dfs_touched_bytes"],
+                "dense_equivalent_bytes_per_launch": st["dfs_bytes"]}
+    elif dom == "ms_pairs" and st["pair_path"] == 1:
+        fl = 2.0 * st["supports_pairs"] * csr.n
+        ach = fl / (avg[dom] / 1000) / 1e12
+        peak = 2 * bf16  # fp8 dense = 2 x bf16 dense (nominal ratio)
+        roof = {"kernel": "pairs_tc_kernel", "bound": "tensor", "achieved": ach, "peak": peak,
+                "unit": "TFLOP/s", "frac": ach / peak,
+                "traffic": _kernel_traffic("pairs_tc_kernel", workload)}
+    else:
+        nm = {"ms_pairs": "pairs_popc_kernel", "ms_compact": "compaction", "ms_build": "build_bitmaps_kernel"}[dom]
+        nbytes = {"ms_pairs": 4 * st["n_frequent_items"] * ((csr.n + 31) // 32),
+                  "ms_compact": 24 * st["n_sets"],
+                  "ms_build": csr.indptr.nbytes + csr.indices.nbytes + 4 * csr.m * ((csr.n + 31) // 32)}[dom]
+        ach = nbytes / (avg[dom] / 1000) / 1e9
+        roof = {"kernel": nm, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                "frac": ach / hbm, "traffic": _kernel_traffic(nm, workload)}
+    roof["peak_source"] = src
+    roof["phase_ms"] = {k: round(v, 4) for k, v in avg.items()}
+    return roof
+
+
 def main():
     args = _args()
     if args.impl == "reference":
@@ -352,6 +530,9 @@ def main():
         return
     if args.workload == "batched_4096":
         run_batched(args)
+        return
+    if args.shard:
+        run_sharded(args)
         return
     import numpy as np
     import torch
@@ -473,35 +654,8 @@ def main():
                            "three host syncs), median"}
 
     # ---- roofline of the dominant phase ---------------------------------
-    hbm, bf16, bf16_s, src = _peaks()
     avg = {p: phase[p] / args.steps for p in phase}
-    dom = max(("ms_pairs", "ms_dfs", "ms_compact", "ms_build"), key=lambda p: avg[p])
-    if dom == "ms_dfs":
-        # bytes of the operands the chosen representations stream, at 32-byte
-        # sector granularity (zero sectors skipped, sparse classes as
-        # (index, word) pairs); the dense-column figure is reported beside it
-        ach = st["dfs_touched_bytes"] / (avg[dom] / 1000) / 1e9
-        roof = {"kernel": "dfs_kernel", "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-                "frac": ach / hbm, "traffic": _kernel_traffic("dfs_kernel", args.workload),
-                "algorithmic_bytes_per_launch": st["dfs_touched_bytes"],
-                "dense_equivalent_bytes_per_launch": st["dfs_bytes"]}
-    elif dom == "ms_pairs" and st["pair_path"] == 1:
-        fl = 2.0 * st["supports_pairs"] * csr.n
-        ach = fl / (avg[dom] / 1000) / 1e12
-        peak = 2 * bf16  # fp8 dense = 2 x bf16 dense (nominal ratio)
-        roof = {"kernel": "pairs_tc_kernel", "bound": "tensor", "achieved": ach, "peak": peak,
-                "unit": "TFLOP/s", "frac": ach / peak,
-                "traffic": _kernel_traffic("pairs_tc_kernel", args.workload)}
-    else:
-        nm = {"ms_pairs": "pairs_popc_kernel", "ms_compact": "compaction", "ms_build": "build_bitmaps_kernel"}[dom]
-        nbytes = {"ms_pairs": 4 * st["n_frequent_items"] * ((csr.n + 31) // 32),
-                  "ms_compact": 24 * st["n_sets"],
-                  "ms_build": csr.indptr.nbytes + csr.indices.nbytes + 4 * csr.m * ((csr.n + 31) // 32)}[dom]
-        ach = nbytes / (avg[dom] / 1000) / 1e9
-        roof = {"kernel": nm, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-                "frac": ach / hbm, "traffic": _kernel_traffic(nm, args.workload)}
-    roof["peak_source"] = src
-    roof["phase_ms"] = {k: round(v, 4) for k, v in avg.items()}
+    roof = _roofline(st, avg, csr, args.workload)
 
     line = {
         "metric": "itemset supports/sec", "value": value, "unit": "supports/s", "n_gpus": world,

@@ -279,7 +279,9 @@ int fim_mine_shard(fim_ctx *ctx, uint64_t minsup, uint32_t flags, int shard, int
  * GPU (FIM_INPUT_DEVICE); they are copied and may be freed on return.
  * n_trans is the database's transaction count (the n of lift in fim_rules).
  * The result is fetched with fim_fetch_results and feeds fim_rules, like a
- * mine's.  Parts that overlap give duplicate sets: the call does not check.
+ * mine's; fim_get_stats then reports the merge's n_sets, max_len,
+ * ms_compact and launches_mine.  Parts that overlap give duplicate sets: the
+ * call does not check.
  * Errors: FIM_E_INVAL (a NULL array, malformed offsets, a set longer than 255
  * items, an item >= n_items, n_trans or n_items out of range), FIM_E_NOMEM,
  * FIM_E_CUDA. */

@@ -214,6 +214,7 @@ int fim_merge_results(fim_ctx *ctx, int64_t n_trans, int32_t n_items, int n_part
     struct Restore { int d; ~Restore() { if (d >= 0) cudaSetDevice(d); } } restore{dev_prev};
     cudaStream_t st = ctx->stream;
     ctx->mined = false;
+    const uint64_t launches0 = ctx->launches;
     const cudaMemcpyKind k = (flags & FIM_INPUT_DEVICE) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     if (R > ctx->rec_cap) ctx->rec_cap = R;
     if (T > ctx->rec_items_cap) ctx->rec_items_cap = T;
@@ -275,6 +276,7 @@ int fim_merge_results(fim_ctx *ctx, int64_t n_trans, int32_t n_items, int n_part
     cudaEventElapsedTime(&ctx->stats.ms_compact, ctx->ev[3], ctx->ev[4]);
     ctx->stats.n_sets = R;
     ctx->stats.max_len = (uint64_t)h[1];
+    ctx->stats.launches_mine = ctx->launches - launches0;
     if (ctx->bytes_held > ctx->stats.peak_device_bytes) ctx->stats.peak_device_bytes = ctx->bytes_held;
     ctx->out_n = n_trans;
     ctx->mined = true;

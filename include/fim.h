@@ -179,6 +179,10 @@ int fim_get_stats(const fim_ctx *ctx, fim_stats *out);
  *   "pairs_kdrain"     0..32768  128-transaction stages one accumulator sums before
  *                                it is drained (0 = 32768: partial sums stay <= 2^24,
  *                                exact in f32)
+ *   "upload_chunks"    1..16     host input to fim_build_bitmaps: the indices go
+ *                                up in this many chunks, each built as soon as it
+ *                                lands (default 4; 1 = one copy, then the build)
+ *   "upload_streams"   1, 2      copy streams the chunks alternate over (default 2)
  * Errors: FIM_E_INVAL for an unknown key or an out-of-range value. */
 int fim_set_tuning(fim_ctx *ctx, const char *key, int64_t value);
 

@@ -161,7 +161,12 @@ void fim_destroy(fim_ctx *ctx) {
     fim_release(ctx, ctx->batch_prefix);
     fim_release(ctx, ctx->batch_slices);
     if (ctx->batch_graph_exec) cudaGraphExecDestroy((cudaGraphExec_t)ctx->batch_graph_exec);
-    if (ctx->compact_graph_exec) cudaGraphExecDestroy((cudaGraphExec_t)ctx->compact_graph_exec);
+    for (void *g : ctx->compact_graph_exec)
+        if (g) cudaGraphExecDestroy((cudaGraphExec_t)g);
+    for (cudaStream_t u : ctx->up_stream)
+        if (u) cudaStreamDestroy(u);
+    for (cudaEvent_t e : ctx->up_ev)
+        if (e) cudaEventDestroy(e);
     for (auto &e : ctx->ev)
         if (e) cudaEventDestroy(e);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
@@ -187,6 +192,7 @@ int fim_build_bitmaps(fim_ctx *ctx, const int64_t *indptr, const int32_t *indice
 
     const int64_t *d_ptr = indptr;
     const int32_t *d_idx = indices;
+    int64_t h_nnz = -1;
     if (!(flags & FIM_INPUT_DEVICE)) {
         const int64_t nnz = indptr[n_trans];
         if (indptr[0] != 0 || nnz < 0 || (nnz > 0 && !indices)) return FIM_E_INVAL;
@@ -194,11 +200,10 @@ int fim_build_bitmaps(fim_ctx *ctx, const int64_t *indptr, const int32_t *indice
         FIM_TRY(fim_reserve(ctx, ctx->csr_idx, sizeof(int32_t) * (size_t)(nnz > 0 ? nnz : 1)));
         FIM_CUDA_TRY(cudaMemcpyAsync(ctx->csr_ptr.p, indptr, sizeof(int64_t) * (size_t)(n_trans + 1),
                                      cudaMemcpyHostToDevice, st));
-        if (nnz > 0)
-            FIM_CUDA_TRY(cudaMemcpyAsync(ctx->csr_idx.p, indices, sizeof(int32_t) * (size_t)nnz,
-                                         cudaMemcpyHostToDevice, st));
+        // (the indices go up inside launch_build_bitmaps, overlapped with the build)
         d_ptr = ctx->csr_ptr.as<int64_t>();
         d_idx = ctx->csr_idx.as<int32_t>();
+        h_nnz = nnz;
     } else {
         int64_t first = -1;
         FIM_CUDA_TRY(cudaMemcpyAsync(&first, indptr, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
@@ -210,7 +215,8 @@ int fim_build_bitmaps(fim_ctx *ctx, const int64_t *indptr, const int32_t *indice
     FIM_TRY(fim_reserve(ctx, ctx->item_sup, sizeof(uint32_t) * mm));
     FIM_TRY(fim_reserve(ctx, ctx->perm, sizeof(int32_t) * mm));
     FIM_TRY(fim_reserve(ctx, ctx->rank, sizeof(int32_t) * mm));
-    FIM_TRY(launch_build_bitmaps(ctx, d_ptr, d_idx));
+    if (flags & FIM_INPUT_DEVICE) FIM_TRY(launch_build_bitmaps(ctx, d_ptr, d_idx, -1, nullptr, nullptr));
+    else FIM_TRY(launch_build_bitmaps(ctx, d_ptr, d_idx, h_nnz, indptr, h_nnz > 0 ? indices : nullptr));
     cudaEventRecord(ctx->ev[1], st);
     FIM_TRY(launch_item_support(ctx));
     cudaEventRecord(ctx->ev[2], st);
@@ -527,6 +533,8 @@ int fim_set_tuning(fim_ctx *ctx, const char *key, int64_t v) {
         {"root_reverse", &ctx->root_reverse, 0, 1},
         {"pairs_split", &ctx->pairs_split, 0, 4096},
         {"pairs_kdrain", &ctx->pairs_kdrain, 0, 32768},
+        {"upload_chunks", &ctx->upload_chunks, 1, 16},
+        {"upload_streams", &ctx->upload_streams, 1, 2},
     };
     for (const Knob &k : knobs)
         if (strcmp(k.name, key) == 0) {

@@ -234,8 +234,11 @@ struct fim_ctx {
     uint64_t batch_graph_key = 0;
     uint64_t batch_graph_launches = 0;
     // compactor pass sequence, captured when a shape repeats
-    void *compact_graph_exec = nullptr; // cudaGraphExec_t
-    uint64_t compact_key = 0, compact_seen_key = 0, compact_graph_launches = 0;
+    // (two slots: a split mine alternates the shard's and the merge's shapes)
+    void *compact_graph_exec[2] = {nullptr, nullptr}; // cudaGraphExec_t
+    uint64_t compact_key[2] = {0, 0}, compact_graph_launches[2] = {0, 0};
+    uint64_t compact_seen_key[2] = {0, 0};
+    int compact_next = 0, compact_seen_next = 0;
 
     // tuning (autotuner may overwrite)
     int dfs_block = 256;
@@ -248,6 +251,10 @@ struct fim_ctx {
     int l2_bytes = 0;
     int pairs_split = 0;        // split-K factor of the tensor-core pair pass (0 = auto)
     int pairs_kdrain = 0;       // stages (x128 transactions) per exact drain (0 = 64)
+    int upload_chunks = 4;      // host input: index upload chunks overlapped with the build
+    int upload_streams = 2;     // copy streams the chunks alternate over
+    cudaStream_t up_stream[2] = {nullptr, nullptr};
+    cudaEvent_t up_ev[16] = {};
 
     // stats + timing
     fim_stats stats{};
@@ -261,7 +268,10 @@ void fim_release(fim_ctx *ctx, DevBuf &b);
 
 // ---------------------------------------------------------------- launchers
 // k_matrix.cu
-int launch_build_bitmaps(fim_ctx *ctx, const int64_t *d_indptr, const int32_t *d_indices);
+// nnz < 0: read indptr[n] from the device.  h_indptr/h_indices (host input):
+// the indices are uploaded into d_indices chunk by chunk, overlapping the build.
+int launch_build_bitmaps(fim_ctx *ctx, const int64_t *d_indptr, const int32_t *d_indices, int64_t nnz,
+                         const int64_t *h_indptr, const int32_t *h_indices);
 int launch_item_support(fim_ctx *ctx);
 int launch_rank_items(fim_ctx *ctx, uint32_t thr, MineCounters *d_ctr);
 int launch_emit_singletons(fim_ctx *ctx, MineCounters *d_ctr);

@@ -430,20 +430,24 @@ int launch_compact(fim_ctx *ctx, uint64_t R, int n_db, int m_max, bool identity_
     mix((uint64_t)(uintptr_t)ctx->dbdesc.p); mix((uint64_t)(uintptr_t)ctx->rec_db.p);
     mix((uint64_t)(uintptr_t)ctx->kv_a.p); mix((uint64_t)(uintptr_t)ctx->kv_b.p);
     mix((uint64_t)(uintptr_t)ctx->scan_part.p);
-    if (ctx->compact_graph_exec && ctx->compact_key == key) {
-        FIM_CUDA_TRY(cudaGraphLaunch((cudaGraphExec_t)ctx->compact_graph_exec, st));
-        ctx->launches += ctx->compact_graph_launches;
-        return FIM_OK;
-    }
-    if (ctx->compact_seen_key != key) {   // first time: launch directly
-        ctx->compact_seen_key = key;
+    for (int i = 0; i < 2; i++)
+        if (ctx->compact_graph_exec[i] && ctx->compact_key[i] == key) {
+            FIM_CUDA_TRY(cudaGraphLaunch((cudaGraphExec_t)ctx->compact_graph_exec[i], st));
+            ctx->launches += ctx->compact_graph_launches[i];
+            return FIM_OK;
+        }
+    if (ctx->compact_seen_key[0] != key && ctx->compact_seen_key[1] != key) {  // first time: launch directly
+        ctx->compact_seen_key[ctx->compact_seen_next] = key;
+        ctx->compact_seen_next ^= 1;
         ctx->launches += enqueue();
         FIM_CUDA_TRY(cudaGetLastError());
         return FIM_OK;
     }
-    if (ctx->compact_graph_exec) {
-        cudaGraphExecDestroy((cudaGraphExec_t)ctx->compact_graph_exec);
-        ctx->compact_graph_exec = nullptr;
+    const int slot = ctx->compact_next;
+    if (ctx->compact_graph_exec[slot]) {
+        cudaGraphExecDestroy((cudaGraphExec_t)ctx->compact_graph_exec[slot]);
+        ctx->compact_graph_exec[slot] = nullptr;
+        ctx->compact_key[slot] = 0;
     }
     cudaGraph_t g = nullptr;
     FIM_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
@@ -454,9 +458,10 @@ int launch_compact(fim_ctx *ctx, uint64_t R, int n_db, int m_max, bool identity_
     const cudaError_t ie = cudaGraphInstantiate(&ex, g, 0);
     cudaGraphDestroy(g);
     if (ie != cudaSuccess) { fim_set_cuda_error(ie, "compact instantiate", __FILE__, __LINE__); return FIM_E_CUDA; }
-    ctx->compact_graph_exec = ex;
-    ctx->compact_key = key;
-    ctx->compact_graph_launches = nk;
+    ctx->compact_graph_exec[slot] = ex;
+    ctx->compact_key[slot] = key;
+    ctx->compact_graph_launches[slot] = nk;
+    ctx->compact_next ^= 1;
     FIM_CUDA_TRY(cudaGraphLaunch(ex, st));
     ctx->launches += nk;
     return FIM_OK;

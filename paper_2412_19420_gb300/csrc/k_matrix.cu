@@ -17,14 +17,14 @@ constexpr int BUILD_THREADS = 512;
 
 __global__ void __launch_bounds__(BUILD_THREADS)
 build_bitmaps_kernel(const int64_t *__restrict__ indptr, const int32_t *__restrict__ indices,
-                     int64_t n, int32_t m, int64_t nnz, int64_t nwp, int ib,
+                     int64_t n, int32_t m, int64_t nnz, int64_t nwp, int ib, int64_t blk0,
                      uint32_t *__restrict__ bm, int *__restrict__ flag, int *__restrict__ max_len) {
     // [WB][ib + 1], word-major and padded: the 32 rows of a warp's group share
     // their word, so their items' bits spread over the banks
     extern __shared__ __align__(16) uint32_t tile[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int ms = ib + 1;
-    const int64_t w0 = (int64_t)blockIdx.x * WB;
+    const int64_t w0 = (blk0 + (int64_t)blockIdx.x) * WB;
     const int i0 = blockIdx.y * ib;
     const int icount = min(ib, m - i0);
     const int64_t t0 = w0 * 32;
@@ -151,7 +151,8 @@ __global__ void emit_singletons_kernel(const uint32_t *__restrict__ sup, const i
 
 }  // namespace
 
-int launch_build_bitmaps(fim_ctx *ctx, const int64_t *d_indptr, const int32_t *d_indices) {
+int launch_build_bitmaps(fim_ctx *ctx, const int64_t *d_indptr, const int32_t *d_indices, int64_t nnz,
+                         const int64_t *h_indptr, const int32_t *h_indices) {
     const int64_t nblk = ctx->nwp / WB;
     int ib = ctx->m < 1024 ? ctx->m : 1024;
     if (ib < 1) ib = 1;
@@ -160,19 +161,52 @@ int launch_build_bitmaps(fim_ctx *ctx, const int64_t *d_indptr, const int32_t *d
     FIM_CUDA_TRY(cudaFuncSetAttribute(build_bitmaps_kernel,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int *flag = ctx->dev_flag.as<int>();
-    FIM_CUDA_TRY(cudaMemsetAsync(flag, 0, 2 * sizeof(int), ctx->stream));
-    if (nblk > 0 && ctx->m > 0) {
-        // nnz is read on the host before the launch (indptr[n])
-        int64_t nnz = 0;
-        FIM_CUDA_TRY(cudaMemcpyAsync(&nnz, d_indptr + ctx->n, sizeof(int64_t),
-                                     cudaMemcpyDeviceToHost, ctx->stream));
-        FIM_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    cudaStream_t st = ctx->stream;
+    FIM_CUDA_TRY(cudaMemsetAsync(flag, 0, 2 * sizeof(int), st));
+    if (nblk <= 0 || ctx->m <= 0) return FIM_OK;
+    if (nnz < 0) {  // device input: nnz is read on the host before the launch (indptr[n])
+        FIM_CUDA_TRY(cudaMemcpyAsync(&nnz, d_indptr + ctx->n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        FIM_CUDA_TRY(cudaStreamSynchronize(st));
         if (nnz < 0) return FIM_E_INVAL;
-        dim3 grid((unsigned)nblk, (unsigned)niblk);
+    }
+    // Host input: the indices go up in chunks of row blocks on side streams,
+    // and each chunk's blocks are built as soon as its copy has landed, so the
+    // upload overlaps the construction.  A chunk needs the elements
+    // [indptr[t0], indptr[t1]) of its transactions; an indptr that is not
+    // monotone there is flagged by the kernel, which then reads nothing.
+    int chunks = h_indices ? ctx->upload_chunks : 1;
+    if (chunks > nblk) chunks = (int)nblk;
+    if (chunks < 1) chunks = 1;
+    const int nstreams = h_indices ? ctx->upload_streams : 0;
+    for (int s = 0; s < nstreams; s++) {
+        if (!ctx->up_stream[s]) FIM_CUDA_TRY(cudaStreamCreateWithFlags(&ctx->up_stream[s], cudaStreamNonBlocking));
+        // the copies overwrite the staging buffer: after all earlier work on the ctx stream
+        FIM_CUDA_TRY(cudaStreamWaitEvent(ctx->up_stream[s], ctx->ev[0], 0));
+    }
+    for (int c = 0; c < chunks && h_indices; c++)
+        if (!ctx->up_ev[c]) FIM_CUDA_TRY(cudaEventCreateWithFlags(&ctx->up_ev[c], cudaEventDisableTiming));
+    const int64_t per = ceil_div64(nblk, chunks);
+    const int64_t tpb = (int64_t)WB * 32;  // transactions per row block
+    for (int c = 0; c < chunks; c++) {
+        const int64_t b0 = (int64_t)c * per, b1 = min64(nblk, b0 + per);
+        if (b0 >= b1) break;
+        if (h_indices) {
+            const int64_t t0 = min64(ctx->n, b0 * tpb), t1 = min64(ctx->n, b1 * tpb);
+            int64_t lo = h_indptr[t0], hi = h_indptr[t1];
+            lo = lo < 0 ? 0 : (lo > nnz ? nnz : lo);
+            hi = hi < lo ? lo : (hi > nnz ? nnz : hi);
+            if (hi > lo) {
+                cudaStream_t cs = ctx->up_stream[c % nstreams];
+                FIM_CUDA_TRY(cudaMemcpyAsync(const_cast<int32_t *>(d_indices) + lo, h_indices + lo,
+                                             sizeof(int32_t) * (size_t)(hi - lo), cudaMemcpyHostToDevice, cs));
+                FIM_CUDA_TRY(cudaEventRecord(ctx->up_ev[c], cs));
+                FIM_CUDA_TRY(cudaStreamWaitEvent(st, ctx->up_ev[c], 0));
+            }
+        }
+        dim3 grid((unsigned)(b1 - b0), (unsigned)niblk);
         ctx->launches++;
-        build_bitmaps_kernel<<<grid, BUILD_THREADS, smem, ctx->stream>>>(
-            d_indptr, d_indices, ctx->n, ctx->m, nnz, ctx->nwp, ib, ctx->bm.as<uint32_t>(),
-            flag, flag + 1);
+        build_bitmaps_kernel<<<grid, BUILD_THREADS, smem, st>>>(d_indptr, d_indices, ctx->n, ctx->m, nnz, ctx->nwp,
+                                                                ib, b0, ctx->bm.as<uint32_t>(), flag, flag + 1);
         FIM_CUDA_TRY(cudaGetLastError());
     }
     return FIM_OK;

@@ -106,3 +106,32 @@ def test_sparse_classes_are_exact(ctx, name, gen, minsup, div):
             assert fim.fim_fetch_results(ctx).sha256() == want, flags
     finally:
         fim.fim_set_tuning(ctx, "sparse_div", -1)
+
+
+@pytest.mark.parametrize("chunks,streams", [(1, 1), (3, 2), (4, 1), (16, 2)])
+def test_chunked_host_upload_is_exact(ctx, chunks, streams):
+    # the host CSR goes up in chunks of 512-transaction row blocks, each built
+    # as it lands; ragged sizes leave a partial last block and empty chunks
+    fim.fim_set_tuning(ctx, "upload_chunks", chunks)
+    fim.fim_set_tuning(ctx, "upload_streams", streams)
+    try:
+        for n, m, thr in [(70_001, 200, 250), (1_500, 40, 10), (513, 9, 3)]:
+            c = datagen.zipf_baskets(n, m, 0.9, 6.0, n)
+            fim.fim_build_bitmaps(ctx, c.indptr, c.indices, c.m)
+            fim.fim_mine(ctx, thr)
+            assert fim.fim_fetch_results(ctx).sha256() == oracle.apriori(c.indptr, c.indices, c.m, thr).sha256()
+        # a malformed host CSR is still rejected, and the ctx stays usable
+        c = datagen.zipf_baskets(5_000, 30, 0.9, 6.0, 1)
+        bad = c.indptr.copy()
+        bad[2600], bad[2601] = bad[2601], bad[2600] - 1  # not monotone
+        with pytest.raises(fim.FimError):
+            fim.fim_build_bitmaps(ctx, bad, c.indices, c.m)
+        fim.fim_build_bitmaps(ctx, c.indptr, c.indices, c.m)
+        fim.fim_mine(ctx, 20)
+        assert fim.fim_fetch_results(ctx).sha256() == oracle.apriori(c.indptr, c.indices, c.m, 20).sha256()
+    finally:
+        fim.fim_set_tuning(ctx, "upload_chunks", 4)
+        fim.fim_set_tuning(ctx, "upload_streams", 2)
+    for key, v in (("upload_chunks", 0), ("upload_chunks", 17), ("upload_streams", 3)):
+        with pytest.raises(fim.FimError):
+            fim.fim_set_tuning(ctx, key, v)

@@ -183,6 +183,8 @@ int fim_get_stats(const fim_ctx *ctx, fim_stats *out);
  *                                up in this many chunks, each built as soon as it
  *                                lands (default 4; 1 = one copy, then the build)
  *   "upload_streams"   1, 2      copy streams the chunks alternate over (default 2)
+ *   "compact_cluster"  0, 1      sort outputs small enough for one thread-block
+ *                                cluster's shared memory in one launch (default 1)
  * Errors: FIM_E_INVAL for an unknown key or an out-of-range value. */
 int fim_set_tuning(fim_ctx *ctx, const char *key, int64_t value);
 

@@ -534,6 +534,7 @@ int fim_set_tuning(fim_ctx *ctx, const char *key, int64_t v) {
         {"pairs_split", &ctx->pairs_split, 0, 4096},
         {"pairs_kdrain", &ctx->pairs_kdrain, 0, 32768},
         {"upload_chunks", &ctx->upload_chunks, 1, 16},
+        {"compact_cluster", &ctx->compact_cluster, 0, 1},
         {"upload_streams", &ctx->upload_streams, 1, 2},
     };
     for (const Knob &k : knobs)

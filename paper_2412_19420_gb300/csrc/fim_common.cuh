@@ -20,6 +20,7 @@
 #include <stdint.h>
 #include <stddef.h>
 
+#include <utility>
 #include <vector>
 
 #include "../../include/fim.h"
@@ -251,6 +252,8 @@ struct fim_ctx {
     int l2_bytes = 0;
     int pairs_split = 0;        // split-K factor of the tensor-core pair pass (0 = auto)
     int pairs_kdrain = 0;       // stages (x128 transactions) per exact drain (0 = 64)
+    int compact_cluster = 1;    // small outputs: sort in one cluster launch
+    int csort_cl[5] = {0, 0, 0, 0, 0};  // cluster size per key width (0 unknown, -1 none)
     int upload_chunks = 4;      // host input: index upload chunks overlapped with the build
     int upload_streams = 2;     // copy streams the chunks alternate over
     cudaStream_t up_stream[2] = {nullptr, nullptr};
@@ -299,6 +302,12 @@ int launch_root_order(fim_ctx *ctx, MineCounters *d_ctr, size_t npairs);
 // k_compact.cu
 // identity_items: the records already hold the caller's item ids (a merge)
 int launch_compact(fim_ctx *ctx, uint64_t n_records, int n_db, int m_max, bool identity_items = false);
+
+// k_csort.cu: the compactor's sort of a small output in one cluster launch
+int cluster_sort_plan(fim_ctx *ctx, uint64_t R, int kw, int *cl, int *cap, int *per);
+int launch_cluster_sort(fim_ctx *ctx, const unsigned long long *keys, uint64_t R, int kw,
+                        const std::vector<std::pair<int, int>> &passes, int cl, int cap, int per,
+                        uint32_t *idx_out, cudaStream_t st);
 
 // k_shard.cu: append the root classes shard `shard` of n_shards owns
 int launch_shard_roots(fim_ctx *ctx, MineCounters *d_ctr, int shard, int n_shards);

@@ -342,6 +342,19 @@ int launch_compact(fim_ctx *ctx, uint64_t R, int n_db, int m_max, bool identity_
     FIM_TRY(fim_reserve(ctx, ctx->scan_tmp, sizeof(unsigned long long) * (size_t)nblk));
 
     unsigned long long *keys = ctx->keys.as<unsigned long long>();
+    // the digit passes, least significant first: (word, shift)
+    const int key_pad = kw * 64 - total_bits;  // zero bits at the key's LSB end
+    std::vector<std::pair<int, int>> passes;
+    for (int w = kw - 1; w >= 0; w--) {
+        const int word_lo_bit = (kw - 1 - w) * 64;  // bit index (from the key's LSB) of this word's bit 0
+        for (int d = 0; d < 8; d++)
+            if (word_lo_bit + d * 8 + 8 > key_pad) passes.push_back({w, d * 8});  // skip pure padding
+    }
+    // a small output is sorted in one cluster launch (keys in distributed
+    // shared memory) instead of a launch triple per digit
+    int cs_cl = 0, cs_cap = 0, cs_per = 0;
+    const bool csort = cluster_sort_plan(ctx, R, kw, &cs_cl, &cs_cap, &cs_per) != 0;
+    int enq_rc = FIM_OK;  // a launch that enqueue() could not make
     // The whole pass sequence, enqueued on st.  Returns the kernel count.
     auto enqueue = [&]() -> uint64_t {
         uint64_t nk = 0;
@@ -351,6 +364,10 @@ int launch_compact(fim_ctx *ctx, uint64_t R, int n_db, int m_max, bool identity_
             ctx->rec_items.as<uint32_t>(), identity_items ? nullptr : ctx->perm.as<int32_t>(), ctx->dbdesc.as<DbDesc>(),
             ctx->rec_db.as<uint32_t>(), db_bits, bits, kw, keys, ia);
         nk++;
+        if (csort) {
+            enq_rc = launch_cluster_sort(ctx, keys, R, kw, passes, cs_cl, cs_cap, cs_per, ia, st);
+            nk++;
+        } else {
         // LSD: least significant word first; within a word, low digits first.
         // (word, record) pairs move together, so each word is gathered into
         // record order once; the least significant word starts in record
@@ -358,14 +375,6 @@ int launch_compact(fim_ctx *ctx, uint64_t R, int n_db, int m_max, bool identity_
         unsigned long long *ka = ctx->kv_a.as<unsigned long long>(), *kb = ctx->kv_b.as<unsigned long long>();
         uint32_t *hist = ctx->hist.as<uint32_t>();
         uint32_t *hist_nxt = fuse ? hist + nhist : nullptr;
-        const int key_pad = kw * 64 - total_bits;  // zero bits at the key's LSB end
-        // the digit passes, least significant first: (word, shift)
-        std::vector<std::pair<int, int>> passes;
-        for (int w = kw - 1; w >= 0; w--) {
-            const int word_lo_bit = (kw - 1 - w) * 64;  // bit index (from the key's LSB) of this word's bit 0
-            for (int d = 0; d < 8; d++)
-                if (word_lo_bit + d * 8 + 8 > key_pad) passes.push_back({w, d * 8});  // skip pure padding
-        }
         const unsigned long long *kin = nullptr;
         for (size_t i = 0; i < passes.size(); i++) {
             const int w = passes[i].first, shift = passes[i].second;
@@ -405,6 +414,7 @@ int launch_compact(fim_ctx *ctx, uint64_t R, int n_db, int m_max, bool identity_
             kin = kout;
             if (fuse) { uint32_t *h = hist; hist = hist_nxt; hist_nxt = h; }
         }
+        }
         unsigned long long *bsum = ctx->scan_tmp.as<unsigned long long>();
         len_block_sums_kernel<<<nblk, ST, 0, st>>>(ia, ctx->rec_len.as<uint32_t>(), R, bsum);
         scan_u64_single_kernel<<<1, 1024, 0, st>>>(bsum, (unsigned long long)nblk);
@@ -430,6 +440,7 @@ int launch_compact(fim_ctx *ctx, uint64_t R, int n_db, int m_max, bool identity_
     mix((uint64_t)(uintptr_t)ctx->dbdesc.p); mix((uint64_t)(uintptr_t)ctx->rec_db.p);
     mix((uint64_t)(uintptr_t)ctx->kv_a.p); mix((uint64_t)(uintptr_t)ctx->kv_b.p);
     mix((uint64_t)(uintptr_t)ctx->scan_part.p);
+    mix(csort ? (uint64_t)(cs_cl * 100000 + cs_per) : 0ull);
     for (int i = 0; i < 2; i++)
         if (ctx->compact_graph_exec[i] && ctx->compact_key[i] == key) {
             FIM_CUDA_TRY(cudaGraphLaunch((cudaGraphExec_t)ctx->compact_graph_exec[i], st));
@@ -440,6 +451,7 @@ int launch_compact(fim_ctx *ctx, uint64_t R, int n_db, int m_max, bool identity_
         ctx->compact_seen_key[ctx->compact_seen_next] = key;
         ctx->compact_seen_next ^= 1;
         ctx->launches += enqueue();
+        FIM_TRY(enq_rc);
         FIM_CUDA_TRY(cudaGetLastError());
         return FIM_OK;
     }
@@ -454,6 +466,10 @@ int launch_compact(fim_ctx *ctx, uint64_t R, int n_db, int m_max, bool identity_
     const uint64_t nk = enqueue();
     const cudaError_t ce = cudaStreamEndCapture(st, &g);
     if (ce != cudaSuccess) { fim_set_cuda_error(ce, "compact capture", __FILE__, __LINE__); return FIM_E_CUDA; }
+    if (enq_rc != FIM_OK) {
+        cudaGraphDestroy(g);
+        return enq_rc;
+    }
     cudaGraphExec_t ex = nullptr;
     const cudaError_t ie = cudaGraphInstantiate(&ex, g, 0);
     cudaGraphDestroy(g);

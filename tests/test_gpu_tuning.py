@@ -135,3 +135,27 @@ def test_chunked_host_upload_is_exact(ctx, chunks, streams):
     for key, v in (("upload_chunks", 0), ("upload_chunks", 17), ("upload_streams", 3)):
         with pytest.raises(fim.FimError):
             fim.fim_set_tuning(ctx, key, v)
+
+
+def test_cluster_sort_equals_launch_sequence(ctx):
+    # outputs from a handful of sets to tens of thousands, both compaction
+    # paths, oracle-exact: 3,265 and 10,275 sets (one key word), 35,517 (one
+    # word, 16 CTAs of ~2,220), 51,640 (three words, 16 x 3,228 of a 3,936
+    # capacity), and 96,497 / 405,597 sets that exceed one cluster
+    plant = datagen.planted(n=20_000, m=800, n_patterns=60, seed=4)
+    cases = [(datagen.from_lists([[0, 1], [1, 2], [0, 1, 2]] * 3, 3), 2),
+             (datagen.zipf_baskets(4_097, 130, 0.9, 6.0, 2), 12),
+             (datagen.zipf_baskets(70_001, 200, 0.9, 6.0, 3), 60),
+             (datagen.zipf_baskets(200_000, 300, 0.8, 8.0, 5), 100),
+             (plant, 400), (plant, 300),
+             (datagen.planted(n=20_000, m=600, n_patterns=40, seed=9), 120)]
+    try:
+        for c, thr in cases:
+            want = oracle.apriori(c.indptr, c.indices, c.m, thr).sha256()
+            fim.fim_build_bitmaps(ctx, c.indptr, c.indices, c.m)
+            for on in (1, 0, 1):
+                fim.fim_set_tuning(ctx, "compact_cluster", on)
+                fim.fim_mine(ctx, thr)
+                assert fim.fim_fetch_results(ctx).sha256() == want, (c.n, thr, on)
+    finally:
+        fim.fim_set_tuning(ctx, "compact_cluster", 1)

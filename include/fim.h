@@ -316,7 +316,8 @@ int fim_merge_results(fim_ctx *ctx, int64_t n_trans, int32_t n_items, int n_part
  * longer than max_len yield no rules (a set of size L has 2^L - 2 of them).
  * The rules stay in device memory of the ctx until the next fim_rules or
  * fim_mine; *n_rules gets their number.  Scratch: 8 bytes per held set and
- * 12 bytes per 32 candidate rules (sum of 2^|Z| - 2).
+ * 12 bytes per 32 candidate rules (sum of 2^|Z| - 2), plus 12 bytes per
+ * candidate when there are at most 2^27 of them.
  * Errors: FIM_E_STATE (no fim_mine result held, or the held sets are not
  * downward closed), FIM_E_INVAL (min_conf_ppm > 10^6, max_len outside
  * {0} u [2, FIM_RULES_MAX_LEN], n_rules NULL), FIM_E_NOMEM (also when the

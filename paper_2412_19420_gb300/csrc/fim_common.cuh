@@ -214,7 +214,7 @@ struct fim_ctx {
 
     // association rules of the held output
     DevBuf rule_base, rule_part, rule_bits, rule_kbase;  // evaluation space, scans, keep words
-    DevBuf rule_set, rule_mask, rule_conf, rule_lift;
+    DevBuf rule_set, rule_mask, rule_conf, rule_lift, rule_sets;
     uint64_t rules_n = 0, rules_evaluated = 0;
     uint64_t rules_of = 0;      // mine_serial the rules belong to
 

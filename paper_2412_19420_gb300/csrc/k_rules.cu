@@ -21,8 +21,10 @@
 //      (every subset of a frequent set is frequent: downward closure), decides
 //      the threshold, and one ballot per 32 evaluations stores a keep word;
 //   4. scan of the keep words' popcounts -> each word's first output slot;
-//   5. write: the kept evaluations redo their two lookups and write (set index,
-//      mask, conf, lift) at their slot, so the output keeps evaluation order.
+//   5. write: the kept evaluations write (set index, mask, conf, lift) at their
+//      slot, so the output keeps evaluation order; the keep pass leaves them
+//      their three set indices (12 bytes a candidate, up to 2^27 candidates;
+//      beyond that the write pass repeats the lookups).
 // The itemsets (offsets, items, supports) stay resident from the mine and the
 // lookups hit L2 for outputs up to tens of MB: the kernels are bound by
 // dependent-load latency, not by HBM bandwidth.
@@ -35,6 +37,7 @@ constexpr int RT = 256;                    // threads per CTA of the evaluation 
 constexpr int SCAN_T = 1024, SCAN_I = 8;   // scan: 1024 threads x 8 elements per CTA
 constexpr int SCAN_CHUNK = SCAN_T * SCAN_I;
 constexpr int NSIZE = 32;                  // size_start entries (sizes 0 .. 31)
+constexpr unsigned long long kRuleSetsMax = 1ull << 27;  // candidates whose lookups are kept (1.5 GB)
 
 struct SetsView {
     const unsigned long long *off;         // [R + 1]
@@ -97,10 +100,16 @@ __device__ __forceinline__ int64_t set_of_eval(const unsigned long long *__restr
 }
 
 struct Eval {
-    int64_t z;
+    int64_t z, rx, ry;
     uint32_t mask;
     uint64_t sz, sx, sy;
     bool ok;  // both subsets found
+};
+
+// The three set indices of a kept candidate, carried from the keep pass to the
+// write pass when the scratch fits (12 bytes per candidate).
+struct RuleSets {
+    uint32_t z, x, y;
 };
 
 __device__ __forceinline__ Eval evaluate(const SetsView &v, const unsigned long long *__restrict__ ebase,
@@ -112,12 +121,12 @@ __device__ __forceinline__ Eval evaluate(const SetsView &v, const unsigned long 
     const uint32_t full = (1u << L) - 1u;
     r.mask = (uint32_t)(e - ebase[r.z]) + 1u;
     const uint32_t *zp = v.items + o;
-    const int64_t rx = find_subset(v, zp, r.mask);
-    const int64_t ry = find_subset(v, zp, full & ~r.mask);
-    r.ok = rx >= 0 && ry >= 0;
+    r.rx = find_subset(v, zp, r.mask);
+    r.ry = find_subset(v, zp, full & ~r.mask);
+    r.ok = r.rx >= 0 && r.ry >= 0;
     r.sz = v.sup[r.z];
-    r.sx = r.ok ? v.sup[rx] : 1;
-    r.sy = r.ok ? v.sup[ry] : 1;
+    r.sx = r.ok ? v.sup[r.rx] : 1;
+    r.sy = r.ok ? v.sup[r.ry] : 1;
     return r;
 }
 
@@ -233,7 +242,7 @@ scan_out_kernel(Src src, unsigned long long n, const unsigned long long *__restr
 // [32w, 32w + 32) and stores their keep bits as one word.
 __global__ void __launch_bounds__(RT)
 rule_keep_kernel(SetsView v, const unsigned long long *__restrict__ ebase, unsigned long long E, uint32_t ppm,
-                 uint32_t *__restrict__ keep_bits, int *__restrict__ err) {
+                 uint32_t *__restrict__ keep_bits, RuleSets *__restrict__ sets, int *__restrict__ err) {
     const int lane = threadIdx.x & 31;
     const unsigned long long nw = (E + 31) / 32;
     const unsigned long long tw = (unsigned long long)gridDim.x * (RT / 32);
@@ -244,6 +253,7 @@ rule_keep_kernel(SetsView v, const unsigned long long *__restrict__ ebase, unsig
             const Eval r = evaluate(v, ebase, e);
             if (!r.ok) atomicExch(err, 1);  // a subset is missing: not a mine's output
             else keep = r.sz * 1000000ull >= (uint64_t)ppm * r.sx;
+            if (keep && sets) sets[e] = RuleSets{(uint32_t)r.z, (uint32_t)r.rx, (uint32_t)r.ry};
         }
         const uint32_t bal = __ballot_sync(0xffffffffu, keep);
         if (lane == 0) keep_bits[w] = bal;
@@ -253,8 +263,8 @@ rule_keep_kernel(SetsView v, const unsigned long long *__restrict__ ebase, unsig
 __global__ void __launch_bounds__(RT)
 rule_write_kernel(SetsView v, const unsigned long long *__restrict__ ebase, unsigned long long E, uint64_t n,
                   const uint32_t *__restrict__ keep_bits, const unsigned long long *__restrict__ kbase,
-                  unsigned long long *__restrict__ set_index, uint32_t *__restrict__ ante_mask,
-                  double *__restrict__ conf, double *__restrict__ lift) {
+                  const RuleSets *__restrict__ sets, unsigned long long *__restrict__ set_index,
+                  uint32_t *__restrict__ ante_mask, double *__restrict__ conf, double *__restrict__ lift) {
     const int lane = threadIdx.x & 31;
     const unsigned long long nw = (E + 31) / 32;
     const unsigned long long tw = (unsigned long long)gridDim.x * (RT / 32);
@@ -262,12 +272,30 @@ rule_write_kernel(SetsView v, const unsigned long long *__restrict__ ebase, unsi
     for (unsigned long long w = ((unsigned long long)blockIdx.x * RT + threadIdx.x) >> 5; w < nw; w += tw) {
         const uint32_t bits = keep_bits[w];
         if (!((bits >> lane) & 1u)) continue;
-        const Eval r = evaluate(v, ebase, w * 32 + lane);
+        const unsigned long long e = w * 32 + lane;
+        int64_t z;
+        uint32_t mask;
+        uint64_t sz, sx, sy;
+        if (sets) {  // the keep pass's lookups
+            const RuleSets q = sets[e];
+            z = q.z;
+            mask = (uint32_t)(e - ebase[z]) + 1u;
+            sz = v.sup[q.z];
+            sx = v.sup[q.x];
+            sy = v.sup[q.y];
+        } else {
+            const Eval r = evaluate(v, ebase, e);
+            z = r.z;
+            mask = r.mask;
+            sz = r.sz;
+            sx = r.sx;
+            sy = r.sy;
+        }
         const unsigned long long at = kbase[w] + __popc(bits & lt);
-        set_index[at] = (unsigned long long)r.z;
-        ante_mask[at] = r.mask;
-        conf[at] = (double)r.sz / (double)r.sx;
-        lift[at] = (double)(r.sz * n) / (double)(r.sx * r.sy);
+        set_index[at] = (unsigned long long)z;
+        ante_mask[at] = mask;
+        conf[at] = (double)sz / (double)sx;
+        lift[at] = (double)(sz * n) / (double)(sx * sy);
     }
 }
 
@@ -325,11 +353,16 @@ int fim_rules(fim_ctx *ctx, uint32_t min_conf_ppm, int max_len, uint64_t *n_rule
             unsigned long long *kbase = ctx->rule_kbase.as<unsigned long long>();
             int *err = ctx->dev_flag.as<int>() + 2;
             FIM_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
+            RuleSets *sets = nullptr;
+            if (E <= kRuleSetsMax && (unsigned long long)R <= 0xFFFFFFFFull) {
+                FIM_TRY(fim_reserve(ctx, ctx->rule_sets, sizeof(RuleSets) * (size_t)E));
+                sets = ctx->rule_sets.as<RuleSets>();
+            }
             const unsigned long long want = (nw + RT / 32 - 1) / (RT / 32);
             const unsigned long long cap = (unsigned long long)(ctx->num_sms > 0 ? ctx->num_sms : 1) * 8ull;  // 2,048 threads per SM
             const unsigned grid = (unsigned)(want < cap ? want : cap);
             ctx->launches++;
-            rule_keep_kernel<<<grid, RT, 0, st>>>(v, ebase, E, min_conf_ppm, bits, err);
+            rule_keep_kernel<<<grid, RT, 0, st>>>(v, ebase, E, min_conf_ppm, bits, sets, err);
             FIM_CUDA_TRY(cudaGetLastError());
             FIM_TRY(scan_into(ctx, WordPop{bits}, nw, kbase));
             unsigned long long total = 0;
@@ -344,7 +377,7 @@ int fim_rules(fim_ctx *ctx, uint32_t min_conf_ppm, int max_len, uint64_t *n_rule
                 FIM_TRY(fim_reserve(ctx, ctx->rule_conf, sizeof(double) * (size_t)total));
                 FIM_TRY(fim_reserve(ctx, ctx->rule_lift, sizeof(double) * (size_t)total));
                 ctx->launches++;
-                rule_write_kernel<<<grid, RT, 0, st>>>(v, ebase, E, (uint64_t)ctx->out_n, bits, kbase,
+                rule_write_kernel<<<grid, RT, 0, st>>>(v, ebase, E, (uint64_t)ctx->out_n, bits, kbase, sets,
                                                        ctx->rule_set.as<unsigned long long>(),
                                                        ctx->rule_mask.as<uint32_t>(), ctx->rule_conf.as<double>(),
                                                        ctx->rule_lift.as<double>());

@@ -90,12 +90,15 @@ cluster_sort_kernel(const unsigned long long *__restrict__ keys, unsigned long l
         }
         cluster.sync();
         // 2. destination base of every digit value for this CTA's records
-        if (tid < 256) {
+        if (tid < 256) {  // all 16 remote reads in flight at once
+            uint32_t h[16];
+#pragma unroll
+            for (int q = 0; q < 16; q++) h[q] = q < ncl ? cluster.map_shared_rank(f.hist, q)[tid] : 0u;
             uint32_t tot = 0, pre = 0;
-            for (int q = 0; q < ncl; q++) {
-                const uint32_t h = cluster.map_shared_rank(f.hist, q)[tid];
-                tot += h;
-                if (q < c) pre += h;
+#pragma unroll
+            for (int q = 0; q < 16; q++) {
+                tot += h[q];
+                pre += q < c ? h[q] : 0u;
             }
             f.tot[tid] = tot;
             f.base[tid] = pre;

@@ -46,6 +46,17 @@ WORKLOAD_DESC = {
 L2_FLUSH_BYTES = 256 << 20
 
 
+def _emit(line: dict) -> None:
+    """Print the result line last: NCCL writes its version line through the C
+    library's stdout buffer, which would otherwise be flushed after Python's."""
+    import ctypes
+    try:
+        ctypes.CDLL(None).fflush(None)
+    except (OSError, AttributeError):
+        pass
+    print(json.dumps(line), flush=True)
+
+
 def _args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -198,7 +209,7 @@ def run_reference(args):
             "cpu_baseline": {"value": value, "unit": "supports/s", "cores": b["cores"], "kind": "oracle",
                              "sample": b["sample"]},
             "e2e": {"value": value, "unit": "supports/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line))
+    _emit(line)
 
 
 def _train_scheduler(ctx, fim, sched, datagen, sample):
@@ -347,7 +358,7 @@ def run_batched(args):
         dt = time.perf_counter() - t0
         line["cpu_baseline"] = {"value": cand / dt, "unit": "supports/s", "cores": _cores(), "kind": "oracle",
                                 "sample": f"first {k} of {len(dbs)} databases ({cand:,} candidate supports)"}
-    print(json.dumps(line))
+    _emit(line)
     fim.fim_destroy(ctx)
 
 
@@ -484,7 +495,7 @@ def run_sharded(args):
         "clocks": clk.summary(),
     }
     if rank == 0:
-        print(json.dumps(line))
+        _emit(line)
     fim.fim_destroy(ctx)
     dist.destroy_process_group()
 
@@ -691,7 +702,7 @@ def main():
         one.pop("frac")
         line["cpu_baseline"]["single_thread"] = {k: one[k] for k in ("value", "sample", "seconds")}
     if rank == 0:
-        print(json.dumps(line))
+        _emit(line)
     _ = (np, got)
     fim.fim_destroy(ctx)
     if world > 1:

@@ -179,6 +179,11 @@ int fim_get_stats(const fim_ctx *ctx, fim_stats *out);
  *   "pairs_kdrain"     0..32768  128-transaction stages one accumulator sums before
  *                                it is drained (0 = 32768: partial sums stay <= 2^24,
  *                                exact in f32)
+ *   "upload_mapped"    0, 1      host input to fim_build_bitmaps that lives in
+ *                                page-locked, mapped memory (cudaHostAlloc,
+ *                                cudaHostRegister) is read by the build kernel in
+ *                                place over the host link, without a staging copy
+ *                                (default 1; other host memory is copied)
  *   "upload_chunks"    1..16     host input to fim_build_bitmaps: the indices go
  *                                up in this many chunks, each built as soon as it
  *                                lands (default 4; 1 = one copy, then the build)

@@ -193,9 +193,29 @@ int fim_build_bitmaps(fim_ctx *ctx, const int64_t *indptr, const int32_t *indice
     const int64_t *d_ptr = indptr;
     const int32_t *d_idx = indices;
     int64_t h_nnz = -1;
+    bool mapped = false;  // pinned host CSR read by the build kernel in place
     if (!(flags & FIM_INPUT_DEVICE)) {
         const int64_t nnz = indptr[n_trans];
         if (indptr[0] != 0 || nnz < 0 || (nnz > 0 && !indices)) return FIM_E_INVAL;
+        if (ctx->upload_mapped) {
+            // page-locked, mapped host memory is addressable from the GPU: the
+            // kernel streams it over the host link, no staging copy
+            cudaPointerAttributes ap{}, ai{};
+            const bool ok_p = cudaPointerGetAttributes(&ap, indptr) == cudaSuccess &&
+                              ap.type == cudaMemoryTypeHost && ap.devicePointer != nullptr;
+            const bool ok_i = nnz == 0 || (cudaPointerGetAttributes(&ai, indices) == cudaSuccess &&
+                                           ai.type == cudaMemoryTypeHost && ai.devicePointer != nullptr);
+            cudaGetLastError();  // a query on unregistered memory leaves no sticky error
+            if (ok_p && ok_i) {
+                d_ptr = static_cast<const int64_t *>(ap.devicePointer);
+                d_idx = nnz ? static_cast<const int32_t *>(ai.devicePointer) : indices;
+                h_nnz = nnz;
+                mapped = true;
+            }
+        }
+    }
+    if (!(flags & FIM_INPUT_DEVICE) && !mapped) {
+        const int64_t nnz = indptr[n_trans];
         FIM_TRY(fim_reserve(ctx, ctx->csr_ptr, sizeof(int64_t) * (size_t)(n_trans + 1)));
         FIM_TRY(fim_reserve(ctx, ctx->csr_idx, sizeof(int32_t) * (size_t)(nnz > 0 ? nnz : 1)));
         FIM_CUDA_TRY(cudaMemcpyAsync(ctx->csr_ptr.p, indptr, sizeof(int64_t) * (size_t)(n_trans + 1),
@@ -204,7 +224,7 @@ int fim_build_bitmaps(fim_ctx *ctx, const int64_t *indptr, const int32_t *indice
         d_ptr = ctx->csr_ptr.as<int64_t>();
         d_idx = ctx->csr_idx.as<int32_t>();
         h_nnz = nnz;
-    } else {
+    } else if (flags & FIM_INPUT_DEVICE) {
         int64_t first = -1;
         FIM_CUDA_TRY(cudaMemcpyAsync(&first, indptr, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
         FIM_CUDA_TRY(cudaStreamSynchronize(st));
@@ -216,6 +236,7 @@ int fim_build_bitmaps(fim_ctx *ctx, const int64_t *indptr, const int32_t *indice
     FIM_TRY(fim_reserve(ctx, ctx->perm, sizeof(int32_t) * mm));
     FIM_TRY(fim_reserve(ctx, ctx->rank, sizeof(int32_t) * mm));
     if (flags & FIM_INPUT_DEVICE) FIM_TRY(launch_build_bitmaps(ctx, d_ptr, d_idx, -1, nullptr, nullptr));
+    else if (mapped) FIM_TRY(launch_build_bitmaps(ctx, d_ptr, d_idx, h_nnz, nullptr, nullptr));
     else FIM_TRY(launch_build_bitmaps(ctx, d_ptr, d_idx, h_nnz, indptr, h_nnz > 0 ? indices : nullptr));
     cudaEventRecord(ctx->ev[1], st);
     FIM_TRY(launch_item_support(ctx));
@@ -535,6 +556,7 @@ int fim_set_tuning(fim_ctx *ctx, const char *key, int64_t v) {
         {"pairs_kdrain", &ctx->pairs_kdrain, 0, 32768},
         {"upload_chunks", &ctx->upload_chunks, 1, 16},
         {"compact_cluster", &ctx->compact_cluster, 0, 1},
+        {"upload_mapped", &ctx->upload_mapped, 0, 1},
         {"upload_streams", &ctx->upload_streams, 1, 2},
     };
     for (const Knob &k : knobs)

@@ -254,6 +254,7 @@ struct fim_ctx {
     int pairs_kdrain = 0;       // stages (x128 transactions) per exact drain (0 = 64)
     int compact_cluster = 1;    // small outputs: sort in one cluster launch
     int csort_cl[5] = {0, 0, 0, 0, 0};  // cluster size per key width (0 unknown, -1 none)
+    int upload_mapped = 1;      // host input in pinned, mapped memory: build reads it in place
     int upload_chunks = 4;      // host input: index upload chunks overlapped with the build
     int upload_streams = 2;     // copy streams the chunks alternate over
     cudaStream_t up_stream[2] = {nullptr, nullptr};

@@ -159,3 +159,30 @@ def test_cluster_sort_equals_launch_sequence(ctx):
                 assert fim.fim_fetch_results(ctx).sha256() == want, (c.n, thr, on)
     finally:
         fim.fim_set_tuning(ctx, "compact_cluster", 1)
+
+
+def test_mapped_host_input_is_exact(ctx):
+    # page-locked host CSR: read in place by the build kernel (upload_mapped 1)
+    # or staged by copies (0); pageable numpy arrays always take the copies
+    torch = pytest.importorskip("torch")
+    try:
+        for n, m, thr in [(70_001, 200, 250), (513, 9, 3)]:
+            c = datagen.zipf_baskets(n, m, 0.9, 6.0, n + 1)
+            want = oracle.apriori(c.indptr, c.indices, c.m, thr).sha256()
+            ip = torch.from_numpy(c.indptr).pin_memory()
+            ix = torch.from_numpy(c.indices).pin_memory()
+            for mapped in (1, 0):
+                fim.fim_set_tuning(ctx, "upload_mapped", mapped)
+                for src in ((ip.numpy(), ix.numpy()), (c.indptr, c.indices)):
+                    fim.fim_build_bitmaps(ctx, src[0], src[1], c.m)
+                    fim.fim_mine(ctx, thr)
+                    assert fim.fim_fetch_results(ctx).sha256() == want
+        # a malformed pinned CSR is rejected in place too
+        c = datagen.zipf_baskets(5_000, 30, 0.9, 6.0, 2)
+        bad = torch.from_numpy(c.indptr.copy()).pin_memory()
+        bad[3000], bad[3001] = int(bad[3001]), int(bad[3000]) - 1
+        fim.fim_set_tuning(ctx, "upload_mapped", 1)
+        with pytest.raises(fim.FimError):
+            fim.fim_build_bitmaps(ctx, bad.numpy(), torch.from_numpy(c.indices).pin_memory().numpy(), c.m)
+    finally:
+        fim.fim_set_tuning(ctx, "upload_mapped", 1)

@@ -667,6 +667,14 @@ def main():
     # ---- roofline of the dominant phase ---------------------------------
     avg = {p: phase[p] / args.steps for p in phase}
     roof = _roofline(st, avg, csr, args.workload)
+    # measured AND/popc issue rate and L2 bandwidth (the L2-resident
+    # workloads' ceiling): the DFS's word pairs against the first
+    popc_rate, l2_gbs = fim.fim_probe(ctx, 0), fim.fim_probe(ctx, 1)
+    probes = {"popc_word_pairs_per_s": popc_rate, "l2_read_gbs": l2_gbs}
+    if roof["kernel"] == "dfs_kernel":
+        words_per_s = st["dfs_touched_bytes"] / 4 / (avg["ms_dfs"] / 1000)
+        probes["dfs_alu_frac"] = words_per_s / popc_rate
+        probes["dfs_vs_l2_frac"] = roof["achieved"] / l2_gbs
 
     line = {
         "metric": "itemset supports/sec", "value": value, "unit": "supports/s", "n_gpus": world,
@@ -691,6 +699,7 @@ def main():
         "roofline": roof,
         "clocks": clk.summary(),
     }
+    line["probes"] = probes
     if rules is not None:
         line["rules"] = rules
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -376,6 +376,15 @@ int fim_fetch_rules(fim_ctx *ctx, uint64_t *n_rules, uint64_t *set_index, uint32
 int fim_pair_supports_noalloc(const int64_t *d_indptr, const int32_t *d_indices, int64_t n_trans,
                               int32_t n_items, uint32_t *d_pair_counts, void *cuda_stream);
 
+/* fim_probe: measurement probes for the counting kernels' rooflines, run on
+ * the ctx's GPU and stream (two short launches, the second timed).
+ *   which = 0: AND/popc word pairs per second over all SMs -- one LOP3, one
+ *              POPC and one IADD per pair, the inner step of the pair and
+ *              prefix-extension passes;
+ *   which = 1: L2 read bandwidth in GB/s, 16-byte loads over a 32 MB buffer.
+ * Errors: FIM_E_INVAL (unknown probe, result NULL), FIM_E_NOMEM, FIM_E_CUDA. */
+int fim_probe(fim_ctx *ctx, int which, double *result);
+
 /* fim_minsup_from_ppm: ceil(n_trans * ppm / 1e6) in integers, at least 1:
  * the threshold of Eq. 3 given as a fraction of the transactions. */
 uint64_t fim_minsup_from_ppm(int64_t n_trans, uint32_t ppm);

@@ -153,7 +153,7 @@ void fim_destroy(fim_ctx *ctx) {
                      &ctx->scan_part, &ctx->out_off,
                      &ctx->out_items, &ctx->out_sup, &ctx->rule_base, &ctx->rule_part, &ctx->rule_bits,
                      &ctx->rule_kbase, &ctx->rule_set, &ctx->rule_mask,
-                     &ctx->rule_conf, &ctx->rule_lift, &ctx->rule_sets, &ctx->mlp_w32, &ctx->mlp_wbf, &ctx->trace_x,
+                     &ctx->rule_conf, &ctx->rule_lift, &ctx->rule_sets, &ctx->probe_buf, &ctx->shard_cost, &ctx->merge_off, &ctx->mlp_w32, &ctx->mlp_wbf, &ctx->trace_x,
                      &ctx->trace_y, &ctx->mlp_scratch, &ctx->root_order, &ctx->root_bucket,
                      &ctx->root_hist, &ctx->rec_db, &ctx->dbdesc, &ctx->epoch, &ctx->sp_idx,
                      &ctx->sp_val, &ctx->sp_z};

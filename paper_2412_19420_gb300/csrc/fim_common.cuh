@@ -211,6 +211,7 @@ struct fim_ctx {
     int64_t out_n = 0;          // transactions behind the held output
     int shard = 0, n_shards = 1; // prefix-class share of the mine in progress
     DevBuf shard_cost, merge_off;
+    DevBuf probe_buf;           // measurement probes' buffer
 
     // association rules of the held output
     DevBuf rule_base, rule_part, rule_bits, rule_kbase;  // evaluation space, scans, keep words

@@ -89,6 +89,7 @@ def _load():
         "fim_merge_results": (ctypes.c_int, [P, I64, I32, ctypes.c_int, P, P, P, P, P, U32]),
         "fim_fetch_rules": (ctypes.c_int, [P, ctypes.POINTER(U64), P, P, P, P, U64, U32]),
         "fim_rules_evaluated": (ctypes.c_int, [P, ctypes.POINTER(U64)]),
+        "fim_probe": (ctypes.c_int, [P, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
         "fim_batch_slices": (ctypes.c_int, [P, P, U64]),
         "fim_pair_supports_noalloc": (ctypes.c_int, [P, P, I64, I32, P, P]),
         "fim_minsup_from_ppm": (U64, [I64, U32]),
@@ -316,6 +317,13 @@ def fim_fetch_rules(ctx, out=None) -> Rules:
     if dev:
         return Rules(si[:N], am[:N], cf[:N], lf[:N])
     return Rules(si[:N].copy(), am[:N].copy(), cf[:N].copy(), lf[:N].copy())
+
+
+def fim_probe(ctx, which: int) -> float:
+    """Measurement probe: 0 = AND/popc word pairs per second, 1 = L2 read GB/s."""
+    r = ctypes.c_double()
+    _check(_lib.fim_probe(ctx, int(which), ctypes.byref(r)), "fim_probe")
+    return float(r.value)
 
 
 def fim_set_tuning(ctx, key: str, value: int) -> None:

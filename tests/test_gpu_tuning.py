@@ -186,3 +186,14 @@ def test_mapped_host_input_is_exact(ctx):
             fim.fim_build_bitmaps(ctx, bad.numpy(), torch.from_numpy(c.indices).pin_memory().numpy(), c.m)
     finally:
         fim.fim_set_tuning(ctx, "upload_mapped", 1)
+
+
+def test_probes_are_plausible(ctx):
+    # measurement probes: the AND/popc word-pair rate and the L2 read
+    # bandwidth of the GPU (GB300: 152 SMs near 2 GHz, L2 well above HBM)
+    popc = fim.fim_probe(ctx, 0)
+    l2 = fim.fim_probe(ctx, 1)
+    assert 1e11 < popc < 1e14
+    assert 1000 < l2 < 200_000
+    with pytest.raises(fim.FimError):
+        fim.fim_probe(ctx, 2)

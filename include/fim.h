@@ -179,6 +179,13 @@ int fim_get_stats(const fim_ctx *ctx, fim_stats *out);
  *   "pairs_kdrain"     0..32768  128-transaction stages one accumulator sums before
  *                                it is drained (0 = 32768: partial sums stay <= 2^24,
  *                                exact in f32)
+ *   "spin_limit_ms"    1..600000 longest a device-side wait (the DFS work queue)
+ *                                spins before the mine ends with FIM_E_TIMEOUT
+ *                                (default 60000); the ctx stays usable
+ *   "test_withhold_task" -1..2^20 fault injection for tests: the DFS never
+ *                                publishes this work-queue slot, so the worker
+ *                                that takes it (and the drain) must time out;
+ *                                -1 (default) = off
  *   "upload_mapped"    0, 1      host input to fim_build_bitmaps that lives in
  *                                page-locked, mapped memory (cudaHostAlloc,
  *                                cudaHostRegister) is read by the build kernel in

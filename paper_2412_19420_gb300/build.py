@@ -66,7 +66,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         for _, log in res:
             print(log)
     tmp = LIB + f".tmp{os.getpid()}"
-    r = subprocess.run([cc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs],
+    r = subprocess.run([cc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs, "-ldl"],
                        capture_output=True, text=True)
     for o in objs:
         os.remove(o)

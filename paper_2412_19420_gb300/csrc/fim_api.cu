@@ -29,7 +29,6 @@ constexpr unsigned long long kTaskCap = 1ull << 20;
 constexpr unsigned long long kCandPoolCap = 1ull << 24;
 constexpr size_t kStackBudget = 8ull << 30;   // first try; grows on FIM_E_STACK
 constexpr size_t kStackBudgetMax = 64ull << 30;
-constexpr unsigned long long kSpinLimitNs = 60ull * 1000 * 1000 * 1000;
 
 }  // namespace
 
@@ -104,6 +103,7 @@ uint64_t fim_minsup_from_ppm(int64_t n_trans, uint32_t ppm) {
 }
 
 int fim_create(fim_ctx **out, int device, void *cuda_stream) {
+    FIM_NVTX("fim_create");
     if (!out) return FIM_E_INVAL;
     *out = nullptr;
     int ndev = 0;
@@ -142,6 +142,7 @@ int fim_create(fim_ctx **out, int device, void *cuda_stream) {
 }
 
 void fim_destroy(fim_ctx *ctx) {
+    FIM_NVTX("fim_destroy");
     if (!ctx) return;
     DeviceGuard g(ctx->device);
     cudaStreamSynchronize(ctx->stream);
@@ -175,6 +176,7 @@ void fim_destroy(fim_ctx *ctx) {
 
 int fim_build_bitmaps(fim_ctx *ctx, const int64_t *indptr, const int32_t *indices, int64_t n_trans,
                       int32_t n_items, uint32_t flags) {
+    FIM_NVTX("fim_build_bitmaps");
     if (!ctx) return FIM_E_INVAL;
     if (n_trans < 0 || n_trans > FIM_MAX_TRANS || n_items < 0 || n_items > FIM_MAX_ITEMS) return FIM_E_INVAL;
     if (!indptr) return FIM_E_INVAL;
@@ -361,7 +363,8 @@ int mine_once(fim_ctx *ctx, uint32_t thr, uint32_t flags, MineState &ms, bool *r
         p.rec_cap = ctx->rec_cap;
         p.rec_items_cap = ctx->rec_items_cap;
         p.ctr = d_ctr;
-        p.spin_limit = kSpinLimitNs;
+        p.spin_limit = (unsigned long long)ctx->spin_limit_ms * 1000000ull;
+        p.withhold_slot = ctx->test_withhold_task;
         // automatic: keep low-support classes sparse when the frequent item
         // columns do not fit in half of L2 (streaming whole columns from HBM
         // is latency-bound; from L2 the dense pass is as fast)
@@ -449,6 +452,7 @@ int mine_once(fim_ctx *ctx, uint32_t thr, uint32_t flags, MineState &ms, bool *r
 extern "C" {
 
 int fim_mine(fim_ctx *ctx, uint64_t minsup, uint32_t flags) {
+    FIM_NVTX("fim_mine");
     if (!ctx) return FIM_E_INVAL;
     if (!ctx->built) return FIM_E_STATE;
     if (!(flags & FIM_STRICT) && minsup == 0) return FIM_E_INVAL;
@@ -504,6 +508,7 @@ int fim_mine(fim_ctx *ctx, uint64_t minsup, uint32_t flags) {
 }
 
 int fim_mine_shard(fim_ctx *ctx, uint64_t minsup, uint32_t flags, int shard, int n_shards) {
+    FIM_NVTX("fim_mine_shard");
     if (!ctx || n_shards < 1 || n_shards > FIM_MAX_SHARDS || shard < 0 || shard >= n_shards) return FIM_E_INVAL;
     ctx->shard = shard;
     ctx->n_shards = n_shards;
@@ -516,6 +521,7 @@ int fim_mine_shard(fim_ctx *ctx, uint64_t minsup, uint32_t flags, int shard, int
 int fim_fetch_results(fim_ctx *ctx, uint64_t *n_sets, uint64_t *n_items_total, uint64_t *offsets,
                       uint32_t *items, uint32_t *supports, uint64_t cap_sets, uint64_t cap_items,
                       uint32_t flags) {
+    FIM_NVTX("fim_fetch_results");
     if (!ctx || !n_sets || !n_items_total) return FIM_E_INVAL;
     if (!ctx->mined) return FIM_E_STATE;
     *n_sets = ctx->out_sets;
@@ -537,12 +543,14 @@ int fim_fetch_results(fim_ctx *ctx, uint64_t *n_sets, uint64_t *n_items_total, u
 }
 
 int fim_get_stats(const fim_ctx *ctx, fim_stats *out) {
+    FIM_NVTX("fim_get_stats");
     if (!ctx || !out) return FIM_E_INVAL;
     *out = ctx->stats;
     return FIM_OK;
 }
 
 int fim_set_tuning(fim_ctx *ctx, const char *key, int64_t v) {
+    FIM_NVTX("fim_set_tuning");
     if (!ctx || !key) return FIM_E_INVAL;
     struct Knob { const char *name; int *field; int64_t lo, hi; } knobs[] = {
         {"dfs_ctas_per_sm", &ctx->dfs_ctas_per_sm, 1, 4},
@@ -557,6 +565,8 @@ int fim_set_tuning(fim_ctx *ctx, const char *key, int64_t v) {
         {"upload_chunks", &ctx->upload_chunks, 1, 16},
         {"compact_cluster", &ctx->compact_cluster, 0, 1},
         {"upload_mapped", &ctx->upload_mapped, 0, 1},
+        {"spin_limit_ms", &ctx->spin_limit_ms, 1, 600000},
+        {"test_withhold_task", &ctx->test_withhold_task, -1, 1 << 20},
         {"upload_streams", &ctx->upload_streams, 1, 2},
     };
     for (const Knob &k : knobs)

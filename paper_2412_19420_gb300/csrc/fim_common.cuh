@@ -25,6 +25,18 @@
 
 #include "../../include/fim.h"
 
+#include <nvtx3/nvToolsExt.h>
+
+// An NVTX range around an ABI call, visible to Nsight tools when one is
+// attached (the header-only NVTX v3 API: no cost without a tool).
+struct FimNvtxRange {
+    explicit FimNvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~FimNvtxRange() { nvtxRangePop(); }
+    FimNvtxRange(const FimNvtxRange &) = delete;
+    FimNvtxRange &operator=(const FimNvtxRange &) = delete;
+};
+#define FIM_NVTX(name) FimNvtxRange fim_nvtx_range_(name)
+
 #define FIM_WORDS_ALIGN 128  // column padding, in 32-bit words (512 bytes)
 
 // ---------------------------------------------------------------- utilities
@@ -166,7 +178,8 @@ struct DfsParams {
     unsigned long long trace_cap;
     int trace;
     MineCounters *ctr;
-    unsigned long long spin_limit;  // bounded waits (iterations)
+    unsigned long long spin_limit;  // bounded waits (ns of %globaltimer)
+    long long withhold_slot;        // test hook: this queue slot is never published (-1: none)
     int sparse_div;                 // store b_Y sparse when S(Y) * sparse_div <= nw (0: never)
     int learned_kmin;               // FIM_LEARNED consults the network for classes with >= this many candidates
     int root_reverse;               // hand out the root classes in reverse emission order
@@ -255,6 +268,8 @@ struct fim_ctx {
     int pairs_kdrain = 0;       // stages (x128 transactions) per exact drain (0 = 64)
     int compact_cluster = 1;    // small outputs: sort in one cluster launch
     int csort_cl[5] = {0, 0, 0, 0, 0};  // cluster size per key width (0 unknown, -1 none)
+    int spin_limit_ms = 60000;  // longest device-side wait before FIM_E_TIMEOUT
+    int test_withhold_task = -1; // test hook: the DFS never publishes this queue slot
     int upload_mapped = 1;      // host input in pinned, mapped memory: build reads it in place
     int upload_chunks = 4;      // host input: index upload chunks overlapped with the build
     int upload_streams = 2;     // copy streams the chunks alternate over

@@ -30,7 +30,6 @@ constexpr int TI = 64;     // pair tile side
 constexpr int KW = 32;     // words per pair k-step
 constexpr unsigned long long kTaskCap = 1ull << 20;
 constexpr unsigned long long kCandPoolCap = 1ull << 24;
-constexpr unsigned long long kSpinLimitNs = 60ull * 1000 * 1000 * 1000;
 
 // largest d with prefix[d] <= x (prefix has n_db + 1 entries, prefix[0] = 0)
 __device__ __forceinline__ int find_db(const int64_t *prefix, int n_db, int64_t x) {
@@ -454,6 +453,7 @@ struct Layout {
 extern "C" {
 
 int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t flags) {
+    FIM_NVTX("fim_mine_batched");
     if (!ctx || n_db <= 0 || n_db > (1 << 20) || !in) return FIM_E_INVAL;
     if (flags & (FIM_TRACE | FIM_PAIRS_POPC)) {
         // traces are per single mine; the batched pair pass is the CUDA-core one
@@ -648,7 +648,8 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
         p.diffset_rule = (flags & FIM_DIFFSET_RULE) ? 1 : 0;
         p.mlp_w = ctx->mlp_wbf.as<__nv_bfloat16>();
         p.ctr = d_ctr;
-        p.spin_limit = kSpinLimitNs;
+        p.spin_limit = (unsigned long long)ctx->spin_limit_ms * 1000000ull;
+        p.withhold_slot = -1;
         p.sparse_div = ctx->sparse_div > 0 ? ctx->sparse_div : 0;  // automatic: dense (small databases)
         p.epoch = ctx->epoch.as<uint32_t>();
         p.learned_kmin = ctx->learned_kmin;
@@ -810,6 +811,7 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
 
 int fim_fetch_batched(fim_ctx *ctx, int db, uint64_t *n_sets, uint64_t *n_items_total, uint64_t *offsets,
                       uint32_t *items, uint32_t *supports, uint64_t cap_sets, uint64_t cap_items, uint32_t flags) {
+    FIM_NVTX("fim_fetch_batched");
     if (!ctx || !n_sets || !n_items_total) return FIM_E_INVAL;
     if (!ctx->batch_mined) return FIM_E_STATE;
     if (db != FIM_ALL_DBS && (db < 0 || db >= ctx->batch_n_db)) return FIM_E_INVAL;
@@ -849,6 +851,7 @@ int fim_fetch_batched(fim_ctx *ctx, int db, uint64_t *n_sets, uint64_t *n_items_
 }
 
 int fim_batch_slices(fim_ctx *ctx, uint64_t *set_start, uint64_t cap) {
+    FIM_NVTX("fim_batch_slices");
     if (!ctx || !set_start) return FIM_E_INVAL;
     if (!ctx->batch_mined) return FIM_E_STATE;
     if (cap < (uint64_t)ctx->batch_n_db + 1) return FIM_E_TOO_SMALL;

@@ -681,7 +681,10 @@ __device__ bool try_push(const DfsParams &p, Smem &s, int plen, uint32_t item, u
         atomicAdd((unsigned long long *)&p.ctr->pending, 1ull);
         atomicAdd(&p.ctr->pushed, 1ull);
         __threadfence();
-        atomicExch(&t->ready, s.epoch);
+        // (the fault-injection hook withholds one publish: the worker that
+        // takes this slot, and every worker waiting for the queue to drain,
+        // must give up at the spin limit)
+        if ((long long)s.ticket != p.withhold_slot) atomicExch(&t->ready, s.epoch);
     }
     __syncthreads();
     return true;

@@ -299,6 +299,7 @@ int launch_root_order(fim_ctx *ctx, MineCounters *d_ctr, size_t npairs) {
 extern "C" {
 
 int fim_sched_load_weights(fim_ctx *ctx, const float *weights, size_t n_params) {
+    FIM_NVTX("fim_sched_load_weights");
     if (!ctx || !weights || n_params != (size_t)P) return FIM_E_INVAL;
     FIM_TRY(fim_reserve(ctx, ctx->mlp_w32, sizeof(float) * P));
     FIM_TRY(fim_reserve(ctx, ctx->mlp_wbf, sizeof(__nv_bfloat16) * P));
@@ -313,6 +314,7 @@ int fim_sched_load_weights(fim_ctx *ctx, const float *weights, size_t n_params) 
 }
 
 int fim_fetch_traces(fim_ctx *ctx, uint64_t *n_rows, float *features, float *targets, uint64_t cap) {
+    FIM_NVTX("fim_fetch_traces");
     if (!ctx || !n_rows) return FIM_E_INVAL;
     if (!ctx->mined || !(ctx->mflags & FIM_TRACE)) return FIM_E_STATE;
     unsigned long long n = ctx->host_ctr.n_traces;
@@ -333,6 +335,7 @@ int fim_fetch_traces(fim_ctx *ctx, uint64_t *n_rows, float *features, float *tar
 
 int fim_mlp_forward(fim_ctx *ctx, const float *params, const float *x, int64_t B, float *y, float *cache,
                     int bf16) {
+    FIM_NVTX("fim_mlp_forward");
     if (!ctx || !params || !x || !y || B < 0) return FIM_E_INVAL;
     if (B == 0) return FIM_OK;
     ctx->launches++;
@@ -343,6 +346,7 @@ int fim_mlp_forward(fim_ctx *ctx, const float *params, const float *x, int64_t B
 
 int fim_mlp_backward(fim_ctx *ctx, const float *params, const float *x, const float *y, const float *t,
                      const float *cache, int64_t B, float *grad, float *loss_out, int bf16) {
+    FIM_NVTX("fim_mlp_backward");
     if (!ctx || !params || !x || !y || !t || !cache || !grad || B <= 0) return FIM_E_INVAL;
     const int nb = (int)ceil_div64(B, 128);
     const int nchunks = (int)ceil_div64(B, GCHUNK);
@@ -366,6 +370,7 @@ int fim_mlp_backward(fim_ctx *ctx, const float *params, const float *x, const fl
 
 int fim_mlp_adam(fim_ctx *ctx, float *params, const float *grad, float *m, float *v, int step, float lr,
                  float beta1, float beta2, float eps) {
+    FIM_NVTX("fim_mlp_adam");
     if (!ctx || !params || !grad || !m || !v || step < 1) return FIM_E_INVAL;
     const float c1 = 1.f - powf(beta1, (float)step), c2 = 1.f - powf(beta2, (float)step);
     ctx->launches++;

@@ -145,6 +145,7 @@ int noalloc_setup(int dev, NoallocSlot *out) {
 
 extern "C" int fim_pair_supports_noalloc(const int64_t *d_indptr, const int32_t *d_indices, int64_t n_trans,
                                          int32_t n_items, uint32_t *d_pair_counts, void *cuda_stream) {
+    FIM_NVTX("fim_pair_supports_noalloc");
     if (!d_indptr || !d_pair_counts || n_trans < 0 || n_items < 0 || n_items > FIM_MAX_ITEMS)
         return FIM_E_INVAL;
     const int64_t nw = ceil_div64(n_trans, 32);

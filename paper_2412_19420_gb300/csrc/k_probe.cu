@@ -57,6 +57,7 @@ l2_probe_kernel(const uint4 *__restrict__ buf, unsigned long long n16, int reps,
 extern "C" {
 
 int fim_probe(fim_ctx *ctx, int which, double *result) {
+    FIM_NVTX("fim_probe");
     if (!ctx || !result || which < 0 || which > 1) return FIM_E_INVAL;
     *result = 0.0;
     int dev_prev = -1;

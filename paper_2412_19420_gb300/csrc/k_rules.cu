@@ -318,6 +318,7 @@ int scan_into(fim_ctx *ctx, Src src, unsigned long long n, unsigned long long *o
 extern "C" {
 
 int fim_rules(fim_ctx *ctx, uint32_t min_conf_ppm, int max_len, uint64_t *n_rules) {
+    FIM_NVTX("fim_rules");
     if (!ctx || !n_rules || min_conf_ppm > 1000000u) return FIM_E_INVAL;
     if (max_len == 0) max_len = RMAX;
     if (max_len < 2 || max_len > RMAX) return FIM_E_INVAL;
@@ -394,6 +395,7 @@ int fim_rules(fim_ctx *ctx, uint32_t min_conf_ppm, int max_len, uint64_t *n_rule
 }
 
 int fim_rules_evaluated(const fim_ctx *ctx, uint64_t *n_evaluated) {
+    FIM_NVTX("fim_rules_evaluated");
     if (!ctx || !n_evaluated) return FIM_E_INVAL;
     if (!ctx->mined || ctx->rules_of != ctx->mine_serial) return FIM_E_STATE;
     *n_evaluated = ctx->rules_evaluated;
@@ -402,6 +404,7 @@ int fim_rules_evaluated(const fim_ctx *ctx, uint64_t *n_evaluated) {
 
 int fim_fetch_rules(fim_ctx *ctx, uint64_t *n_rules, uint64_t *set_index, uint32_t *ante_mask, double *conf,
                     double *lift, uint64_t cap, uint32_t flags) {
+    FIM_NVTX("fim_fetch_rules");
     if (!ctx || !n_rules) return FIM_E_INVAL;
     if (!ctx->mined || ctx->rules_of != ctx->mine_serial) return FIM_E_STATE;
     *n_rules = ctx->rules_n;

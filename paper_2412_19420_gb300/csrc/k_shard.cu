@@ -199,6 +199,7 @@ extern "C" {
 int fim_merge_results(fim_ctx *ctx, int64_t n_trans, int32_t n_items, int n_parts, const uint64_t *n_sets,
                       const uint64_t *n_items_total, const uint64_t *const *offsets, const uint32_t *const *items,
                       const uint32_t *const *supports, uint32_t flags) {
+    FIM_NVTX("fim_merge_results");
     if (!ctx || n_parts < 1 || !n_sets || !n_items_total || !offsets || !items || !supports) return FIM_E_INVAL;
     if (n_trans < 0 || n_trans > FIM_MAX_TRANS || n_items < 0 || n_items > FIM_MAX_ITEMS) return FIM_E_INVAL;
     unsigned long long R = 0, T = 0;

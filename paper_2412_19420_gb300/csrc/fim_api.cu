@@ -166,6 +166,9 @@ void fim_destroy(fim_ctx *ctx) {
         if (g) cudaGraphExecDestroy((cudaGraphExec_t)g);
     for (cudaStream_t u : ctx->up_stream)
         if (u) cudaStreamDestroy(u);
+    if (ctx->aux_stream) cudaStreamDestroy(ctx->aux_stream);
+    for (cudaEvent_t e : ctx->aux_ev)
+        if (e) cudaEventDestroy(e);
     for (cudaEvent_t e : ctx->up_ev)
         if (e) cudaEventDestroy(e);
     for (auto &e : ctx->ev)
@@ -297,6 +300,28 @@ int mine_once(fim_ctx *ctx, uint32_t thr, uint32_t flags, MineState &ms, bool *r
     }
     cudaEventRecord(ctx->ev[1], st);
     const bool do_pairs = mf >= 2 && (maxlen == 0 || maxlen >= 2);
+    const bool do_dfs = do_pairs && mf >= 3 && (maxlen == 0 || maxlen >= 3);
+    // automatic: keep low-support classes sparse when the frequent item
+    // columns do not fit in half of L2 (streaming whole columns from HBM
+    // is latency-bound; from L2 the dense pass is as fast)
+    const int sparse_div = ctx->sparse_div >= 0 ? ctx->sparse_div
+                           : ((double)mf * (double)ctx->nwp * 4.0 > 0.5 * (double)ctx->l2_bytes ? 4 : 0);
+    // sparse copies of the low-support item columns, for the root classes
+    // (bounded: at most 1 GiB of (index, word) pairs); a child of a sparse
+    // parent is stored sparse, so the copies must fit half a stack level.
+    // They depend only on the ranking, so they are made on a side stream
+    // while the pair pass runs (their kernel fits beside its CTAs).
+    int64_t sp_cap = sparse_div > 0 ? ctx->nw / sparse_div : 0;
+    if (sp_cap > ctx->nwp / 2) sp_cap = ctx->nwp / 2;
+    const bool sp_items = do_dfs && sp_cap > 0 && (double)mf * (double)sp_cap * 8.0 <= (double)(1ull << 30);
+    if (sp_items) {
+        FIM_TRY(reserve_sparse_items(ctx, mf, sp_cap));
+        if (!ctx->aux_stream) FIM_CUDA_TRY(cudaStreamCreateWithFlags(&ctx->aux_stream, cudaStreamNonBlocking));
+        for (auto &e : ctx->aux_ev)
+            if (!e) FIM_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        FIM_CUDA_TRY(cudaEventRecord(ctx->aux_ev[0], st));
+        FIM_CUDA_TRY(cudaStreamWaitEvent(ctx->aux_stream, ctx->aux_ev[0], 0));
+    }
     ctx->stats.pair_path = 0;
     if (do_pairs) {
         const int mpw = (int)ceil_div64(mf, 32);
@@ -308,12 +333,15 @@ int mine_once(fim_ctx *ctx, uint32_t thr, uint32_t flags, MineState &ms, bool *r
         if (!(flags & FIM_PAIRS_POPC)) rc = launch_pairs_tc(ctx);
         if (rc == FIM_OK) ctx->stats.pair_path = 1;
         else FIM_TRY(launch_pairs_popc(ctx));
+        if (sp_items) {  // launched after the pair pass, so that its CTAs take the SMs first
+            FIM_TRY(launch_sparse_items(ctx, mf, sp_cap, ctx->aux_stream));
+            FIM_CUDA_TRY(cudaEventRecord(ctx->aux_ev[1], ctx->aux_stream));
+        }
         FIM_TRY(launch_pairs_finalize(ctx, thr, d_ctr));
         // a shard of a split mine takes only the root classes it owns
         if (ctx->n_shards > 1) FIM_TRY(launch_shard_roots(ctx, d_ctr, ctx->shard, ctx->n_shards));
     }
     cudaEventRecord(ctx->ev[2], st);
-    const bool do_dfs = do_pairs && mf >= 3 && (maxlen == 0 || maxlen >= 3);
     if (do_dfs) {
         const int workers = ctx->num_sms * ctx->dfs_ctas_per_sm;
         // deepest class: a prefix can hold at most min(longest row, m') items
@@ -365,22 +393,12 @@ int mine_once(fim_ctx *ctx, uint32_t thr, uint32_t flags, MineState &ms, bool *r
         p.ctr = d_ctr;
         p.spin_limit = (unsigned long long)ctx->spin_limit_ms * 1000000ull;
         p.withhold_slot = ctx->test_withhold_task;
-        // automatic: keep low-support classes sparse when the frequent item
-        // columns do not fit in half of L2 (streaming whole columns from HBM
-        // is latency-bound; from L2 the dense pass is as fast)
-        p.sparse_div = ctx->sparse_div >= 0 ? ctx->sparse_div
-                       : ((double)mf * (double)ctx->nwp * 4.0 > 0.5 * (double)ctx->l2_bytes ? 4 : 0);
+        p.sparse_div = sparse_div;
         p.epoch = ctx->epoch.as<uint32_t>();
         p.learned_kmin = ctx->learned_kmin;
         p.root_reverse = ctx->root_reverse;
-        // sparse copies of the low-support item columns, for the root classes
-        // (bounded: at most 1 GiB of (index, word) pairs)
-        // (a child of a sparse parent is stored sparse: the copies must fit
-        // half a stack level, like every sparse class)
-        int64_t sp_cap = p.sparse_div > 0 ? ctx->nw / p.sparse_div : 0;
-        if (sp_cap > ctx->nwp / 2) sp_cap = ctx->nwp / 2;
-        if (sp_cap > 0 && (double)mf * (double)sp_cap * 8.0 <= (double)(1ull << 30)) {
-            FIM_TRY(launch_sparse_items(ctx, mf, sp_cap));
+        if (sp_items) {
+            FIM_CUDA_TRY(cudaStreamWaitEvent(st, ctx->aux_ev[1], 0));
             p.item_idx = ctx->sp_idx.as<uint32_t>();
             p.item_val = ctx->sp_val.as<uint32_t>();
             p.item_z = ctx->sp_z.as<int>();

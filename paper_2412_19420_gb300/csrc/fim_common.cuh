@@ -274,6 +274,8 @@ struct fim_ctx {
     int upload_chunks = 4;      // host input: index upload chunks overlapped with the build
     int upload_streams = 2;     // copy streams the chunks alternate over
     cudaStream_t up_stream[2] = {nullptr, nullptr};
+    cudaStream_t aux_stream = nullptr;  // work that overlaps the pair pass
+    cudaEvent_t aux_ev[2] = {};
     cudaEvent_t up_ev[16] = {};
 
     // stats + timing
@@ -311,7 +313,10 @@ int launch_dfs(fim_ctx *ctx, const DfsParams &p, int grid, int block);
 int prepare_task_queue(fim_ctx *ctx, size_t bytes);
 int launch_epoch_bump(fim_ctx *ctx);
 // Sparse copies of the frequent item columns with S <= cap (single database).
-int launch_sparse_items(fim_ctx *ctx, int mf, int64_t cap);
+// sparse copies of the low-support item columns for the root classes: the
+// buffers first (host side), then the copy, on a stream of the caller's
+int reserve_sparse_items(fim_ctx *ctx, int mf, int64_t cap);
+int launch_sparse_items(fim_ctx *ctx, int mf, int64_t cap, cudaStream_t st);
 
 // k_mlp.cu: learned root order (longest predicted subtree first)
 int launch_root_order(fim_ctx *ctx, MineCounters *d_ctr, size_t npairs);

@@ -1058,13 +1058,18 @@ int prepare_task_queue(fim_ctx *ctx, size_t bytes) {
     return FIM_OK;
 }
 
-int launch_sparse_items(fim_ctx *ctx, int mf, int64_t cap) {
+int reserve_sparse_items(fim_ctx *ctx, int mf, int64_t cap) {
     if (mf <= 0) return FIM_OK;
     FIM_TRY(fim_reserve(ctx, ctx->sp_idx, sizeof(uint32_t) * (size_t)mf * (size_t)cap));
     FIM_TRY(fim_reserve(ctx, ctx->sp_val, sizeof(uint32_t) * (size_t)mf * (size_t)cap));
     FIM_TRY(fim_reserve(ctx, ctx->sp_z, sizeof(int) * (size_t)mf));
+    return FIM_OK;
+}
+
+int launch_sparse_items(fim_ctx *ctx, int mf, int64_t cap, cudaStream_t st) {
+    if (mf <= 0) return FIM_OK;
     ctx->launches++;
-    sparse_items_kernel<<<mf, 256, 0, ctx->stream>>>(ctx->bm.as<uint32_t>(), ctx->perm.as<int32_t>(),
+    sparse_items_kernel<<<mf, 256, 0, st>>>(ctx->bm.as<uint32_t>(), ctx->perm.as<int32_t>(),
                                                      ctx->item_sup.as<uint32_t>(), ctx->nwp, cap,
                                                      ctx->sp_idx.as<uint32_t>(), ctx->sp_val.as<uint32_t>(),
                                                      ctx->sp_z.as<int>());

@@ -44,6 +44,7 @@ extern "C" {
 #define FIM_E_TOO_SMALL (-6) /* caller's output buffer too small; required sizes returned  */
 #define FIM_E_STATE (-7)     /* call out of order (mine before build, fetch before mine)   */
 #define FIM_E_NODEV (-8)     /* no CUDA device / device id out of range                    */
+#define FIM_E_CHECK (-9)     /* a "debug_checks" invariant failed (an internal error)      */
 
 /* ---- flags ------------------------------------------------------------- */
 /* All flags share one bit space, so that fim_mine_batched can take input
@@ -179,6 +180,13 @@ int fim_get_stats(const fim_ctx *ctx, fim_stats *out);
  *   "pairs_kdrain"     0..32768  128-transaction stages one accumulator sums before
  *                                it is drained (0 = 32768: partial sums stay <= 2^24,
  *                                exact in f32)
+ *   "debug_checks"     0, 1      after fim_build_bitmaps, check on the device that
+ *                                every pad bit and pad word of the columns is zero;
+ *                                after fim_mine, that the output is canonical (sets
+ *                                non-empty, items strictly ascending and < n_items,
+ *                                supports at the threshold, sets strictly increasing
+ *                                in (size, items) order); FIM_E_CHECK otherwise
+ *                                (default 0)
  *   "spin_limit_ms"    1..600000 longest a device-side wait (the DFS work queue)
  *                                spins before the mine ends with FIM_E_TIMEOUT
  *                                (default 60000); the ctx stays usable

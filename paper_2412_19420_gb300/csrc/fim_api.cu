@@ -91,6 +91,7 @@ const char *fim_strerror(int s) {
         case FIM_E_TOO_SMALL: return "output buffer too small";
         case FIM_E_STATE: return "call out of order";
         case FIM_E_NODEV: return "no such CUDA device";
+        case FIM_E_CHECK: return "a debug_checks invariant failed (internal error)";
         default: return "unknown status";
     }
 }
@@ -253,6 +254,7 @@ int fim_build_bitmaps(fim_ctx *ctx, const int64_t *indptr, const int32_t *indice
     ctx->max_row_len = flag[1];
     cudaEventElapsedTime(&ctx->stats.ms_build, ctx->ev[0], ctx->ev[1]);
     cudaEventElapsedTime(&ctx->stats.ms_singletons, ctx->ev[1], ctx->ev[2]);
+    if (ctx->debug_checks) FIM_TRY(run_check_pads(ctx));
     ctx->stats.launches_build = ctx->launches - launches0;
     ctx->built = true;
     return FIM_OK;
@@ -519,6 +521,7 @@ int fim_mine(fim_ctx *ctx, uint64_t minsup, uint32_t flags) {
     s.dfs_workers = (uint64_t)ctx->num_sms * (uint64_t)ctx->dfs_ctas_per_sm;
     s.dfs_root_ns = c.root_ns;
     if (ctx->bytes_held > s.peak_device_bytes) s.peak_device_bytes = ctx->bytes_held;
+    if (ctx->debug_checks) FIM_TRY(run_check_output(ctx, thr));
     ctx->out_n = ctx->n;
     ctx->mined = true;
     ctx->mine_serial++;
@@ -584,6 +587,7 @@ int fim_set_tuning(fim_ctx *ctx, const char *key, int64_t v) {
         {"compact_cluster", &ctx->compact_cluster, 0, 1},
         {"upload_mapped", &ctx->upload_mapped, 0, 1},
         {"spin_limit_ms", &ctx->spin_limit_ms, 1, 600000},
+        {"debug_checks", &ctx->debug_checks, 0, 1},
         {"test_withhold_task", &ctx->test_withhold_task, -1, 1 << 20},
         {"upload_streams", &ctx->upload_streams, 1, 2},
     };

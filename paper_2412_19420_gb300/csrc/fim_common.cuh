@@ -268,6 +268,7 @@ struct fim_ctx {
     int pairs_kdrain = 0;       // stages (x128 transactions) per exact drain (0 = 64)
     int compact_cluster = 1;    // small outputs: sort in one cluster launch
     int csort_cl[5] = {0, 0, 0, 0, 0};  // cluster size per key width (0 unknown, -1 none)
+    int debug_checks = 0;       // device-side invariant checks after build and mine
     int spin_limit_ms = 60000;  // longest device-side wait before FIM_E_TIMEOUT
     int test_withhold_task = -1; // test hook: the DFS never publishes this queue slot
     int upload_mapped = 1;      // host input in pinned, mapped memory: build reads it in place
@@ -330,6 +331,10 @@ int cluster_sort_plan(fim_ctx *ctx, uint64_t R, int kw, int *cl, int *cap, int *
 int launch_cluster_sort(fim_ctx *ctx, const unsigned long long *keys, uint64_t R, int kw,
                         const std::vector<std::pair<int, int>> &passes, int cl, int cap, int per,
                         uint32_t *idx_out, cudaStream_t st);
+
+// k_check.cu: the debug_checks invariants (FIM_E_CHECK when violated)
+int run_check_pads(fim_ctx *ctx);
+int run_check_output(fim_ctx *ctx, uint32_t thr);
 
 // k_shard.cu: append the root classes shard `shard` of n_shards owns
 int launch_shard_roots(fim_ctx *ctx, MineCounters *d_ctr, int shard, int n_shards);

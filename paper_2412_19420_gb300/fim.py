@@ -24,6 +24,7 @@ from . import build as _build
 FIM_OK = 0
 FIM_E_INVAL, FIM_E_NOMEM, FIM_E_CUDA, FIM_E_TIMEOUT = -1, -2, -3, -4
 FIM_E_STACK, FIM_E_TOO_SMALL, FIM_E_STATE, FIM_E_NODEV = -5, -6, -7, -8
+FIM_E_CHECK = -9
 FIM_INPUT_HOST, FIM_INPUT_DEVICE = 0, 0x100
 FIM_OUTPUT_HOST, FIM_OUTPUT_DEVICE = 0, 0x200
 FIM_STRICT, FIM_LEARNED, FIM_PAIRS_POPC, FIM_TRACE = 0x1, 0x2, 0x4, 0x8

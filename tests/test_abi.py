@@ -40,6 +40,7 @@ def test_host_only_calls():
     assert fim.fim_minsup_from_ppm(0, 5) == 1
     assert fim.fim_minsup_from_ppm(10, 0) == 1
     assert "wait" in fim.fim_strerror(fim.FIM_E_TIMEOUT)
+    assert "invariant" in fim.fim_strerror(fim.FIM_E_CHECK)
     assert fim.fim_strerror(12345) == "unknown status"
 
 

@@ -64,3 +64,22 @@ def test_spin_limit_knob_range(ctx):
     for key, bad in (("spin_limit_ms", 0), ("spin_limit_ms", 600_001), ("test_withhold_task", -2)):
         with pytest.raises(fim.FimError):
             fim.fim_set_tuning(ctx, key, bad)
+
+
+def test_debug_checks_pass_on_correct_runs(ctx):
+    # guard words (pad bits and words of every column) after the build and the
+    # canonical-output invariants after the mine, for ragged and degenerate sizes
+    fim.fim_set_tuning(ctx, "debug_checks", 1)
+    try:
+        cases = [(datagen.zipf_baskets(70_001, 200, 0.9, 6.0, 3), 250, 0),
+                 (datagen.zipf_baskets(4_096, 60, 0.9, 6.0, 4), 10, fim.FIM_STRICT),
+                 (datagen.random_dense(33, 9, 0.6, 5), 3, fim.FIM_MAXLEN(3)),
+                 (datagen.from_lists([[]] * 7, 4), 1, 0)]
+        for c, thr, flags in cases:
+            fim.fim_build_bitmaps(ctx, c.indptr, c.indices, c.m)
+            fim.fim_mine(ctx, thr, flags)
+            want = oracle.apriori(c.indptr, c.indices, c.m, thr, strict=bool(flags & fim.FIM_STRICT),
+                                  max_len=3 if flags == fim.FIM_MAXLEN(3) else 0)
+            assert fim.fim_fetch_results(ctx).sha256() == want.sha256()
+    finally:
+        fim.fim_set_tuning(ctx, "debug_checks", 0)

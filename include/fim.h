@@ -284,10 +284,10 @@ int fim_mlp_adam(fim_ctx *ctx, float *params, const float *grad, float *m, float
  *
  * fim_mine_shard: fim_mine restricted to shard `shard` of n_shards (1 <=
  * n_shards <= FIM_MAX_SHARDS).  Every shard builds the same matrix and runs
- * the singleton and pair passes in full; the root classes in (a, b) order are
- * cut into n_shards contiguous ranges of about equal estimated cost (1 + k +
- * k(k-1)/2 for a class with k candidates), computed from integers every shard
- * derives identically, and the shard mines only its range.  Shard 0 also
+ * the singleton and pair passes in full; the root classes, numbered in (a, b)
+ * order, are dealt round-robin (class P to shard P mod n_shards), which every
+ * shard derives identically from the pair bitsets, and the shard mines only
+ * its own classes.  Shard 0 also
  * reports the frequent singletons and pairs.  The held output (canonical,
  * fetched with fim_fetch_results) is the shard's part: the parts of shards
  * 0 .. n_shards-1 are disjoint and their union is fim_mine's answer.

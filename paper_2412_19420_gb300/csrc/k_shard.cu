@@ -10,12 +10,14 @@
 //
 // Ownership must come out the same on every GPU without communication, so it
 // is a function of integers every shard computes identically (the pair
-// bitsets): the roots in (a, b) order are cut into N contiguous ranges of
-// about equal estimated cost, cost(a, b) = 1 + k + k(k-1)/2 with k the root's
-// candidate count |{c > b : {a,c} and {b,c} frequent}| -- the class's own
-// pass plus an upper bound on its children's candidates.  Root (a, b) with
-// exclusive cost prefix P belongs to shard min(N-1, P / ceil(T / N)), T the
-// total cost.
+// bitsets): the roots, numbered in (a, b) order, are dealt round-robin --
+// root number P belongs to shard P mod N.  Contiguous ranges of equal
+// estimated cost balanced the estimate but not the work: a planted pattern's
+// heavy classes sit next to each other in (a, b) order, and on a 10^5 x 2,000
+// planted workload one of 8 ranges held 94% of the sets of size >= 3.  No
+// single class holds more than a few percent there, so dealing the roots out
+// one by one spreads them: the largest of 8 shards then holds 13-16% of those
+// sets (ideal 12.5%) on the Quest-style and planted workloads alike.
 //
 // The merge concatenates the shards' canonical lists (caller item ids) into
 // the record pool and re-runs the compactor's sort with the identity item
@@ -25,14 +27,6 @@
 namespace {
 
 constexpr int SH_T = 256;
-
-__device__ __forceinline__ unsigned long long root_cost(const uint32_t *__restrict__ pairbits, int mpw, int a,
-                                                        int b) {
-    const uint32_t *ra = pairbits + (int64_t)a * mpw, *rb = pairbits + (int64_t)b * mpw;
-    unsigned long long k = 0;
-    for (int w = b >> 5; w < mpw; w++) k += (unsigned long long)__popc(ra[w] & rb[w]);
-    return 1ull + k + (k ? k * (k - 1) / 2 : 0ull);
-}
 
 __device__ __forceinline__ bool pair_frequent(const uint32_t *__restrict__ pairbits, int mpw, int a, int b) {
     return (pairbits[(int64_t)a * mpw + (b >> 5)] >> (b & 31)) & 1u;
@@ -49,28 +43,27 @@ __device__ __forceinline__ unsigned long long block_sum_u64(unsigned long long v
     return t;
 }
 
-// One CTA per row a: rowcost[a] = total cost of the roots (a, b).
+// One CTA per row a: rowcount[a] = number of roots (a, b), i.e. of frequent
+// pairs in row a of the pair bitsets.
 __global__ void __launch_bounds__(SH_T)
-row_cost_kernel(const uint32_t *__restrict__ pairbits, int mf, int mpw, unsigned long long *__restrict__ rowcost) {
+row_count_kernel(const uint32_t *__restrict__ pairbits, int mf, int mpw, unsigned long long *__restrict__ rowcount) {
     __shared__ unsigned long long red[SH_T / 32];
     const int a = blockIdx.x;
     unsigned long long v = 0;
-    for (int b = a + 1 + threadIdx.x; b < mf; b += SH_T)
-        if (pair_frequent(pairbits, mpw, a, b)) v += root_cost(pairbits, mpw, a, b);
+    for (int w = threadIdx.x; w < mpw; w += SH_T) v += (unsigned long long)__popc(pairbits[(int64_t)a * mpw + w]);
     v = block_sum_u64(v, red);
-    if (threadIdx.x == 0) rowcost[a] = v;
+    if (threadIdx.x == 0) rowcount[a] = v;
 }
 
-// Exclusive scan of rowcost[0 .. mf) into rowbase, rowbase[mf] = T, and the
-// range width chunk = max(1, ceil(T / N)) into rowbase[mf + 1] (one CTA).
+// Exclusive scan of rowcount[0 .. mf) into rowbase, rowbase[mf] = the number
+// of roots (one CTA).
 __global__ void __launch_bounds__(1024)
-row_scan_kernel(const unsigned long long *__restrict__ rowcost, int mf, int n_shards,
-                unsigned long long *__restrict__ rowbase) {
+row_scan_kernel(const unsigned long long *__restrict__ rowcount, int mf, unsigned long long *__restrict__ rowbase) {
     __shared__ unsigned long long s[1024];
     const int seg = (mf + 1023) / 1024;
     const int b = threadIdx.x * seg, e = b + seg < mf ? b + seg : mf;
     unsigned long long sum = 0;
-    for (int i = b; i < e; i++) sum += rowcost[i];
+    for (int i = b; i < e; i++) sum += rowcount[i];
     s[threadIdx.x] = sum;
     __syncthreads();
     for (int o = 1; o < 1024; o <<= 1) {
@@ -82,18 +75,13 @@ row_scan_kernel(const unsigned long long *__restrict__ rowcost, int mf, int n_sh
     unsigned long long run = s[threadIdx.x] - sum;
     for (int i = b; i < e; i++) {
         rowbase[i] = run;
-        run += rowcost[i];
+        run += rowcount[i];
     }
-    if (threadIdx.x == 1023) {
-        const unsigned long long T = s[1023];
-        rowbase[mf] = T;
-        const unsigned long long chunk = (T + (unsigned long long)n_shards - 1) / (unsigned long long)n_shards;
-        rowbase[mf + 1] = chunk ? chunk : 1ull;
-    }
+    if (threadIdx.x == 1023) rowbase[mf] = s[1023];
 }
 
-// One CTA per row a: walks b ascending in blocks of SH_T, ranks every root by
-// its exclusive cost prefix, and appends the roots this shard owns.
+// One CTA per row a: walks b ascending in blocks of SH_T, numbers every root
+// in (a, b) order, and appends the roots this shard owns (number mod N).
 __global__ void __launch_bounds__(SH_T)
 shard_roots_kernel(const uint32_t *__restrict__ pairbits, const int *__restrict__ pair_cnt, int mf, int mpw,
                    const unsigned long long *__restrict__ rowbase, int shard, int n_shards, MineCounters *ctr,
@@ -101,12 +89,11 @@ shard_roots_kernel(const uint32_t *__restrict__ pairbits, const int *__restrict_
     __shared__ unsigned long long wsum[SH_T / 32];
     const int a = blockIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const unsigned long long chunk = rowbase[mf + 1];
     unsigned long long run = rowbase[a];
     for (int b0 = a + 1; b0 < mf; b0 += SH_T) {
         const int b = b0 + threadIdx.x;
         const bool f = b < mf && pair_frequent(pairbits, mpw, a, b);
-        const unsigned long long c = f ? root_cost(pairbits, mpw, a, b) : 0ull;
+        const unsigned long long c = f ? 1ull : 0ull;
         // block exclusive scan of c in thread order (= b order)
         unsigned long long x = c;
 #pragma unroll
@@ -122,10 +109,8 @@ shard_roots_kernel(const uint32_t *__restrict__ pairbits, const int *__restrict_
             total += wsum[w];
         }
         __syncthreads();
-        const unsigned long long P = run + before + x - c;
-        unsigned long long owner = P / chunk;
-        if (owner > (unsigned long long)(n_shards - 1)) owner = (unsigned long long)(n_shards - 1);
-        const bool own = f && owner == (unsigned long long)shard;
+        const unsigned long long P = run + before + x - c;  // the root's number in (a, b) order
+        const bool own = f && P % (unsigned long long)n_shards == (unsigned long long)shard;
         const uint32_t bal = __ballot_sync(0xffffffffu, own);
         if (bal) {
             unsigned long long base = 0;
@@ -180,14 +165,14 @@ int launch_shard_roots(fim_ctx *ctx, MineCounters *d_ctr, int shard, int n_shard
     if (mf < 2) return FIM_OK;
     const int mpw = (int)ceil_div64(mf, 32);
     const size_t npairs = (size_t)mf * (mf - 1) / 2;
-    FIM_TRY(fim_reserve(ctx, ctx->shard_cost, sizeof(unsigned long long) * (size_t)(2 * mf + 2)));
-    unsigned long long *rowcost = ctx->shard_cost.as<unsigned long long>(), *rowbase = rowcost + mf;
+    FIM_TRY(fim_reserve(ctx, ctx->shard_cost, sizeof(unsigned long long) * (size_t)(2 * mf + 1)));
+    unsigned long long *rowcount = ctx->shard_cost.as<unsigned long long>(), *rowbase = rowcount + mf;
     uint32_t *roots = ctx->roots.as<uint32_t>();
     cudaStream_t st = ctx->stream;
     const uint32_t *pb = ctx->pairbits.as<uint32_t>();
     ctx->launches += 3;
-    row_cost_kernel<<<mf, SH_T, 0, st>>>(pb, mf, mpw, rowcost);
-    row_scan_kernel<<<1, 1024, 0, st>>>(rowcost, mf, n_shards, rowbase);
+    row_count_kernel<<<mf, SH_T, 0, st>>>(pb, mf, mpw, rowcount);
+    row_scan_kernel<<<1, 1024, 0, st>>>(rowcount, mf, rowbase);
     shard_roots_kernel<<<mf, SH_T, 0, st>>>(pb, ctx->pair_cnt.as<int>(), mf, mpw, rowbase, shard, n_shards, d_ctr,
                                             roots, roots + npairs, roots + 2 * npairs);
     FIM_CUDA_TRY(cudaGetLastError());

@@ -53,8 +53,11 @@ def test_split_zipf_and_dense(ctx, n_shards):
 def test_split_planted_and_flags(ctx):
     c = datagen.planted(n=20_000, m=800, n_patterns=60, seed=4)
     parts = _check_split(ctx, c, 100, 4)
-    # the cost split spreads the classes of size >= 3 over several shards
-    assert sum(any(len(x) > 2 for x in p.as_dict()) for p in parts) >= 2
+    # dealing the root classes round-robin balances the work: no shard holds
+    # far more than a quarter of the sets of size >= 3 (contiguous ranges of
+    # equal estimated cost gave one shard 55% on this workload)
+    deep = [sum(len(x) > 2 for x in p.as_dict()) for p in parts]
+    assert max(deep) <= 0.35 * sum(deep), deep
     z = datagen.zipf_baskets(5000, 60, 0.8, 6.0, 3)
     _check_split(ctx, z, 10, 3, flags=fim.FIM_STRICT, strict=True)
     _check_split(ctx, z, 10, 3, flags=fim.FIM_MAXLEN(3), max_len=3)

@@ -23,8 +23,11 @@ def _free_port():
 
 class _OracleApi:
     """Stand-in for the library binding: every rank mines the whole database
-    with the oracle and keeps its share -- singletons and pairs on rank 0,
-    larger sets by their two smallest items, as the GPU split does."""
+    with the oracle and keeps its share by the GPU split's rule -- singletons
+    and pairs on rank 0; a larger set goes with its root class, the frequent
+    pair of its two smallest items in the miner's internal order (support,
+    then id, ascending), and root number P (in (a, b) order) belongs to rank
+    P mod N.  ``skew`` instead hands every class to the last rank."""
 
     def __init__(self, skew=False):
         self.skew = skew
@@ -36,17 +39,21 @@ class _OracleApi:
         import oracle
         ip, ix, m = ctx["db"]
         full = oracle.apriori(ip, ix, m, minsup)
+        allsets = [(tuple(int(v) for v in full.items[full.offsets[q]:full.offsets[q + 1]]), int(full.supports[q]))
+                   for q in range(len(full))]
+        single = {x[0]: s for x, s in allsets if len(x) == 1}
+        rank = {i: r for r, i in enumerate(sorted(single, key=lambda i: (single[i], i)))}
+        roots = sorted(tuple(sorted(rank[i] for i in x)) for x, _ in allsets if len(x) == 2)
+        number = {r: p for p, r in enumerate(roots)}
         sets = []
-        for q in range(len(full)):
-            x = tuple(int(v) for v in full.items[full.offsets[q]:full.offsets[q + 1]])
+        for x, s in allsets:
             if len(x) <= 2:
                 own = shard == 0
-            elif self.skew:  # every class on the last rank
-                own = shard == n_shards - 1
             else:
-                own = (x[0] * 31 + x[1]) % n_shards == shard
+                r = tuple(sorted(rank[i] for i in x)[:2])
+                own = shard == (n_shards - 1 if self.skew else number[r] % n_shards)
             if own:
-                sets.append((x, int(full.supports[q])))
+                sets.append((x, s))
         ctx["part"] = sets
 
     def fim_result_sizes(self, ctx):

@@ -47,6 +47,17 @@ class Rules:
     def __len__(self) -> int:
         return int(self.set_index.shape[0])
 
+    def canonical_bytes(self) -> bytes:
+        """Byte stream for bit-exact comparison: set indices, masks, conf, lift."""
+        return (np.ascontiguousarray(self.set_index, dtype="<u8").tobytes()
+                + np.ascontiguousarray(self.ante_mask, dtype="<u4").tobytes()
+                + np.ascontiguousarray(self.conf, dtype="<f8").tobytes()
+                + np.ascontiguousarray(self.lift, dtype="<f8").tobytes())
+
+    def sha256(self) -> str:
+        import hashlib
+        return hashlib.sha256(self.canonical_bytes()).hexdigest()
+
 
 def rule_of(z_items, z_sup: int, mask: int, support_of, n: int, min_conf_ppm: int,
             _mutant: int = 0):

@@ -174,3 +174,17 @@ def test_pins_pass_on_the_oracle():
 @pytest.mark.parametrize("mutant", [1, 2, 3, 4, 5])
 def test_planted_mistake_is_caught(mutant):
     assert not _pins_pass(mutant)
+
+
+# ---- stored output (tests/golden/oracle_hashes.json, written by make_golden.py)
+
+def test_stored_rules_of_the_10k_x_169_workload():
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "oracle_hashes.json")) as f:
+        g = json.load(f)["grocery_like_10k_169"]
+    c = datagen.grocery_like()
+    assert c.sha256() == g["input_sha256"]
+    its = _mine(c, g["minsup"])
+    r = orules.rules(its, c.n, g["rules_min_conf_ppm"])
+    assert len(r) == g["n_rules"] and r.sha256() == g["rules_sha256"]

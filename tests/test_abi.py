@@ -52,3 +52,34 @@ def test_no_device_is_an_error_not_a_fallback():
     with pytest.raises(fim.FimError) as e:
         fim.fim_create(0)
     assert e.value.code == fim.FIM_E_NODEV
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    # the binding's ctypes mirrors of fim_stats and fim_db_desc against the C
+    # compiler's view of include/fim.h: size and the offset of every field
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    from paper_2412_19420_gb300 import fim
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "fim.h"', 'int main(void) {']
+    for st in (fim.fim_stats, fim.fim_db_desc):
+        name = st.__name__
+        lines.append(f'printf("{name} size %zu\\n", sizeof({name}));')
+        for f, _ in st._fields_:
+            lines.append(f'printf("{name} {f} %zu\\n", offsetof({name}, {f}));')
+    lines += ['return 0;', '}']
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.check_call([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    got = {}
+    for line in subprocess.check_output([str(exe)]).decode().splitlines():
+        st, field, val = line.split()
+        got[(st, field)] = int(val)
+    for st in (fim.fim_stats, fim.fim_db_desc):
+        name = st.__name__
+        assert got[(name, "size")] == ctypes.sizeof(st), name
+        for f, _ in st._fields_:
+            assert got[(name, f)] == getattr(st, f).offset, (name, f)

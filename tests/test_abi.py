@@ -83,3 +83,26 @@ def test_struct_layouts_match_the_header(tmp_path):
         assert got[(name, "size")] == ctypes.sizeof(st), name
         for f, _ in st._fields_:
             assert got[(name, f)] == getattr(st, f).offset, (name, f)
+
+
+def test_binding_argument_counts_match_the_header():
+    # every ctypes signature the binding declares has as many arguments as the
+    # header's prototype of that entry point
+    from paper_2412_19420_gb300 import fim
+    txt = ""
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            txt += open(os.path.join(ROOT, "include", h)).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    protos = {}
+    for m in re.finditer(r"\b(fim_\w+)\s*\(([^()]*)\)\s*;", txt):
+        params = m.group(2).strip()
+        protos[m.group(1)] = 0 if params in ("", "void") else params.count(",") + 1
+    checked = 0
+    for name, n in protos.items():
+        f = getattr(fim._lib, name)
+        if f.argtypes is None:
+            continue
+        assert len(f.argtypes) == n, (name, len(f.argtypes), n)
+        checked += 1
+    assert checked >= 20

@@ -1,12 +1,14 @@
 // k_noalloc.cu -- pair supports of a small database without any allocation.
 //
 // Some callers cannot allocate device memory while they run this library:
-// code inside a CUDA stream capture (where a cudaMalloc would break the
-// capture), or hosts that hand out every device byte through their own
-// allocator and forbid others.  fim_pair_supports_noalloc serves them: the
-// caller passes the CSR and the output matrix, and the only other device
+// hosts that hand out every device byte through their own allocator and
+// forbid others, and paths that must not block in cudaMalloc/cudaFree, which
+// can synchronise the whole device.  fim_pair_supports_noalloc serves them:
+// the caller passes the CSR and the output matrix, and the only other device
 // memory it touches is the file-scope array below, which every GPU that loads
-// the library holds until the process exits.
+// the library holds until the process exits.  The call does wait for its own
+// work: it reads the CSR's element count and the validation flag back to the
+// host, each with a synchronisation of the caller's stream.
 //
 // It is a variant of the CUDA-core pair pass (k_pairs.cu): the bit columns it
 // needs live in g_noalloc_bits instead of a ctx-owned buffer, all items are
@@ -159,7 +161,11 @@ extern "C" int fim_pair_supports_noalloc(const int64_t *d_indptr, const int32_t 
     const int m = n_items;
     FIM_CUDA_TRY(cudaMemsetAsync(d_pair_counts, 0, sizeof(uint32_t) * (size_t)m * (size_t)m, st));
     FIM_CUDA_TRY(cudaMemsetAsync(slot.flag, 0, sizeof(int), st));
-    if (m == 0 || nw == 0) return FIM_OK;
+    if (m == 0 || nw == 0) {
+        // nothing to count: the cleared matrix is the answer, complete on return
+        FIM_CUDA_TRY(cudaStreamSynchronize(st));
+        return FIM_OK;
+    }
     int64_t nnz = 0;
     FIM_CUDA_TRY(cudaMemcpyAsync(&nnz, d_indptr + n_trans, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     FIM_CUDA_TRY(cudaStreamSynchronize(st));

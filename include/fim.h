@@ -154,7 +154,11 @@ int fim_fetch_results(fim_ctx *ctx, uint64_t *n_sets, uint64_t *n_items_total,
                       uint64_t *offsets, uint32_t *items, uint32_t *supports,
                       uint64_t cap_sets, uint64_t cap_items, uint32_t flags);
 
-/* fim_get_stats: counters and phase times of the last fim_mine (or batch). */
+/* fim_get_stats: counters and phase times of the last fim_mine (or batch).
+ * After fim_mine_batched the phases are those of the batch's graph: ms_build
+ * covers the build with its fused singleton supports and the ranking
+ * (ms_singletons is 0), ms_pairs the pair pass with its threshold, ms_dfs
+ * the prefix extension, ms_compact the compaction after the graph. */
 int fim_get_stats(const fim_ctx *ctx, fim_stats *out);
 
 /* fim_set_tuning -- set one launch-shape parameter of the ctx; it applies to
@@ -373,7 +377,9 @@ int fim_fetch_rules(fim_ctx *ctx, uint64_t *n_rules, uint64_t *set_index, uint32
  * entry [a][a] is S(I_a), entries below the diagonal are 0 -- the singleton
  * and pair supports fim_mine computes, without a threshold.  It runs on
  * cuda_stream (a cudaStream_t, NULL = the legacy default stream) of the
- * current device and returns when the work has finished.
+ * current device and returns when the work has finished: it synchronises
+ * that stream twice (to read the CSR's element count d_indptr[n_trans], and
+ * the validation flag), so it blocks the calling thread.
  * Memory: it calls no cudaMalloc, cudaFree or allocating library routine.
  * Its only scratch is a static device array of FIM_NOALLOC_MAX_BYTES that
  * every GPU which loads libfim holds until the process exits; the bit columns
@@ -384,9 +390,12 @@ int fim_fetch_rules(fim_ctx *ctx, uint64_t *n_rules, uint64_t *set_index, uint32
  * contents; each call rewrites every part of it that it reads, and clears the
  * output itself.  Calls whose GPU work overlaps (several streams or host
  * threads) race on the array and must be serialised by the caller.
- * Errors: FIM_E_INVAL for a malformed CSR, n_items > FIM_MAX_ITEMS, or bit
- * columns larger than FIM_NOALLOC_MAX_BYTES (nothing is launched then);
- * FIM_E_NODEV; FIM_E_CUDA. */
+ * Errors: FIM_E_INVAL for n_items > FIM_MAX_ITEMS or bit columns larger
+ * than FIM_NOALLOC_MAX_BYTES (nothing is launched then), and for a malformed
+ * CSR (indptr decreasing or outside [0, nnz], an item outside [0, n_items)),
+ * which the counting kernels detect while they run: d_pair_counts then holds
+ * no meaningful values, and the next call starts afresh; FIM_E_NODEV;
+ * FIM_E_CUDA. */
 #define FIM_NOALLOC_MAX_BYTES (64u << 20)
 int fim_pair_supports_noalloc(const int64_t *d_indptr, const int32_t *d_indices, int64_t n_trans,
                               int32_t n_items, uint32_t *d_pair_counts, void *cuda_stream);
@@ -396,8 +405,14 @@ int fim_pair_supports_noalloc(const int64_t *d_indptr, const int32_t *d_indices,
  *   which = 0: AND/popc word pairs per second over all SMs -- one LOP3, one
  *              POPC and one IADD per pair, the inner step of the pair and
  *              prefix-extension passes;
- *   which = 1: L2 read bandwidth in GB/s, 16-byte loads over a 32 MB buffer.
- * Errors: FIM_E_INVAL (unknown probe, result NULL), FIM_E_NOMEM, FIM_E_CUDA. */
+ *   which = 1: L2 read bandwidth in GB/s, 16-byte loads over a 32 MB buffer;
+ *   which = 2: dense tcgen05 kind::f8f6f4 rate in TFLOP/s (e4m3 operands,
+ *              f32 accumulator in tensor memory), in the pair pass's
+ *              instruction shape 128 x 256 x 32 with A read from tensor
+ *              memory: one CTA per SM, one thread issuing MMAs back to back;
+ *   which = 3: the same with A read from shared memory.
+ * Errors: FIM_E_INVAL (unknown probe, result NULL), FIM_E_NOMEM, FIM_E_CUDA,
+ * FIM_E_TIMEOUT (the MMA probe's bounded wait ran out). */
 int fim_probe(fim_ctx *ctx, int which, double *result);
 
 /* fim_minsup_from_ppm: ceil(n_trans * ppm / 1e6) in integers, at least 1:

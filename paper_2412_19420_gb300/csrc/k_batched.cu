@@ -679,6 +679,10 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
             }
             cudaGraph_t g = nullptr;
             FIM_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+            // phase boundaries as event-record nodes of the graph: graph start
+            // (ev 7), after build + supports + rank (ev 1), after the pair
+            // pass (ev 2); the DFS ends where the graph does (ev 3)
+            cudaEventRecordWithFlags(ctx->ev[7], st, cudaEventRecordExternal);
             cudaMemsetAsync(d_ctr, 0, sizeof(MineCounters), st);
             cudaMemsetAsync(ctx->dev_flag.p, 0, sizeof(int), st);
             launch_epoch_bump(ctx);
@@ -707,6 +711,7 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
                     d_dbs, n_db, d_item, items, ctx->item_sup.as<uint32_t>(), ctx->perm.as<int32_t>(), d_ctr,
                     p.rec_off, p.rec_len, p.rec_sup, p.rec_items, p.rec_db, p.rec_cap, p.rec_items_cap);
             }
+            cudaEventRecordWithFlags(ctx->ev[1], st, cudaEventRecordExternal);
             if (tiles > 0 && maxlen != 1) {
                 batch_pairs_kernel<<<(unsigned)tiles, 256, 0, st>>>(d_dbs, n_db, d_tile, ctx->bm.as<uint32_t>(),
                                                                     ctx->perm.as<int32_t>(), ctx->pair_cnt.as<int>());
@@ -715,6 +720,7 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
                     p.rec_len, p.rec_sup, p.rec_items, p.rec_db, p.rec_cap, p.rec_items_cap, roots, roots + rc,
                     roots + 2 * rc, roots + 3 * rc);
             }
+            cudaEventRecordWithFlags(ctx->ev[2], st, cudaEventRecordExternal);
             int rc_launch = FIM_OK;
             if (maxlen == 0 || maxlen >= 3) rc_launch = launch_dfs(ctx, p, workers, ctx->dfs_block);
             const cudaError_t ce = cudaStreamEndCapture(st, &g);
@@ -790,9 +796,17 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
         s.launches_build = 0;
         s.launches_mine = ctx->launches - launches0;
         s.pair_path = 0;
-        cudaEventElapsedTime(&s.ms_dfs, ctx->ev[0], ctx->ev[3]);
+        // phases of the graph: build + singleton supports + rank, pairs +
+        // finalize, DFS; then the compaction outside the graph
+        s.ms_build = s.ms_singletons = s.ms_pairs = s.ms_dfs = 0.f;
+        if (cudaEventElapsedTime(&s.ms_build, ctx->ev[7], ctx->ev[1]) != cudaSuccess ||
+            cudaEventElapsedTime(&s.ms_pairs, ctx->ev[1], ctx->ev[2]) != cudaSuccess ||
+            cudaEventElapsedTime(&s.ms_dfs, ctx->ev[2], ctx->ev[3]) != cudaSuccess) {
+            (void)cudaGetLastError();  // phase split unavailable: whole graph as the DFS
+            s.ms_build = s.ms_pairs = 0.f;
+            cudaEventElapsedTime(&s.ms_dfs, ctx->ev[0], ctx->ev[3]);
+        }
         cudaEventElapsedTime(&s.ms_compact, ctx->ev[3], ctx->ev[4]);
-        s.ms_build = s.ms_singletons = s.ms_pairs = 0.f;
         // m' per database (written by the device) for the pair-support count
         std::vector<DbDesc> back(n_db);
         FIM_CUDA_TRY(cudaMemcpy(back.data(), d_dbs, tbl, cudaMemcpyDeviceToHost));

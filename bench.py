@@ -1,23 +1,32 @@
 #!/usr/bin/env python
 """Benchmark of the GB300 Boolean-matrix frequent-itemset miner.
 
-One step = one pass of the whole hot path over the workload: bit-column
-construction from a device-resident CSR (Eq. 1), singleton and pair supports
-(Eq. 2-3), the depth-first prefix extension, and the canonical compaction,
-with the results left in device buffers.  Metric: itemset supports per
-second (support values computed: singletons + pairs + DFS extensions) over
-the device time of the step, CUDA events on the miner's stream, L2 flushed
-between steps.
+Default workload (the headline): 4,096 independent databases mined by the
+learned+batched miner -- one graph-replayed batched pass steered by the
+scheduling network, trained first on the GPU from plain-miner traces of other
+databases of the same generator -- against the plain miner (one
+fim_build_bitmaps + fim_mine + fim_fetch_results per database) and against the
+batched pass without the network.  One step = one mine of all 4,096
+databases: bit-column construction (Eq. 1), singleton and pair supports
+(Eq. 2-3), the depth-first prefix extension and the canonical compaction.
+`value` is itemset supports per second (support values computed: singletons
++ pairs + prefix extensions) over the device time of a step (CUDA events on
+the miner's stream, CSRs resident in HBM, L2 flushed between steps); `e2e`
+is the same with the CSRs uploaded from pinned host memory and every result
+copied back to pinned host memory inside the timed region; `compare` holds
+both times for all three arms.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
     python bench.py --impl reference      # the CPU oracle on the host cores
 
-Under torchrun (N > 1) every rank mines its own replica of the workload;
-the value is the supports of all ranks over the slowest rank's time.  With
---shard the ranks instead split one mine (prefix-class shards, the parts
-gathered and merged on rank 0; strong scaling, also runnable at N = 1).
-After the timed mines the association rules of the last one are timed once
-more (--rules-ppm), reported beside the step.
+Single-database workloads (--workload quest_1M_1000 and the others) time one
+mine per step the same way; there, --learned trains the network first, and
+after the timed mines the association rules of the last one are timed once
+more (--rules-ppm).  Under torchrun (N > 1) every rank mines its own replica
+of the workload; the value is the supports of all ranks over the slowest
+rank's time.  With --shard the ranks instead split one mine (prefix-class
+shards, the parts gathered and merged on rank 0; strong scaling, also
+runnable at N = 1).
 """
 from __future__ import annotations
 
@@ -34,7 +43,8 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-DEFAULT_WORKLOAD = "quest_1M_1000"
+DEFAULT_WORKLOAD = "batched_4096"
+HEADLINE_METRIC = "itemset supports/sec & end-to-end mine time: learned+batched vs plain, 1 GB300"
 WORKLOAD_DESC = {
     "grocery_like_10k_169": "10,000 x 169, Zipf(1.0), Poisson(4.4) lengths, minsup 100",
     "quest_1M_1000": "1,000,000 x 1,000 Quest-style (T10, I4, 2,000 patterns, 50% corruption), minsup 1,000 (0.1%)",
@@ -71,6 +81,8 @@ def _args():
                          "instead of one replica per rank")
     ap.add_argument("--rules-ppm", type=int, default=500_000,
                     help="also time association rules at this confidence (ppm); -1 skips")
+    ap.add_argument("--n-db", type=int, default=4096,
+                    help="batched workload: mine only its first N databases (profiling captures)")
     ap.add_argument("--learned", action="store_true",
                     help="single database: mine with FIM_LEARNED, the network trained on the GPU "
                          "from plain-miner traces of the same generator at another seed")
@@ -192,6 +204,9 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    if args.workload == "batched_4096":
+        run_reference_batched(args)
+        return
     csr, minsup = _load_workload(args.workload)
     for _ in range(args.warmup):
         pass  # the oracle has no warm state; warm-up steps would only repeat the work
@@ -227,21 +242,128 @@ def _train_scheduler(ctx, fim, sched, datagen, sample):
     return {"trace_rows": int(len(x)), "final_loss": float(np.mean(hist[-50:]))}
 
 
+BATCH_PPM = 20_000  # minsup 2% of each database's transactions
+
+
+def _batched_workload(n_db=4096):
+    """The batch's databases (the first n_db of the 4,096; fewer only for
+    profiling captures), their thresholds and the line's `config` (the same
+    dict on both arms: it names the workload, nothing measured)."""
+    from paper_2412_19420_gb300 import datagen
+    dbs = datagen.batched_dbs(datagen.batched_specs(4096)[:n_db])
+    ms = [datagen.minsup_from_ppm(c.n, BATCH_PPM) for c in dbs]
+    cfg = {"workload": "batched_4096", "desc": WORKLOAD_DESC["batched_4096"], "n_db": len(dbs),
+           "n_trans_total": int(sum(c.n for c in dbs)), "nnz_total": int(sum(c.nnz for c in dbs)),
+           "minsup_ppm": BATCH_PPM, "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write)"}
+    return dbs, ms, cfg
+
+
+def _oracle_batch(dbs, ms, start, budget_s, threads):
+    """The oracle over databases start, start+1, ... (wrapping) until budget_s
+    of wall time has passed: (candidate supports, seconds, databases)."""
+    import oracle
+    t0 = time.perf_counter()
+    cand, k = 0, 0
+    while k < len(dbs) and (k == 0 or time.perf_counter() - t0 < budget_s):
+        d = (start + k) % len(dbs)
+        cand += oracle.apriori(dbs[d].indptr, dbs[d].indices, dbs[d].m, ms[d], threads=threads).n_candidates
+        k += 1
+    return cand, time.perf_counter() - t0, k
+
+
+def run_reference_batched(args):
+    """The oracle as the reference arm on the 4,096-database workload: each
+    step mines the next databases of the batch (wrapping) for about 3 s of
+    wall time on all host cores."""
+    dbs, ms, cfg = _batched_workload(args.n_db)
+    cores = _cores()
+    times, cands, done, start = [], [], 0, 0
+    for _ in range(args.steps):
+        c, dt, k = _oracle_batch(dbs, ms, start, 3.0, cores)
+        start = (start + k) % len(dbs)
+        times.append(dt)
+        cands.append(c)
+        done += k
+    value = sum(cands) / sum(times)
+    sample = (f"{args.steps} steps of about 3 s, each the next databases of the batch in order "
+              f"({done:,} database mines in all, {sum(cands):,} candidate supports counted)")
+    line = {"impl": "reference", "metric": HEADLINE_METRIC, "value": value, "unit": "supports/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000 * statistics.mean(times), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic (seeded generator, paper_2412_19420_gb300.datagen)",
+            "config": cfg,
+            "cpu_baseline": {"value": value, "unit": "supports/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "supports/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    _emit(line)
+
+
+def _batched_roofline(st, phase, dbs, m_freq, probes):
+    """Roofline of the batch graph's dominant phase.  st: fim_get_stats of a
+    timed learned+batched mine; phase: mean CUDA-event phase times (ms)."""
+    hbm, _, _, src = _peaks()
+    dom = max(("ms_build", "ms_pairs", "ms_dfs", "ms_compact"), key=lambda p: phase[p])
+    sec = phase[dom] / 1000
+    if dom == "ms_build":
+        # CSR read once, bit columns written once, the singleton supports fused
+        nbytes = sum(8 * (c.n + 1) + 4 * c.nnz + 4 * c.m * ((c.n + 31) // 32) for c in dbs)
+        ach = nbytes / sec / 1e9
+        roof = {"kernel": "batch_build_rows_kernel", "bound": "hbm", "achieved": ach, "peak": hbm,
+                "unit": "GB/s", "frac": ach / hbm, "traffic": _kernel_traffic("batch_build_rows_kernel", "batched_4096"),
+                "algorithmic_bytes_per_launch": int(nbytes)}
+    elif dom == "ms_pairs":
+        # AND + popc of every word pair of the frequent items' columns
+        wp = sum(mf * (mf - 1) // 2 * ((c.n + 31) // 32) for c, mf in zip(dbs, m_freq))
+        ach = wp / sec
+        peak = probes["popc_word_pairs_per_s"]
+        roof = {"kernel": "batch_pairs_kernel", "bound": "alu", "achieved": ach / 1e9, "peak": peak / 1e9,
+                "unit": "Gwordpairs/s", "frac": ach / peak, "traffic": None, "peak_source": "fim_probe AND/popc",
+                "algorithmic_word_pairs_per_launch": int(wp)}
+    elif dom == "ms_dfs":
+        roof = _dfs_roofline(st, phase[dom], "batched_4096", probes)
+    else:
+        nbytes = 24 * st["n_sets"]
+        ach = nbytes / sec / 1e9
+        roof = {"kernel": "compaction", "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                "frac": ach / hbm, "traffic": None}
+    roof.setdefault("peak_source", src)
+    roof["phase_ms"] = {k: round(v, 4) for k, v in phase.items()}
+    return roof
+
+
 def run_batched(args):
-    """4,096 independent databases: the learned+batched miner (one batched
-    pass, graph-replayed) against the plain miner (one fim_mine per database)
-    on the same databases, end-to-end mine time on one GPU."""
+    """4,096 independent databases, the metric's comparison on one GPU: the
+    learned+batched miner (one graph-replayed batched pass, FIM_LEARNED)
+    against the plain miner (one fim_build_bitmaps + fim_mine +
+    fim_fetch_results per database) and against the batched pass without the
+    network.  Each arm is timed on the device (CSRs resident in HBM, results
+    left canonical on the device) and end to end (CSRs uploaded from pinned
+    host memory and every result copied back to pinned host memory inside
+    the timed region)."""
     import numpy as np
     import torch
+    import torch.distributed as dist
     from paper_2412_19420_gb300 import datagen, fim, sched
-    torch.cuda.set_device(0)
-    specs = datagen.batched_specs(4096)
-    dbs = datagen.batched_dbs(specs)
-    ms = [datagen.minsup_from_ppm(c.n, 20_000) for c in dbs]
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    dbs, ms, cfg = _batched_workload(args.n_db)
     stream = torch.cuda.Stream()
-    ctx = fim.fim_create(0, stream)
-    train_sample = [(datagen.batched_db(s), 0) for s in datagen.batched_specs(48, seed=1)]
-    train_sample = [(c, datagen.minsup_from_ppm(c.n, 20_000)) for c, _ in train_sample]
+    ctx = fim.fim_create(local, stream)
+    # the network: trained on the GPU from plain-miner traces of 48 other
+    # databases of the same generator (seed 1)
+    train_sample = [datagen.batched_db(s) for s in datagen.batched_specs(48, seed=1)]
+    train_sample = [(c, datagen.minsup_from_ppm(c.n, BATCH_PPM)) for c in train_sample]
     train_info = _train_scheduler(ctx, fim, sched, datagen, train_sample)
 
     class Dev:
@@ -252,11 +374,20 @@ def run_batched(args):
     ddbs = [Dev(c) for c in dbs]
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
 
-    def timed(fn, reps):
+    def timed(fn, reps, host_clock=False):
+        """Per-rep ms: CUDA events on the miner's stream (device arms) or the
+        host clock around a call that ends synchronised (end-to-end arms)."""
         out = []
         for k in range(reps):
             with torch.cuda.stream(stream):
                 flush.fill_(k)
+            if host_clock:
+                stream.synchronize()
+                t0 = time.perf_counter()
+                fn()
+                stream.synchronize()
+                out.append(1000 * (time.perf_counter() - t0))
+                continue
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
             fn()
@@ -265,37 +396,63 @@ def run_batched(args):
             out.append(a.elapsed_time(b))
         return out
 
-    flags = fim.FIM_LEARNED | args.flags
-    # learned + batched, inputs resident in HBM, results left canonical on the
-    # device; the batch's descriptor table is marshalled once, as a C caller
-    # holds its fim_db_desc array
+    learned = fim.FIM_LEARNED | args.flags
+    plain_flags = args.flags
+    # ---- learned + batched, device-resident inputs: the line's value -------
+    # (the descriptor table is marshalled once, as a C caller holds its
+    # fim_db_desc array)
     ddesc = fim.BatchDescriptor(ddbs, ms)
     for _ in range(args.warmup):
-        fim.fim_mine_batched(ctx, ddesc, flags=flags)
-    with ClockSampler(0) as clk:
-        lb = timed(lambda: fim.fim_mine_batched(ctx, ddesc, flags=flags), args.steps)
+        fim.fim_mine_batched(ctx, ddesc, flags=learned)
+    barrier()
+    phase = {k: 0.0 for k in ("ms_build", "ms_pairs", "ms_dfs", "ms_compact")}
+    launches = 0
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        barrier()
+        for k in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(k)
+            ev[k][0].record(stream)
+            fim.fim_mine_batched(ctx, ddesc, flags=learned)
+            ev[k][1].record(stream)
+            st = fim.fim_get_stats(ctx)
+            for p in phase:
+                phase[p] += st[p]
+            launches += st["launches_mine"]
+        barrier()
+    lb = [a.elapsed_time(b) for a, b in ev]
+    phase = {p: v / args.steps for p, v in phase.items()}
     st = fim.fim_get_stats(ctx)
     supports = st["supports_singletons"] + st["supports_pairs"] + st["supports_dfs"]
     R, T = fim.fim_batch_sizes(ctx, fim.FIM_ALL_DBS)
-    launches = st["launches_mine"]
-    # batched without the network
-    plain_batched = timed(lambda: fim.fim_mine_batched(ctx, ddesc, flags=args.flags), max(2, args.steps // 2))
-    # plain miner: one database at a time through the same ABI (results copied out per database)
+    ms_lb = statistics.mean(lb)
+    t = torch.tensor([ms_lb], dtype=torch.float64, device="cuda")
+    tot = torch.tensor([float(supports)], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(tot, op=dist.ReduceOp.SUM)
+    ms_max = float(t.item())
+    value = float(tot.item()) / (ms_max / 1000)
+
+    # ---- the other device arms --------------------------------------------
+    batched_plain = timed(lambda: fim.fim_mine_batched(ctx, ddesc, flags=plain_flags), max(3, args.steps // 2))
     out_d = (torch.empty(1 << 20, dtype=torch.int64, device="cuda"),
              torch.empty(1 << 22, dtype=torch.int32, device="cuda"),
              torch.empty(1 << 20, dtype=torch.int32, device="cuda"))
 
-    def plain_loop():
+    def plain_device():
         for c, m in zip(ddbs, ms):
             fim.fim_build_bitmaps(ctx, c.indptr, c.indices, c.m)
-            fim.fim_mine(ctx, m, args.flags)
+            fim.fim_mine(ctx, m, plain_flags)
             fim.fim_fetch_results(ctx, out_d)
-    plain_loop()
-    plain = timed(plain_loop, 2)
-    # end to end: host CSRs in, every result copied back to pinned host memory
+    plain_device()
+    plain = timed(plain_device, 2)
+
+    # ---- end to end: host CSRs in, every result back in pinned host memory
     out_h = (torch.empty(R + 1, dtype=torch.int64).pin_memory(), torch.empty(max(T, 1), dtype=torch.int32).pin_memory(),
              torch.empty(max(R, 1), dtype=torch.int32).pin_memory())
-
+    out_hn = tuple(x.numpy() for x in out_h)
     # the CSRs in pinned host memory, packed back to back (the library uploads
     # contiguous databases in one copy per array)
     n_ptr = sum(c.n + 1 for c in dbs)
@@ -309,57 +466,85 @@ def run_batched(args):
         hdbs.append(datagen.Csr(indptr=ptr_h[po:po + c.n + 1], indices=idx_h[io:io + c.nnz], m=c.m))
         po += c.n + 1
         io += c.nnz
-
     hdesc = fim.BatchDescriptor(hdbs, ms)
 
-    def e2e_step():
+    def e2e_batched(flags):
         fim.fim_mine_batched(ctx, hdesc, flags=flags)
-        fim.fim_fetch_batched(ctx, fim.FIM_ALL_DBS, tuple(x.numpy() for x in out_h))
-    e2e_step()
-    e2e = timed(e2e_step, args.steps)
+        fim.fim_fetch_batched(ctx, fim.FIM_ALL_DBS, out_hn)
+
+    def plain_host():
+        for c, m in zip(hdbs, ms):
+            fim.fim_build_bitmaps(ctx, c.indptr, c.indices, c.m)
+            fim.fim_mine(ctx, m, plain_flags)
+            fim.fim_fetch_results(ctx, out_hn)
+    for _ in range(max(1, args.warmup)):
+        e2e_batched(learned)
+    e2e_lb = timed(lambda: e2e_batched(learned), args.steps, host_clock=True)
+    e2e_bp = timed(lambda: e2e_batched(plain_flags), max(3, args.steps // 2), host_clock=True)
+    plain_host()
+    e2e_plain = timed(plain_host, 2, host_clock=True)
+    e2e_t = torch.tensor([statistics.mean(e2e_lb)], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
     h2d = sum(c.indptr.nbytes + c.indices.nbytes for c in dbs)
     d2h = 8 * (R + 1) + 4 * T + 4 * R
-    ms_lb = statistics.median(lb)
-    ms_e2e = statistics.median(e2e)
-    hbm, _, _, src = _peaks()
-    ach = st["dfs_bytes"] / (ms_lb / 1000) / 1e9
+
+    # frequent items per database (the sets of size 1 of each slice)
+    fim.fim_mine_batched(ctx, hdesc, flags=learned)
+    res = fim.fim_fetch_batched(ctx, fim.FIM_ALL_DBS, out_hn)
+    sl = fim.fim_batch_slices(ctx, len(dbs)).astype(np.int64)
+    single = (np.diff(res.offsets.astype(np.int64)) == 1).astype(np.int64)
+    csum = np.concatenate([[0], np.cumsum(single)])
+    m_freq = [int(csum[sl[d + 1]] - csum[sl[d]]) for d in range(len(dbs))]
+
+    probes = _probes(fim, ctx)
+    roof = _batched_roofline(st, phase, dbs, m_freq, probes)
+    med = statistics.median
+    compare = {
+        "unit": f"ms per mine of all {len(dbs):,} databases",
+        "device": {"learned_batched": ms_lb, "batched_plain": med(batched_plain), "plain_per_database": med(plain)},
+        "e2e": {"learned_batched": statistics.mean(e2e_lb), "batched_plain": med(e2e_bp),
+                "plain_per_database": med(e2e_plain)},
+        "speedup_learned_batched_vs_plain": {"device": med(plain) / ms_lb,
+                                             "e2e": med(e2e_plain) / statistics.mean(e2e_lb)},
+        "network_gain_vs_batched_plain": {"device": med(batched_plain) / ms_lb,
+                                          "e2e": med(e2e_bp) / statistics.mean(e2e_lb)},
+        "timing": "device: CUDA events on the miner's stream; e2e: host clock around calls that end "
+                  "synchronised; L2 flushed before every rep",
+    }
     line = {
-        "metric": "itemset supports/sec", "value": supports / (ms_lb / 1000), "unit": "supports/s",
-        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_lb,
+        "metric": HEADLINE_METRIC, "value": value, "unit": "supports/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic (seeded generator, paper_2412_19420_gb300.datagen)",
-        "config": {"workload": "batched_4096", "desc": WORKLOAD_DESC["batched_4096"], "n_db": len(dbs),
-                   "n_trans_total": int(sum(c.n for c in dbs)), "frequent_itemsets": int(R),
-                   "supports_per_step": int(supports), "mode": "learned+batched (FIM_LEARNED, one graph-replayed batch)",
-                   "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write)",
-                   "scheduler_training": train_info},
-        "e2e": {"value": supports / (ms_e2e / 1000), "unit": "supports/s", "h2d_bytes_per_step": int(h2d),
-                "d2h_bytes_per_step": int(d2h), "ms_per_step": ms_e2e},
-        "compare": {"unit": "ms per mine of all 4,096 databases (device-resident inputs)",
-                    "plain_per_database": statistics.median(plain),
-                    "batched_plain": statistics.median(plain_batched),
-                    "learned_batched": ms_lb,
-                    "speedup_learned_batched_vs_plain": statistics.median(plain) / ms_lb},
-        "gpu_launches": int(launches) * args.steps,
-        "roofline": {"kernel": "build..dfs batched graph", "bound": "hbm", "achieved": ach, "peak": hbm,
-                     "unit": "GB/s", "frac": ach / hbm, "traffic": None, "peak_source": src,
-                     "note": "DFS algorithmic bytes over the whole graph's time (build, pairs, DFS)"},
+        "config": cfg,
+        "e2e": {"value": float(tot.item()) / (float(e2e_t.item()) / 1000), "unit": "supports/s",
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                "ms_per_step": float(e2e_t.item())},
+        "compare": compare,
+        "gpu_launches": int(launches),
+        "roofline": roof,
+        "probes": probes,
+        "details": {"mode": "learned+batched (FIM_LEARNED, one graph-replayed batched pass)",
+                    "parallelism": f"replicas x{world}" if world > 1 else "one GPU",
+                    "frequent_itemsets": int(R), "max_len": int(st["max_len"]),
+                    "supports_per_step": int(supports), "classes": int(st["classes"]),
+                    "diffset_classes": int(st["diffset_classes"]),
+                    "dfs_utilisation": (st["dfs_busy_ns"] / max(1, st["dfs_span_ns"] * st["dfs_workers"])),
+                    "peak_device_mib": round(st["peak_device_bytes"] / 2**20, 1),
+                    "scheduler_training": train_info},
         "clocks": clk.summary(),
     }
-    if not args.no_cpu_baseline:
-        import oracle
-        t0 = time.perf_counter()
-        cand = 0
-        k = 0
-        while time.perf_counter() - t0 < 15.0 and k < len(dbs):
-            r = oracle.apriori(dbs[k].indptr, dbs[k].indices, dbs[k].m, ms[k], threads=_cores())
-            cand += r.n_candidates
-            k += 1
-        dt = time.perf_counter() - t0
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cand, dt, k = _oracle_batch(dbs, ms, 0, 25.0, _cores())
         line["cpu_baseline"] = {"value": cand / dt, "unit": "supports/s", "cores": _cores(), "kind": "oracle",
-                                "sample": f"first {k} of {len(dbs)} databases ({cand:,} candidate supports)"}
-    _emit(line)
+                                "sample": (f"{'all' if k == len(dbs) else f'the first {k} of'} {len(dbs)} databases "
+                                           f"({cand:,} candidate supports), {dt:.1f} s")}
+    if rank == 0:
+        _emit(line)
     fim.fim_destroy(ctx)
+    if world > 1:
+        dist.destroy_process_group()
 
 
 def run_sharded(args):
@@ -475,7 +660,7 @@ def run_sharded(args):
     e2e_value = supports / (float(e2e_t.item()) / 1000.0)
 
     avg = {p: phase[p] / args.steps for p in phase}
-    roof = _roofline(st_mine, avg, csr, args.workload)
+    roof = _roofline(st_mine, avg, csr, args.workload, _probes(fim, ctx))
     line = {
         "metric": "itemset supports/sec", "value": value, "unit": "supports/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
@@ -500,26 +685,60 @@ def run_sharded(args):
     dist.destroy_process_group()
 
 
-def _roofline(st, avg, csr, workload):
+def _probes(fim, ctx):
+    """Measured ceilings on this GPU: the AND/popc word-pair rate, the L2 read
+    bandwidth (the L2-resident operands' ceiling) and the tcgen05 f8f6f4 MMA
+    rate with A from tensor or shared memory."""
+    return {"popc_word_pairs_per_s": fim.fim_probe(ctx, 0), "l2_read_gbs": fim.fim_probe(ctx, 1),
+            "mma_f8f6f4_tflops_a_tmem": fim.fim_probe(ctx, 2), "mma_f8f6f4_tflops_a_smem": fim.fim_probe(ctx, 3)}
+
+
+def _dfs_roofline(st, ms_dfs, workload, probes):
+    """The prefix-extension kernel against its ceiling.  Its algorithmic bytes
+    are those of the operands the chosen representations stream, at 32-byte
+    sector granularity (zero sectors skipped, sparse classes as (index,
+    word) pairs); the dense-column figure is reported beside it.  Where the
+    ncu DRAM traffic of the kernel (taken on its current source) is well
+    below those bytes, they are served by L2, and the ceiling is the measured
+    L2 read bandwidth; else HBM.  Both fractions are reported either way."""
+    hbm, _, _, src = _peaks()
+    sec = ms_dfs / 1000
+    ach = st["dfs_touched_bytes"] / sec / 1e9
+    traffic = _kernel_traffic("dfs_kernel", workload)
+    l2 = probes["l2_read_gbs"]
+    roof = {"kernel": "dfs_kernel", "achieved": ach, "unit": "GB/s", "traffic": traffic,
+            "algorithmic_bytes_per_launch": st["dfs_touched_bytes"],
+            "dense_equivalent_bytes_per_launch": st["dfs_bytes"],
+            "hbm_frac": ach / hbm, "l2_frac": ach / l2,
+            "alu_frac": st["dfs_touched_bytes"] / 4 / sec / probes["popc_word_pairs_per_s"]}
+    if traffic is not None:
+        roof["dram_frac"] = traffic / sec / 1e9 / hbm
+    if traffic is not None and traffic < 0.5 * st["dfs_touched_bytes"]:
+        roof.update({"bound": "l2", "peak": l2, "frac": ach / l2, "peak_source": "measured L2 read (fim_probe 1)"})
+    else:
+        roof.update({"bound": "hbm", "peak": hbm, "frac": ach / hbm, "peak_source": src})
+    return roof
+
+
+def _roofline(st, avg, csr, workload, probes):
     """Roofline of the dominant phase of a mine: st = fim_get_stats of a
-    timed mine, avg = mean CUDA-event phase times (ms)."""
+    timed mine, avg = mean CUDA-event phase times (ms); probes = fim_probe's
+    measured AND/popc rate, L2 bandwidth and tcgen05 f8f6f4 rate (the pair
+    pass's ceiling)."""
+    mma_tflops = probes.get("mma_f8f6f4_tflops_a_tmem")
     hbm, bf16, bf16_s, src = _peaks()
     dom = max(("ms_pairs", "ms_dfs", "ms_compact", "ms_build"), key=lambda p: avg[p])
     if dom == "ms_dfs":
-        # bytes of the operands the chosen representations stream, at 32-byte
-        # sector granularity (zero sectors skipped, sparse classes as
-        # (index, word) pairs); the dense-column figure is reported beside it
-        ach = st["dfs_touched_bytes"] / (avg[dom] / 1000) / 1e9
-        roof = {"kernel": "dfs_kernel", "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-                "frac": ach / hbm, "traffic": _kernel_traffic("dfs_kernel", workload),
-                "algorithmic_bytes_per_launch": st["dfs_touched_bytes"],
-                "dense_equivalent_bytes_per_launch": st["dfs_bytes"]}
+        roof = _dfs_roofline(st, avg[dom], workload, probes)
     elif dom == "ms_pairs" and st["pair_path"] == 1:
         fl = 2.0 * st["supports_pairs"] * csr.n
         ach = fl / (avg[dom] / 1000) / 1e12
-        peak = 2 * bf16  # fp8 dense = 2 x bf16 dense (nominal ratio)
+        if mma_tflops:
+            peak, psrc = mma_tflops, "measured tcgen05 f8f6f4 rate (fim_probe 2)"
+        else:
+            peak, psrc = 2 * bf16, f"2 x {src} bf16 (nominal fp8 / bf16 ratio)"
         roof = {"kernel": "pairs_tc_kernel", "bound": "tensor", "achieved": ach, "peak": peak,
-                "unit": "TFLOP/s", "frac": ach / peak,
+                "unit": "TFLOP/s", "frac": ach / peak, "peak_source": psrc,
                 "traffic": _kernel_traffic("pairs_tc_kernel", workload)}
     else:
         nm = {"ms_pairs": "pairs_popc_kernel", "ms_compact": "compaction", "ms_build": "build_bitmaps_kernel"}[dom]
@@ -529,7 +748,7 @@ def _roofline(st, avg, csr, workload):
         ach = nbytes / (avg[dom] / 1000) / 1e9
         roof = {"kernel": nm, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
                 "frac": ach / hbm, "traffic": _kernel_traffic(nm, workload)}
-    roof["peak_source"] = src
+    roof.setdefault("peak_source", src)
     roof["phase_ms"] = {k: round(v, 4) for k, v in avg.items()}
     return roof
 
@@ -666,16 +885,11 @@ def main():
 
     # ---- roofline of the dominant phase ---------------------------------
     avg = {p: phase[p] / args.steps for p in phase}
-    roof = _roofline(st, avg, csr, args.workload)
-    # measured AND/popc issue rate and L2 bandwidth (the L2-resident
-    # workloads' ceiling): the DFS's word pairs against the first
-    popc_rate, l2_gbs = fim.fim_probe(ctx, 0), fim.fim_probe(ctx, 1)
-    probes = {"popc_word_pairs_per_s": popc_rate, "l2_read_gbs": l2_gbs}
-    if roof["kernel"] == "dfs_kernel":
-        words_per_s = st["dfs_touched_bytes"] / 4 / (avg["ms_dfs"] / 1000)
-        probes["dfs_alu_frac"] = words_per_s / popc_rate
-        probes["dfs_vs_l2_frac"] = roof["achieved"] / l2_gbs
+    probes = _probes(fim, ctx)
+    roof = _roofline(st, avg, csr, args.workload, probes)
 
+    from paper_2412_19420_gb300 import report
+    tables = report.table_columns(out_d[2][:R], csr.n, st)
     line = {
         "metric": "itemset supports/sec", "value": value, "unit": "supports/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
@@ -688,9 +902,8 @@ def main():
                    "l2": f"flushed between steps ({L2_FLUSH_BYTES >> 20} MiB write)",
                    "frequent_itemsets": int(st["n_sets"]), "max_len": int(st["max_len"]),
                    # the paper's Table 1 / Table 2 columns, on this workload
-                   "avg_support_pct": round(100.0 * float(out_d[2][:R].to(torch.float64).mean().item())
-                                            / max(1, csr.n), 4) if R else 0.0,
-                   "peak_device_mib": round(st["peak_device_bytes"] / 2**20, 1),
+                   "avg_support_pct": round(tables["avg_support_pct"], 4),
+                   "peak_device_mib": round(tables["peak_device_mib"], 1),
                    "supports_per_step": int(supports),
                    "pair_path": "tcgen05" if st["pair_path"] == 1 else "popc"},
         "e2e": {"value": e2e_value, "unit": "supports/s", "h2d_bytes_per_step": int(h2d),

@@ -400,8 +400,11 @@ def run_batched(args):
     plain_flags = args.flags
     # ---- learned + batched, device-resident inputs: the line's value -------
     # (the descriptor table is marshalled once, as a C caller holds its
-    # fim_db_desc array)
+    # fim_db_desc array); launch shapes picked by the autotuner first
     ddesc = fim.BatchDescriptor(ddbs, ms)
+    from paper_2412_19420_gb300 import autotune
+    tuned, tuned_ms, tune_table = autotune.tune_batched(ctx, dbs, ms, flags=learned, desc=ddesc)
+    cfg = dict(cfg, tuned={k: int(tuned[k]) for k in sorted(autotune.BATCH_SPACE)})
     for _ in range(args.warmup):
         fim.fim_mine_batched(ctx, ddesc, flags=learned)
     barrier()
@@ -441,6 +444,10 @@ def run_batched(args):
              torch.empty(1 << 22, dtype=torch.int32, device="cuda"),
              torch.empty(1 << 20, dtype=torch.int32, device="cuda"))
 
+    # the plain miner runs with the library's default launch shapes
+    batched_shape = {k: tuned[k] for k in tuned}
+    autotune.apply(ctx, autotune.DEFAULT)
+
     def plain_device():
         for c, m in zip(ddbs, ms):
             fim.fim_build_bitmaps(ctx, c.indptr, c.indices, c.m)
@@ -469,10 +476,12 @@ def run_batched(args):
     hdesc = fim.BatchDescriptor(hdbs, ms)
 
     def e2e_batched(flags):
+        autotune.apply(ctx, batched_shape)
         fim.fim_mine_batched(ctx, hdesc, flags=flags)
         fim.fim_fetch_batched(ctx, fim.FIM_ALL_DBS, out_hn)
 
     def plain_host():
+        autotune.apply(ctx, autotune.DEFAULT)
         for c, m in zip(hdbs, ms):
             fim.fim_build_bitmaps(ctx, c.indptr, c.indices, c.m)
             fim.fim_mine(ctx, m, plain_flags)
@@ -490,6 +499,7 @@ def run_batched(args):
     d2h = 8 * (R + 1) + 4 * T + 4 * R
 
     # frequent items per database (the sets of size 1 of each slice)
+    autotune.apply(ctx, batched_shape)
     fim.fim_mine_batched(ctx, hdesc, flags=learned)
     res = fim.fim_fetch_batched(ctx, fim.FIM_ALL_DBS, out_hn)
     sl = fim.fim_batch_slices(ctx, len(dbs)).astype(np.int64)
@@ -532,7 +542,9 @@ def run_batched(args):
                     "diffset_classes": int(st["diffset_classes"]),
                     "dfs_utilisation": (st["dfs_busy_ns"] / max(1, st["dfs_span_ns"] * st["dfs_workers"])),
                     "peak_device_mib": round(st["peak_device_bytes"] / 2**20, 1),
-                    "scheduler_training": train_info},
+                    "scheduler_training": train_info,
+                    "autotune": {"ms_best": tuned_ms, "tried": [[{k: c[k] for k in sorted(autotune.BATCH_SPACE)},
+                                                                 round(t, 4)] for c, t in tune_table]}},
         "clocks": clk.summary(),
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

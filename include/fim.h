@@ -209,6 +209,15 @@ int fim_get_stats(const fim_ctx *ctx, fim_stats *out);
  *   "upload_streams"   1, 2      copy streams the chunks alternate over (default 2)
  *   "compact_cluster"  0, 1      sort outputs small enough for one thread-block
  *                                cluster's shared memory in one launch (default 1)
+ *   "batch_pairs_shape" 0..4     launch shape of fim_mine_batched's tensor-core
+ *                                pair pass: (operand stages in the ring, stages of
+ *                                raw bits staged ahead, CTAs per SM) = 0 (4, 8, 1),
+ *                                1 (4, 16, 1), 2 (2, 8, 2), 3 (2, 24, 1),
+ *                                4 (3, 12, 1); default 0
+ *   "batch_build_block" 32, 64   words of every column one CTA of fim_mine_batched's
+ *                                build covers (32 x that many transactions); 64
+ *                                applies where the block fits shared memory
+ *                                (default 32)
  * Errors: FIM_E_INVAL for an unknown key or an out-of-range value. */
 int fim_set_tuning(fim_ctx *ctx, const char *key, int64_t value);
 

@@ -25,6 +25,16 @@ SPACE = {
 }
 DEFAULT = {"dfs_threads": 256, "dfs_ctas_per_sm": 4, "split_depth": 8, "sparse_div": -1,
            "root_reverse": 0, "pairs_kdrain": 0, "pairs_split": 0}
+# a batch: the tensor-core pair pass's launch shape (ring stages, raw-bit
+# staging depth, CTAs per SM), the build's words per column and CTA, and the
+# DFS workers; searched one knob at a time from BATCH_DEFAULT
+BATCH_SPACE = {
+    "batch_pairs_shape": [0, 1, 2, 3, 4],
+    "batch_build_block": [32, 64],
+    "dfs_ctas_per_sm": [2, 4],
+    "split_depth": [4, 8],
+}
+BATCH_DEFAULT = dict(DEFAULT, batch_pairs_shape=0, batch_build_block=32)
 
 
 def valid(cfg: dict) -> bool:
@@ -81,6 +91,33 @@ def _search(ctx, run, space, repeats):
     return best, best_ms, table
 
 
+def _coordinate_search(ctx, run, space, start, repeats, sweeps=2):
+    """One knob at a time: each value of each knob with the others held, a
+    change kept when it is at least 1% faster; up to `sweeps` passes."""
+    cur = dict(start)
+    apply(ctx, cur)
+    best_ms = _time_ms(run, repeats)
+    table = [(dict(cur), best_ms)]
+    for _ in range(sweeps):
+        improved = False
+        for k in sorted(space):
+            for v in space[k]:
+                if v == cur.get(k):
+                    continue
+                cfg = dict(cur, **{k: v})
+                if not valid(cfg):
+                    continue
+                apply(ctx, cfg)
+                ms = _time_ms(run, repeats)
+                table.append((cfg, ms))
+                if ms < 0.99 * best_ms:
+                    cur, best_ms, improved = cfg, ms, True
+        if not improved:
+            break
+    apply(ctx, cur)
+    return cur, best_ms, table
+
+
 def _cached(cache_path, sig):
     if cache_path and os.path.exists(cache_path):
         with open(cache_path) as f:
@@ -123,8 +160,13 @@ def tune(ctx, csr, minsup: int, flags: int = 0, space=None, repeats: int = 3, ca
 
 
 def tune_batched(ctx, dbs, minsups, flags: int = 0, space=None, repeats: int = 2,
-                 cache_path: str | None = None):
-    """Best knob setting for a batch (DFS workers and split depth)."""
+                 cache_path: str | None = None, desc=None):
+    """Best knob setting for a batch: the tensor-core pair pass's launch shape,
+    the build's block, the DFS workers and split depth (BATCH_SPACE), by a
+    coordinate search timed around whole batched mines.  dbs/minsups give the
+    workload signature; `desc` (a fim.BatchDescriptor of the same batch, host
+    or device arrays) is what is mined, else dbs/minsups themselves.
+    Returns (config, ms of the best config, table of (config, ms))."""
     n = sum(c.n for c in dbs)
     sig = signature(f"batch{len(dbs)}", n, max(c.m for c in dbs), sum(c.nnz for c in dbs),
                     int(sum(minsups) // max(1, len(minsups))), flags)
@@ -132,12 +174,14 @@ def tune_batched(ctx, dbs, minsups, flags: int = 0, space=None, repeats: int = 2
     if hit:
         cfg = {k: v for k, v in hit.items() if not k.startswith("_")}
         apply(ctx, cfg)
-        return cfg
+        return cfg, hit.get("_ms"), []
 
     def run():
-        fim.fim_mine_batched(ctx, dbs, minsups, flags)
+        if desc is not None:
+            fim.fim_mine_batched(ctx, desc, flags=flags)
+        else:
+            fim.fim_mine_batched(ctx, dbs, minsups, flags)
 
-    sp = space or {k: v for k, v in SPACE.items() if k != "pairs_kdrain"}
-    best, ms, _ = _search(ctx, run, sp, repeats)
+    best, ms, table = _coordinate_search(ctx, run, space or BATCH_SPACE, BATCH_DEFAULT, repeats)
     _store(cache_path, sig, best, ms)
-    return best
+    return best, ms, table

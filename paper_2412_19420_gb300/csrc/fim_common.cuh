@@ -242,6 +242,7 @@ struct fim_ctx {
 
     // batched mines: device prefix arrays, result slices, the captured graph
     DevBuf batch_prefix, batch_slices;
+    DevBuf batch_units;         // (database, tile) units of the batched tensor-core pair pass
     bool batch_mined = false;
     int batch_n_db = 0;
     std::vector<unsigned long long> batch_set_start, batch_item_start;
@@ -266,6 +267,8 @@ struct fim_ctx {
     int l2_bytes = 0;
     int pairs_split = 0;        // split-K factor of the tensor-core pair pass (0 = auto)
     int pairs_kdrain = 0;       // stages (x128 transactions) per exact drain (0 = 64)
+    int batch_pairs_shape = 0;  // launch shape of the batched tensor-core pair pass
+    int batch_build_block = 32; // words per column a batched build CTA covers (32 or 64)
     int compact_cluster = 1;    // small outputs: sort in one cluster launch
     int csort_cl[5] = {0, 0, 0, 0, 0};  // cluster size per key width (0 unknown, -1 none)
     int debug_checks = 0;       // device-side invariant checks after build and mine
@@ -331,6 +334,13 @@ int cluster_sort_plan(fim_ctx *ctx, uint64_t R, int kw, int *cl, int *cap, int *
 int launch_cluster_sort(fim_ctx *ctx, const unsigned long long *keys, uint64_t R, int kw,
                         const std::vector<std::pair<int, int>> &passes, int cl, int cap, int per,
                         uint32_t *idx_out, cudaStream_t st);
+
+// k_batch_pairs_tc.cu: the batch's pair supports on the tensor cores
+bool batch_pairs_tc_units(const std::vector<DbDesc> &dbs, std::vector<unsigned long long> &units,
+                          size_t max_units);
+int launch_batch_pairs_tc(fim_ctx *ctx, const DbDesc *d_dbs, const unsigned long long *d_units, int64_t n_units,
+                          cudaStream_t st);
+extern const int kBatchPairsShapeCount;
 
 // k_check.cu: the debug_checks invariants (FIM_E_CHECK when violated)
 int run_check_pads(fim_ctx *ctx);

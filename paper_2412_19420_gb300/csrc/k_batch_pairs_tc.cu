@@ -1,0 +1,374 @@
+// k_batch_pairs_tc.cu -- pair supports of every database of a batch on the
+// 5th-generation tensor cores.
+//
+// For database d with m'_d frequent items, S(I_a n I_b) = sum_i M[i,a] M[i,b]
+// (Eq. 2) for a < b < m'_d is the upper triangle of A_d^T A_d, A_d its n_d x m'_d
+// 0/1 matrix of frequent columns.  The 0/1 entries are fed as e4m3 2.0 / 0.0 to
+// tcgen05.mma kind::f8f6f4 with an f32 accumulator in tensor memory (every
+// product is 4; a partial over at most kdrain x 128 <= 2^22 transactions is 4 x
+// an integer <= 2^22, exact in f32), as in the single-database pass.
+//
+// Work: the units are (database, ta, tb) with ta <= tb, the 128 x 128 tiles of
+// each database's item blocks, listed by the host in descending order of the
+// database's stage count (128 transactions per stage).  Which units hold pairs
+// depends on m'_d, known only on the device: a unit with 128 tb >= m'_d is
+// empty, and every role of the CTA skips it alike.  CTA c takes units c,
+// c + grid, c + 2 grid, ...: the longest first, so the persistent grid ends
+// nearly together.  A unit's K range runs in segments of at most kdrain
+// stages; each segment is one accumulator run, and the two accumulator
+// buffers let a segment's drain overlap the next segment's MMAs.
+//
+// CTA (416 threads):
+//   warps 0-3   A producers, one row each (item block ta): copy the row's
+//               bits 8 stages ahead into shared memory (cp.async, 64-byte
+//               runs), expand each bit to an e4m3 byte into the SWIZZLE_128B
+//               K-major A tile.  On a diagonal tile (ta == tb) the B tile is
+//               also the A operand, and these warps only arrive;
+//   warps 4-7   B producers, one row each (item block tb), likewise;
+//   warps 8-11  epilogue: per segment, tcgen05.ld the accumulator (warp q
+//               reads lane quarter q = rows 32q .. 32q + 31), convert to
+//               counts and write row a's counts for b > a: the first segment
+//               of a unit stores, later ones add (a thread owns its row);
+//   warp 12     one elected thread issues 4 MMAs (128 x N x 32, N = the
+//               tile's columns rounded up to 16) per stage.
+// Rows outside the tile's items are zero; a producer remembers which of its
+// ring slots already hold its zero row and does not rewrite them.
+// Every mbarrier wait is bounded; on expiry the CTA records FIM_E_TIMEOUT,
+// lets its MMAs finish, frees its tensor memory and returns.
+#include <algorithm>
+#include <vector>
+
+#include "fim_common.cuh"
+#include "tc_util.cuh"
+
+namespace {
+
+using namespace fim_tc;
+
+constexpr int BT = 128;                // tile side: items a (A rows), items b (B rows)
+constexpr int KB = 128;                // transactions per stage = bytes per operand row
+constexpr int BNPROD = 2 * BT;         // producer threads: A rows, then B rows
+constexpr int BNEPI = 128;             // epilogue threads: one TMEM lane quarter per warp
+constexpr int BTHREADS = BNPROD + BNEPI + 32;
+constexpr int TILE_BYTES = BT * KB;    // 16 KB per operand tile and stage
+constexpr int BG = 2;                  // stages a producer publishes per fence
+constexpr uint32_t ACC_COLS = BT;      // one f32 accumulator: 128 columns; two buffers
+constexpr uint32_t BTMEM_COLS = 256;
+constexpr int BKDRAIN_MAX = 32768;     // 2^22 transactions: partials stay <= 2^24
+constexpr unsigned long long BWAIT_NS = 2000000000ull;
+
+// STG expanded operand stages in the ring; DEPTH stages of raw bits staged
+// ahead (a multiple of 4: copies go in quads of 4 stages).
+template <int STG, int DEPTH>
+struct __align__(1024) BtcSmem {
+    uint8_t a[STG][TILE_BYTES];
+    uint8_t b[STG][TILE_BYTES];
+    uint4 stg[DEPTH][BNPROD];          // raw bits: producer t's row, stage k at stg[k % DEPTH][t]
+    uint64_t full[STG];
+    uint64_t empty[STG];
+    uint64_t acc_full[2];
+    uint64_t acc_empty[2];
+    uint64_t done;
+    uint32_t tmem_base;
+    int abort;
+};
+
+// What every role of the CTA derives from a unit code, identically.
+struct BUnit {
+    const DbDesc *D;
+    int ta, tb, mf, N;
+    int64_t S;      // stages of 128 transactions
+    bool diag;
+    bool empty;
+};
+
+__device__ __forceinline__ BUnit decode_unit(const DbDesc *__restrict__ dbs, unsigned long long code) {
+    BUnit u;
+    u.D = dbs + (code >> 32);
+    u.ta = (int)((code >> 16) & 0xFFFFu);
+    u.tb = (int)(code & 0xFFFFu);
+    u.mf = *(volatile const int32_t *)&u.D->mfreq;  // written by the rank pass of this mine
+    u.diag = u.ta == u.tb;
+    u.empty = u.mf < 2 || u.D->maxlen == 1 || u.tb * BT >= u.mf;
+    const int cols = u.empty ? 16 : min(BT, u.mf - u.tb * BT);
+    u.N = (cols + 15) & ~15;
+    u.S = (u.D->nw + 3) / 4;
+    return u;
+}
+
+template <typename S>
+__device__ __forceinline__ bool bwait(S &s, uint64_t *b, uint32_t parity) {
+    return mbar_wait_bounded(b, parity, &s.abort, BWAIT_NS);
+}
+
+template <int STG, int DEPTH, int MINB>
+__global__ void __launch_bounds__(BTHREADS, MINB)
+batch_pairs_tc_kernel(const DbDesc *__restrict__ dbs, const unsigned long long *__restrict__ units,
+                      int64_t n_units, const uint32_t *__restrict__ bm, const int32_t *__restrict__ perm_base,
+                      int *__restrict__ pair_cnt, int kd, int *__restrict__ err) {
+    static_assert(DEPTH % 4 == 0 && DEPTH >= 8, "raw bits go in quads, two or more in flight");
+    using Smem = BtcSmem<STG, DEPTH>;
+    constexpr int BSTAGES = STG, BD = DEPTH;
+    extern __shared__ uint8_t smem_raw[];
+    Smem &s = *reinterpret_cast<Smem *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < BSTAGES; i++) { mbar_init(&s.full[i], BNPROD / 32); mbar_init(&s.empty[i], 1); }
+        for (int i = 0; i < 2; i++) { mbar_init(&s.acc_full[i], 1); mbar_init(&s.acc_empty[i], BNEPI); }
+        mbar_init(&s.done, 1);
+        s.abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_addr(&s.tmem_base)),
+                     "r"(BTMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = s.tmem_base;
+
+    if (warp < BNPROD / 32) {
+        // ---------------- producers: one operand row each ----------------
+        const bool is_a = threadIdx.x < BT;
+        const int r = threadIdx.x & (BT - 1);
+        uint8_t(*const tiles)[TILE_BYTES] = is_a ? s.a : s.b;
+        uint4 *const my = &s.stg[0][threadIdx.x];
+        const int row0 = threadIdx.x - lane;  // the warp's first producer thread
+        uint32_t zeroed = 0;                  // bit q: my row of ring slot q holds zeros
+        int it = 0;                           // stages produced by this CTA (ring position)
+        bool ok = true;
+        for (int64_t ui = blockIdx.x; ui < n_units && ok; ui += gridDim.x) {
+            const BUnit u = decode_unit(dbs, units[ui]);
+            if (u.empty) continue;
+            const DbDesc &D = *u.D;
+            const bool store = !(is_a && u.diag);  // warp-uniform: a warp's rows are all A or all B
+            const int item = (is_a ? u.ta : u.tb) * BT + r;
+            const uint32_t *col =
+                (store && item < u.mf) ? bm + D.bm_off + (int64_t)__ldg(perm_base + D.item_off + item) * D.nwp
+                                       : nullptr;
+            const int64_t len = u.S;
+            // stage k of the unit lives in stg[k % BD]; a quad of 4 stages is
+            // refilled at a time, 4 lanes per row copying 64 contiguous bytes
+            auto refill = [&](int64_t q0) {
+#pragma unroll
+                for (int i = 0; i < 4; i++) {
+                    const int piece = i * 32 + lane, rw = piece >> 2;
+                    const int64_t k = q0 + (piece & 3);
+                    const uint32_t *c = reinterpret_cast<const uint32_t *>(
+                        __shfl_sync(0xffffffffu, reinterpret_cast<uintptr_t>(col), rw));
+                    if (c && k < len) cp_async16(smem_addr(&s.stg[k % BD][row0 + rw]), c + k * 4);
+                }
+                cp_async_commit();
+            };
+#pragma unroll
+            for (int q = 0; q < BD; q += 4) refill(q);
+            for (int64_t q0 = 0; q0 < len && ok; q0 += 4) {
+                cp_async_wait<BD / 4 - 1>();  // this lane's copies of quad q0 have landed ...
+                __syncwarp();        // ... and so have the other lanes' (they filled my row)
+#pragma unroll
+                for (int64_t k0 = q0; k0 < q0 + 4; k0 += BG) {
+                    const int cnt = (int)min64(BG, len - k0);
+                    if (cnt <= 0 || !ok) break;
+                    uint4 x[BG];
+#pragma unroll
+                    for (int v = 0; v < BG; v++)
+                        x[v] = (col && v < cnt) ? my[((k0 + v) % BD) * BNPROD] : make_uint4(0, 0, 0, 0);
+                    bool wok = true;  // lane 0 waits for the warp
+                    if (lane == 0) {
+#pragma unroll
+                        for (int v = 0; v < BG; v++)
+                            if (v < cnt && wok) {
+                                const int sl = (it + v) % BSTAGES;
+                                wok = bwait(s, &s.empty[sl], ((uint32_t)((it + v) / BSTAGES) & 1u) ^ 1u);
+                            }
+                    }
+                    ok = __shfl_sync(0xffffffffu, wok, 0);
+                    if (!ok) break;
+                    if (store) {
+#pragma unroll
+                        for (int v = 0; v < BG; v++)
+                            if (v < cnt) {
+                                const int sl = (it + v) % BSTAGES;
+                                if (col) {
+                                    store_row(tiles[sl], r, x[v]);
+                                    zeroed &= ~(1u << sl);
+                                } else if (!(zeroed & (1u << sl))) {
+                                    zero_row(tiles[sl], r);
+                                    zeroed |= 1u << sl;
+                                }
+                            }
+                        fence_proxy_async();
+                    }
+                    __syncwarp();  // the warp's stores are fenced: lane 0 arrives for it
+#pragma unroll
+                    for (int v = 0; v < BG; v++)
+                        if (v < cnt && lane == 0) mbar_arrive(&s.full[(it + v) % BSTAGES]);
+                    it += cnt;
+                }
+                if (!ok) break;
+                __syncwarp();  // every lane has consumed its row of quad q0
+                refill(q0 + BD);
+            }
+            cp_async_wait<0>();  // the staging slots serve the next unit
+        }
+    } else if (warp < (BNPROD + BNEPI) / 32) {
+        // ---------------- epilogue ----------------
+        const int q = warp & 3;  // TMEM lane quarter this warp may read
+        int j = 0;               // segments drained by this CTA
+        bool ok = true;
+        for (int64_t ui = blockIdx.x; ui < n_units && ok; ui += gridDim.x) {
+            const BUnit u = decode_unit(dbs, units[ui]);
+            if (u.empty) continue;
+            const int a = u.ta * BT + q * 32 + lane;
+            int *const row = pair_cnt + u.D->pair_off + (int64_t)a * u.mf;
+            for (int64_t st0 = 0; st0 < u.S; st0 += kd, j++) {
+                const int buf = j & 1;
+                // warp-uniform: tcgen05.ld below is a .sync.aligned warp instruction
+                ok = __all_sync(0xffffffffu, bwait(s, &s.acc_full[buf], (uint32_t)(j >> 1) & 1u));
+                if (!ok) break;
+                tc_fence_after();
+#pragma unroll 1
+                for (int x = 0; x < u.N / 16; x++) {
+                    uint32_t v[16];
+                    const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)buf * ACC_COLS +
+                                           (uint32_t)(x * 16);
+                    asm volatile(
+                        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+                          "=r"(v[14]), "=r"(v[15])
+                        : "r"(taddr)
+                        : "memory");
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    if (a < u.mf) {
+#pragma unroll
+                        for (int c = 0; c < 16; c++) {
+                            const int b = u.tb * BT + x * 16 + c;
+                            if (a < b && b < u.mf) {
+                                const int val = __float2int_rn(__uint_as_float(v[c])) >> 2;
+                                row[b] = st0 == 0 ? val : row[b] + val;
+                            }
+                        }
+                    }
+                }
+                tc_fence_before();
+                mbar_arrive(&s.acc_empty[buf]);
+            }
+        }
+    } else if (lane == 0) {
+        // ---------------- MMA issuer ----------------
+        bool ok = true;
+        int it = 0, j = 0;
+        for (int64_t ui = blockIdx.x; ui < n_units && ok; ui += gridDim.x) {
+            const BUnit u = decode_unit(dbs, units[ui]);
+            if (u.empty) continue;
+            const uint32_t idesc = idesc_f8(BT, u.N);
+            for (int64_t st0 = 0; st0 < u.S && ok; st0 += kd, j++) {
+                const int64_t len = min64(kd, u.S - st0);
+                const int buf = j & 1;
+                // buffer buf's previous run has been drained
+                if (!(ok = bwait(s, &s.acc_empty[buf], ((uint32_t)(j >> 1) & 1u) ^ 1u))) break;
+                tc_fence_after();
+                const uint32_t d = tmem + (uint32_t)buf * ACC_COLS;
+                for (int64_t k = 0; k < len; k++, it++) {
+                    const int slot = it % BSTAGES;
+                    if (!(ok = bwait(s, &s.full[slot], (uint32_t)(it / BSTAGES) & 1u))) break;
+                    tc_fence_after();
+                    const uint32_t b0 = smem_addr(s.b[slot]);
+                    const uint32_t a0 = u.diag ? b0 : smem_addr(s.a[slot]);
+#pragma unroll
+                    for (int kk = 0; kk < KB / 32; kk++)
+                        mma_f8(d, sdesc(a0 + kk * 32), sdesc(b0 + kk * 32), idesc, (k == 0 && kk == 0) ? 0u : 1u);
+                    mma_commit(&s.empty[slot]);
+                }
+                if (ok) mma_commit(&s.acc_full[buf]);
+            }
+        }
+        // no MMA may be in flight when the tensor memory is freed
+        mma_commit(&s.done);
+        const unsigned long long t0 = globaltimer_ns();
+        while (!mbar_try(&s.done, 0) && globaltimer_ns() - t0 < BWAIT_NS) {
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (s.abort && threadIdx.x == 0) atomicExch(err, FIM_E_TIMEOUT);
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BTMEM_COLS)
+                     : "memory");
+    }
+}
+
+// The batch's (database, tile) units in the order the pass takes them:
+// databases by descending stage count (ties by index), each database's
+// upper-triangle tiles of its n_items (an upper bound of m'_d) in row order.
+// Returns false when there are more than max_units of them.
+}  // namespace
+
+bool batch_pairs_tc_units(const std::vector<DbDesc> &dbs, std::vector<unsigned long long> &units,
+                          size_t max_units) {
+    std::vector<int> order(dbs.size());
+    for (size_t d = 0; d < dbs.size(); d++) order[d] = (int)d;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return dbs[x].nw > dbs[y].nw; });
+    units.clear();
+    for (int d : order) {
+        const int nt = (int)ceil_div64(dbs[d].m, BT);
+        if ((size_t)nt * (size_t)(nt + 1) / 2 > max_units - units.size()) return false;
+        for (int ta = 0; ta < nt; ta++)
+            for (int tb = ta; tb < nt; tb++)
+                units.push_back(((unsigned long long)d << 32) | ((unsigned long long)ta << 16) | (unsigned)tb);
+    }
+    return true;
+}
+
+namespace {
+
+template <int STG, int DEPTH, int MINB>
+int launch_shape(fim_ctx *ctx, const DbDesc *d_dbs, const unsigned long long *d_units, int64_t n_units,
+                 cudaStream_t st) {
+    using Smem = BtcSmem<STG, DEPTH>;
+    static_assert(sizeof(Smem) + 1024 <= 232448, "shared memory per CTA");
+    // MINB CTAs share an SM: their tensor memory (256 columns each) and shared
+    // memory must fit it together
+    static_assert(MINB * BTMEM_COLS <= 512, "tensor memory per SM");
+    static_assert(MINB == 1 ? sizeof(Smem) > 116 * 1024 : MINB * (sizeof(Smem) + 2048) <= 233472,
+                  "CTAs per SM as planned");
+    const int kd = ctx->pairs_kdrain > 0 ? ctx->pairs_kdrain : BKDRAIN_MAX;
+    int64_t grid = ctx->pairs_split > 0 ? ctx->pairs_split : (int64_t)ctx->num_sms * MINB;
+    if (grid > n_units) grid = n_units;
+    const size_t smem = sizeof(Smem) + 1024;
+    auto *kern = batch_pairs_tc_kernel<STG, DEPTH, MINB>;
+    FIM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int *err = &ctx->counters.as<MineCounters>()->err;  // zeroed at the start of every batch
+    ctx->launches++;
+    kern<<<(unsigned)grid, BTHREADS, smem, st>>>(d_dbs, d_units, n_units, ctx->bm.as<uint32_t>(),
+                                                 ctx->perm.as<int32_t>(), ctx->pair_cnt.as<int>(), kd, err);
+    FIM_CUDA_TRY(cudaGetLastError());
+    return FIM_OK;
+}
+
+}  // namespace
+
+// Launch shapes of the batched tensor-core pair pass (the "batch_pairs_shape"
+// knob): expanded operand stages in the ring, stages of raw bits staged
+// ahead, CTAs per SM.
+const int kBatchPairsShapes[][3] = {{4, 8, 1}, {4, 16, 1}, {2, 8, 2}, {2, 24, 1}, {3, 12, 1}};
+const int kBatchPairsShapeCount = (int)(sizeof(kBatchPairsShapes) / sizeof(kBatchPairsShapes[0]));
+
+int launch_batch_pairs_tc(fim_ctx *ctx, const DbDesc *d_dbs, const unsigned long long *d_units, int64_t n_units,
+                          cudaStream_t st) {
+    if (n_units <= 0) return FIM_OK;
+    switch (ctx->batch_pairs_shape) {
+        case 1: return launch_shape<4, 16, 1>(ctx, d_dbs, d_units, n_units, st);
+        case 2: return launch_shape<2, 8, 2>(ctx, d_dbs, d_units, n_units, st);
+        case 3: return launch_shape<2, 24, 1>(ctx, d_dbs, d_units, n_units, st);
+        case 4: return launch_shape<3, 12, 1>(ctx, d_dbs, d_units, n_units, st);
+        default: return launch_shape<4, 8, 1>(ctx, d_dbs, d_units, n_units, st);
+    }
+}

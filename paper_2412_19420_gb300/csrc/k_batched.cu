@@ -85,70 +85,80 @@ batch_build_kernel(const DbDesc *__restrict__ dbs, int n_db, const int64_t *__re
         col0[(int64_t)(i0 + k / WB) * D.nwp + w0 + k % WB] = tile[k];
 }
 
-// Databases with at most 1,024 items: one CTA per 1,024-transaction block of
-// one database holds the block's 32 words of every item column in shared
-// memory.  Each thread takes whole rows (no search for a row's position),
-// sets its rows' bits with shared atomics, then the block is written out
-// coalesced (128 bytes per column) and each column's popcount over the block
-// is added into S(I_j) (Eq. 3): no second pass reads the columns.
+// Databases with at most 1,024 items: one CTA per block of 32 x WBK
+// transactions (WBK words of every column) of one database holds the
+// block's words of every item column in shared memory, word-major with an odd
+// pitch.  Lane i of a warp owns row i of a 32-row group (one tile word) and
+// ORs bit i into its items' words with shared atomics -- no search for a
+// row's position.  The block is then written out 16 bytes per thread, a
+// column's WBK words by WBK/4 consecutive lanes (coalesced), and each
+// column's popcount over the block rides along: a shuffle sum over those
+// lanes, added into S(I_j) (Eq. 3), so no second pass reads the columns.
+// Blocks past the last transaction hold padding words only and just write
+// zeros.
 constexpr int BUILD_ROWS_THREADS = 512;
+template <int WBK>
 __global__ void __launch_bounds__(BUILD_ROWS_THREADS)
 batch_build_rows_kernel(const DbDesc *__restrict__ dbs, int n_db, const int64_t *__restrict__ unit_prefix,
                         uint32_t *__restrict__ bm, uint32_t *__restrict__ sup, int *__restrict__ flag) {
-    // [WB][m + 1]: a warp's 32 consecutive rows share their word, so the
-    // word-major layout (padded) spreads their items' bits over the banks
-    extern __shared__ uint32_t tile[];
+    static_assert(WBK % 4 == 0 && WBK / 4 <= 32 && 32 % (WBK / 4) == 0, "a column's chunks share a warp");
+    constexpr int NWARP = BUILD_ROWS_THREADS / 32;
+    constexpr int QPC = WBK / 4;  // 16-byte chunks of a column in this block
+    extern __shared__ __align__(16) uint32_t tile[];  // [WBK][ms]
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int d = find_db(unit_prefix, n_db, blockIdx.x);
     const DbDesc &D = dbs[d];
-    const int m = D.m, ms = m + 1;
-    const int64_t w0 = (int64_t)(blockIdx.x - unit_prefix[d]) * WB;
+    const int m = D.m, ms = m | 1;  // odd pitch: the transposed reads below are conflict-free
+    const int64_t w0 = (int64_t)(blockIdx.x - unit_prefix[d]) * WBK;
     const int64_t n = D.n;
-    const int64_t nnz = n > 0 ? D.indptr[n] : 0;
-    const int64_t t0 = w0 * 32, t1 = min64(n, t0 + WB * 32);
-    for (int k = threadIdx.x; k < ms * WB; k += blockDim.x) tile[k] = 0u;
+    uint32_t *const col0 = bm + D.bm_off;
+    const int64_t t0 = w0 * 32;
+    if (t0 >= n) {  // padding words only
+        for (int k = threadIdx.x; k < m * QPC; k += BUILD_ROWS_THREADS)
+            *reinterpret_cast<uint4 *>(col0 + (int64_t)(k / QPC) * D.nwp + w0 + 4 * (k % QPC)) =
+                make_uint4(0u, 0u, 0u, 0u);
+        return;
+    }
+    const int64_t nnz = D.indptr[n];
+    for (int k = threadIdx.x; k < WBK * ms / 4; k += BUILD_ROWS_THREADS)
+        reinterpret_cast<uint4 *>(tile)[k] = make_uint4(0u, 0u, 0u, 0u);
     __syncthreads();
     int bad = 0;
-    // warp w takes rows in groups of 32 (one tile word): lane i holds the
-    // group's row start i, the warp streams the group's elements 32 at a
-    // time (coalesced), and each element finds its row by a binary search
-    // over the lanes' starts
-    for (int64_t rb = t0 + 32 * warp; rb < t1; rb += 32 * (int64_t)(blockDim.x >> 5)) {
-        const int nr = (int)min64(32, t1 - rb);
-        const int64_t off = D.indptr[rb + (lane < nr ? lane : nr)];  // lane i < nr: start of row i
-        const int64_t e_end = D.indptr[rb + nr];                       // the group's end (broadcast)
-        int64_t off_next = __shfl_down_sync(0xffffffffu, off, 1);
-        if (lane == nr - 1) off_next = e_end;
-        if (lane < nr && (off_next < off || off < 0 || off_next > nnz)) bad = 1;
-        const int64_t e_begin = __shfl_sync(0xffffffffu, off, 0);
-        if (__any_sync(0xffffffffu, bad)) continue;  // a malformed group: flagged, not read
-        const uint32_t wl = (uint32_t)((rb - t0) >> 5);
-        for (int64_t e0 = max64(0, e_begin); e0 < min64(nnz, e_end); e0 += 32) {
-            const int64_t e = e0 + lane;
-            const bool v = e < min64(nnz, e_end);
-            const int32_t it = v ? D.indices[e] : 0;
-            int r = 0;  // largest r < nr with start(r) <= e
-#pragma unroll
-            for (int step = 16; step > 0; step >>= 1) {
-                const int c = r + step;
-                const int64_t oc = __shfl_sync(0xffffffffu, off, c < 32 ? c : 31);
-                if (c < nr && oc <= e) r = c;
+    for (int g = warp; g < WBK; g += NWARP) {
+        const int64_t r = t0 + 32 * g + lane;
+        if (r < n) {
+            int64_t e0 = D.indptr[r], e1 = D.indptr[r + 1];
+            if (e1 < e0 || e0 < 0 || e1 > nnz) {  // a malformed row: flagged, not read
+                bad = 1;
+                e1 = e0;
             }
-            if (!v) continue;
-            if (it < 0 || it >= m) { bad = 1; continue; }
-            atomicOr(&tile[wl * ms + it], 1u << r);
+            uint32_t *const trow = tile + g * ms;
+            const uint32_t bit = 1u << lane;
+            for (int64_t e = e0; e < e1; e++) {
+                const int32_t it = __ldg(D.indices + e);
+                if ((unsigned)it >= (unsigned)m) { bad = 1; continue; }
+                atomicOr(trow + it, bit);
+            }
         }
     }
     if (bad) atomicExch(flag, 1);
     __syncthreads();
-    uint32_t *col0 = bm + D.bm_off;
-    for (int k = threadIdx.x; k < m * WB; k += blockDim.x)
-        col0[(int64_t)(k / WB) * D.nwp + w0 + k % WB] = tile[(k % WB) * ms + k / WB];
-    for (int j = threadIdx.x; j < m; j += blockDim.x) {  // a thread per item: 32 words
+    for (int base = 0; base < m * QPC; base += BUILD_ROWS_THREADS) {  // warp-uniform trips
+        const int k = base + threadIdx.x;
+        const int j = k / QPC, q = k % QPC;
         uint32_t c = 0;
-#pragma unroll 8
-        for (int w = 0; w < WB; w++) c += __popc(tile[w * ms + j]);
-        if (c) atomicAdd(&sup[D.item_off + j], c);
+        if (j < m) {
+            uint4 v;
+            v.x = tile[(4 * q + 0) * ms + j];
+            v.y = tile[(4 * q + 1) * ms + j];
+            v.z = tile[(4 * q + 2) * ms + j];
+            v.w = tile[(4 * q + 3) * ms + j];
+            *reinterpret_cast<uint4 *>(col0 + (int64_t)j * D.nwp + w0 + 4 * q) = v;
+            c = __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
+        }
+#pragma unroll
+        for (int o = QPC / 2; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+        if (j < m && q == 0 && c) atomicAdd(&sup[D.item_off + j], c);
     }
 }
 
@@ -213,6 +223,205 @@ __global__ void batch_rank_kernel(DbDesc *__restrict__ dbs, int n_db, const int6
             atomicOr(&ctr->overflow, r < rec_cap ? 2 : 1);
         }
         if (D.maxlen == 0 || D.maxlen >= 1) atomicMax(&ctr->max_len, 1);
+    }
+}
+
+// One CTA per database, the database's frequent items at most RANK_CAP:
+// threads flag the frequent items, a block scan lists them in id order in
+// shared memory, and each ranks its item among them by (support, id) -- the
+// internal id (Eq. 3's threshold, then the relabelling of the miner).  The
+// database's singleton records and m' are published with one global atomic
+// per counter, not one per item.
+constexpr int RANK_THREADS = 256;
+constexpr int RANK_CAP = 4096;
+__global__ void __launch_bounds__(RANK_THREADS)
+batch_rank_db_kernel(DbDesc *__restrict__ dbs, const uint32_t *__restrict__ sup, int32_t *__restrict__ perm,
+                     MineCounters *ctr, unsigned long long *rec_off, uint32_t *rec_len, uint32_t *rec_sup,
+                     uint32_t *rec_items, uint32_t *rec_db, unsigned long long rec_cap,
+                     unsigned long long items_cap) {
+    __shared__ uint32_t f_sup[RANK_CAP];
+    __shared__ int32_t f_id[RANK_CAP];
+    __shared__ uint32_t s_warp[RANK_THREADS / 32 + 1];
+    __shared__ unsigned long long s_base[2];
+    __shared__ int s_nf;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int d = blockIdx.x;
+    DbDesc &D = dbs[d];
+    const int m = D.m;
+    const uint32_t *sp = sup + D.item_off;
+    const uint32_t thr = D.thr;
+    if (threadIdx.x == 0) s_nf = 0;
+    __syncthreads();
+    // compact the frequent items, ascending id, in chunks of RANK_THREADS
+    for (int j0 = 0; j0 < m; j0 += RANK_THREADS) {
+        const int j = j0 + threadIdx.x;
+        const uint32_t sj = j < m ? sp[j] : 0u;
+        const bool f = j < m && sj >= thr;
+        const uint32_t bal = __ballot_sync(0xffffffffu, f);
+        if (lane == 0) s_warp[warp] = __popc(bal);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t acc = 0;
+            for (int w = 0; w < RANK_THREADS / 32; w++) {
+                const uint32_t t = s_warp[w];
+                s_warp[w] = acc;
+                acc += t;
+            }
+            s_warp[RANK_THREADS / 32] = acc;
+        }
+        __syncthreads();
+        const int at = s_nf + (int)s_warp[warp] + __popc(bal & ((1u << lane) - 1u));
+        if (f && at < RANK_CAP) {
+            f_sup[at] = sj;
+            f_id[at] = j;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) s_nf += (int)s_warp[RANK_THREADS / 32];
+        __syncthreads();
+    }
+    const int mf = s_nf;  // <= RANK_CAP: the host picks this kernel only for m <= RANK_CAP
+    if (threadIdx.x == 0) {
+        D.mfreq = mf;
+        s_base[0] = mf ? atomicAdd(&ctr->n_records, (unsigned long long)mf) : 0ull;
+        s_base[1] = mf ? atomicAdd(&ctr->n_rec_items, (unsigned long long)mf) : 0ull;
+        if (mf && (D.maxlen == 0 || D.maxlen >= 1)) atomicMax(&ctr->max_len, 1);
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < mf; k += RANK_THREADS) {
+        const uint32_t sk = f_sup[k];
+        int below = 0;
+        for (int i = 0; i < mf; i++) {  // every thread reads f_sup[i] at once: a broadcast
+            const uint32_t si = f_sup[i];
+            below += si < sk || (si == sk && i < k);
+        }
+        perm[D.item_off + below] = f_id[k];
+        const unsigned long long r = s_base[0] + below, it = s_base[1] + below;
+        if (r < rec_cap && it < items_cap) {
+            rec_off[r] = it;
+            rec_len[r] = 1;
+            rec_sup[r] = sk;
+            rec_items[it] = (uint32_t)below;
+            rec_db[r] = (uint32_t)d;
+        } else {
+            atomicOr(&ctr->overflow, r < rec_cap ? 2 : 1);
+        }
+    }
+}
+
+// One CTA per database with at most FIN_CAP frequent items: the threshold
+// on every pair (Eq. 3), the pair bitset, and the pair records and root
+// classes.  A warp takes rows a; a first pass counts each row's frequent
+// pairs and writes the bitset, a block scan gives each row its place, and a
+// second pass writes the records: one global atomic per counter and
+// database.
+constexpr int FIN_THREADS = 512;
+constexpr int FIN_CAP = 4096;
+__global__ void __launch_bounds__(FIN_THREADS)
+batch_finalize_db_kernel(const DbDesc *__restrict__ dbs, const int *__restrict__ pair_cnt,
+                         uint32_t *__restrict__ pairbits, MineCounters *ctr, unsigned long long *rec_off,
+                         uint32_t *rec_len, uint32_t *rec_sup, uint32_t *rec_items, uint32_t *rec_db,
+                         unsigned long long rec_cap, unsigned long long items_cap, uint32_t *root_a,
+                         uint32_t *root_b, uint32_t *root_sup, uint32_t *root_db) {
+    __shared__ uint32_t s_off[FIN_CAP + 1];
+    __shared__ uint32_t s_warp[FIN_THREADS / 32 + 1];
+    __shared__ unsigned long long s_base[3];
+    constexpr int NW = FIN_THREADS / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int d = blockIdx.x;
+    const DbDesc &D = dbs[d];
+    const int mf = *(volatile const int32_t *)&D.mfreq;
+    const int mpw = (mf + 31) / 32;
+    const bool emit = D.maxlen == 0 || D.maxlen >= 2;
+    const int *cnt = pair_cnt + D.pair_off;
+    uint32_t *pb = pairbits + D.pb_off;
+    // pass 1: bitset rows and per-row counts
+    for (int a = warp; a < mf; a += NW) {
+        const int *row = cnt + (int64_t)a * mf;
+        uint32_t c = 0;
+        for (int w = (a + 1) >> 5; w < mpw; w++) {
+            const int b = w * 32 + lane;
+            const bool f = emit && b > a && b < mf && (uint32_t)row[b] >= D.thr;
+            const uint32_t bal = __ballot_sync(0xffffffffu, f);
+            if (lane == 0) pb[(int64_t)a * mpw + w] = bal;
+            c += __popc(bal);
+        }
+        for (int w = lane; w < ((a + 1) >> 5); w += 32) pb[(int64_t)a * mpw + w] = 0u;  // words left of a
+        if (lane == 0) s_off[a] = c;
+    }
+    __syncthreads();
+    // exclusive scan of the row counts (mf <= FIN_CAP: at most 8 per thread)
+    constexpr int PER = (FIN_CAP + FIN_THREADS - 1) / FIN_THREADS;
+    uint32_t v[PER], sum = 0;
+#pragma unroll
+    for (int i = 0; i < PER; i++) {
+        const int a = threadIdx.x * PER + i;
+        v[i] = a < mf ? s_off[a] : 0u;
+        sum += v[i];
+    }
+    uint32_t x = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t acc = 0;
+        for (int w = 0; w < NW; w++) {
+            const uint32_t t = s_warp[w];
+            s_warp[w] = acc;
+            acc += t;
+        }
+        s_warp[NW] = acc;
+    }
+    __syncthreads();
+    uint32_t run = s_warp[warp] + x - sum;
+#pragma unroll
+    for (int i = 0; i < PER; i++) {
+        const int a = threadIdx.x * PER + i;
+        if (a < mf) s_off[a] = run;
+        run += v[i];
+    }
+    const uint32_t total = s_warp[NW];
+    if (threadIdx.x == 0 && total) {
+        s_base[0] = atomicAdd(&ctr->n_records, (unsigned long long)total);
+        s_base[1] = atomicAdd(&ctr->n_rec_items, 2ull * total);
+        s_base[2] = atomicAdd(&ctr->n_roots, (unsigned long long)total);
+        atomicAdd((unsigned long long *)&ctr->pending, (unsigned long long)total);
+        atomicMax(&ctr->max_len, 2);
+    }
+    __syncthreads();
+    if (!total) return;
+    // pass 2: the records, in (a, b) order within the database
+    for (int a = warp; a < mf; a += NW) {
+        const int *row = cnt + (int64_t)a * mf;
+        uint32_t pos = s_off[a];
+        for (int w = (a + 1) >> 5; w < mpw; w++) {
+            const uint32_t bal = pb[(int64_t)a * mpw + w];
+            if (!bal) continue;
+            const int b = w * 32 + lane;
+            if ((bal >> lane) & 1u) {
+                const uint32_t p = pos + __popc(bal & ((1u << lane) - 1u));
+                const uint32_t sv = (uint32_t)row[b];
+                const unsigned long long r = s_base[0] + p, it = s_base[1] + 2ull * p, q = s_base[2] + p;
+                if (r < rec_cap && it + 2 <= items_cap) {
+                    rec_off[r] = it;
+                    rec_len[r] = 2;
+                    rec_sup[r] = sv;
+                    rec_db[r] = (uint32_t)d;
+                    rec_items[it] = (uint32_t)a;
+                    rec_items[it + 1] = (uint32_t)b;
+                } else {
+                    atomicOr(&ctr->overflow, r < rec_cap ? 2 : 1);
+                }
+                root_a[q] = (uint32_t)a;
+                root_b[q] = (uint32_t)b;
+                root_sup[q] = sv;
+                root_db[q] = (uint32_t)d;
+            }
+            pos += __popc(bal);
+        }
     }
 }
 
@@ -460,6 +669,8 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
         if (flags & FIM_TRACE) return FIM_E_INVAL;
     }
     if ((flags & FIM_LEARNED) && !ctx->has_weights) return FIM_E_STATE;
+    // pair supports on the tensor cores unless FIM_PAIRS_POPC asks for the
+    // CUDA-core tiles
     int dev_prev = -1;
     cudaGetDevice(&dev_prev);
     if (cudaSetDevice(ctx->device) != cudaSuccess) return FIM_E_CUDA;
@@ -479,6 +690,12 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
     L.tile_prefix.assign(n_db + 1, 0);
     for (int d = 0; d < n_db; d++) L.m_max = in[d].n_items > L.m_max ? in[d].n_items : L.m_max;
     L.ib = L.m_max < 1024 ? (L.m_max > 0 ? L.m_max : 1) : 1024;
+    // rows build (every database's columns fit one CTA's shared memory):
+    // words per block as tuned, where the block's tile fits
+    const bool rows_build = L.ib == L.m_max;
+    int wbk = ctx->batch_build_block == 64 ? 64 : 32;
+    if ((size_t)wbk * (size_t)(L.m_max | 1) * sizeof(uint32_t) > 227u * 1024u) wbk = 32;
+    const int unit_words = rows_build ? wbk : WB;
     int64_t host_nnz_total = 0, host_ptr_total = 0;
     for (int d = 0; d < n_db; d++) {
         const fim_db_desc &x = in[d];
@@ -507,7 +724,7 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
         L.root_cap += (int64_t)D.m * (D.m > 0 ? D.m - 1 : 0) / 2;
         L.nwp_max = D.nwp > L.nwp_max ? D.nwp : L.nwp_max;
         const int nt = (int)ceil_div64(D.m, TI);
-        L.unit_prefix[d + 1] = L.unit_prefix[d] + (D.m > 0 ? (D.nwp / WB) * ceil_div64(D.m, L.ib) : 0);
+        L.unit_prefix[d + 1] = L.unit_prefix[d] + (D.m > 0 ? (D.nwp / unit_words) * ceil_div64(D.m, L.ib) : 0);
         L.item_prefix[d + 1] = L.items;
         L.tile_prefix[d + 1] = L.tile_prefix[d] + (int64_t)nt * (nt + 1) / 2;
         if (D.m > L.max_row_bound) L.max_row_bound = D.m;
@@ -518,6 +735,9 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
             host_ptr_total += x.n_trans + 1;
         }
     }
+    // the tensor-core pair pass's (database, tile) units, longest first
+    std::vector<unsigned long long> pair_units;
+    const bool pairs_tc = !(flags & FIM_PAIRS_POPC) && batch_pairs_tc_units(L.dbs, pair_units, (size_t)1 << 24);
     // ---- inputs: one staging copy for host CSRs -----------------------------
     if (!on_device) {
         FIM_TRY(fim_reserve(ctx, ctx->csr_ptr, sizeof(int64_t) * (size_t)(host_ptr_total ? host_ptr_total : 1)));
@@ -583,6 +803,8 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
     FIM_TRY(fim_reserve(ctx, ctx->frame_sups, sizeof(uint32_t) * (size_t)workers * frame_pool));
     FIM_TRY(prepare_task_queue(ctx, sizeof(Task) * kTaskCap));
     FIM_TRY(fim_reserve(ctx, ctx->cand_pool, sizeof(uint32_t) * kCandPoolCap));
+    if (pairs_tc)
+        FIM_TRY(fim_reserve(ctx, ctx->batch_units, sizeof(unsigned long long) * (pair_units.size() ? pair_units.size() : 1)));
     if (ctx->rec_cap < (1ull << 22)) {
         ctx->rec_cap = 1ull << 22;
         ctx->rec_items_cap = 1ull << 24;
@@ -610,6 +832,10 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
         FIM_CUDA_TRY(cudaMemcpyAsync(d_dbs, L.dbs.data(), tbl, cudaMemcpyHostToDevice, st));
         FIM_CUDA_TRY(cudaMemcpyAsync(ctx->batch_prefix.p, pre.data(), sizeof(int64_t) * pre.size(),
                                      cudaMemcpyHostToDevice, st));
+        if (pairs_tc && !pair_units.empty())
+            FIM_CUDA_TRY(cudaMemcpyAsync(ctx->batch_units.p, pair_units.data(),
+                                         sizeof(unsigned long long) * pair_units.size(),
+                                         cudaMemcpyHostToDevice, st));
         FIM_CUDA_TRY(cudaStreamSynchronize(st));  // host staging vectors go out of scope later
 
         DfsParams p{};
@@ -666,11 +892,26 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
         mix(pre.data(), sizeof(int64_t) * pre.size());
         mix(&p, sizeof(p));
         mix(&L.ib, sizeof(L.ib));
+        mix(&pairs_tc, sizeof(pairs_tc));
+        mix(&wbk, sizeof(wbk));
+        // every launch-shape knob the captured launches depend on
+        const int shape[6] = {workers, ctx->dfs_block, ctx->pairs_kdrain, ctx->pairs_split, ctx->batch_pairs_shape,
+                              ctx->dfs_ctas_per_sm};
+        mix(shape, sizeof(shape));
+        if (pairs_tc) {
+            const void *up = ctx->batch_units.p;
+            mix(&up, sizeof(up));
+            for (unsigned long long w : pair_units) key = (key ^ w) * 1099511628211ull;  // word at a time
+            const int64_t nu = (int64_t)pair_units.size();
+            mix(&nu, sizeof(nu));
+        }
         const size_t smem_build = (size_t)L.ib * WB * sizeof(uint32_t);
         FIM_CUDA_TRY(cudaFuncSetAttribute(batch_build_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)smem_build));
-        FIM_CUDA_TRY(cudaFuncSetAttribute(batch_build_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)((size_t)(L.m_max + 1) * WB * sizeof(uint32_t))));
+        if (rows_build)
+            FIM_CUDA_TRY(cudaFuncSetAttribute(wbk == 64 ? batch_build_rows_kernel<64> : batch_build_rows_kernel<32>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)((size_t)(L.m_max | 1) * wbk * sizeof(uint32_t))));
         const bool reuse = ctx->batch_graph_exec && ctx->batch_graph_key == key;
         if (!reuse) {
             if (ctx->batch_graph_exec) {
@@ -689,13 +930,16 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
             const int64_t units = L.unit_prefix[n_db], items = L.item_prefix[n_db], tiles = L.tile_prefix[n_db];
             // rows-per-thread build with fused supports when every database's
             // block of columns fits shared memory (ib == m_max <= 1,024)
-            const bool rows_build = L.ib == L.m_max;
-            const size_t smem_rows = (size_t)(L.m_max + 1) * WB * sizeof(uint32_t);
+            const size_t smem_rows = (size_t)(L.m_max | 1) * wbk * sizeof(uint32_t);
             if (rows_build && items > 0)
                 cudaMemsetAsync(ctx->item_sup.p, 0, sizeof(uint32_t) * (size_t)items, st);
             if (units > 0) {
-                if (rows_build)
-                    batch_build_rows_kernel<<<(unsigned)units, BUILD_ROWS_THREADS, smem_rows, st>>>(
+                if (rows_build && wbk == 64)
+                    batch_build_rows_kernel<64><<<(unsigned)units, BUILD_ROWS_THREADS, smem_rows, st>>>(
+                        d_dbs, n_db, d_unit, ctx->bm.as<uint32_t>(), ctx->item_sup.as<uint32_t>(),
+                        ctx->dev_flag.as<int>());
+                else if (rows_build)
+                    batch_build_rows_kernel<32><<<(unsigned)units, BUILD_ROWS_THREADS, smem_rows, st>>>(
                         d_dbs, n_db, d_unit, ctx->bm.as<uint32_t>(), ctx->item_sup.as<uint32_t>(),
                         ctx->dev_flag.as<int>());
                 else
@@ -707,18 +951,41 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
                     batch_support_kernel<<<(unsigned)items, 256, 0, st>>>(d_dbs, n_db, d_item,
                                                                           ctx->bm.as<uint32_t>(),
                                                                           ctx->item_sup.as<uint32_t>());
-                batch_rank_kernel<<<(unsigned)ceil_div64(items * 32, 256), 256, 0, st>>>(
-                    d_dbs, n_db, d_item, items, ctx->item_sup.as<uint32_t>(), ctx->perm.as<int32_t>(), d_ctr,
-                    p.rec_off, p.rec_len, p.rec_sup, p.rec_items, p.rec_db, p.rec_cap, p.rec_items_cap);
+                if (L.m_max <= RANK_CAP)
+                    batch_rank_db_kernel<<<(unsigned)n_db, RANK_THREADS, 0, st>>>(
+                        d_dbs, ctx->item_sup.as<uint32_t>(), ctx->perm.as<int32_t>(), d_ctr, p.rec_off, p.rec_len,
+                        p.rec_sup, p.rec_items, p.rec_db, p.rec_cap, p.rec_items_cap);
+                else
+                    batch_rank_kernel<<<(unsigned)ceil_div64(items * 32, 256), 256, 0, st>>>(
+                        d_dbs, n_db, d_item, items, ctx->item_sup.as<uint32_t>(), ctx->perm.as<int32_t>(), d_ctr,
+                        p.rec_off, p.rec_len, p.rec_sup, p.rec_items, p.rec_db, p.rec_cap, p.rec_items_cap);
             }
             cudaEventRecordWithFlags(ctx->ev[1], st, cudaEventRecordExternal);
             if (tiles > 0 && maxlen != 1) {
-                batch_pairs_kernel<<<(unsigned)tiles, 256, 0, st>>>(d_dbs, n_db, d_tile, ctx->bm.as<uint32_t>(),
-                                                                    ctx->perm.as<int32_t>(), ctx->pair_cnt.as<int>());
-                batch_finalize_kernel<<<(unsigned)ceil_div64(items * 32, 256), 256, 0, st>>>(
-                    d_dbs, n_db, d_item, items, ctx->pair_cnt.as<int>(), ctx->pairbits.as<uint32_t>(), d_ctr, p.rec_off,
-                    p.rec_len, p.rec_sup, p.rec_items, p.rec_db, p.rec_cap, p.rec_items_cap, roots, roots + rc,
-                    roots + 2 * rc, roots + 3 * rc);
+                if (pairs_tc) {
+                    const int rc_pairs = launch_batch_pairs_tc(ctx, d_dbs, ctx->batch_units.as<unsigned long long>(),
+                                                               (int64_t)pair_units.size(), st);
+                    if (rc_pairs != FIM_OK) {
+                        cudaGraph_t junk = nullptr;
+                        cudaStreamEndCapture(st, &junk);
+                        if (junk) cudaGraphDestroy(junk);
+                        return rc_pairs;
+                    }
+                } else {
+                    batch_pairs_kernel<<<(unsigned)tiles, 256, 0, st>>>(d_dbs, n_db, d_tile, ctx->bm.as<uint32_t>(),
+                                                                        ctx->perm.as<int32_t>(),
+                                                                        ctx->pair_cnt.as<int>());
+                }
+                if (L.m_max <= FIN_CAP)
+                    batch_finalize_db_kernel<<<(unsigned)n_db, FIN_THREADS, 0, st>>>(
+                        d_dbs, ctx->pair_cnt.as<int>(), ctx->pairbits.as<uint32_t>(), d_ctr, p.rec_off, p.rec_len,
+                        p.rec_sup, p.rec_items, p.rec_db, p.rec_cap, p.rec_items_cap, roots, roots + rc,
+                        roots + 2 * rc, roots + 3 * rc);
+                else
+                    batch_finalize_kernel<<<(unsigned)ceil_div64(items * 32, 256), 256, 0, st>>>(
+                        d_dbs, n_db, d_item, items, ctx->pair_cnt.as<int>(), ctx->pairbits.as<uint32_t>(), d_ctr,
+                        p.rec_off, p.rec_len, p.rec_sup, p.rec_items, p.rec_db, p.rec_cap, p.rec_items_cap, roots,
+                        roots + rc, roots + 2 * rc, roots + 3 * rc);
             }
             cudaEventRecordWithFlags(ctx->ev[2], st, cudaEventRecordExternal);
             int rc_launch = FIM_OK;
@@ -795,7 +1062,7 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
         s.dfs_workers = (uint64_t)ctx->num_sms * (uint64_t)ctx->dfs_ctas_per_sm;
         s.launches_build = 0;
         s.launches_mine = ctx->launches - launches0;
-        s.pair_path = 0;
+        s.pair_path = pairs_tc ? 1u : 0u;
         // phases of the graph: build + singleton supports + rank, pairs +
         // finalize, DFS; then the compaction outside the graph
         s.ms_build = s.ms_singletons = s.ms_pairs = s.ms_dfs = 0.f;

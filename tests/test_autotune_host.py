@@ -40,3 +40,32 @@ def test_signature_buckets_by_log2():
     assert a == b and a != c
     assert a != autotune.signature("single", 1_000_000, 1000, 10_000_000, 1000, 2)
     assert a != autotune.signature("batched", 1_000_000, 1000, 10_000_000, 1000, 0)
+
+
+def test_coordinate_search_keeps_only_real_gains(monkeypatch):
+    # a fake cost surface: batch_pairs_shape 3 is 10% faster, build block 64
+    # 0.5% faster (below the 1% bar), everything else neutral
+    state = {}
+
+    def fake_apply(ctx, cfg):
+        state.clear()
+        state.update(cfg)
+
+    def fake_time(run, repeats):
+        t = 10.0
+        if state.get("batch_pairs_shape") == 3:
+            t *= 0.9
+        if state.get("batch_build_block") == 64:
+            t *= 0.995
+        return t
+
+    monkeypatch.setattr(autotune, "apply", fake_apply)
+    monkeypatch.setattr(autotune, "_time_ms", fake_time)
+    best, ms, table = autotune._coordinate_search(None, None, autotune.BATCH_SPACE, autotune.BATCH_DEFAULT, 1)
+    assert best["batch_pairs_shape"] == 3 and best["batch_build_block"] == 32
+    assert abs(ms - 9.0) < 1e-9
+    assert state == best  # the chosen shape is the one left applied
+    # every knob value was tried from the starting point, and only valid shapes
+    tried = {(k, c[k]) for c, _ in table for k in autotune.BATCH_SPACE}
+    assert all((k, v) in tried for k, vals in autotune.BATCH_SPACE.items() for v in vals)
+    assert all(autotune.valid(c) for c, _ in table)

@@ -1,0 +1,113 @@
+"""The batched pair pass on the tensor cores (the default) against the oracle
+and against the CUDA-core tiles (FIM_PAIRS_POPC): databases whose frequent
+items fill one 128 x 128 tile partly, exactly, or spill into several tiles
+(off-diagonal ones included), ragged transaction counts, and launch shapes
+that force many accumulator drains per tile and one CTA for every tile."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2412_19420_gb300 import datagen
+
+pytestmark = pytest.mark.gpu
+fim = pytest.importorskip("paper_2412_19420_gb300.fim")
+
+
+@pytest.fixture()
+def ctx():
+    c = fim.fim_create(0)
+    yield c
+    fim.fim_destroy(c)
+
+
+def _dense(n, m, p, seed):
+    """n transactions over m items, each item present with probability p: with
+    minsup 1 every item and pair is frequent, so m' = m."""
+    rng = np.random.default_rng(seed)
+    A = rng.random((n, m)) < p
+    rows = [np.nonzero(r)[0].tolist() for r in A]
+    return datagen.from_lists(rows, m)
+
+
+def _pair_batch():
+    # (n, m) pairs chosen so that m' = m crosses the tile edges 128 and 256
+    shapes = [(1, 2), (37, 3), (129, 64), (1000, 127), (777, 128), (300, 129), (2049, 200),
+              (513, 256), (260, 257), (131, 300), (4096, 130), (5, 400)]
+    dbs = [_dense(n, m, 0.3, [7, i]) for i, (n, m) in enumerate(shapes)]
+    return dbs, [1] * len(dbs)
+
+
+def _check(ctx, dbs, ms, max_len):
+    for d, (c, m) in enumerate(zip(dbs, ms)):
+        got = fim.fim_fetch_batched(ctx, d)
+        want = oracle.apriori(c.indptr, c.indices, c.m, m, max_len=max_len)
+        assert got.sha256() == want.sha256(), (d, c.n, c.m, len(got), len(want))
+
+
+@pytest.mark.parametrize("tuning", [{}, {"pairs_kdrain": 1}, {"pairs_kdrain": 3}, {"pairs_split": 1},
+                                    {"pairs_split": 5, "pairs_kdrain": 2}])
+def test_pairs_of_every_tile_shape(ctx, tuning):
+    for k, v in tuning.items():
+        fim.fim_set_tuning(ctx, k, v)
+    dbs, ms = _pair_batch()
+    fim.fim_mine_batched(ctx, dbs, ms, fim.FIM_MAXLEN(2))
+    assert fim.fim_get_stats(ctx)["pair_path"] == 1
+    _check(ctx, dbs, ms, 2)
+
+
+def test_tensor_and_cuda_core_pair_paths_agree(ctx):
+    dbs, ms = _pair_batch()
+    fim.fim_mine_batched(ctx, dbs, ms, fim.FIM_MAXLEN(2))
+    tc = [fim.fim_fetch_batched(ctx, d).sha256() for d in range(len(dbs))]
+    fim.fim_mine_batched(ctx, dbs, ms, fim.FIM_MAXLEN(2) | fim.FIM_PAIRS_POPC)
+    assert fim.fim_get_stats(ctx)["pair_path"] == 0
+    assert [fim.fim_fetch_batched(ctx, d).sha256() for d in range(len(dbs))] == tc
+
+
+def test_full_mines_with_thresholds(ctx):
+    # whole mines (pairs feed the prefix extension) on Zipf baskets whose
+    # frequent items span one to three tiles
+    dbs, ms = [], []
+    for i, (n, m, ppm) in enumerate([(3000, 150, 20_000), (20_000, 400, 5_000), (700, 90, 50_000),
+                                     (9000, 300, 4_000)]):
+        c = datagen.zipf_baskets(n, m, 0.6, 9.0, [11, i])
+        dbs.append(c)
+        ms.append(datagen.minsup_from_ppm(c.n, ppm))
+    fim.fim_set_tuning(ctx, "pairs_kdrain", 2)
+    fim.fim_mine_batched(ctx, dbs, ms)
+    _check(ctx, dbs, ms, 0)
+
+
+@pytest.mark.parametrize("shape", range(5))
+def test_every_pair_pass_shape_is_exact(ctx, shape):
+    fim.fim_set_tuning(ctx, "batch_pairs_shape", shape)
+    dbs, ms = _pair_batch()
+    fim.fim_mine_batched(ctx, dbs, ms, fim.FIM_MAXLEN(2))
+    _check(ctx, dbs, ms, 2)
+
+
+@pytest.mark.parametrize("block", [32, 64])
+def test_build_blocks_are_exact(ctx, block):
+    # ragged transaction counts around the 1,024 / 2,048-row blocks and the
+    # 4,096-row column padding; duplicates and empty rows
+    fim.fim_set_tuning(ctx, "batch_build_block", block)
+    rng = np.random.default_rng(block)
+    dbs, ms = [], []
+    for i, n in enumerate([1, 31, 1023, 1024, 1025, 2047, 2049, 4095, 4097, 9000]):
+        m = int(rng.integers(3, 400))
+        rows = [list(rng.integers(0, m, int(rng.integers(0, 9)))) for _ in range(n)]
+        c = datagen.from_lists(rows, m)
+        dbs.append(c)
+        ms.append(max(1, n // 40))
+    fim.fim_mine_batched(ctx, dbs, ms)
+    _check(ctx, dbs, ms, 0)
+
+
+def test_autotuned_batch_shape_is_exact(ctx):
+    from paper_2412_19420_gb300 import autotune
+    dbs = [datagen.batched_db(s) for s in datagen.batched_specs(64)]
+    ms = [datagen.minsup_from_ppm(c.n, 20_000) for c in dbs]
+    cfg, best_ms, table = autotune.tune_batched(ctx, dbs, ms, repeats=1)
+    assert set(autotune.BATCH_SPACE) <= set(cfg) and best_ms > 0 and len(table) >= 2
+    fim.fim_mine_batched(ctx, dbs, ms)
+    _check(ctx, dbs, ms, 0)

@@ -702,7 +702,8 @@ def _probes(fim, ctx):
     bandwidth (the L2-resident operands' ceiling) and the tcgen05 f8f6f4 MMA
     rate with A from tensor or shared memory."""
     return {"popc_word_pairs_per_s": fim.fim_probe(ctx, 0), "l2_read_gbs": fim.fim_probe(ctx, 1),
-            "mma_f8f6f4_tflops_a_tmem": fim.fim_probe(ctx, 2), "mma_f8f6f4_tflops_a_smem": fim.fim_probe(ctx, 3)}
+            "mma_f8f6f4_tflops_a_tmem": fim.fim_probe(ctx, 2), "mma_f8f6f4_tflops_a_smem": fim.fim_probe(ctx, 3),
+            "mma_f8f6f4_tflops_n128": fim.fim_probe(ctx, 4), "mma_f8f6f4_tflops_n64": fim.fim_probe(ctx, 5)}
 
 
 def _dfs_roofline(st, ms_dfs, workload, probes):

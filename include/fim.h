@@ -172,6 +172,15 @@ int fim_get_stats(const fim_ctx *ctx, fim_stats *out);
  *                                first (default 0)
  *   "learned_order"    0, 1      FIM_LEARNED also hands out the roots longest-
  *                                predicted-subtree first (default 0)
+ *   "root_sort"        0, 1      without the network's order, hand out the roots
+ *                                as the pair pass lists them (0) or most
+ *                                candidates first (1, default).  Either way a root whose
+ *                                class has no candidate is dropped before the
+ *                                prefix extension starts
+ *   "record_chunk"     1..1024   result slots a prefix-extension worker reserves
+ *                                at a time (default 1: exactly a class's sets);
+ *                                the ones a worker leaves unused are sorted out
+ *                                by the compaction
  *   "learned_kmin"     1..2^20   FIM_LEARNED consults the network only for classes
  *                                with at least this many candidates (default 8;
  *                                smaller ones are counted dense)
@@ -211,9 +220,9 @@ int fim_get_stats(const fim_ctx *ctx, fim_stats *out);
  *                                cluster's shared memory in one launch (default 1)
  *   "batch_pairs_shape" 0..4     launch shape of fim_mine_batched's tensor-core
  *                                pair pass: (operand stages in the ring, stages of
- *                                raw bits staged ahead, CTAs per SM) = 0 (4, 8, 1),
- *                                1 (4, 16, 1), 2 (2, 8, 2), 3 (2, 24, 1),
- *                                4 (3, 12, 1); default 0
+ *                                raw bits staged ahead, CTAs per SM) = 0 (8, 8, 1),
+ *                                1 (6, 8, 1), 2 (8, 16, 1), 3 (4, 8, 1),
+ *                                4 (7, 12, 1); default 0
  *   "batch_build_block" 32, 64   words of every column one CTA of fim_mine_batched's
  *                                build covers (32 x that many transactions); 64
  *                                applies where the block fits shared memory
@@ -419,7 +428,9 @@ int fim_pair_supports_noalloc(const int64_t *d_indptr, const int32_t *d_indices,
  *              f32 accumulator in tensor memory), in the pair pass's
  *              instruction shape 128 x 256 x 32 with A read from tensor
  *              memory: one CTA per SM, one thread issuing MMAs back to back;
- *   which = 3: the same with A read from shared memory.
+ *   which = 3: the same with A read from shared memory;
+ *   which = 4, 5: A from shared memory, N = 128 and N = 64 (the batched
+ *              pair pass's tile widths for databases with few frequent items).
  * Errors: FIM_E_INVAL (unknown probe, result NULL), FIM_E_NOMEM, FIM_E_CUDA,
  * FIM_E_TIMEOUT (the MMA probe's bounded wait ran out). */
 int fim_probe(fim_ctx *ctx, int which, double *result);

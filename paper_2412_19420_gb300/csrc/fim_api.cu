@@ -399,6 +399,7 @@ int mine_once(fim_ctx *ctx, uint32_t thr, uint32_t flags, MineState &ms, bool *r
         p.sparse_div = sparse_div;
         p.epoch = ctx->epoch.as<uint32_t>();
         p.learned_kmin = ctx->learned_kmin;
+        p.rec_chunk = ctx->rec_chunk;
         p.root_reverse = ctx->root_reverse;
         if (sp_items) {
             FIM_CUDA_TRY(cudaStreamWaitEvent(st, ctx->aux_ev[1], 0));
@@ -413,8 +414,10 @@ int mine_once(fim_ctx *ctx, uint32_t thr, uint32_t flags, MineState &ms, bool *r
         p.learned = (flags & FIM_LEARNED) ? 1 : 0;
         p.diffset_rule = (flags & FIM_DIFFSET_RULE) ? 1 : 0;
         p.mlp_w = ctx->mlp_wbf.as<__nv_bfloat16>();
-        if (p.learned && ctx->learned_order) {
-            FIM_TRY(launch_root_order(ctx, d_ctr, npairs));
+        {   // candidate-less roots dropped, the others ordered
+            const int mode = (p.learned && ctx->learned_order) ? 2 : ctx->root_sort;
+            FIM_TRY(reserve_root_plan(ctx, npairs));
+            FIM_TRY(launch_root_plan(ctx, d_ctr, npairs, nullptr, mode, st));
             p.root_order = ctx->root_order.as<uint32_t>();
         }
         p.trace = (flags & FIM_TRACE) ? 1 : 0;
@@ -456,9 +459,10 @@ int mine_once(fim_ctx *ctx, uint32_t thr, uint32_t flags, MineState &ms, bool *r
     }
     int lmax = c.max_len;
     if (ctx->shard == 0 && mf >= 1 && lmax < 1) lmax = 1;
-    if (ctx->shard == 0 && c.n_records > (unsigned long long)mf && lmax < 2) lmax = 2;
+    const unsigned long long n_sets = c.n_records - c.rec_holes;
+    if (ctx->shard == 0 && n_sets > (unsigned long long)mf && lmax < 2) lmax = 2;
     ctx->host_ctr.max_len = lmax;
-    FIM_TRY(launch_compact(ctx, c.n_records, 1, ctx->m));
+    FIM_TRY(launch_compact(ctx, c.n_records, n_sets, 1, ctx->m));
     cudaEventRecord(ctx->ev[4], st);
     FIM_CUDA_TRY(cudaStreamSynchronize(st));
     FIM_CUDA_TRY(cudaGetLastError());
@@ -503,7 +507,7 @@ int fim_mine(fim_ctx *ctx, uint64_t minsup, uint32_t flags) {
     s.n_trans = (uint64_t)ctx->n;
     s.n_items = (uint64_t)ctx->m;
     s.n_frequent_items = (uint64_t)ctx->mfreq;
-    s.n_sets = c.n_records;
+    s.n_sets = c.n_records - c.rec_holes;
     s.max_len = (uint64_t)c.max_len;
     s.supports_singletons = (uint64_t)ctx->m;
     const uint64_t mf = (uint64_t)ctx->mfreq;
@@ -593,6 +597,8 @@ int fim_set_tuning(fim_ctx *ctx, const char *key, int64_t v) {
         {"upload_streams", &ctx->upload_streams, 1, 2},
         {"batch_pairs_shape", &ctx->batch_pairs_shape, 0, kBatchPairsShapeCount - 1},
         {"batch_build_block", &ctx->batch_build_block, 32, 64},
+        {"root_sort", &ctx->root_sort, 0, 1},
+        {"record_chunk", &ctx->rec_chunk, 1, 1024},
     };
     for (const Knob &k : knobs)
         if (strcmp(k.name, key) == 0) {

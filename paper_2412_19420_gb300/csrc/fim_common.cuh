@@ -97,6 +97,11 @@ struct MineCounters {
     int m_freq;                      // m' (frequent items)
     int max_row_freq;                // most frequent items in one transaction
     int pad[3];
+    // DFS workers reserve record and item slots in chunks; the slots a
+    // worker leaves unused are holes (records of length 0, items nobody
+    // references), left out of the canonical output
+    unsigned long long rec_holes;
+    unsigned long long item_holes;
 };
 
 // A pushed prefix class: items (internal ids) + support + candidate list.
@@ -182,6 +187,7 @@ struct DfsParams {
     long long withhold_slot;        // test hook: this queue slot is never published (-1: none)
     int sparse_div;                 // store b_Y sparse when S(Y) * sparse_div <= nw (0: never)
     int learned_kmin;               // FIM_LEARNED consults the network for classes with >= this many candidates
+    int rec_chunk;                  // record slots a DFS worker reserves at a time (1: exactly per class)
     int root_reverse;               // hand out the root classes in reverse emission order
 };
 
@@ -269,6 +275,8 @@ struct fim_ctx {
     int pairs_kdrain = 0;       // stages (x128 transactions) per exact drain (0 = 64)
     int batch_pairs_shape = 0;  // launch shape of the batched tensor-core pair pass
     int batch_build_block = 32; // words per column a batched build CTA covers (32 or 64)
+    int root_sort = 1;          // root order without the network: 0 pair-pass order, 1 candidate count
+    int rec_chunk = 1;          // record slots a DFS worker reserves at a time
     int compact_cluster = 1;    // small outputs: sort in one cluster launch
     int csort_cl[5] = {0, 0, 0, 0, 0};  // cluster size per key width (0 unknown, -1 none)
     int debug_checks = 0;       // device-side invariant checks after build and mine
@@ -323,11 +331,19 @@ int reserve_sparse_items(fim_ctx *ctx, int mf, int64_t cap);
 int launch_sparse_items(fim_ctx *ctx, int mf, int64_t cap, cudaStream_t st);
 
 // k_mlp.cu: learned root order (longest predicted subtree first)
-int launch_root_order(fim_ctx *ctx, MineCounters *d_ctr, size_t npairs);
+// k_mlp.cu: drop the candidate-less roots, order the others (mode 0 about
+// the pair pass's order, 1 by candidate count, 2 by the network's predicted
+// subtree work); d_dbs = the batch's table, or null for a single database
+int reserve_root_plan(fim_ctx *ctx, size_t root_cap);
+int launch_root_plan(fim_ctx *ctx, MineCounters *d_ctr, size_t root_cap, const DbDesc *d_dbs, int mode,
+                     cudaStream_t st);
 
 // k_compact.cu
 // identity_items: the records already hold the caller's item ids (a merge)
-int launch_compact(fim_ctx *ctx, uint64_t n_records, int n_db, int m_max, bool identity_items = false);
+// Sorts records [0, n_records) into the canonical output; n_valid of them are
+// itemsets, the rest holes (length 0), which sort last and are left out.
+int launch_compact(fim_ctx *ctx, uint64_t n_records, uint64_t n_valid, int n_db, int m_max,
+                   bool identity_items = false);
 
 // k_csort.cu: the compactor's sort of a small output in one cluster launch
 int cluster_sort_plan(fim_ctx *ctx, uint64_t R, int kw, int *cl, int *cap, int *per);

@@ -9,10 +9,10 @@
 // an integer <= 2^22, exact in f32), as in the single-database pass.
 //
 // Work: the units are (database, ta, tb) with ta <= tb, the 128 x 128 tiles of
-// each database's item blocks, listed by the host in descending order of the
-// database's stage count (128 transactions per stage).  Which units hold pairs
-// depends on m'_d, known only on the device: a unit with 128 tb >= m'_d is
-// empty, and every role of the CTA skips it alike.  CTA c takes units c,
+// each database's item blocks, listed by the host tile number first and then
+// by descending stage count (128 transactions per stage) of the database.
+// Which units hold pairs depends on m'_d, known only on the device: a unit
+// with 128 tb >= m'_d is empty, and every role of the CTA skips it alike.  CTA c takes units c,
 // c + grid, c + 2 grid, ...: the longest first, so the persistent grid ends
 // nearly together.  A unit's K range runs in segments of at most kdrain
 // stages; each segment is one accumulator run, and the two accumulator
@@ -20,19 +20,25 @@
 //
 // CTA (416 threads):
 //   warps 0-3   A producers, one row each (item block ta): copy the row's
-//               bits 8 stages ahead into shared memory (cp.async, 64-byte
-//               runs), expand each bit to an e4m3 byte into the SWIZZLE_128B
-//               K-major A tile.  On a diagonal tile (ta == tb) the B tile is
+//               bits DEPTH stages ahead into shared memory (cp.async, 64-byte
+//               runs), expand each bit to an e4m3 byte and write the 128-byte
+//               row into tensor memory (tcgen05.st, lane = row; the MMA reads
+//               A from there).  On a diagonal tile (ta == tb) the B tile is
 //               also the A operand, and these warps only arrive;
-//   warps 4-7   B producers, one row each (item block tb), likewise;
+//   warps 4-7   B producers, one row each (item block tb): the same expansion
+//               into the SWIZZLE_128B K-major B tile of the stage's ring slot;
 //   warps 8-11  epilogue: per segment, tcgen05.ld the accumulator (warp q
 //               reads lane quarter q = rows 32q .. 32q + 31), convert to
 //               counts and write row a's counts for b > a: the first segment
 //               of a unit stores, later ones add (a thread owns its row);
 //   warp 12     one elected thread issues 4 MMAs (128 x N x 32, N = the
 //               tile's columns rounded up to 16) per stage.
-// Rows outside the tile's items are zero; a producer remembers which of its
-// ring slots already hold its zero row and does not rewrite them.
+// Tensor memory: two 128-column f32 accumulators, then one 32-column A slot
+// per ring stage.  Shared memory holds only the B ring, so the ring is deep
+// (the MMA -> producer round trip, not bandwidth, bounds a stage when a
+// tile's columns are few).  Rows outside the tile's items are zero; a B
+// producer remembers which of its ring slots already hold its zero row and
+// does not rewrite them.
 // Every mbarrier wait is bounded; on expiry the CTA records FIM_E_TIMEOUT,
 // lets its MMAs finish, frees its tensor memory and returns.
 #include <algorithm>
@@ -53,7 +59,9 @@ constexpr int BTHREADS = BNPROD + BNEPI + 32;
 constexpr int TILE_BYTES = BT * KB;    // 16 KB per operand tile and stage
 constexpr int BG = 2;                  // stages a producer publishes per fence
 constexpr uint32_t ACC_COLS = BT;      // one f32 accumulator: 128 columns; two buffers
-constexpr uint32_t BTMEM_COLS = 256;
+constexpr uint32_t A_COL = 2 * ACC_COLS;  // A slot of ring stage q: columns [A_COL + 32 q, + 32)
+constexpr uint32_t A_SLOT_COLS = KB / 4;
+constexpr uint32_t BTMEM_COLS = 512;
 constexpr int BKDRAIN_MAX = 32768;     // 2^22 transactions: partials stay <= 2^24
 constexpr unsigned long long BWAIT_NS = 2000000000ull;
 
@@ -61,7 +69,7 @@ constexpr unsigned long long BWAIT_NS = 2000000000ull;
 // ahead (a multiple of 4: copies go in quads of 4 stages).
 template <int STG, int DEPTH>
 struct __align__(1024) BtcSmem {
-    uint8_t a[STG][TILE_BYTES];
+    static_assert(A_COL + STG * A_SLOT_COLS <= BTMEM_COLS, "tensor memory layout");
     uint8_t b[STG][TILE_BYTES];
     uint4 stg[DEPTH][BNPROD];          // raw bits: producer t's row, stage k at stg[k % DEPTH][t]
     uint64_t full[STG];
@@ -136,7 +144,6 @@ batch_pairs_tc_kernel(const DbDesc *__restrict__ dbs, const unsigned long long *
         // ---------------- producers: one operand row each ----------------
         const bool is_a = threadIdx.x < BT;
         const int r = threadIdx.x & (BT - 1);
-        uint8_t(*const tiles)[TILE_BYTES] = is_a ? s.a : s.b;
         uint4 *const my = &s.stg[0][threadIdx.x];
         const int row0 = threadIdx.x - lane;  // the warp's first producer thread
         uint32_t zeroed = 0;                  // bit q: my row of ring slot q holds zeros
@@ -189,16 +196,28 @@ batch_pairs_tc_kernel(const DbDesc *__restrict__ dbs, const unsigned long long *
                     }
                     ok = __shfl_sync(0xffffffffu, wok, 0);
                     if (!ok) break;
-                    if (store) {
+                    if (is_a) {
+                        if (store) {  // off-diagonal tile: A rows into tensor memory
+                            tc_fence_after();  // after the MMAs that read these slots
+#pragma unroll
+                            for (int v = 0; v < BG; v++)
+                                if (v < cnt)
+                                    store_row_tmem(tmem + ((uint32_t)(warp * 32) << 16) +
+                                                       (A_COL + (uint32_t)((it + v) % BSTAGES) * A_SLOT_COLS),
+                                                   x[v]);
+                            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+                            tc_fence_before();
+                        }
+                    } else {
 #pragma unroll
                         for (int v = 0; v < BG; v++)
                             if (v < cnt) {
                                 const int sl = (it + v) % BSTAGES;
                                 if (col) {
-                                    store_row(tiles[sl], r, x[v]);
+                                    store_row(s.b[sl], r, x[v]);
                                     zeroed &= ~(1u << sl);
                                 } else if (!(zeroed & (1u << sl))) {
-                                    zero_row(tiles[sl], r);
+                                    zero_row(s.b[sl], r);
                                     zeroed |= 1u << sl;
                                 }
                             }
@@ -280,10 +299,16 @@ batch_pairs_tc_kernel(const DbDesc *__restrict__ dbs, const unsigned long long *
                     if (!(ok = bwait(s, &s.full[slot], (uint32_t)(it / BSTAGES) & 1u))) break;
                     tc_fence_after();
                     const uint32_t b0 = smem_addr(s.b[slot]);
-                    const uint32_t a0 = u.diag ? b0 : smem_addr(s.a[slot]);
+                    if (u.diag) {  // A is the B tile's 128 rows
 #pragma unroll
-                    for (int kk = 0; kk < KB / 32; kk++)
-                        mma_f8(d, sdesc(a0 + kk * 32), sdesc(b0 + kk * 32), idesc, (k == 0 && kk == 0) ? 0u : 1u);
+                        for (int kk = 0; kk < KB / 32; kk++)
+                            mma_f8(d, sdesc(b0 + kk * 32), sdesc(b0 + kk * 32), idesc, (k == 0 && kk == 0) ? 0u : 1u);
+                    } else {
+                        const uint32_t a0 = tmem + A_COL + (uint32_t)slot * A_SLOT_COLS;
+#pragma unroll
+                        for (int kk = 0; kk < KB / 32; kk++)  // 32 e4m3 elements = 8 columns per MMA
+                            mma_f8_ts(d, a0 + 8u * kk, sdesc(b0 + kk * 32), idesc, (k == 0 && kk == 0) ? 0u : 1u);
+                    }
                     mma_commit(&s.empty[slot]);
                 }
                 if (ok) mma_commit(&s.acc_full[buf]);
@@ -305,25 +330,41 @@ batch_pairs_tc_kernel(const DbDesc *__restrict__ dbs, const unsigned long long *
     }
 }
 
-// The batch's (database, tile) units in the order the pass takes them:
-// databases by descending stage count (ties by index), each database's
-// upper-triangle tiles of its n_items (an upper bound of m'_d) in row order.
-// Returns false when there are more than max_units of them.
 }  // namespace
 
+// The batch's (database, tile) units in the order the pass takes them.  The
+// upper-triangle tiles of a database's n_items (an upper bound of m'_d) are
+// numbered in row order; the units go by tile number first -- every
+// database's tile 0, then every tile 1, ... -- and within one tile number
+// by descending stage count (ties by database).  Tile 0 holds pairs whenever
+// m'_d >= 2, so the first units are all real work, longest first, and the
+// round-robin deal gives every CTA a fair share of it; the later tile numbers
+// are empty wherever m'_d is small.  Returns false when there are more than
+// max_units of them.
 bool batch_pairs_tc_units(const std::vector<DbDesc> &dbs, std::vector<unsigned long long> &units,
                           size_t max_units) {
     std::vector<int> order(dbs.size());
-    for (size_t d = 0; d < dbs.size(); d++) order[d] = (int)d;
+    size_t total = 0;
+    int max_tiles = 0;
+    for (size_t d = 0; d < dbs.size(); d++) {
+        order[d] = (int)d;
+        const int nt = (int)ceil_div64(dbs[d].m, BT);
+        total += (size_t)nt * (size_t)(nt + 1) / 2;
+        max_tiles = std::max(max_tiles, nt * (nt + 1) / 2);
+    }
+    if (total > max_units) return false;
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return dbs[x].nw > dbs[y].nw; });
     units.clear();
-    for (int d : order) {
-        const int nt = (int)ceil_div64(dbs[d].m, BT);
-        if ((size_t)nt * (size_t)(nt + 1) / 2 > max_units - units.size()) return false;
-        for (int ta = 0; ta < nt; ta++)
-            for (int tb = ta; tb < nt; tb++)
-                units.push_back(((unsigned long long)d << 32) | ((unsigned long long)ta << 16) | (unsigned)tb);
-    }
+    units.reserve(total);
+    for (int t = 0; t < max_tiles; t++)
+        for (int d : order) {
+            const int nt = (int)ceil_div64(dbs[d].m, BT);
+            if (t >= nt * (nt + 1) / 2) continue;
+            int ta = 0, r = t;  // tile t in row order: (ta, tb) with ta <= tb
+            while (r >= nt - ta) { r -= nt - ta; ta++; }
+            const int tb = ta + r;
+            units.push_back(((unsigned long long)d << 32) | ((unsigned long long)ta << 16) | (unsigned)tb);
+        }
     return true;
 }
 
@@ -334,15 +375,17 @@ int launch_shape(fim_ctx *ctx, const DbDesc *d_dbs, const unsigned long long *d_
                  cudaStream_t st) {
     using Smem = BtcSmem<STG, DEPTH>;
     static_assert(sizeof(Smem) + 1024 <= 232448, "shared memory per CTA");
-    // MINB CTAs share an SM: their tensor memory (256 columns each) and shared
-    // memory must fit it together
+    // MINB CTAs share an SM: their tensor memory and shared memory must fit
+    // it together
     static_assert(MINB * BTMEM_COLS <= 512, "tensor memory per SM");
-    static_assert(MINB == 1 ? sizeof(Smem) > 116 * 1024 : MINB * (sizeof(Smem) + 2048) <= 233472,
-                  "CTAs per SM as planned");
+    static_assert(MINB * (sizeof(Smem) + 2048) <= 233472, "CTAs per SM as planned");
     const int kd = ctx->pairs_kdrain > 0 ? ctx->pairs_kdrain : BKDRAIN_MAX;
     int64_t grid = ctx->pairs_split > 0 ? ctx->pairs_split : (int64_t)ctx->num_sms * MINB;
     if (grid > n_units) grid = n_units;
-    const size_t smem = sizeof(Smem) + 1024;
+    // one CTA per SM when MINB is 1: more shared memory than half an SM
+    // keeps a second CTA (and its tensor-memory allocation) off
+    size_t smem = sizeof(Smem) + 1024;
+    if (MINB == 1 && smem < 120 * 1024) smem = 120 * 1024;
     auto *kern = batch_pairs_tc_kernel<STG, DEPTH, MINB>;
     FIM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int *err = &ctx->counters.as<MineCounters>()->err;  // zeroed at the start of every batch
@@ -358,17 +401,17 @@ int launch_shape(fim_ctx *ctx, const DbDesc *d_dbs, const unsigned long long *d_
 // Launch shapes of the batched tensor-core pair pass (the "batch_pairs_shape"
 // knob): expanded operand stages in the ring, stages of raw bits staged
 // ahead, CTAs per SM.
-const int kBatchPairsShapes[][3] = {{4, 8, 1}, {4, 16, 1}, {2, 8, 2}, {2, 24, 1}, {3, 12, 1}};
+const int kBatchPairsShapes[][3] = {{8, 8, 1}, {6, 8, 1}, {8, 16, 1}, {4, 8, 1}, {7, 12, 1}};
 const int kBatchPairsShapeCount = (int)(sizeof(kBatchPairsShapes) / sizeof(kBatchPairsShapes[0]));
 
 int launch_batch_pairs_tc(fim_ctx *ctx, const DbDesc *d_dbs, const unsigned long long *d_units, int64_t n_units,
                           cudaStream_t st) {
     if (n_units <= 0) return FIM_OK;
     switch (ctx->batch_pairs_shape) {
-        case 1: return launch_shape<4, 16, 1>(ctx, d_dbs, d_units, n_units, st);
-        case 2: return launch_shape<2, 8, 2>(ctx, d_dbs, d_units, n_units, st);
-        case 3: return launch_shape<2, 24, 1>(ctx, d_dbs, d_units, n_units, st);
-        case 4: return launch_shape<3, 12, 1>(ctx, d_dbs, d_units, n_units, st);
-        default: return launch_shape<4, 8, 1>(ctx, d_dbs, d_units, n_units, st);
+        case 1: return launch_shape<6, 8, 1>(ctx, d_dbs, d_units, n_units, st);
+        case 2: return launch_shape<8, 16, 1>(ctx, d_dbs, d_units, n_units, st);
+        case 3: return launch_shape<4, 8, 1>(ctx, d_dbs, d_units, n_units, st);
+        case 4: return launch_shape<7, 12, 1>(ctx, d_dbs, d_units, n_units, st);
+        default: return launch_shape<8, 8, 1>(ctx, d_dbs, d_units, n_units, st);
     }
 }

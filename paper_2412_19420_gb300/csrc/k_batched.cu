@@ -134,10 +134,20 @@ batch_build_rows_kernel(const DbDesc *__restrict__ dbs, int n_db, const int64_t 
             }
             uint32_t *const trow = tile + g * ms;
             const uint32_t bit = 1u << lane;
-            for (int64_t e = e0; e < e1; e++) {
-                const int32_t it = __ldg(D.indices + e);
-                if ((unsigned)it >= (unsigned)m) { bad = 1; continue; }
-                atomicOr(trow + it, bit);
+            // four independent loads in flight per lane
+            for (int64_t e = e0; e < e1; e += 4) {
+                int32_t it[4];
+#pragma unroll
+                for (int u = 0; u < 4; u++) it[u] = e + u < e1 ? __ldg(D.indices + e + u) : 0;
+#pragma unroll
+                for (int u = 0; u < 4; u++)
+                    if (e + u < e1) {
+                        if ((unsigned)it[u] >= (unsigned)m) {
+                            bad = 1;
+                            continue;
+                        }
+                        atomicOr(trow + it[u], bit);
+                    }
             }
         }
     }
@@ -617,7 +627,10 @@ batch_finalize_kernel(const DbDesc *__restrict__ dbs, int n_db, const int64_t *_
 __global__ void db_count_kernel(const uint32_t *__restrict__ rec_db, unsigned long long R,
                                 unsigned long long *__restrict__ cnt) {
     const unsigned long long r = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r < R) atomicAdd(&cnt[rec_db[r]], 1ull);
+    if (r < R) {
+        const uint32_t d = rec_db[r];
+        if (d != 0xFFFFFFFFu) atomicAdd(&cnt[d], 1ull);  // holes carry no database
+    }
 }
 
 __global__ void __launch_bounds__(1024)
@@ -803,6 +816,11 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
     FIM_TRY(fim_reserve(ctx, ctx->frame_sups, sizeof(uint32_t) * (size_t)workers * frame_pool));
     FIM_TRY(prepare_task_queue(ctx, sizeof(Task) * kTaskCap));
     FIM_TRY(fim_reserve(ctx, ctx->cand_pool, sizeof(uint32_t) * kCandPoolCap));
+    FIM_TRY(reserve_root_plan(ctx, (size_t)(L.root_cap ? L.root_cap : 1)));
+    // roots without candidates are dropped before the DFS; the others ordered
+    // by the network's predicted work (FIM_LEARNED with learned_order) or as
+    // root_sort says
+    const int plan_mode = ((flags & FIM_LEARNED) && ctx->learned_order) ? 2 : ctx->root_sort;
     if (pairs_tc)
         FIM_TRY(fim_reserve(ctx, ctx->batch_units, sizeof(unsigned long long) * (pair_units.size() ? pair_units.size() : 1)));
     if (ctx->rec_cap < (1ull << 22)) {
@@ -852,7 +870,7 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
         p.root_b = roots + rc;
         p.root_sup = roots + 2 * rc;
         p.root_db = roots + 3 * rc;
-        p.root_order = nullptr;
+        p.root_order = ctx->root_order.as<uint32_t>();
         p.tasks = ctx->tasks.as<Task>();
         p.task_cap = kTaskCap;
         p.cand_pool = ctx->cand_pool.as<uint32_t>();
@@ -879,6 +897,7 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
         p.sparse_div = ctx->sparse_div > 0 ? ctx->sparse_div : 0;  // automatic: dense (small databases)
         p.epoch = ctx->epoch.as<uint32_t>();
         p.learned_kmin = ctx->learned_kmin;
+        p.rec_chunk = ctx->rec_chunk;
         p.root_reverse = ctx->root_reverse;
 
         // graph key: everything the captured launches depend on
@@ -895,8 +914,8 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
         mix(&pairs_tc, sizeof(pairs_tc));
         mix(&wbk, sizeof(wbk));
         // every launch-shape knob the captured launches depend on
-        const int shape[6] = {workers, ctx->dfs_block, ctx->pairs_kdrain, ctx->pairs_split, ctx->batch_pairs_shape,
-                              ctx->dfs_ctas_per_sm};
+        const int shape[8] = {workers, ctx->dfs_block, ctx->pairs_kdrain, ctx->pairs_split, ctx->batch_pairs_shape,
+                              ctx->dfs_ctas_per_sm, plan_mode, ctx->learned_order};
         mix(shape, sizeof(shape));
         if (pairs_tc) {
             const void *up = ctx->batch_units.p;
@@ -989,7 +1008,10 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
             }
             cudaEventRecordWithFlags(ctx->ev[2], st, cudaEventRecordExternal);
             int rc_launch = FIM_OK;
-            if (maxlen == 0 || maxlen >= 3) rc_launch = launch_dfs(ctx, p, workers, ctx->dfs_block);
+            if (maxlen == 0 || maxlen >= 3) {
+                rc_launch = launch_root_plan(ctx, d_ctr, rc, d_dbs, plan_mode, st);
+                if (rc_launch == FIM_OK) rc_launch = launch_dfs(ctx, p, workers, ctx->dfs_block);
+            }
             const cudaError_t ce = cudaStreamEndCapture(st, &g);
             if (rc_launch != FIM_OK) { if (g) cudaGraphDestroy(g); return rc_launch; }
             if (ce != cudaSuccess) { fim_set_cuda_error(ce, "capture", __FILE__, __LINE__); return FIM_E_CUDA; }
@@ -999,7 +1021,7 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
             if (ie != cudaSuccess) { fim_set_cuda_error(ie, "instantiate", __FILE__, __LINE__); return FIM_E_CUDA; }
             ctx->batch_graph_exec = ex;
             ctx->batch_graph_key = key;
-            ctx->batch_graph_launches = 6;  // build, support, rank, pairs, finalize, DFS
+            ctx->batch_graph_launches = 9;  // build, rank, pairs, finalize, 3 root plan, DFS, epoch
         }
         FIM_CUDA_TRY(cudaGraphLaunch((cudaGraphExec_t)ctx->batch_graph_exec, st));
         ctx->launches += ctx->batch_graph_launches;
@@ -1017,7 +1039,7 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
             continue;  // buffers grow; the new pointers give a new graph key
         }
         // ---- canonical order by (database, size, items) ----------------------
-        FIM_TRY(launch_compact(ctx, c.n_records, n_db, L.m_max > 0 ? L.m_max : 1));
+        FIM_TRY(launch_compact(ctx, c.n_records, c.n_records - c.rec_holes, n_db, L.m_max > 0 ? L.m_max : 1));
         FIM_TRY(fim_reserve(ctx, ctx->batch_slices, sizeof(unsigned long long) * 2 * (size_t)(n_db + 1)));
         unsigned long long *cnt = ctx->batch_slices.as<unsigned long long>();
         unsigned long long *istart = cnt + (n_db + 1);
@@ -1045,7 +1067,7 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
         s.n_trans = 0;
         for (int d = 0; d < n_db; d++) s.n_trans += (uint64_t)in[d].n_trans;
         s.n_items = (uint64_t)L.items;
-        s.n_sets = c.n_records;
+        s.n_sets = c.n_records - c.rec_holes;
         s.max_len = (uint64_t)c.max_len;
         s.supports_singletons = (uint64_t)L.items;
         s.supports_pairs = 0;  // sum over databases of m'(m'-1)/2: filled below

@@ -34,8 +34,12 @@ __global__ void prep_keys_kernel(unsigned long long R, const unsigned long long 
     const unsigned long long r = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= R) return;
     idx[r] = (uint32_t)r;
-    const unsigned long long off = rec_off[r];
     const int len = (int)rec_len[r];
+    if (len == 0) {  // a hole: the largest key, after every itemset
+        for (int w = 0; w < kw; w++) keys[(unsigned long long)w * R + r] = ~0ull;
+        return;
+    }
+    const unsigned long long off = rec_off[r];
     const uint32_t db = db_bits ? rec_db[r] : 0u;
     uint32_t *it = items + off;
     if (perm_base) {  // null: the items are already the caller's ids
@@ -308,14 +312,15 @@ int bits_for(int m) {
 
 }  // namespace
 
-int launch_compact(fim_ctx *ctx, uint64_t R, int n_db, int m_max, bool identity_items) {
+int launch_compact(fim_ctx *ctx, uint64_t R, uint64_t R_valid, int n_db, int m_max, bool identity_items) {
     cudaStream_t st = ctx->stream;
     const int db_bits = n_db > 1 ? bits_for(n_db) : 0;
-    const unsigned long long total_items = ctx->host_ctr.n_rec_items;
+    // items of the itemsets (the record pool's holes excluded)
+    const unsigned long long total_items = ctx->host_ctr.n_rec_items - ctx->host_ctr.item_holes;
     FIM_TRY(fim_reserve(ctx, ctx->out_off, sizeof(unsigned long long) * (R + 1)));
     FIM_TRY(fim_reserve(ctx, ctx->out_items, sizeof(uint32_t) * (total_items ? total_items : 1)));
     FIM_TRY(fim_reserve(ctx, ctx->out_sup, sizeof(uint32_t) * (R ? R : 1)));
-    ctx->out_sets = R;
+    ctx->out_sets = R_valid;  // the holes sort after every itemset: emitted last, never fetched
     ctx->out_items_total = total_items;
     if (R == 0) {
         FIM_CUDA_TRY(cudaMemsetAsync(ctx->out_off.p, 0, sizeof(unsigned long long), st));

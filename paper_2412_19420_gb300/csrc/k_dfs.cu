@@ -35,6 +35,8 @@ constexpr int MAXPATH = 256;             // longest itemset a worker tracks
 constexpr int V = 2;                     // uint4 per lane per chunk (chunk = 256 words)
 constexpr int CHUNK = 128 * V;
 constexpr int NF = FIM_MLP_FEATURES;
+constexpr int PCAP = 1024;               // perm entries a worker keeps in shared memory
+constexpr unsigned ICH = 1024;           // item slots a worker reserves at a time
 
 // The database of the task a worker is on.
 struct DbView {
@@ -50,6 +52,7 @@ struct DbView {
 
 struct Smem {
     DbView db;
+    int32_t perm_c[PCAP];                // the task database's perm[0 .. min(m', PCAP))
     const uint32_t *src[MAXSRC];
     const uint32_t *cptr[CB];
     uint32_t sup[CB];
@@ -81,6 +84,8 @@ struct Smem {
     unsigned int iter;                   // classes since the worker started
     unsigned long long ticket;
     unsigned long long rbase, ibase;
+    unsigned long long rec_next, rec_end;   // this worker's reserved record slots
+    unsigned long long it_next, it_end;     // and item slots (thread 0 alone)
     int flag;
     int hungry;
     int kc;                              // candidates of the child being set up (-1: overflow)
@@ -125,8 +130,11 @@ __device__ __forceinline__ bool pairbit(const DbView &d, uint32_t a, uint32_t b)
     return (__ldg(d.pairbits + (int64_t)a * d.mpw + (b >> 5)) >> (b & 31)) & 1u;
 }
 
-__device__ __forceinline__ const uint32_t *column(const DbView &d, uint32_t item) {
-    return d.bm + (int64_t)__ldg(d.perm + item) * d.nwp;
+// Bit column of internal item `item` (< m') of the task's database: its
+// perm entry from shared memory when cached, else from global memory.
+__device__ __forceinline__ const uint32_t *column(const Smem &s, uint32_t item) {
+    const int32_t j = item < (uint32_t)PCAP ? s.perm_c[item] : __ldg(s.db.perm + item);
+    return s.db.bm + (int64_t)j * s.db.nwp;
 }
 
 __device__ void set_err(const DfsParams &p, int code) { atomicCAS(&p.ctr->err, 0, code); }
@@ -401,6 +409,50 @@ __device__ __forceinline__ void sparse_sweep(const DfsParams &p, Smem &s, int kb
         }
 }
 
+// Thread 0: record and item slots for tot itemsets of nitems items in all.
+// A worker reserves slots in chunks (one returning global atomic per chunk,
+// not per class); when a chunk cannot hold the class, its unused slots
+// become holes -- records of length 0, which the compactor sorts after every
+// itemset and leaves out -- and a new chunk is reserved.
+__device__ __noinline__ void retire_records(const DfsParams &p, Smem &s) {
+    const unsigned long long h = s.rec_end - s.rec_next;
+    if (h) {
+        for (unsigned long long r = s.rec_next; r < s.rec_end; r++)
+            if (r < p.rec_cap) {
+                p.rec_len[r] = 0u;
+                p.rec_db[r] = 0xFFFFFFFFu;
+            }
+        atomicAdd(&p.ctr->rec_holes, h);
+    }
+    s.rec_next = s.rec_end;
+}
+
+__device__ __noinline__ void retire_slots(const DfsParams &p, Smem &s) {
+    retire_records(p, s);
+    if (s.it_end > s.it_next) atomicAdd(&p.ctr->item_holes, s.it_end - s.it_next);
+    s.it_next = s.it_end;
+}
+
+__device__ __forceinline__ void reserve_slots(const DfsParams &p, Smem &s, unsigned tot, unsigned long long nitems,
+                                           unsigned long long *rb, unsigned long long *ib) {
+    if (s.rec_next + tot > s.rec_end) {
+        retire_records(p, s);
+        const unsigned long long want = tot > (unsigned)p.rec_chunk ? tot : (unsigned)p.rec_chunk;
+        s.rec_next = atomicAdd(&p.ctr->n_records, want);
+        s.rec_end = s.rec_next + want;
+    }
+    if (s.it_next + nitems > s.it_end) {
+        if (s.it_end > s.it_next) atomicAdd(&p.ctr->item_holes, s.it_end - s.it_next);
+        const unsigned long long want = nitems > ICH ? nitems : ICH;
+        s.it_next = atomicAdd(&p.ctr->n_rec_items, want);
+        s.it_end = s.it_next + want;
+    }
+    *rb = s.rec_next;
+    *ib = s.it_next;
+    s.rec_next += tot;
+    s.it_next += nitems;
+}
+
 template <int NT>
 __device__ int class_pass(const DfsParams &p, Smem &s, const uint32_t *cand, const uint32_t *psup,
                           int k, int plen, uint32_t *fi, uint32_t *fs) {
@@ -418,7 +470,7 @@ __device__ int class_pass(const DfsParams &p, Smem &s, const uint32_t *cand, con
     for (int b0 = 0; b0 < k; b0 += CB) {
         const int kb = min(CB, k - b0);
         for (int c = threadIdx.x; c < kb; c += NT) {
-            s.cptr[c] = column(db, cand[b0 + c]);
+            s.cptr[c] = column(s, cand[b0 + c]);
             s.sup[c] = 0;
         }
         __syncthreads();
@@ -440,10 +492,7 @@ __device__ int class_pass(const DfsParams &p, Smem &s, const uint32_t *cand, con
                 const uint32_t tot = __popc(bal);
                 if (tot) {
                     unsigned long long rb = 0, ib = 0;
-                    if (lane == 0) {
-                        rb = atomicAdd(&p.ctr->n_records, (unsigned long long)tot);
-                        ib = atomicAdd(&p.ctr->n_rec_items, (unsigned long long)tot * (plen + 1));
-                    }
+                    if (lane == 0) reserve_slots(p, s, tot, (unsigned long long)tot * (plen + 1), &rb, &ib);
                     rb = __shfl_sync(0xffffffffu, rb, 0);
                     ib = __shfl_sync(0xffffffffu, ib, 0);
                     if (f) {
@@ -482,10 +531,7 @@ __device__ int class_pass(const DfsParams &p, Smem &s, const uint32_t *cand, con
             uint32_t tot;
             const uint32_t pos = block_scan<NT>(s, f, &tot);
             if (tot) {
-                if (threadIdx.x == 0) {
-                    s.rbase = atomicAdd(&p.ctr->n_records, (unsigned long long)tot);
-                    s.ibase = atomicAdd(&p.ctr->n_rec_items, (unsigned long long)tot * (plen + 1));
-                }
+                if (threadIdx.x == 0) reserve_slots(p, s, tot, (unsigned long long)tot * (plen + 1), &s.rbase, &s.ibase);
                 __syncthreads();
                 if (f) {
                     fi[nF + pos] = item;
@@ -737,6 +783,8 @@ dfs_kernel(const DfsParams p) {
         s.epoch = *(volatile const uint32_t *)p.epoch;
         s.err_seen = 0;
         s.iter = 0;
+        s.rec_next = s.rec_end = 0;
+        s.it_next = s.it_end = 0;
     }
 
     while (true) {
@@ -751,7 +799,8 @@ dfs_kernel(const DfsParams p) {
                 // roots come out of the pair pass by ascending first item, i.e.
                 // ascending item support; root_reverse hands out the pairs of
                 // the most frequent items (the largest subtrees) first
-                const unsigned long long rt = p.root_order ? p.root_order[t] : (p.root_reverse ? nr - 1 - t : t);
+                const unsigned long long tt = p.root_reverse ? nr - 1 - t : t;
+                const unsigned long long rt = p.root_order ? p.root_order[tt] : tt;
                 s.path[0] = p.root_a[rt];
                 s.path[1] = p.root_b[rt];
                 s.task_len = 2;
@@ -804,6 +853,9 @@ dfs_kernel(const DfsParams p) {
         }
         __syncthreads();
         if (!s.flag) break;
+        // the task database's perm, for the column pointers of its classes
+        // (the barriers of the candidate setup below publish it)
+        for (int i = threadIdx.x; i < min(s.db.mfreq, PCAP); i += NT) s.perm_c[i] = __ldg(s.db.perm + i);
 
         // ---- level 0: the task's own class ---------------------------
         const int tlen = s.task_len;
@@ -829,7 +881,7 @@ dfs_kernel(const DfsParams p) {
             if (p.trace || infer) class_features(s, tlen, s.task_sup, supX, fs, root ? k : 0, s.feat[0]);
             const int diff = root ? choose_diff(p, s, s.feat[0], s.task_sup, supX, infer) : 0;
             if (threadIdx.x == 0) {
-                for (int r = 0; r < tlen; r++) s.src[r] = column(s.db, s.path[r]);
+                for (int r = 0; r < tlen; r++) s.src[r] = column(s, s.path[r]);
                 s.nsrc = tlen;
                 s.diff = diff;
                 s.psparse = 0;
@@ -868,10 +920,20 @@ dfs_kernel(const DfsParams p) {
             int L = 0;
             while (L >= 0) {
                 // the error flag is read with the queue counters at each push
-                // decision; a class without one re-reads it every 16 classes
+                // decision; a class without one re-reads it every 16 classes.
+                // The counters are loaded here, before the barrier and the
+                // sibling gather, and first used after them: their round trip
+                // overlaps that work instead of adding to it
+                int q_err = 0;
+                unsigned long long q_ticket = 0, q_tail = 0;
                 if (threadIdx.x == 0) {
                     if ((++s.iter & 15u) == 0u) s.err_seen = *(volatile int *)&p.ctr->err;
                     s.stop = s.err_seen != 0;
+                    if (tlen + L + 1 <= p.split_depth && tlen + L + 1 <= FIM_TASK_MAXR) {
+                        q_err = *(volatile int *)&p.ctr->err;
+                        q_ticket = *(volatile unsigned long long *)&p.ctr->ticket;
+                        q_tail = *(volatile unsigned long long *)&p.ctr->qtail;
+                    }
                 }
                 __syncthreads();
                 if (s.stop) break;
@@ -929,14 +991,12 @@ dfs_kernel(const DfsParams p) {
                     }
                 }
                 if (threadIdx.x == 0 && may_push) {
-                    // the queue's hunger and the error flag: three loads, one
-                    // round trip, published by the barrier below (s.hungry,
-                    // not s.flag: thread 0 rewrites s.flag inside try_push)
-                    const int e = *(volatile int *)&p.ctr->err;
-                    const unsigned long long t = *(volatile unsigned long long *)&p.ctr->ticket;
-                    const unsigned long long q = *(volatile unsigned long long *)&p.ctr->qtail;
-                    s.hungry = t > s.n_roots + q;
-                    s.err_seen = e;
+                    // the queue's hunger and the error flag, loaded at the top
+                    // of this iteration, published by the barrier below
+                    // (s.hungry, not s.flag: thread 0 rewrites s.flag inside
+                    // try_push)
+                    s.hungry = q_ticket > s.n_roots + q_tail;
+                    s.err_seen = q_err;
                 }
                 __syncthreads();
                 kc = s.kc;
@@ -958,7 +1018,7 @@ dfs_kernel(const DfsParams p) {
                     uint32_t *lv = stk + (int64_t)L * p.nwp_max;  // b_X, the class at level L
                     s.path[plen] = citem;
                     s.src[0] = lv;
-                    s.src[1] = column(s.db, citem);
+                    s.src[1] = column(s, citem);
                     s.nsrc = 2;
                     s.psparse = s.lz[L] >= 0;
                     s.pz = s.lz[L];
@@ -991,6 +1051,7 @@ dfs_kernel(const DfsParams p) {
         }
     }
     if (threadIdx.x == 0) {
+        retire_slots(p, s);  // the worker's unused slots become holes
         atomicAdd(&p.ctr->busy_ns, s.busy);
         atomicAdd(&p.ctr->root_ns, s.root_busy);
         atomicMax(&p.ctr->t_last, globaltimer_ns());

@@ -194,61 +194,98 @@ __global__ void to_bf16_kernel(const float *__restrict__ w, __nv_bfloat16 *__res
     if (j < P) o[j] = __float2bfloat16_rn(w[j]);
 }
 
-// ---- learned root order: longest predicted subtree first -------------------
-// Root {a, b}: the features of its class (as the DFS computes them), the
-// bf16 MLP's y0, then a descending bucket sort on round(4 * y0).
+// ---- root plan: drop the roots without candidates, order the rest ---------
+// A root {a, b} roots the prefix class of the sets whose two smallest items
+// are a and b; its candidates are the c > b with {a, c} and {b, c} frequent
+// (a row AND of the pair bitsets).  A root without candidates has no subtree,
+// so it is dropped before the prefix extension starts: no worker spends a
+// task fetch on it.  The others are ordered by a bucket sort on a priority,
+// largest first: the scheduling network's predicted subtree work (the bf16
+// MLP's y0 on the root class's features, as the DFS computes them), or the
+// candidate count, or none (bucket 0: about the pair pass's order).
 constexpr int NBUCKET = 256;
+constexpr uint8_t DROP = NBUCKET - 1;
+
+struct RootView {
+    const uint32_t *pairbits;
+    const int *pair_cnt;
+    const uint32_t *item_sup;
+    const int32_t *perm;
+    int64_t n, nw;
+    int mf, mpw;
+    uint32_t thr;
+};
+
 __global__ void __launch_bounds__(256)
-root_predict_kernel(const uint32_t *__restrict__ root_a, const uint32_t *__restrict__ root_b,
-                    const uint32_t *__restrict__ root_sup, const MineCounters *ctr,
-                    const uint32_t *__restrict__ pairbits, int mpw, const int *__restrict__ pair_cnt, int mf,
-                    const uint32_t *__restrict__ item_sup, const int32_t *__restrict__ perm, int64_t n, int64_t nw,
-                    uint32_t thr, const __nv_bfloat16 *__restrict__ wbf, uint8_t *__restrict__ bucket,
-                    uint32_t *__restrict__ hist) {
+root_plan_kernel(const uint32_t *__restrict__ root_a, const uint32_t *__restrict__ root_b,
+                 const uint32_t *__restrict__ root_sup, const uint32_t *__restrict__ root_db,
+                 const MineCounters *ctr, const DbDesc *__restrict__ dbs, RootView single, int mode,
+                 const __nv_bfloat16 *__restrict__ wbf, uint8_t *__restrict__ bucket, uint32_t *__restrict__ hist) {
     __shared__ float w[P];
     __shared__ uint32_t h[NBUCKET];
-    for (int i = threadIdx.x; i < P; i += blockDim.x) w[i] = __bfloat162float(wbf[i]);
+    if (mode == 2)
+        for (int i = threadIdx.x; i < P; i += blockDim.x) w[i] = __bfloat162float(wbf[i]);
     for (int i = threadIdx.x; i < NBUCKET; i += blockDim.x) h[i] = 0;
     __syncthreads();
     const unsigned long long nr = ctr->n_roots;
-    const unsigned long long r = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r < nr) {
-        const uint32_t a = root_a[r], bb = root_b[r], sy = root_sup[r];
-        const uint32_t sx = item_sup[perm[a]];
-        // candidates c > b with {a,c}, {b,c} frequent, and the mean S({a,c})
+    for (unsigned long long r = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; r < nr;
+         r += (unsigned long long)gridDim.x * blockDim.x) {
+        RootView v = single;
+        if (dbs) {  // a batch: the root's database
+            const DbDesc &D = dbs[root_db[r]];
+            v.mf = *(volatile const int32_t *)&D.mfreq;
+            v.mpw = (v.mf + 31) / 32;
+            v.pairbits = single.pairbits + D.pb_off;
+            v.pair_cnt = single.pair_cnt + D.pair_off;
+            v.item_sup = single.item_sup + D.item_off;
+            v.perm = single.perm + D.item_off;
+            v.n = D.n;
+            v.nw = D.nw;
+            v.thr = D.thr;
+        }
+        const uint32_t a = root_a[r], bb = root_b[r];
+        const uint32_t *ra = v.pairbits + (int64_t)a * v.mpw, *rbp = v.pairbits + (int64_t)bb * v.mpw;
         int k = 0;
         float ps = 0.f;
-        const uint32_t *ra = pairbits + (int64_t)a * mpw, *rbp = pairbits + (int64_t)bb * mpw;
-        for (int wd = (int)(bb >> 5); wd < mpw; wd++) {
+        for (int wd = (int)(bb >> 5); wd < v.mpw; wd++) {
             uint32_t bits = ra[wd] & rbp[wd];
             if (wd == (int)(bb >> 5)) bits &= 0xFFFFFFFEu << (bb & 31);
-            while (bits) {
-                const int c = wd * 32 + __ffs(bits) - 1;
-                bits &= bits - 1;
-                ps += (float)pair_cnt[(int64_t)a * mf + c];
-                k++;
+            k += __popc(bits);
+            if (mode == 2)
+                while (bits) {
+                    const int c = wd * 32 + __ffs(bits) - 1;
+                    bits &= bits - 1;
+                    ps += (float)v.pair_cnt[(int64_t)a * v.mf + c];
+                }
+        }
+        uint8_t bq = DROP;
+        if (k > 0 && mode == 1) {
+            bq = (uint8_t)(254 - (k < 254 ? k : 254));  // more candidates first
+        } else if (k > 0 && mode == 2) {
+            const uint32_t sy = root_sup[r], sx = v.item_sup[v.perm[a]];
+            const float fx = sx > 0 ? (float)sx : 1.f, fy = sy > 0 ? (float)sy : 1.f;
+            // the DFS kernel's feature vector of the root class (same scaling)
+            float x[8] = {2.f / 16.f, log2f(1.f + (float)sy) / 32.f, (float)sy / (float)(v.n > 0 ? v.n : 1),
+                          log2f(1.f + (float)k) / 16.f, (float)sy / fx, ps / ((float)k * fx),
+                          log2f(1.f + (float)v.nw) / 32.f, (float)v.thr / fy};
+            float h1[64];
+            for (int i = 0; i < 64; i++) {
+                float acc = w[OFF_B1 + i];
+                for (int q = 0; q < 8; q++) acc = fmaf(w[i * 8 + q], __bfloat162float(__float2bfloat16_rn(x[q])), acc);
+                h1[i] = __bfloat162float(__float2bfloat16_rn(fmaxf(acc, 0.f)));
             }
+            float y0 = w[OFF_B3];
+            for (int i = 0; i < 64; i++) {
+                float acc = w[OFF_B2 + i];
+                for (int q = 0; q < 64; q++) acc = fmaf(w[OFF_W2 + i * 64 + q], h1[q], acc);
+                y0 = fmaf(w[OFF_W3 + i], __bfloat162float(__float2bfloat16_rn(fmaxf(acc, 0.f))), y0);
+            }
+            int q = (int)lrintf(4.f * y0);  // predicted log2(1 + subtree words), quarter steps
+            q = q < 0 ? 0 : (q > 254 ? 254 : q);
+            bq = (uint8_t)(254 - q);  // most predicted work first
+        } else if (k > 0) {
+            bq = 0;
         }
-        const float fx = sx > 0 ? (float)sx : 1.f, fy = sy > 0 ? (float)sy : 1.f;
-        // the DFS kernel's feature vector of the root class (same scaling)
-        float x[8] = {2.f / 16.f, log2f(1.f + (float)sy) / 32.f, (float)sy / (float)(n > 0 ? n : 1),
-                      log2f(1.f + (float)k) / 16.f, (float)sy / fx, k > 0 ? ps / ((float)k * fx) : 0.f,
-                      log2f(1.f + (float)nw) / 32.f, (float)thr / fy};
-        float h1[64];
-        for (int i = 0; i < 64; i++) {
-            float acc = w[OFF_B1 + i];
-            for (int q = 0; q < 8; q++) acc = fmaf(w[i * 8 + q], __bfloat162float(__float2bfloat16_rn(x[q])), acc);
-            h1[i] = __bfloat162float(__float2bfloat16_rn(fmaxf(acc, 0.f)));
-        }
-        float y0 = w[OFF_B3];
-        for (int i = 0; i < 64; i++) {
-            float acc = w[OFF_B2 + i];
-            for (int q = 0; q < 64; q++) acc = fmaf(w[OFF_W2 + i * 64 + q], h1[q], acc);
-            y0 = fmaf(w[OFF_W3 + i], __bfloat162float(__float2bfloat16_rn(fmaxf(acc, 0.f))), y0);
-        }
-        int q = k == 0 ? 0 : (int)lrintf(4.f * y0);
-        q = q < 0 ? 0 : (q >= NBUCKET ? NBUCKET - 1 : q);
-        const uint8_t bq = (uint8_t)(NBUCKET - 1 - q);  // descending predicted work
         bucket[r] = bq;
         atomicAdd(&h[bq], 1u);
     }
@@ -257,41 +294,69 @@ root_predict_kernel(const uint32_t *__restrict__ root_a, const uint32_t *__restr
         if (h[i]) atomicAdd(&hist[i], h[i]);
 }
 
-__global__ void bucket_scan_kernel(uint32_t *hist) {
+// Exclusive scan of the bucket counts; the dropped roots leave the root
+// count and the pending-task count.  hist[NBUCKET] keeps the count before.
+__global__ void root_plan_scan_kernel(uint32_t *hist, MineCounters *ctr) {
     if (threadIdx.x == 0) {
+        const unsigned long long total = ctr->n_roots;
+        const uint32_t dropped = hist[DROP];
         uint32_t acc = 0;
         for (int i = 0; i < NBUCKET; i++) { const uint32_t v = hist[i]; hist[i] = acc; acc += v; }
+        hist[NBUCKET] = (uint32_t)total;
+        ctr->n_roots = total - dropped;
+        ctr->pending -= (long long)dropped;
     }
 }
 
-__global__ void bucket_scatter_kernel(const MineCounters *ctr, const uint8_t *__restrict__ bucket,
-                                      uint32_t *__restrict__ hist, uint32_t *__restrict__ order) {
-    const unsigned long long r = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r < ctr->n_roots) order[atomicAdd(&hist[bucket[r]], 1u)] = (uint32_t)r;
+__global__ void root_plan_scatter_kernel(const uint8_t *__restrict__ bucket, uint32_t *__restrict__ hist,
+                                         uint32_t *__restrict__ order) {
+    const unsigned long long nr = hist[NBUCKET];
+    for (unsigned long long r = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; r < nr;
+         r += (unsigned long long)gridDim.x * blockDim.x)
+        if (bucket[r] != DROP) order[atomicAdd(&hist[bucket[r]], 1u)] = (uint32_t)r;
 }
 
 }  // namespace
 
-int launch_root_order(fim_ctx *ctx, MineCounters *d_ctr, size_t npairs) {
-    if (!ctx->has_weights) return FIM_E_STATE;
-    FIM_TRY(fim_reserve(ctx, ctx->root_order, sizeof(uint32_t) * (npairs ? npairs : 1)));
-    FIM_TRY(fim_reserve(ctx, ctx->root_bucket, npairs ? npairs : 1));
-    FIM_TRY(fim_reserve(ctx, ctx->root_hist, sizeof(uint32_t) * NBUCKET));
-    cudaStream_t st = ctx->stream;
-    FIM_CUDA_TRY(cudaMemsetAsync(ctx->root_hist.p, 0, sizeof(uint32_t) * NBUCKET, st));
-    const int mf = ctx->mfreq;
+int reserve_root_plan(fim_ctx *ctx, size_t root_cap) {
+    FIM_TRY(fim_reserve(ctx, ctx->root_order, sizeof(uint32_t) * (root_cap ? root_cap : 1)));
+    FIM_TRY(fim_reserve(ctx, ctx->root_bucket, root_cap ? root_cap : 1));
+    FIM_TRY(fim_reserve(ctx, ctx->root_hist, sizeof(uint32_t) * (NBUCKET + 1)));
+    return FIM_OK;
+}
+
+// (allocates nothing: it may run inside a stream capture once
+// reserve_root_plan has sized the buffers)
+int launch_root_plan(fim_ctx *ctx, MineCounters *d_ctr, size_t root_cap, const DbDesc *d_dbs, int mode,
+                     cudaStream_t st) {
+    if (mode == 2 && !ctx->has_weights) return FIM_E_STATE;
+    FIM_CUDA_TRY(cudaMemsetAsync(ctx->root_hist.p, 0, sizeof(uint32_t) * (NBUCKET + 1), st));
     const uint32_t *roots = ctx->roots.as<uint32_t>();
-    const unsigned grid = (unsigned)ceil_div64((int64_t)(npairs ? npairs : 1), 256);
+    RootView v{};
+    v.pairbits = ctx->pairbits.as<uint32_t>();
+    v.pair_cnt = ctx->pair_cnt.as<int>();
+    v.item_sup = ctx->item_sup.as<uint32_t>();
+    v.perm = ctx->perm.as<int32_t>();
+    if (!d_dbs) {
+        v.mf = ctx->mfreq;
+        v.mpw = (int)ceil_div64(v.mf, 32);
+        v.n = ctx->n;
+        v.nw = ctx->nw;
+        v.thr = ctx->cur_thr;
+    }
+    // the root count is known only on the device: a grid-stride loop over at
+    // most the capacity, with a grid of a few CTAs per SM
+    int64_t grid = ceil_div64((int64_t)(root_cap ? root_cap : 1), 256);
+    const int64_t resident = (int64_t)(ctx->num_sms > 0 ? ctx->num_sms : 1) * 8;
+    if (grid > resident) grid = resident;
     ctx->launches += 3;
-    root_predict_kernel<<<grid, 256, 0, st>>>(roots, roots + npairs, roots + 2 * npairs, d_ctr,
-                                              ctx->pairbits.as<uint32_t>(), (int)ceil_div64(mf, 32),
-                                              ctx->pair_cnt.as<int>(), mf, ctx->item_sup.as<uint32_t>(),
-                                              ctx->perm.as<int32_t>(), ctx->n, ctx->nw, ctx->cur_thr,
-                                              ctx->mlp_wbf.as<__nv_bfloat16>(), ctx->root_bucket.as<uint8_t>(),
-                                              ctx->root_hist.as<uint32_t>());
-    bucket_scan_kernel<<<1, 32, 0, st>>>(ctx->root_hist.as<uint32_t>());
-    bucket_scatter_kernel<<<grid, 256, 0, st>>>(d_ctr, ctx->root_bucket.as<uint8_t>(),
-                                                ctx->root_hist.as<uint32_t>(), ctx->root_order.as<uint32_t>());
+    root_plan_kernel<<<(unsigned)grid, 256, 0, st>>>(roots, roots + root_cap, roots + 2 * root_cap,
+                                           d_dbs ? roots + 3 * root_cap : nullptr, d_ctr, d_dbs, v, mode,
+                                           ctx->mlp_wbf.as<__nv_bfloat16>(), ctx->root_bucket.as<uint8_t>(),
+                                           ctx->root_hist.as<uint32_t>());
+    root_plan_scan_kernel<<<1, 32, 0, st>>>(ctx->root_hist.as<uint32_t>(), d_ctr);
+    root_plan_scatter_kernel<<<(unsigned)grid, 256, 0, st>>>(ctx->root_bucket.as<uint8_t>(), ctx->root_hist.as<uint32_t>(),
+                                                   ctx->root_order.as<uint32_t>());
     FIM_CUDA_TRY(cudaGetLastError());
     return FIM_OK;
 }

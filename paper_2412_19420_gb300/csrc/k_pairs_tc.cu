@@ -87,20 +87,6 @@ __device__ __forceinline__ bool mbar_wait(TcSmem &s, uint64_t *b, uint32_t parit
     return mbar_wait_bounded(b, parity, &s.abort, WAIT_NS);
 }
 
-// Row of A (this thread's TMEM lane) at columns [col, col + 32): word t of
-// the 128-byte row holds K elements 4t .. 4t + 3.
-__device__ __forceinline__ void store_row_tmem(uint32_t taddr, uint4 w) {
-    const uint32_t words[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-    for (int q = 0; q < 4; q++) {  // 32 bits = 32 elements = 8 columns per store
-        uint32_t v[8];
-        const uint4 lo = bits16_to_e4m3(words[q] & 0xFFFFu), hi = bits16_to_e4m3(words[q] >> 16);
-        v[0] = lo.x; v[1] = lo.y; v[2] = lo.z; v[3] = lo.w;
-        v[4] = hi.x; v[5] = hi.y; v[6] = hi.z; v[7] = hi.w;
-        tmem_st8(taddr + 8u * q, v);
-    }
-}
-
 // Tiles (ta, tb) with at least one pair a < b < mf, ta-major.  The first
 // B-block that reaches past a = 128 ta is tb = ta / 2; the last A-block may
 // hold only the last item, which pairs with nothing.

@@ -79,7 +79,7 @@ __device__ __forceinline__ uint64_t mp_sdesc(uint32_t addr) {
 }
 
 __global__ void __launch_bounds__(MP_THREADS, 1)
-mma_probe_kernel(int iters, int a_in_tmem, int *__restrict__ err) {
+mma_probe_kernel(int iters, int a_in_tmem, int n_cols, int *__restrict__ err) {
     extern __shared__ uint8_t raw[];
     MmaProbeSmem &s = *reinterpret_cast<MmaProbeSmem *>((reinterpret_cast<uintptr_t>(raw) + 1023) & ~uintptr_t(1023));
     const int warp = threadIdx.x >> 5;
@@ -118,7 +118,7 @@ mma_probe_kernel(int iters, int a_in_tmem, int *__restrict__ err) {
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (threadIdx.x == 0) {
-        const uint32_t idesc = (1u << 4) | ((uint32_t)(MP_N >> 3) << 17) | ((uint32_t)(MP_M >> 4) << 24);
+        const uint32_t idesc = (1u << 4) | ((uint32_t)(n_cols >> 3) << 17) | ((uint32_t)(MP_M >> 4) << 24);
         const uint32_t b0 = mp_smem(s.b), a0 = mp_smem(s.a);
         for (int i = 0; i < iters; i++) {
             const uint32_t kk = (uint32_t)(i & 3), acc = i > 0 ? 1u : 0u;
@@ -168,7 +168,7 @@ extern "C" {
 
 int fim_probe(fim_ctx *ctx, int which, double *result) {
     FIM_NVTX("fim_probe");
-    if (!ctx || !result || which < 0 || which > 3) return FIM_E_INVAL;
+    if (!ctx || !result || which < 0 || which > 5) return FIM_E_INVAL;
     *result = 0.0;
     int dev_prev = -1;
     cudaGetDevice(&dev_prev);
@@ -194,9 +194,12 @@ int fim_probe(fim_ctx *ctx, int which, double *result) {
             const int nsm = ctx->num_sms > 0 ? ctx->num_sms : 1;
             const size_t smem = mp_smem_bytes;
             ctx->launches++;
-            mma_probe_kernel<<<(unsigned)nsm, MP_THREADS, smem, st>>>(iters, which == 2 ? 1 : 0,
+            // which 2, 3: N = 256 with A in tensor / shared memory; 4, 5: N = 128,
+            // 64 with A in shared memory (the batched pair pass's small tiles)
+            const int n_cols = which == 4 ? 128 : which == 5 ? 64 : MP_N;
+            mma_probe_kernel<<<(unsigned)nsm, MP_THREADS, smem, st>>>(iters, which == 2 ? 1 : 0, n_cols,
                                                                     reinterpret_cast<int *>(sink));
-            work = 2.0 * MP_M * MP_N * MP_K * (double)iters * nsm;  // flops
+            work = 2.0 * MP_M * n_cols * MP_K * (double)iters * nsm;  // flops
         } else if (which == 0) {
             const int iters = 4096;
             ctx->launches++;

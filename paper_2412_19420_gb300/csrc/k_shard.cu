@@ -255,7 +255,7 @@ int fim_merge_results(fim_ctx *ctx, int64_t n_trans, int32_t n_items, int n_part
     ctx->host_ctr.n_rec_items = T;
     ctx->host_ctr.max_len = h[1];
     cudaEventRecord(ctx->ev[3], st);
-    FIM_TRY(launch_compact(ctx, R, 1, n_items > 0 ? n_items : 1, /*identity_items=*/true));
+    FIM_TRY(launch_compact(ctx, R, R, 1, n_items > 0 ? n_items : 1, /*identity_items=*/true));
     cudaEventRecord(ctx->ev[4], st);
     FIM_CUDA_TRY(cudaStreamSynchronize(st));
     FIM_CUDA_TRY(cudaGetLastError());

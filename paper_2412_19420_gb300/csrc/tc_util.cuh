@@ -128,6 +128,20 @@ __device__ __forceinline__ void store_row(uint8_t *tile, int r, uint4 w) {
     }
 }
 
+// Row of A (this thread's TMEM lane) at columns [col, col + 32): word t of
+// the 128-byte row holds K elements 4t .. 4t + 3.
+__device__ __forceinline__ void store_row_tmem(uint32_t taddr, uint4 w) {
+    const uint32_t words[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+    for (int q = 0; q < 4; q++) {  // 32 bits = 32 elements = 8 columns per store
+        uint32_t v[8];
+        const uint4 lo = bits16_to_e4m3(words[q] & 0xFFFFu), hi = bits16_to_e4m3(words[q] >> 16);
+        v[0] = lo.x; v[1] = lo.y; v[2] = lo.z; v[3] = lo.w;
+        v[4] = hi.x; v[5] = hi.y; v[6] = hi.z; v[7] = hi.w;
+        tmem_st8(taddr + 8u * q, v);
+    }
+}
+
 // Row r of a SWIZZLE_128B K-major tile (128 bytes per row) filled with zeros.
 __device__ __forceinline__ void zero_row(uint8_t *tile, int r) {
     uint8_t *row = tile + (r >> 3) * 1024 + (r & 7) * 128;

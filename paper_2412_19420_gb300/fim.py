@@ -322,7 +322,8 @@ def fim_fetch_rules(ctx, out=None) -> Rules:
 
 def fim_probe(ctx, which: int) -> float:
     """Measurement probe: 0 = AND/popc word pairs per second, 1 = L2 read GB/s,
-    2 / 3 = tcgen05 kind::f8f6f4 TFLOP/s with A from tensor / shared memory."""
+    2 / 3 = tcgen05 kind::f8f6f4 TFLOP/s with A from tensor / shared memory (N = 256),
+    4 / 5 = the same with A from shared memory at N = 128 / 64."""
     r = ctypes.c_double()
     _check(_lib.fim_probe(ctx, int(which), ctypes.byref(r)), "fim_probe")
     return float(r.value)

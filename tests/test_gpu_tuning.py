@@ -190,10 +190,15 @@ def test_mapped_host_input_is_exact(ctx):
 
 def test_probes_are_plausible(ctx):
     # measurement probes: the AND/popc word-pair rate and the L2 read
-    # bandwidth of the GPU (GB300: 152 SMs near 2 GHz, L2 well above HBM)
+    # bandwidth of the GPU (GB300: 152 SMs near 2 GHz, L2 well above HBM),
+    # and the tcgen05 f8f6f4 MMA rate (dense fp8 nominal 4.5 PFLOP/s)
     popc = fim.fim_probe(ctx, 0)
     l2 = fim.fim_probe(ctx, 1)
     assert 1e11 < popc < 1e14
     assert 1000 < l2 < 200_000
+    mma = [fim.fim_probe(ctx, w) for w in (2, 3, 4, 5)]
+    assert all(100 < t < 6000 for t in mma), mma
+    # A from tensor memory is the fastest form, and N = 64 the slowest
+    assert mma[0] >= mma[1] and mma[3] <= mma[2]
     with pytest.raises(fim.FimError):
-        fim.fim_probe(ctx, 2)
+        fim.fim_probe(ctx, 6)

@@ -207,11 +207,14 @@ int fim_get_stats(const fim_ctx *ctx, fim_stats *out);
  *                                publishes this work-queue slot, so the worker
  *                                that takes it (and the drain) must time out;
  *                                -1 (default) = off
- *   "upload_mapped"    0, 1      host input to fim_build_bitmaps that lives in
- *                                page-locked, mapped memory (cudaHostAlloc,
- *                                cudaHostRegister) is read by the build kernel in
- *                                place over the host link, without a staging copy
- *                                (default 1; other host memory is copied)
+ *   "upload_mapped"    0, 1      host input to fim_build_bitmaps and
+ *                                fim_mine_batched that lives in page-locked, mapped
+ *                                memory (cudaHostAlloc, cudaHostRegister) is read
+ *                                by the build kernel in place over the host link,
+ *                                without a staging copy (default 1; other host
+ *                                memory is copied; a batch is read in place when
+ *                                its arrays form at most 64 contiguous runs, each
+ *                                inside one such allocation)
  *   "upload_chunks"    1..16     host input to fim_build_bitmaps: the indices go
  *                                up in this many chunks, each built as soon as it
  *                                lands (default 4; 1 = one copy, then the build)

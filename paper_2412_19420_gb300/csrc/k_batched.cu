@@ -17,6 +17,8 @@
 // Sizes that only the device knows (m' per database) never reach the host
 // before the DFS ends, so build -> DFS is captured once in a CUDA graph and
 // replayed for later batches of the same shape.
+#include <cuda.h>
+
 #include <cstring>
 #include <vector>
 
@@ -670,6 +672,42 @@ struct Layout {
     int m_max = 0, ib = 1;
 };
 
+// True when every range lies inside one page-locked host allocation that the
+// GPU addresses at the host address itself (unified addressing): the start
+// and the last byte of a range must be the same allocation (driver buffer
+// id), so no pageable memory can sit inside it.
+bool mapped_host_ranges(const std::vector<std::pair<const char *, size_t>> &runs) {
+    static CUresult (*get_attrs)(unsigned, CUpointer_attribute *, void **, CUdeviceptr) = nullptr;
+    static bool looked_up = false;
+    if (!looked_up) {
+        looked_up = true;
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPoint("cuPointerGetAttributes", &fn, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_attrs = reinterpret_cast<CUresult (*)(unsigned, CUpointer_attribute *, void **, CUdeviceptr)>(fn);
+        cudaGetLastError();
+    }
+    if (!get_attrs || runs.empty()) return false;
+    for (const auto &r : runs) {
+        unsigned long long id[2] = {0, 0};
+        for (int e = 0; e < 2; e++) {
+            const char *p = e == 0 ? r.first : r.first + r.second - 1;
+            cudaPointerAttributes a{};
+            if (cudaPointerGetAttributes(&a, p) != cudaSuccess || a.type != cudaMemoryTypeHost ||
+                a.devicePointer != (const void *)p) {
+                cudaGetLastError();  // a query on unregistered memory leaves no sticky error
+                return false;
+            }
+            CUpointer_attribute which = CU_POINTER_ATTRIBUTE_BUFFER_ID;
+            void *out = &id[e];
+            if (get_attrs(1, &which, &out, (CUdeviceptr)(uintptr_t)p) != CUDA_SUCCESS) return false;
+        }
+        if (id[0] == 0 || id[0] != id[1]) return false;
+    }
+    return true;
+}
+
 }  // namespace
 
 extern "C" {
@@ -751,8 +789,34 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
     // the tensor-core pair pass's (database, tile) units, longest first
     std::vector<unsigned long long> pair_units;
     const bool pairs_tc = !(flags & FIM_PAIRS_POPC) && batch_pairs_tc_units(L.dbs, pair_units, (size_t)1 << 24);
-    // ---- inputs: one staging copy for host CSRs -----------------------------
-    if (!on_device) {
+    // ---- inputs: host CSRs in page-locked memory are read in place ----------
+    // (the build kernel streams them over the host link, which caps copies
+    // and in-kernel reads alike, so the upload and the build become one pass);
+    // other host memory goes up in one staging copy per contiguous run
+    bool mapped = false;
+    if (!on_device && ctx->upload_mapped) {
+        // contiguous host ranges of the indptr arrays and of the index arrays
+        std::vector<std::pair<const char *, size_t>> rp, ri;
+        auto note = [](std::vector<std::pair<const char *, size_t>> &runs, const void *p, size_t bytes) {
+            if (!bytes) return;
+            if (!runs.empty() && runs.back().first + runs.back().second == (const char *)p)
+                runs.back().second += bytes;
+            else
+                runs.push_back({(const char *)p, bytes});
+        };
+        for (int d = 0; d < n_db && rp.size() + ri.size() <= 64; d++) {
+            note(rp, in[d].indptr, sizeof(int64_t) * (size_t)(in[d].n_trans + 1));
+            note(ri, in[d].indices, sizeof(int32_t) * (size_t)in[d].indptr[in[d].n_trans]);
+        }
+        rp.insert(rp.end(), ri.begin(), ri.end());
+        mapped = rp.size() <= 64 && mapped_host_ranges(rp);
+        if (mapped)
+            for (int d = 0; d < n_db; d++) {
+                L.dbs[d].indptr = in[d].indptr;  // unified addressing: the host address is the device address
+                L.dbs[d].indices = in[d].indices;
+            }
+    }
+    if (!on_device && !mapped) {
         FIM_TRY(fim_reserve(ctx, ctx->csr_ptr, sizeof(int64_t) * (size_t)(host_ptr_total ? host_ptr_total : 1)));
         FIM_TRY(fim_reserve(ctx, ctx->csr_idx, sizeof(int32_t) * (size_t)(host_nnz_total ? host_nnz_total : 1)));
         // databases whose arrays follow each other in host memory (one packed

@@ -125,3 +125,32 @@ def test_batched_workload_sample(ctx):
         got = fim.fim_fetch_batched(ctx, int(d))
         want = oracle.apriori(dbs[d].indptr, dbs[d].indices, dbs[d].m, ms[d])
         assert got.sha256() == want.sha256()
+
+
+def test_pinned_host_input_read_in_place(ctx):
+    # page-locked host CSRs packed back to back: the build reads them over
+    # the host link in place; a batch with one pageable database among them
+    # goes up by staging copies instead -- both exact
+    import torch
+    dbs, ms = _mixed_batch(7, 24)
+    ptr = torch.from_numpy(np.concatenate([c.indptr for c in dbs])).pin_memory()
+    idx = torch.from_numpy(np.concatenate([c.indices for c in dbs] + [np.zeros(1, np.int32)])).pin_memory()
+    pn, inn = ptr.numpy(), idx.numpy()
+    packed, po, io = [], 0, 0
+    for c in dbs:
+        packed.append(datagen.Csr(indptr=pn[po:po + c.n + 1], indices=inn[io:io + c.nnz], m=c.m))
+        po += c.n + 1
+        io += c.nnz
+    for _ in range(2):
+        fim.fim_mine_batched(ctx, packed, ms)
+        _check_all(ctx, dbs, ms)
+    mixed = list(packed)
+    mixed[5] = dbs[5]  # pageable
+    fim.fim_mine_batched(ctx, mixed, ms)
+    _check_all(ctx, dbs, ms)
+    fim.fim_set_tuning(ctx, "upload_mapped", 0)
+    try:
+        fim.fim_mine_batched(ctx, packed, ms)
+        _check_all(ctx, dbs, ms)
+    finally:
+        fim.fim_set_tuning(ctx, "upload_mapped", 1)

@@ -177,6 +177,14 @@ int fim_get_stats(const fim_ctx *ctx, fim_stats *out);
  *                                candidates first (1, default).  Either way a root whose
  *                                class has no candidate is dropped before the
  *                                prefix extension starts
+ *   "batch_segments"   1..8      fim_mine_batched pipelines this many groups of
+ *                                databases (about equal transactions): a group's
+ *                                pair pass runs while the next group is built
+ *                                (default 1 = one group)
+ *   "dfs_warp"         0, 1      fim_mine_batched with every database's columns at
+ *                                most 4,096 words: one warp per prefix-extension
+ *                                worker instead of one CTA (default 1)
+ *   "dfs_warp_ctas"    2, 3      CTAs of eight such warp workers per SM (default 2)
  *   "record_chunk"     1..1024   result slots a prefix-extension worker reserves
  *                                at a time (default 1: exactly a class's sets);
  *                                the ones a worker leaves unused are sorted out

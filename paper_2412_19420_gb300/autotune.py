@@ -33,8 +33,10 @@ BATCH_SPACE = {
     "batch_build_block": [32, 64],
     "dfs_ctas_per_sm": [2, 4],
     "split_depth": [4, 8],
+    "batch_segments": [1, 4],
+    "dfs_warp_ctas": [2, 3],
 }
-BATCH_DEFAULT = dict(DEFAULT, batch_pairs_shape=0, batch_build_block=32)
+BATCH_DEFAULT = dict(DEFAULT, batch_pairs_shape=0, batch_build_block=32, batch_segments=1, dfs_warp_ctas=2)
 
 
 def valid(cfg: dict) -> bool:

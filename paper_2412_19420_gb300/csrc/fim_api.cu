@@ -169,6 +169,8 @@ void fim_destroy(fim_ctx *ctx) {
     for (cudaStream_t u : ctx->up_stream)
         if (u) cudaStreamDestroy(u);
     if (ctx->aux_stream) cudaStreamDestroy(ctx->aux_stream);
+    for (cudaEvent_t e : ctx->seg_ev)
+        if (e) cudaEventDestroy(e);
     for (cudaEvent_t e : ctx->aux_ev)
         if (e) cudaEventDestroy(e);
     for (cudaEvent_t e : ctx->up_ev)
@@ -599,6 +601,9 @@ int fim_set_tuning(fim_ctx *ctx, const char *key, int64_t v) {
         {"batch_build_block", &ctx->batch_build_block, 32, 64},
         {"root_sort", &ctx->root_sort, 0, 1},
         {"record_chunk", &ctx->rec_chunk, 1, 1024},
+        {"batch_segments", &ctx->batch_segments, 1, 8},
+        {"dfs_warp", &ctx->dfs_warp, 0, 1},
+        {"dfs_warp_ctas", &ctx->dfs_warp_ctas, 2, 3},
     };
     for (const Knob &k : knobs)
         if (strcmp(k.name, key) == 0) {

@@ -277,6 +277,11 @@ struct fim_ctx {
     int batch_build_block = 32; // words per column a batched build CTA covers (32 or 64)
     int root_sort = 1;          // root order without the network: 0 pair-pass order, 1 candidate count
     int rec_chunk = 1;          // record slots a DFS worker reserves at a time
+    int batch_segments = 1;     // database groups the batch graph pipelines (build || pairs)
+    int dfs_warp = 1;           // batches of short columns: one warp per prefix-extension worker
+    int dfs_warp_ctas = 2;      // CTAs of warp workers per SM (2 or 3)
+    bool force_cta_dfs = false; // set while a batch is re-mined with CTA workers
+    cudaEvent_t seg_ev[10] = {};  // fork, join and per-group events of that pipeline
     int compact_cluster = 1;    // small outputs: sort in one cluster launch
     int csort_cl[5] = {0, 0, 0, 0, 0};  // cluster size per key width (0 unknown, -1 none)
     int debug_checks = 0;       // device-side invariant checks after build and mine
@@ -352,11 +357,16 @@ int launch_cluster_sort(fim_ctx *ctx, const unsigned long long *keys, uint64_t R
                         uint32_t *idx_out, cudaStream_t st);
 
 // k_batch_pairs_tc.cu: the batch's pair supports on the tensor cores
-bool batch_pairs_tc_units(const std::vector<DbDesc> &dbs, std::vector<unsigned long long> &units,
+bool batch_pairs_tc_units(const std::vector<DbDesc> &dbs, int d0, int d1, std::vector<unsigned long long> &units,
                           size_t max_units);
 int launch_batch_pairs_tc(fim_ctx *ctx, const DbDesc *d_dbs, const unsigned long long *d_units, int64_t n_units,
                           cudaStream_t st);
 extern const int kBatchPairsShapeCount;
+
+// k_dfs_warp.cu: the prefix extension with one warp per worker
+int launch_dfs_warp(fim_ctx *ctx, const DfsParams &p, int n_warps, int ctas_per_sm, cudaStream_t st);
+int dfs_warp_max_depth();
+int dfs_warp_per_cta();
 
 // k_check.cu: the debug_checks invariants (FIM_E_CHECK when violated)
 int run_check_pads(fim_ctx *ctx);

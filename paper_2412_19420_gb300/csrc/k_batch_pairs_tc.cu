@@ -339,23 +339,22 @@ batch_pairs_tc_kernel(const DbDesc *__restrict__ dbs, const unsigned long long *
 // by descending stage count (ties by database).  Tile 0 holds pairs whenever
 // m'_d >= 2, so the first units are all real work, longest first, and the
 // round-robin deal gives every CTA a fair share of it; the later tile numbers
-// are empty wherever m'_d is small.  Returns false when there are more than
-// max_units of them.
-bool batch_pairs_tc_units(const std::vector<DbDesc> &dbs, std::vector<unsigned long long> &units,
+// are empty wherever m'_d is small.  The units of databases [d0, d1) are
+// appended to `units`; returns false when there would be more than max_units.
+bool batch_pairs_tc_units(const std::vector<DbDesc> &dbs, int d0, int d1, std::vector<unsigned long long> &units,
                           size_t max_units) {
-    std::vector<int> order(dbs.size());
+    std::vector<int> order;
     size_t total = 0;
     int max_tiles = 0;
-    for (size_t d = 0; d < dbs.size(); d++) {
-        order[d] = (int)d;
+    for (int d = d0; d < d1; d++) {
+        order.push_back(d);
         const int nt = (int)ceil_div64(dbs[d].m, BT);
         total += (size_t)nt * (size_t)(nt + 1) / 2;
         max_tiles = std::max(max_tiles, nt * (nt + 1) / 2);
     }
-    if (total > max_units) return false;
+    if (units.size() + total > max_units) return false;
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return dbs[x].nw > dbs[y].nw; });
-    units.clear();
-    units.reserve(total);
+    units.reserve(units.size() + total);
     for (int t = 0; t < max_tiles; t++)
         for (int d : order) {
             const int nt = (int)ceil_div64(dbs[d].m, BT);

@@ -102,16 +102,18 @@ constexpr int BUILD_ROWS_THREADS = 512;
 template <int WBK>
 __global__ void __launch_bounds__(BUILD_ROWS_THREADS)
 batch_build_rows_kernel(const DbDesc *__restrict__ dbs, int n_db, const int64_t *__restrict__ unit_prefix,
-                        uint32_t *__restrict__ bm, uint32_t *__restrict__ sup, int *__restrict__ flag) {
+                        int64_t unit_base, uint32_t *__restrict__ bm, uint32_t *__restrict__ sup,
+                        int *__restrict__ flag) {
     static_assert(WBK % 4 == 0 && WBK / 4 <= 32 && 32 % (WBK / 4) == 0, "a column's chunks share a warp");
     constexpr int NWARP = BUILD_ROWS_THREADS / 32;
     constexpr int QPC = WBK / 4;  // 16-byte chunks of a column in this block
     extern __shared__ __align__(16) uint32_t tile[];  // [WBK][ms]
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int d = find_db(unit_prefix, n_db, blockIdx.x);
+    const int64_t unit = unit_base + blockIdx.x;
+    const int d = find_db(unit_prefix, n_db, unit);
     const DbDesc &D = dbs[d];
     const int m = D.m, ms = m | 1;  // odd pitch: the transposed reads below are conflict-free
-    const int64_t w0 = (int64_t)(blockIdx.x - unit_prefix[d]) * WBK;
+    const int64_t w0 = (unit - unit_prefix[d]) * WBK;
     const int64_t n = D.n;
     uint32_t *const col0 = bm + D.bm_off;
     const int64_t t0 = w0 * 32;
@@ -247,7 +249,7 @@ __global__ void batch_rank_kernel(DbDesc *__restrict__ dbs, int n_db, const int6
 constexpr int RANK_THREADS = 256;
 constexpr int RANK_CAP = 4096;
 __global__ void __launch_bounds__(RANK_THREADS)
-batch_rank_db_kernel(DbDesc *__restrict__ dbs, const uint32_t *__restrict__ sup, int32_t *__restrict__ perm,
+batch_rank_db_kernel(DbDesc *__restrict__ dbs, int d0, const uint32_t *__restrict__ sup, int32_t *__restrict__ perm,
                      MineCounters *ctr, unsigned long long *rec_off, uint32_t *rec_len, uint32_t *rec_sup,
                      uint32_t *rec_items, uint32_t *rec_db, unsigned long long rec_cap,
                      unsigned long long items_cap) {
@@ -257,7 +259,7 @@ batch_rank_db_kernel(DbDesc *__restrict__ dbs, const uint32_t *__restrict__ sup,
     __shared__ unsigned long long s_base[2];
     __shared__ int s_nf;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int d = blockIdx.x;
+    const int d = d0 + (int)blockIdx.x;
     DbDesc &D = dbs[d];
     const int m = D.m;
     const uint32_t *sp = sup + D.item_off;
@@ -329,7 +331,7 @@ batch_rank_db_kernel(DbDesc *__restrict__ dbs, const uint32_t *__restrict__ sup,
 constexpr int FIN_THREADS = 512;
 constexpr int FIN_CAP = 4096;
 __global__ void __launch_bounds__(FIN_THREADS)
-batch_finalize_db_kernel(const DbDesc *__restrict__ dbs, const int *__restrict__ pair_cnt,
+batch_finalize_db_kernel(const DbDesc *__restrict__ dbs, int d0, const int *__restrict__ pair_cnt,
                          uint32_t *__restrict__ pairbits, MineCounters *ctr, unsigned long long *rec_off,
                          uint32_t *rec_len, uint32_t *rec_sup, uint32_t *rec_items, uint32_t *rec_db,
                          unsigned long long rec_cap, unsigned long long items_cap, uint32_t *root_a,
@@ -339,7 +341,7 @@ batch_finalize_db_kernel(const DbDesc *__restrict__ dbs, const int *__restrict__
     __shared__ unsigned long long s_base[3];
     constexpr int NW = FIN_THREADS / 32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int d = blockIdx.x;
+    const int d = d0 + (int)blockIdx.x;
     const DbDesc &D = dbs[d];
     const int mf = *(volatile const int32_t *)&D.mfreq;
     const int mpw = (mf + 31) / 32;
@@ -787,8 +789,39 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
         }
     }
     // the tensor-core pair pass's (database, tile) units, longest first
+    // Pipelined groups of databases: group s is built and ranked on the ctx
+    // stream while the pair pass of group s - 1 runs on the side stream.
+    // Groups hold about equal transactions.  Only the fast paths pipeline:
+    // rows build, per-database rank and finalize, tensor-core pairs.
+    const bool pairs_tc_wanted = !(flags & FIM_PAIRS_POPC);
+    int n_seg = (pairs_tc_wanted && rows_build && L.m_max <= RANK_CAP && L.m_max <= FIN_CAP && maxlen != 1)
+                    ? ctx->batch_segments : 1;
+    if (n_seg > n_db) n_seg = n_db > 0 ? n_db : 1;
+    std::vector<int> seg_db(n_seg + 1, 0);
+    {
+        int64_t total_n = 0;
+        for (int d = 0; d < n_db; d++) total_n += L.dbs[d].n + 1;
+        int64_t acc = 0;
+        int s = 1;
+        for (int d = 0; d < n_db && s < n_seg; d++) {
+            acc += L.dbs[d].n + 1;
+            if (acc * n_seg >= total_n * s) seg_db[s++] = d + 1;
+        }
+        while (s < n_seg) { seg_db[s] = seg_db[s - 1]; s++; }
+        seg_db[n_seg] = n_db;
+    }
+    // the tensor-core pair pass's (database, tile) units, each group's longest first
     std::vector<unsigned long long> pair_units;
-    const bool pairs_tc = !(flags & FIM_PAIRS_POPC) && batch_pairs_tc_units(L.dbs, pair_units, (size_t)1 << 24);
+    std::vector<int64_t> seg_unit(n_seg + 1, 0);
+    bool pairs_tc = pairs_tc_wanted;
+    for (int sg = 0; sg < n_seg && pairs_tc; sg++) {
+        pairs_tc = batch_pairs_tc_units(L.dbs, seg_db[sg], seg_db[sg + 1], pair_units, (size_t)1 << 24);
+        seg_unit[sg + 1] = (int64_t)pair_units.size();
+    }
+    if (!pairs_tc) {
+        n_seg = 1;
+        seg_db.assign({0, n_db});
+    }
     // ---- inputs: host CSRs in page-locked memory are read in place ----------
     // (the build kernel streams them over the host link, which caps copies
     // and in-kernel reads alike, so the upload and the build become one pass);
@@ -861,9 +894,17 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
     }
     // ---- device buffers -------------------------------------------------------
     const int workers = ctx->num_sms * ctx->dfs_ctas_per_sm;
+    // databases of short columns: one warp per prefix-extension worker (CTAs
+    // of eight, dfs_warp_ctas of them per SM); a stack deeper than WARP_DEPTH levels re-mines
+    // the batch with CTA workers
+    constexpr int kWarpDfsMaxWords = 4096, WARP_DEPTH = 24;
+    const bool warp_dfs = ctx->dfs_warp && !ctx->force_cta_dfs && L.nwp_max <= kWarpDfsMaxWords;
+    const int n_warps = ctx->num_sms * ctx->dfs_warp_ctas * dfs_warp_per_cta();
+    const int dfs_workers = warp_dfs ? n_warps : workers;
     int depth_cap = (int)(L.max_row_bound < 240 ? L.max_row_bound : 240);
+    if (warp_dfs && depth_cap > WARP_DEPTH) depth_cap = WARP_DEPTH;
     if (depth_cap < 2) depth_cap = 2;
-    const size_t per_level = (size_t)workers * (size_t)(L.nwp_max > 0 ? L.nwp_max : 1) * sizeof(uint32_t);
+    const size_t per_level = (size_t)dfs_workers * (size_t)(L.nwp_max > 0 ? L.nwp_max : 1) * sizeof(uint32_t);
     while (depth_cap > 2 && per_level * (size_t)depth_cap > (8ull << 30)) depth_cap /= 2;
     const int64_t frame_pool = 4LL * (L.m_max > 0 ? L.m_max : 1) + 1024;
     const size_t tbl = sizeof(DbDesc) * (size_t)n_db;
@@ -876,8 +917,8 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
     FIM_TRY(fim_reserve(ctx, ctx->pairbits, sizeof(uint32_t) * (size_t)(L.pb ? L.pb : 1)));
     FIM_TRY(fim_reserve(ctx, ctx->roots, sizeof(uint32_t) * 4 * (size_t)(L.root_cap ? L.root_cap : 1)));
     FIM_TRY(fim_reserve(ctx, ctx->stack_bits, per_level * (size_t)depth_cap));
-    FIM_TRY(fim_reserve(ctx, ctx->frame_items, sizeof(uint32_t) * (size_t)workers * frame_pool));
-    FIM_TRY(fim_reserve(ctx, ctx->frame_sups, sizeof(uint32_t) * (size_t)workers * frame_pool));
+    FIM_TRY(fim_reserve(ctx, ctx->frame_items, sizeof(uint32_t) * (size_t)dfs_workers * frame_pool));
+    FIM_TRY(fim_reserve(ctx, ctx->frame_sups, sizeof(uint32_t) * (size_t)dfs_workers * frame_pool));
     FIM_TRY(prepare_task_queue(ctx, sizeof(Task) * kTaskCap));
     FIM_TRY(fim_reserve(ctx, ctx->cand_pool, sizeof(uint32_t) * kCandPoolCap));
     FIM_TRY(reserve_root_plan(ctx, (size_t)(L.root_cap ? L.root_cap : 1)));
@@ -978,8 +1019,10 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
         mix(&pairs_tc, sizeof(pairs_tc));
         mix(&wbk, sizeof(wbk));
         // every launch-shape knob the captured launches depend on
-        const int shape[8] = {workers, ctx->dfs_block, ctx->pairs_kdrain, ctx->pairs_split, ctx->batch_pairs_shape,
-                              ctx->dfs_ctas_per_sm, plan_mode, ctx->learned_order};
+        const int shape[9] = {workers, ctx->dfs_block, ctx->pairs_kdrain, ctx->pairs_split, ctx->batch_pairs_shape,
+                              ctx->dfs_ctas_per_sm, plan_mode, ctx->learned_order, n_seg};
+        mix(&warp_dfs, sizeof(warp_dfs));
+        mix(&ctx->dfs_warp_ctas, sizeof(ctx->dfs_warp_ctas));
         mix(shape, sizeof(shape));
         if (pairs_tc) {
             const void *up = ctx->batch_units.p;
@@ -1002,6 +1045,11 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
                 ctx->batch_graph_exec = nullptr;
             }
             cudaGraph_t g = nullptr;
+            if (n_seg > 1) {  // the side stream and the group events, made outside the capture
+                if (!ctx->aux_stream) FIM_CUDA_TRY(cudaStreamCreateWithFlags(&ctx->aux_stream, cudaStreamNonBlocking));
+                for (int sg = 0; sg <= n_seg; sg++)
+                    if (!ctx->seg_ev[sg]) FIM_CUDA_TRY(cudaEventCreateWithFlags(&ctx->seg_ev[sg], cudaEventDisableTiming));
+            }
             FIM_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
             // phase boundaries as event-record nodes of the graph: graph start
             // (ev 7), after build + supports + rank (ev 1), after the pair
@@ -1016,65 +1064,103 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
             const size_t smem_rows = (size_t)(L.m_max | 1) * wbk * sizeof(uint32_t);
             if (rows_build && items > 0)
                 cudaMemsetAsync(ctx->item_sup.p, 0, sizeof(uint32_t) * (size_t)items, st);
-            if (units > 0) {
-                if (rows_build && wbk == 64)
-                    batch_build_rows_kernel<64><<<(unsigned)units, BUILD_ROWS_THREADS, smem_rows, st>>>(
-                        d_dbs, n_db, d_unit, ctx->bm.as<uint32_t>(), ctx->item_sup.as<uint32_t>(),
-                        ctx->dev_flag.as<int>());
-                else if (rows_build)
-                    batch_build_rows_kernel<32><<<(unsigned)units, BUILD_ROWS_THREADS, smem_rows, st>>>(
-                        d_dbs, n_db, d_unit, ctx->bm.as<uint32_t>(), ctx->item_sup.as<uint32_t>(),
+            auto build_rows = [&](int64_t u0, int64_t u1, cudaStream_t s_) {
+                if (u1 <= u0) return;
+                if (wbk == 64)
+                    batch_build_rows_kernel<64><<<(unsigned)(u1 - u0), BUILD_ROWS_THREADS, smem_rows, s_>>>(
+                        d_dbs, n_db, d_unit, u0, ctx->bm.as<uint32_t>(), ctx->item_sup.as<uint32_t>(),
                         ctx->dev_flag.as<int>());
                 else
-                    batch_build_kernel<<<(unsigned)units, 256, smem_build, st>>>(
-                        d_dbs, n_db, d_unit, L.ib, ctx->bm.as<uint32_t>(), ctx->dev_flag.as<int>());
-            }
-            if (items > 0) {
-                if (!rows_build)
-                    batch_support_kernel<<<(unsigned)items, 256, 0, st>>>(d_dbs, n_db, d_item,
-                                                                          ctx->bm.as<uint32_t>(),
-                                                                          ctx->item_sup.as<uint32_t>());
-                if (L.m_max <= RANK_CAP)
-                    batch_rank_db_kernel<<<(unsigned)n_db, RANK_THREADS, 0, st>>>(
-                        d_dbs, ctx->item_sup.as<uint32_t>(), ctx->perm.as<int32_t>(), d_ctr, p.rec_off, p.rec_len,
-                        p.rec_sup, p.rec_items, p.rec_db, p.rec_cap, p.rec_items_cap);
-                else
-                    batch_rank_kernel<<<(unsigned)ceil_div64(items * 32, 256), 256, 0, st>>>(
-                        d_dbs, n_db, d_item, items, ctx->item_sup.as<uint32_t>(), ctx->perm.as<int32_t>(), d_ctr,
-                        p.rec_off, p.rec_len, p.rec_sup, p.rec_items, p.rec_db, p.rec_cap, p.rec_items_cap);
-            }
-            cudaEventRecordWithFlags(ctx->ev[1], st, cudaEventRecordExternal);
-            if (tiles > 0 && maxlen != 1) {
-                if (pairs_tc) {
-                    const int rc_pairs = launch_batch_pairs_tc(ctx, d_dbs, ctx->batch_units.as<unsigned long long>(),
-                                                               (int64_t)pair_units.size(), st);
-                    if (rc_pairs != FIM_OK) {
-                        cudaGraph_t junk = nullptr;
-                        cudaStreamEndCapture(st, &junk);
-                        if (junk) cudaGraphDestroy(junk);
-                        return rc_pairs;
-                    }
-                } else {
-                    batch_pairs_kernel<<<(unsigned)tiles, 256, 0, st>>>(d_dbs, n_db, d_tile, ctx->bm.as<uint32_t>(),
-                                                                        ctx->perm.as<int32_t>(),
-                                                                        ctx->pair_cnt.as<int>());
-                }
-                if (L.m_max <= FIN_CAP)
-                    batch_finalize_db_kernel<<<(unsigned)n_db, FIN_THREADS, 0, st>>>(
-                        d_dbs, ctx->pair_cnt.as<int>(), ctx->pairbits.as<uint32_t>(), d_ctr, p.rec_off, p.rec_len,
-                        p.rec_sup, p.rec_items, p.rec_db, p.rec_cap, p.rec_items_cap, roots, roots + rc,
+                    batch_build_rows_kernel<32><<<(unsigned)(u1 - u0), BUILD_ROWS_THREADS, smem_rows, s_>>>(
+                        d_dbs, n_db, d_unit, u0, ctx->bm.as<uint32_t>(), ctx->item_sup.as<uint32_t>(),
+                        ctx->dev_flag.as<int>());
+            };
+            auto rank_db = [&](int da, int db_, cudaStream_t s_) {
+                if (db_ > da)
+                    batch_rank_db_kernel<<<(unsigned)(db_ - da), RANK_THREADS, 0, s_>>>(
+                        d_dbs, da, ctx->item_sup.as<uint32_t>(), ctx->perm.as<int32_t>(), d_ctr, p.rec_off,
+                        p.rec_len, p.rec_sup, p.rec_items, p.rec_db, p.rec_cap, p.rec_items_cap);
+            };
+            auto finalize_db = [&](int da, int db_, cudaStream_t s_) {
+                if (db_ > da)
+                    batch_finalize_db_kernel<<<(unsigned)(db_ - da), FIN_THREADS, 0, s_>>>(
+                        d_dbs, da, ctx->pair_cnt.as<int>(), ctx->pairbits.as<uint32_t>(), d_ctr, p.rec_off,
+                        p.rec_len, p.rec_sup, p.rec_items, p.rec_db, p.rec_cap, p.rec_items_cap, roots, roots + rc,
                         roots + 2 * rc, roots + 3 * rc);
-                else
-                    batch_finalize_kernel<<<(unsigned)ceil_div64(items * 32, 256), 256, 0, st>>>(
-                        d_dbs, n_db, d_item, items, ctx->pair_cnt.as<int>(), ctx->pairbits.as<uint32_t>(), d_ctr,
-                        p.rec_off, p.rec_len, p.rec_sup, p.rec_items, p.rec_db, p.rec_cap, p.rec_items_cap, roots,
-                        roots + rc, roots + 2 * rc, roots + 3 * rc);
+            };
+            int rc_pairs = FIM_OK;
+            if (n_seg > 1) {
+                // group s: build + rank on the ctx stream, then its pair pass
+                // and finalize on the side stream, overlapping group s + 1's
+                // build; the ctx stream joins the side stream before the DFS
+                cudaStream_t aux = ctx->aux_stream;
+                for (int sg = 0; sg < n_seg; sg++) {
+                    const int da = seg_db[sg], db_ = seg_db[sg + 1];
+                    build_rows(L.unit_prefix[da], L.unit_prefix[db_], st);
+                    rank_db(da, db_, st);
+                    cudaEventRecord(ctx->seg_ev[sg], st);
+                    cudaStreamWaitEvent(aux, ctx->seg_ev[sg], 0);
+                    if (rc_pairs == FIM_OK)
+                        rc_pairs = launch_batch_pairs_tc(ctx, d_dbs,
+                                                         ctx->batch_units.as<unsigned long long>() + seg_unit[sg],
+                                                         seg_unit[sg + 1] - seg_unit[sg], aux);
+                    finalize_db(da, db_, aux);
+                }
+                cudaEventRecordWithFlags(ctx->ev[1], st, cudaEventRecordExternal);
+                cudaEventRecord(ctx->seg_ev[n_seg], aux);
+                cudaStreamWaitEvent(st, ctx->seg_ev[n_seg], 0);
+            } else {
+                if (units > 0) {
+                    if (rows_build)
+                        build_rows(0, units, st);
+                    else
+                        batch_build_kernel<<<(unsigned)units, 256, smem_build, st>>>(
+                            d_dbs, n_db, d_unit, L.ib, ctx->bm.as<uint32_t>(), ctx->dev_flag.as<int>());
+                }
+                if (items > 0) {
+                    if (!rows_build)
+                        batch_support_kernel<<<(unsigned)items, 256, 0, st>>>(d_dbs, n_db, d_item,
+                                                                              ctx->bm.as<uint32_t>(),
+                                                                              ctx->item_sup.as<uint32_t>());
+                    if (L.m_max <= RANK_CAP)
+                        rank_db(0, n_db, st);
+                    else
+                        batch_rank_kernel<<<(unsigned)ceil_div64(items * 32, 256), 256, 0, st>>>(
+                            d_dbs, n_db, d_item, items, ctx->item_sup.as<uint32_t>(), ctx->perm.as<int32_t>(), d_ctr,
+                            p.rec_off, p.rec_len, p.rec_sup, p.rec_items, p.rec_db, p.rec_cap, p.rec_items_cap);
+                }
+                cudaEventRecordWithFlags(ctx->ev[1], st, cudaEventRecordExternal);
+                if (tiles > 0 && maxlen != 1) {
+                    if (pairs_tc)
+                        rc_pairs = launch_batch_pairs_tc(ctx, d_dbs, ctx->batch_units.as<unsigned long long>(),
+                                                         (int64_t)pair_units.size(), st);
+                    else
+                        batch_pairs_kernel<<<(unsigned)tiles, 256, 0, st>>>(d_dbs, n_db, d_tile,
+                                                                            ctx->bm.as<uint32_t>(),
+                                                                            ctx->perm.as<int32_t>(),
+                                                                            ctx->pair_cnt.as<int>());
+                    if (L.m_max <= FIN_CAP)
+                        finalize_db(0, n_db, st);
+                    else
+                        batch_finalize_kernel<<<(unsigned)ceil_div64(items * 32, 256), 256, 0, st>>>(
+                            d_dbs, n_db, d_item, items, ctx->pair_cnt.as<int>(), ctx->pairbits.as<uint32_t>(),
+                            d_ctr, p.rec_off, p.rec_len, p.rec_sup, p.rec_items, p.rec_db, p.rec_cap,
+                            p.rec_items_cap, roots, roots + rc, roots + 2 * rc, roots + 3 * rc);
+                }
+            }
+            if (rc_pairs != FIM_OK) {
+                cudaGraph_t junk = nullptr;
+                cudaStreamEndCapture(st, &junk);
+                if (junk) cudaGraphDestroy(junk);
+                return rc_pairs;
             }
             cudaEventRecordWithFlags(ctx->ev[2], st, cudaEventRecordExternal);
             int rc_launch = FIM_OK;
             if (maxlen == 0 || maxlen >= 3) {
                 rc_launch = launch_root_plan(ctx, d_ctr, rc, d_dbs, plan_mode, st);
-                if (rc_launch == FIM_OK) rc_launch = launch_dfs(ctx, p, workers, ctx->dfs_block);
+                if (rc_launch == FIM_OK)
+                    rc_launch = warp_dfs ? launch_dfs_warp(ctx, p, n_warps, ctx->dfs_warp_ctas, st)
+                                         : launch_dfs(ctx, p, workers, ctx->dfs_block);
             }
             const cudaError_t ce = cudaStreamEndCapture(st, &g);
             if (rc_launch != FIM_OK) { if (g) cudaGraphDestroy(g); return rc_launch; }
@@ -1096,6 +1182,13 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
         FIM_CUDA_TRY(cudaStreamSynchronize(st));
         if (bad) return FIM_E_INVAL;
         const MineCounters &c = ctx->host_ctr;
+        if (c.err == FIM_E_STACK && warp_dfs) {
+            // deeper than the warp workers' stack: the batch again with CTA workers
+            ctx->force_cta_dfs = true;
+            const int rc2 = fim_mine_batched(ctx, n_db, in, flags);
+            ctx->force_cta_dfs = false;
+            return rc2;
+        }
         if (c.err != 0) return c.err;
         if (c.overflow) {
             ctx->rec_cap = c.n_records + c.n_records / 4 + 1024;
@@ -1145,7 +1238,7 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
         s.dfs_busy_ns = c.busy_ns;
         s.dfs_root_ns = c.root_ns;
         s.dfs_span_ns = c.t_last > c.t_first && c.t_first != 0 ? c.t_last - c.t_first : 0;
-        s.dfs_workers = (uint64_t)ctx->num_sms * (uint64_t)ctx->dfs_ctas_per_sm;
+        s.dfs_workers = (uint64_t)dfs_workers;
         s.launches_build = 0;
         s.launches_mine = ctx->launches - launches0;
         s.pair_path = pairs_tc ? 1u : 0u;

@@ -111,3 +111,17 @@ def test_autotuned_batch_shape_is_exact(ctx):
     assert set(autotune.BATCH_SPACE) <= set(cfg) and best_ms > 0 and len(table) >= 2
     fim.fim_mine_batched(ctx, dbs, ms)
     _check(ctx, dbs, ms, 0)
+
+
+@pytest.mark.parametrize("segments", [1, 2, 3, 8])
+def test_pipelined_groups_are_exact(ctx, segments):
+    # the batch graph pipelines groups of databases (build and rank of one
+    # group beside the pair pass of the one before); any grouping is exact,
+    # and so is a graph re-captured for another grouping
+    fim.fim_set_tuning(ctx, "batch_segments", segments)
+    dbs = [datagen.batched_db(s) for s in datagen.batched_specs(40, seed=5)]
+    dbs[7] = datagen.from_lists([], 9)  # an empty database inside a group
+    ms = [datagen.minsup_from_ppm(c.n, 20_000) for c in dbs]
+    for _ in range(2):
+        fim.fim_mine_batched(ctx, dbs, ms)
+        _check(ctx, dbs, ms, 0)

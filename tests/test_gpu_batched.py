@@ -154,3 +154,19 @@ def test_pinned_host_input_read_in_place(ctx):
         _check_all(ctx, dbs, ms)
     finally:
         fim.fim_set_tuning(ctx, "upload_mapped", 1)
+
+
+@pytest.mark.parametrize("warp_workers,ctas", [(1, 2), (1, 3), (0, 2)])
+def test_warp_and_cta_workers_agree(ctx, warp_workers, ctas):
+    # batches of short columns run the prefix extension with one warp per
+    # worker; dense random databases give deep subtrees (long itemsets)
+    fim.fim_set_tuning(ctx, "dfs_warp", warp_workers)
+    fim.fim_set_tuning(ctx, "dfs_warp_ctas", ctas)
+    try:
+        dbs, ms = _mixed_batch(8, 45)
+        for flags in (0, fim.FIM_STRICT, fim.FIM_MAXLEN(3)):
+            fim.fim_mine_batched(ctx, dbs, ms, flags)
+            _check_all(ctx, dbs, ms, strict=bool(flags & fim.FIM_STRICT), max_len=3 if flags >> 24 else 0)
+    finally:
+        fim.fim_set_tuning(ctx, "dfs_warp", 1)
+        fim.fim_set_tuning(ctx, "dfs_warp_ctas", 2)

@@ -316,11 +316,24 @@ def _batched_roofline(st, phase, dbs, m_freq, probes):
         wp = sum(mf * (mf - 1) // 2 * ((c.n + 31) // 32) for c, mf in zip(dbs, m_freq))
         ach = wp / sec
         peak = probes["popc_word_pairs_per_s"]
-        roof = {"kernel": "batch_pairs_kernel", "bound": "alu", "achieved": ach / 1e9, "peak": peak / 1e9,
-                "unit": "Gwordpairs/s", "frac": ach / peak, "traffic": None, "peak_source": "fim_probe AND/popc",
-                "algorithmic_word_pairs_per_launch": int(wp)}
+        if st["pair_path"] == 1:
+            # tensor cores: the pair supports' flops (2 per word-pair bit) against
+            # the measured f8f6f4 rate at the tiles' width (A from shared memory)
+            fl = 64.0 * wp
+            peak_t = probes.get("mma_f8f6f4_tflops_n128") or probes["mma_f8f6f4_tflops_a_smem"]
+            roof = {"kernel": "batch_pairs_tc_kernel", "bound": "tensor", "achieved": fl / sec / 1e12,
+                    "peak": peak_t, "unit": "TFLOP/s", "frac": fl / sec / 1e12 / peak_t,
+                    "traffic": _kernel_traffic("batch_pairs_tc_kernel", "batched_4096"),
+                    "peak_source": "measured tcgen05 f8f6f4 rate at N = 128 (fim_probe 4)",
+                    "algorithmic_word_pairs_per_launch": int(wp)}
+        else:
+            roof = {"kernel": "batch_pairs_kernel", "bound": "alu", "achieved": ach / 1e9, "peak": peak / 1e9,
+                    "unit": "Gwordpairs/s", "frac": ach / peak, "traffic": None, "peak_source": "fim_probe AND/popc",
+                    "algorithmic_word_pairs_per_launch": int(wp)}
     elif dom == "ms_dfs":
-        roof = _dfs_roofline(st, phase[dom], "batched_4096", probes)
+        # warp workers (eight per CTA) when the batch's columns are short
+        kern = "dfs_warp_kernel" if st["dfs_workers"] > 1024 else "dfs_kernel"
+        roof = _dfs_roofline(st, phase[dom], "batched_4096", probes, kern)
     else:
         nbytes = 24 * st["n_sets"]
         ach = nbytes / sec / 1e9
@@ -706,7 +719,7 @@ def _probes(fim, ctx):
             "mma_f8f6f4_tflops_n128": fim.fim_probe(ctx, 4), "mma_f8f6f4_tflops_n64": fim.fim_probe(ctx, 5)}
 
 
-def _dfs_roofline(st, ms_dfs, workload, probes):
+def _dfs_roofline(st, ms_dfs, workload, probes, kernel="dfs_kernel"):
     """The prefix-extension kernel against its ceiling.  Its algorithmic bytes
     are those of the operands the chosen representations stream, at 32-byte
     sector granularity (zero sectors skipped, sparse classes as (index,
@@ -717,9 +730,9 @@ def _dfs_roofline(st, ms_dfs, workload, probes):
     hbm, _, _, src = _peaks()
     sec = ms_dfs / 1000
     ach = st["dfs_touched_bytes"] / sec / 1e9
-    traffic = _kernel_traffic("dfs_kernel", workload)
+    traffic = _kernel_traffic(kernel, workload)
     l2 = probes["l2_read_gbs"]
-    roof = {"kernel": "dfs_kernel", "achieved": ach, "unit": "GB/s", "traffic": traffic,
+    roof = {"kernel": kernel, "achieved": ach, "unit": "GB/s", "traffic": traffic,
             "algorithmic_bytes_per_launch": st["dfs_touched_bytes"],
             "dense_equivalent_bytes_per_launch": st["dfs_bytes"],
             "hbm_frac": ach / hbm, "l2_frac": ach / l2,

@@ -229,11 +229,12 @@ int fim_get_stats(const fim_ctx *ctx, fim_stats *out);
  *   "upload_streams"   1, 2      copy streams the chunks alternate over (default 2)
  *   "compact_cluster"  0, 1      sort outputs small enough for one thread-block
  *                                cluster's shared memory in one launch (default 1)
- *   "batch_pairs_shape" 0..4     launch shape of fim_mine_batched's tensor-core
+ *   "batch_pairs_shape" 0..6     launch shape of fim_mine_batched's tensor-core
  *                                pair pass: (operand stages in the ring, stages of
- *                                raw bits staged ahead, CTAs per SM) = 0 (8, 8, 1),
- *                                1 (6, 8, 1), 2 (8, 16, 1), 3 (4, 8, 1),
- *                                4 (7, 12, 1); default 0
+ *                                raw bits staged ahead, CTAs per SM, stages per
+ *                                producer fence) = 0 (8, 8, 1, 2), 1 (6, 8, 1, 2),
+ *                                2 (8, 16, 1, 2), 3 (4, 8, 1, 2), 4 (7, 12, 1, 2),
+ *                                5 (8, 8, 1, 4), 6 (8, 16, 1, 4); default 0
  *   "batch_build_block" 32, 64   words of every column one CTA of fim_mine_batched's
  *                                build covers (32 x that many transactions); 64
  *                                applies where the block fits shared memory

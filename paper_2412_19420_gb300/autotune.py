@@ -29,7 +29,7 @@ DEFAULT = {"dfs_threads": 256, "dfs_ctas_per_sm": 4, "split_depth": 8, "sparse_d
 # staging depth, CTAs per SM), the build's words per column and CTA, and the
 # DFS workers; searched one knob at a time from BATCH_DEFAULT
 BATCH_SPACE = {
-    "batch_pairs_shape": [0, 1, 2, 3, 4],
+    "batch_pairs_shape": [0, 1, 2, 3, 4, 5, 6],
     "batch_build_block": [32, 64],
     "dfs_ctas_per_sm": [2, 4],
     "split_depth": [4, 8],

@@ -57,7 +57,6 @@ constexpr int BNPROD = 2 * BT;         // producer threads: A rows, then B rows
 constexpr int BNEPI = 128;             // epilogue threads: one TMEM lane quarter per warp
 constexpr int BTHREADS = BNPROD + BNEPI + 32;
 constexpr int TILE_BYTES = BT * KB;    // 16 KB per operand tile and stage
-constexpr int BG = 2;                  // stages a producer publishes per fence
 constexpr uint32_t ACC_COLS = BT;      // one f32 accumulator: 128 columns; two buffers
 constexpr uint32_t A_COL = 2 * ACC_COLS;  // A slot of ring stage q: columns [A_COL + 32 q, + 32)
 constexpr uint32_t A_SLOT_COLS = KB / 4;
@@ -109,12 +108,15 @@ __device__ __forceinline__ bool bwait(S &s, uint64_t *b, uint32_t parity) {
     return mbar_wait_bounded(b, parity, &s.abort, BWAIT_NS);
 }
 
-template <int STG, int DEPTH, int MINB>
+// BG: stages a producer publishes per fence (2 or 4; a quad is 4 stages)
+template <int STG, int DEPTH, int MINB, int BG>
 __global__ void __launch_bounds__(BTHREADS, MINB)
 batch_pairs_tc_kernel(const DbDesc *__restrict__ dbs, const unsigned long long *__restrict__ units,
                       int64_t n_units, const uint32_t *__restrict__ bm, const int32_t *__restrict__ perm_base,
                       int *__restrict__ pair_cnt, int kd, int *__restrict__ err) {
     static_assert(DEPTH % 4 == 0 && DEPTH >= 8, "raw bits go in quads, two or more in flight");
+    static_assert(BG == 2 || BG == 4, "a quad publishes in two or one fences");
+    static_assert(STG >= 2 * BG, "two publishing groups in flight");
     using Smem = BtcSmem<STG, DEPTH>;
     constexpr int BSTAGES = STG, BD = DEPTH;
     extern __shared__ uint8_t smem_raw[];
@@ -369,7 +371,7 @@ bool batch_pairs_tc_units(const std::vector<DbDesc> &dbs, int d0, int d1, std::v
 
 namespace {
 
-template <int STG, int DEPTH, int MINB>
+template <int STG, int DEPTH, int MINB, int BG>
 int launch_shape(fim_ctx *ctx, const DbDesc *d_dbs, const unsigned long long *d_units, int64_t n_units,
                  cudaStream_t st) {
     using Smem = BtcSmem<STG, DEPTH>;
@@ -385,7 +387,7 @@ int launch_shape(fim_ctx *ctx, const DbDesc *d_dbs, const unsigned long long *d_
     // keeps a second CTA (and its tensor-memory allocation) off
     size_t smem = sizeof(Smem) + 1024;
     if (MINB == 1 && smem < 120 * 1024) smem = 120 * 1024;
-    auto *kern = batch_pairs_tc_kernel<STG, DEPTH, MINB>;
+    auto *kern = batch_pairs_tc_kernel<STG, DEPTH, MINB, BG>;
     FIM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int *err = &ctx->counters.as<MineCounters>()->err;  // zeroed at the start of every batch
     ctx->launches++;
@@ -399,18 +401,21 @@ int launch_shape(fim_ctx *ctx, const DbDesc *d_dbs, const unsigned long long *d_
 
 // Launch shapes of the batched tensor-core pair pass (the "batch_pairs_shape"
 // knob): expanded operand stages in the ring, stages of raw bits staged
-// ahead, CTAs per SM.
-const int kBatchPairsShapes[][3] = {{8, 8, 1}, {6, 8, 1}, {8, 16, 1}, {4, 8, 1}, {7, 12, 1}};
+// ahead, CTAs per SM, stages a producer publishes per fence.
+const int kBatchPairsShapes[][4] = {{8, 8, 1, 2}, {6, 8, 1, 2}, {8, 16, 1, 2}, {4, 8, 1, 2},
+                                    {7, 12, 1, 2}, {8, 8, 1, 4}, {8, 16, 1, 4}};
 const int kBatchPairsShapeCount = (int)(sizeof(kBatchPairsShapes) / sizeof(kBatchPairsShapes[0]));
 
 int launch_batch_pairs_tc(fim_ctx *ctx, const DbDesc *d_dbs, const unsigned long long *d_units, int64_t n_units,
                           cudaStream_t st) {
     if (n_units <= 0) return FIM_OK;
     switch (ctx->batch_pairs_shape) {
-        case 1: return launch_shape<6, 8, 1>(ctx, d_dbs, d_units, n_units, st);
-        case 2: return launch_shape<8, 16, 1>(ctx, d_dbs, d_units, n_units, st);
-        case 3: return launch_shape<4, 8, 1>(ctx, d_dbs, d_units, n_units, st);
-        case 4: return launch_shape<7, 12, 1>(ctx, d_dbs, d_units, n_units, st);
-        default: return launch_shape<8, 8, 1>(ctx, d_dbs, d_units, n_units, st);
+        case 1: return launch_shape<6, 8, 1, 2>(ctx, d_dbs, d_units, n_units, st);
+        case 2: return launch_shape<8, 16, 1, 2>(ctx, d_dbs, d_units, n_units, st);
+        case 3: return launch_shape<4, 8, 1, 2>(ctx, d_dbs, d_units, n_units, st);
+        case 4: return launch_shape<7, 12, 1, 2>(ctx, d_dbs, d_units, n_units, st);
+        case 5: return launch_shape<8, 8, 1, 4>(ctx, d_dbs, d_units, n_units, st);
+        case 6: return launch_shape<8, 16, 1, 4>(ctx, d_dbs, d_units, n_units, st);
+        default: return launch_shape<8, 8, 1, 2>(ctx, d_dbs, d_units, n_units, st);
     }
 }

@@ -78,7 +78,7 @@ def test_full_mines_with_thresholds(ctx):
     _check(ctx, dbs, ms, 0)
 
 
-@pytest.mark.parametrize("shape", range(5))
+@pytest.mark.parametrize("shape", range(7))
 def test_every_pair_pass_shape_is_exact(ctx, shape):
     fim.fim_set_tuning(ctx, "batch_pairs_shape", shape)
     dbs, ms = _pair_batch()

@@ -235,10 +235,14 @@ int fim_get_stats(const fim_ctx *ctx, fim_stats *out);
  *                                producer fence) = 0 (8, 8, 1, 2), 1 (6, 8, 1, 2),
  *                                2 (8, 16, 1, 2), 3 (4, 8, 1, 2), 4 (7, 12, 1, 2),
  *                                5 (8, 8, 1, 4), 6 (8, 16, 1, 4); default 0
- *   "batch_build_block" 32, 64   words of every column one CTA of fim_mine_batched's
- *                                build covers (32 x that many transactions); 64
- *                                applies where the block fits shared memory
- *                                (default 32)
+ *   "batch_build_block" 16, 32, 64  words of every column one CTA of
+ *                                fim_mine_batched's build covers (32 x that many
+ *                                transactions); a block that does not fit shared
+ *                                memory falls back to the next smaller (default 32)
+ *   "batch_build_coal" 0, 1      fim_mine_batched's build: a warp reads its 32
+ *                                rows' item ids 32 at a time (coalesced) and finds
+ *                                each id's row among the lanes; 0 = lane-per-row
+ *                                reads (default 1)
  * Errors: FIM_E_INVAL for an unknown key or an out-of-range value. */
 int fim_set_tuning(fim_ctx *ctx, const char *key, int64_t value);
 

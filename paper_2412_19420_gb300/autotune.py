@@ -30,10 +30,9 @@ DEFAULT = {"dfs_threads": 256, "dfs_ctas_per_sm": 4, "split_depth": 8, "sparse_d
 # DFS workers; searched one knob at a time from BATCH_DEFAULT
 BATCH_SPACE = {
     "batch_pairs_shape": [0, 1, 2, 3, 4, 5, 6],
-    "batch_build_block": [32, 64],
+    "batch_build_block": [16, 32, 64],
     "dfs_ctas_per_sm": [2, 4],
     "split_depth": [4, 8],
-    "batch_segments": [1, 4],
     "dfs_warp_ctas": [2, 3],
 }
 BATCH_DEFAULT = dict(DEFAULT, batch_pairs_shape=0, batch_build_block=32, batch_segments=1, dfs_warp_ctas=2)

@@ -162,6 +162,7 @@ void fim_destroy(fim_ctx *ctx) {
     for (DevBuf *b : all) fim_release(ctx, *b);
     fim_release(ctx, ctx->batch_prefix);
     fim_release(ctx, ctx->batch_units);
+    fim_release(ctx, ctx->batch_unit_db);
     fim_release(ctx, ctx->batch_slices);
     if (ctx->batch_graph_exec) cudaGraphExecDestroy((cudaGraphExec_t)ctx->batch_graph_exec);
     for (void *g : ctx->compact_graph_exec)
@@ -598,7 +599,8 @@ int fim_set_tuning(fim_ctx *ctx, const char *key, int64_t v) {
         {"test_withhold_task", &ctx->test_withhold_task, -1, 1 << 20},
         {"upload_streams", &ctx->upload_streams, 1, 2},
         {"batch_pairs_shape", &ctx->batch_pairs_shape, 0, kBatchPairsShapeCount - 1},
-        {"batch_build_block", &ctx->batch_build_block, 32, 64},
+        {"batch_build_block", &ctx->batch_build_block, 16, 64},
+        {"batch_build_coal", &ctx->batch_build_coal, 0, 1},
         {"root_sort", &ctx->root_sort, 0, 1},
         {"record_chunk", &ctx->rec_chunk, 1, 1024},
         {"batch_segments", &ctx->batch_segments, 1, 8},
@@ -611,7 +613,7 @@ int fim_set_tuning(fim_ctx *ctx, const char *key, int64_t v) {
             // the DFS worker exists in two widths; a worker is capped at 64
             // registers a thread, so at most 1024 worker threads fit an SM
             if (k.field == &ctx->dfs_block && v != 256 && v != 512) return FIM_E_INVAL;
-            if (k.field == &ctx->batch_build_block && v != 32 && v != 64) return FIM_E_INVAL;
+            if (k.field == &ctx->batch_build_block && v != 16 && v != 32 && v != 64) return FIM_E_INVAL;
             const int64_t block = k.field == &ctx->dfs_block ? v : ctx->dfs_block;
             const int64_t per_sm = k.field == &ctx->dfs_ctas_per_sm ? v : ctx->dfs_ctas_per_sm;
             if (block * per_sm > 1024) return FIM_E_INVAL;

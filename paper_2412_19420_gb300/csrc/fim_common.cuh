@@ -249,6 +249,7 @@ struct fim_ctx {
     // batched mines: device prefix arrays, result slices, the captured graph
     DevBuf batch_prefix, batch_slices;
     DevBuf batch_units;         // (database, tile) units of the batched tensor-core pair pass
+    DevBuf batch_unit_db;       // database of each unit of the batched rows build
     bool batch_mined = false;
     int batch_n_db = 0;
     std::vector<unsigned long long> batch_set_start, batch_item_start;
@@ -274,7 +275,8 @@ struct fim_ctx {
     int pairs_split = 0;        // split-K factor of the tensor-core pair pass (0 = auto)
     int pairs_kdrain = 0;       // stages (x128 transactions) per exact drain (0 = 64)
     int batch_pairs_shape = 0;  // launch shape of the batched tensor-core pair pass
-    int batch_build_block = 32; // words per column a batched build CTA covers (32 or 64)
+    int batch_build_block = 32; // words per column a batched build CTA covers (16, 32 or 64)
+    int batch_build_coal = 1;   // batched build: a warp reads its rows' ids coalesced
     int root_sort = 1;          // root order without the network: 0 pair-pass order, 1 candidate count
     int rec_chunk = 1;          // record slots a DFS worker reserves at a time
     int batch_segments = 1;     // database groups the batch graph pipelines (build || pairs)

@@ -9,7 +9,8 @@
 //     bitset);
 //   * each stage's grid is the concatenation of the databases' work units
 //     (word blocks, item columns, pair tiles, pair rows); a CTA finds its
-//     database by binary search over the prefix sums of those counts;
+//     database in a unit -> database map (the build) or by binary search over
+//     the prefix sums of those counts;
 //   * the persistent DFS kernel takes root classes of all databases from one
 //     queue (root_db tags them) and loads the task's database view;
 //   * the compactor sorts by (database, size, items), so each database's
@@ -97,20 +98,20 @@ batch_build_kernel(const DbDesc *__restrict__ dbs, int n_db, const int64_t *__re
 // column's popcount over the block rides along: a shuffle sum over those
 // lanes, added into S(I_j) (Eq. 3), so no second pass reads the columns.
 // Blocks past the last transaction hold padding words only and just write
-// zeros.
+// zeros.  A CTA finds its database in a unit -> database map.
 constexpr int BUILD_ROWS_THREADS = 512;
-template <int WBK>
+template <int WBK, bool COAL>
 __global__ void __launch_bounds__(BUILD_ROWS_THREADS)
-batch_build_rows_kernel(const DbDesc *__restrict__ dbs, int n_db, const int64_t *__restrict__ unit_prefix,
-                        int64_t unit_base, uint32_t *__restrict__ bm, uint32_t *__restrict__ sup,
-                        int *__restrict__ flag) {
+batch_build_rows_kernel(const DbDesc *__restrict__ dbs, const int *__restrict__ unit_db,
+                        const int64_t *__restrict__ unit_prefix, int64_t unit_base, uint32_t *__restrict__ bm,
+                        uint32_t *__restrict__ sup, int *__restrict__ flag) {
     static_assert(WBK % 4 == 0 && WBK / 4 <= 32 && 32 % (WBK / 4) == 0, "a column's chunks share a warp");
     constexpr int NWARP = BUILD_ROWS_THREADS / 32;
     constexpr int QPC = WBK / 4;  // 16-byte chunks of a column in this block
     extern __shared__ __align__(16) uint32_t tile[];  // [WBK][ms]
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t unit = unit_base + blockIdx.x;
-    const int d = find_db(unit_prefix, n_db, unit);
+    const int d = unit_db[unit];
     const DbDesc &D = dbs[d];
     const int m = D.m, ms = m | 1;  // odd pitch: the transposed reads below are conflict-free
     const int64_t w0 = (unit - unit_prefix[d]) * WBK;
@@ -128,30 +129,80 @@ batch_build_rows_kernel(const DbDesc *__restrict__ dbs, int n_db, const int64_t 
         reinterpret_cast<uint4 *>(tile)[k] = make_uint4(0u, 0u, 0u, 0u);
     __syncthreads();
     int bad = 0;
-    for (int g = warp; g < WBK; g += NWARP) {
-        const int64_t r = t0 + 32 * g + lane;
-        if (r < n) {
-            int64_t e0 = D.indptr[r], e1 = D.indptr[r + 1];
-            if (e1 < e0 || e0 < 0 || e1 > nnz) {  // a malformed row: flagged, not read
+    if (COAL) {
+        // a warp's 32 rows hold consecutive ids [A, B): the warp reads them
+        // 32 at a time (coalesced, U loads in flight per lane) and finds each
+        // id's row by a 5-step search over the rows' starts held by the lanes
+        constexpr int U = 8;
+        for (int g = warp; g < WBK; g += NWARP) {
+            const int64_t r0 = t0 + 32 * g;
+            if (r0 >= n) break;  // warp-uniform
+            const int nrw = (int)min64(n - r0, 32);
+            const int64_t a = D.indptr[r0 + (lane < nrw ? lane : nrw)], B = D.indptr[r0 + nrw];
+            const int64_t A = __shfl_sync(0xffffffffu, a, 0);
+            int64_t nx = __shfl_down_sync(0xffffffffu, a, 1);
+            if (lane == 31) nx = B;
+            const bool ok = A >= 0 && B >= A && B <= nnz && B - A < (1ll << 30) && (lane >= nrw || nx >= a);
+            if (!__all_sync(0xffffffffu, ok)) {  // a malformed row: flagged, the word not read
                 bad = 1;
-                e1 = e0;
+                continue;
             }
+            const int ar = (int)(a - A), span = (int)(B - A);  // lanes past the last row hold span
+            const int32_t *const src = D.indices + A;
             uint32_t *const trow = tile + g * ms;
-            const uint32_t bit = 1u << lane;
-            // four independent loads in flight per lane
-            for (int64_t e = e0; e < e1; e += 4) {
-                int32_t it[4];
+            for (int base = 0; base < span; base += 32 * U) {
+                int32_t it[U];
 #pragma unroll
-                for (int u = 0; u < 4; u++) it[u] = e + u < e1 ? __ldg(D.indices + e + u) : 0;
+                for (int u = 0; u < U; u++) {
+                    const int p = base + 32 * u + lane;
+                    it[u] = p < span ? __ldg(src + p) : 0;
+                }
 #pragma unroll
-                for (int u = 0; u < 4; u++)
-                    if (e + u < e1) {
+                for (int u = 0; u < U; u++) {
+                    if (base + 32 * u >= span) break;  // warp-uniform
+                    const int p = base + 32 * u + lane;
+                    int r = 0;  // last row whose start is <= p
+#pragma unroll
+                    for (int st = 16; st > 0; st >>= 1) {
+                        const int c = __shfl_sync(0xffffffffu, ar, r + st);
+                        if (c <= p) r += st;
+                    }
+                    if (p < span) {
                         if ((unsigned)it[u] >= (unsigned)m) {
                             bad = 1;
                             continue;
                         }
-                        atomicOr(trow + it[u], bit);
+                        atomicOr(trow + it[u], 1u << r);
                     }
+                }
+            }
+        }
+    } else {
+        for (int g = warp; g < WBK; g += NWARP) {
+            const int64_t r = t0 + 32 * g + lane;
+            if (r < n) {
+                int64_t e0 = D.indptr[r], e1 = D.indptr[r + 1];
+                if (e1 < e0 || e0 < 0 || e1 > nnz) {  // a malformed row: flagged, not read
+                    bad = 1;
+                    e1 = e0;
+                }
+                uint32_t *const trow = tile + g * ms;
+                const uint32_t bit = 1u << lane;
+                // four independent loads in flight per lane
+                for (int64_t e = e0; e < e1; e += 4) {
+                    int32_t it[4];
+#pragma unroll
+                    for (int u = 0; u < 4; u++) it[u] = e + u < e1 ? __ldg(D.indices + e + u) : 0;
+#pragma unroll
+                    for (int u = 0; u < 4; u++)
+                        if (e + u < e1) {
+                            if ((unsigned)it[u] >= (unsigned)m) {
+                                bad = 1;
+                                continue;
+                            }
+                            atomicOr(trow + it[u], bit);
+                        }
+                }
             }
         }
     }
@@ -174,6 +225,13 @@ batch_build_rows_kernel(const DbDesc *__restrict__ dbs, int n_db, const int64_t 
         for (int o = QPC / 2; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
         if (j < m && q == 0 && c) atomicAdd(&sup[D.item_off + j], c);
     }
+}
+
+
+// unit -> database map of the rows build: one CTA per database
+__global__ void batch_unit_db_kernel(const int64_t *__restrict__ unit_prefix, int *__restrict__ unit_db) {
+    const int d = blockIdx.x;
+    for (int64_t u = unit_prefix[d] + threadIdx.x; u < unit_prefix[d + 1]; u += blockDim.x) unit_db[u] = d;
 }
 
 // One CTA per item column of the batch: S(I_j) by popcount.
@@ -746,7 +804,7 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
     // rows build (every database's columns fit one CTA's shared memory):
     // words per block as tuned, where the block's tile fits
     const bool rows_build = L.ib == L.m_max;
-    int wbk = ctx->batch_build_block == 64 ? 64 : 32;
+    int wbk = ctx->batch_build_block == 64 ? 64 : ctx->batch_build_block == 16 ? 16 : 32;
     if ((size_t)wbk * (size_t)(L.m_max | 1) * sizeof(uint32_t) > 227u * 1024u) wbk = 32;
     const int unit_words = rows_build ? wbk : WB;
     int64_t host_nnz_total = 0, host_ptr_total = 0;
@@ -787,40 +845,6 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
             host_nnz_total += x.indptr[x.n_trans];
             host_ptr_total += x.n_trans + 1;
         }
-    }
-    // the tensor-core pair pass's (database, tile) units, longest first
-    // Pipelined groups of databases: group s is built and ranked on the ctx
-    // stream while the pair pass of group s - 1 runs on the side stream.
-    // Groups hold about equal transactions.  Only the fast paths pipeline:
-    // rows build, per-database rank and finalize, tensor-core pairs.
-    const bool pairs_tc_wanted = !(flags & FIM_PAIRS_POPC);
-    int n_seg = (pairs_tc_wanted && rows_build && L.m_max <= RANK_CAP && L.m_max <= FIN_CAP && maxlen != 1)
-                    ? ctx->batch_segments : 1;
-    if (n_seg > n_db) n_seg = n_db > 0 ? n_db : 1;
-    std::vector<int> seg_db(n_seg + 1, 0);
-    {
-        int64_t total_n = 0;
-        for (int d = 0; d < n_db; d++) total_n += L.dbs[d].n + 1;
-        int64_t acc = 0;
-        int s = 1;
-        for (int d = 0; d < n_db && s < n_seg; d++) {
-            acc += L.dbs[d].n + 1;
-            if (acc * n_seg >= total_n * s) seg_db[s++] = d + 1;
-        }
-        while (s < n_seg) { seg_db[s] = seg_db[s - 1]; s++; }
-        seg_db[n_seg] = n_db;
-    }
-    // the tensor-core pair pass's (database, tile) units, each group's longest first
-    std::vector<unsigned long long> pair_units;
-    std::vector<int64_t> seg_unit(n_seg + 1, 0);
-    bool pairs_tc = pairs_tc_wanted;
-    for (int sg = 0; sg < n_seg && pairs_tc; sg++) {
-        pairs_tc = batch_pairs_tc_units(L.dbs, seg_db[sg], seg_db[sg + 1], pair_units, (size_t)1 << 24);
-        seg_unit[sg + 1] = (int64_t)pair_units.size();
-    }
-    if (!pairs_tc) {
-        n_seg = 1;
-        seg_db.assign({0, n_db});
     }
     // ---- inputs: host CSRs in page-locked memory are read in place ----------
     // (the build kernel streams them over the host link, which caps copies
@@ -892,6 +916,40 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
             L.dbs[d].indices = in[d].indices;
         }
     }
+    const bool coal = ctx->batch_build_coal != 0;  // warp-coalesced id loads in the one-CTA-per-block build
+    // Pipelined groups of databases: group s is built and ranked on the ctx
+    // stream while the pair pass of group s - 1 runs on the side stream.
+    // Groups hold about equal transactions.  Only the fast paths pipeline:
+    // rows build, per-database rank and finalize, tensor-core pairs.
+    const bool pairs_tc_wanted = !(flags & FIM_PAIRS_POPC);
+    int n_seg = (pairs_tc_wanted && rows_build && L.m_max <= RANK_CAP && L.m_max <= FIN_CAP && maxlen != 1)
+                    ? ctx->batch_segments : 1;
+    if (n_seg > n_db) n_seg = n_db > 0 ? n_db : 1;
+    std::vector<int> seg_db(n_seg + 1, 0);
+    {
+        int64_t total_n = 0;
+        for (int d = 0; d < n_db; d++) total_n += L.dbs[d].n + 1;
+        int64_t acc = 0;
+        int s = 1;
+        for (int d = 0; d < n_db && s < n_seg; d++) {
+            acc += L.dbs[d].n + 1;
+            if (acc * n_seg >= total_n * s) seg_db[s++] = d + 1;
+        }
+        while (s < n_seg) { seg_db[s] = seg_db[s - 1]; s++; }
+        seg_db[n_seg] = n_db;
+    }
+    // the tensor-core pair pass's (database, tile) units, each group's longest first
+    std::vector<unsigned long long> pair_units;
+    std::vector<int64_t> seg_unit(n_seg + 1, 0);
+    bool pairs_tc = pairs_tc_wanted;
+    for (int sg = 0; sg < n_seg && pairs_tc; sg++) {
+        pairs_tc = batch_pairs_tc_units(L.dbs, seg_db[sg], seg_db[sg + 1], pair_units, (size_t)1 << 24);
+        seg_unit[sg + 1] = (int64_t)pair_units.size();
+    }
+    if (!pairs_tc) {
+        n_seg = 1;
+        seg_db.assign({0, n_db});
+    }
     // ---- device buffers -------------------------------------------------------
     const int workers = ctx->num_sms * ctx->dfs_ctas_per_sm;
     // databases of short columns: one warp per prefix-extension worker (CTAs
@@ -928,6 +986,8 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
     const int plan_mode = ((flags & FIM_LEARNED) && ctx->learned_order) ? 2 : ctx->root_sort;
     if (pairs_tc)
         FIM_TRY(fim_reserve(ctx, ctx->batch_units, sizeof(unsigned long long) * (pair_units.size() ? pair_units.size() : 1)));
+    if (rows_build)
+        FIM_TRY(fim_reserve(ctx, ctx->batch_unit_db, sizeof(int) * (size_t)(L.unit_prefix[n_db] ? L.unit_prefix[n_db] : 1)));
     if (ctx->rec_cap < (1ull << 22)) {
         ctx->rec_cap = 1ull << 22;
         ctx->rec_items_cap = 1ull << 24;
@@ -1018,6 +1078,9 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
         mix(&L.ib, sizeof(L.ib));
         mix(&pairs_tc, sizeof(pairs_tc));
         mix(&wbk, sizeof(wbk));
+        mix(&coal, sizeof(coal));
+        const void *udb_ptr = ctx->batch_unit_db.p;
+        mix(&udb_ptr, sizeof(udb_ptr));
         // every launch-shape knob the captured launches depend on
         const int shape[9] = {workers, ctx->dfs_block, ctx->pairs_kdrain, ctx->pairs_split, ctx->batch_pairs_shape,
                               ctx->dfs_ctas_per_sm, plan_mode, ctx->learned_order, n_seg};
@@ -1034,10 +1097,15 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
         const size_t smem_build = (size_t)L.ib * WB * sizeof(uint32_t);
         FIM_CUDA_TRY(cudaFuncSetAttribute(batch_build_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)smem_build));
-        if (rows_build)
-            FIM_CUDA_TRY(cudaFuncSetAttribute(wbk == 64 ? batch_build_rows_kernel<64> : batch_build_rows_kernel<32>,
-                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)((size_t)(L.m_max | 1) * wbk * sizeof(uint32_t))));
+        const size_t smem_rows = (size_t)(L.m_max | 1) * wbk * sizeof(uint32_t);
+        if (rows_build) {
+            auto (*const kern)(const DbDesc *, const int *, const int64_t *, int64_t, uint32_t *, uint32_t *,
+                               int *) -> void =
+                wbk == 64   ? (coal ? batch_build_rows_kernel<64, true> : batch_build_rows_kernel<64, false>)
+                : wbk == 16 ? (coal ? batch_build_rows_kernel<16, true> : batch_build_rows_kernel<16, false>)
+                            : (coal ? batch_build_rows_kernel<32, true> : batch_build_rows_kernel<32, false>);
+            FIM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_rows));
+        }
         const bool reuse = ctx->batch_graph_exec && ctx->batch_graph_key == key;
         if (!reuse) {
             if (ctx->batch_graph_exec) {
@@ -1061,19 +1129,25 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
             const int64_t units = L.unit_prefix[n_db], items = L.item_prefix[n_db], tiles = L.tile_prefix[n_db];
             // rows-per-thread build with fused supports when every database's
             // block of columns fits shared memory (ib == m_max <= 1,024)
-            const size_t smem_rows = (size_t)(L.m_max | 1) * wbk * sizeof(uint32_t);
             if (rows_build && items > 0)
                 cudaMemsetAsync(ctx->item_sup.p, 0, sizeof(uint32_t) * (size_t)items, st);
+            if (rows_build && units > 0)
+                batch_unit_db_kernel<<<(unsigned)n_db, 256, 0, st>>>(d_unit, ctx->batch_unit_db.as<int>());
             auto build_rows = [&](int64_t u0, int64_t u1, cudaStream_t s_) {
                 if (u1 <= u0) return;
+                const unsigned grid = (unsigned)(u1 - u0);
+                int *const udb = ctx->batch_unit_db.as<int>();
+                uint32_t *const bmp = ctx->bm.as<uint32_t>(), *const sup = ctx->item_sup.as<uint32_t>();
+                int *const flg = ctx->dev_flag.as<int>();
+                auto go = [&](auto kern) {
+                    kern<<<grid, BUILD_ROWS_THREADS, smem_rows, s_>>>(d_dbs, udb, d_unit, u0, bmp, sup, flg);
+                };
                 if (wbk == 64)
-                    batch_build_rows_kernel<64><<<(unsigned)(u1 - u0), BUILD_ROWS_THREADS, smem_rows, s_>>>(
-                        d_dbs, n_db, d_unit, u0, ctx->bm.as<uint32_t>(), ctx->item_sup.as<uint32_t>(),
-                        ctx->dev_flag.as<int>());
+                    coal ? go(batch_build_rows_kernel<64, true>) : go(batch_build_rows_kernel<64, false>);
+                else if (wbk == 16)
+                    coal ? go(batch_build_rows_kernel<16, true>) : go(batch_build_rows_kernel<16, false>);
                 else
-                    batch_build_rows_kernel<32><<<(unsigned)(u1 - u0), BUILD_ROWS_THREADS, smem_rows, s_>>>(
-                        d_dbs, n_db, d_unit, u0, ctx->bm.as<uint32_t>(), ctx->item_sup.as<uint32_t>(),
-                        ctx->dev_flag.as<int>());
+                    coal ? go(batch_build_rows_kernel<32, true>) : go(batch_build_rows_kernel<32, false>);
             };
             auto rank_db = [&](int da, int db_, cudaStream_t s_) {
                 if (db_ > da)
@@ -1171,7 +1245,7 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
             if (ie != cudaSuccess) { fim_set_cuda_error(ie, "instantiate", __FILE__, __LINE__); return FIM_E_CUDA; }
             ctx->batch_graph_exec = ex;
             ctx->batch_graph_key = key;
-            ctx->batch_graph_launches = 9;  // build, rank, pairs, finalize, 3 root plan, DFS, epoch
+            ctx->batch_graph_launches = 10;  // unit map, build, rank, pairs, finalize, 3 root plan, DFS, epoch
         }
         FIM_CUDA_TRY(cudaGraphLaunch((cudaGraphExec_t)ctx->batch_graph_exec, st));
         ctx->launches += ctx->batch_graph_launches;

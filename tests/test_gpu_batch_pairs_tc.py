@@ -2,7 +2,9 @@
 and against the CUDA-core tiles (FIM_PAIRS_POPC): databases whose frequent
 items fill one 128 x 128 tile partly, exactly, or spill into several tiles
 (off-diagonal ones included), ragged transaction counts, and launch shapes
-that force many accumulator drains per tile and one CTA for every tile."""
+that force many accumulator drains per tile and one CTA for every tile.
+Also the batched build's blocks, with coalesced and lane-per-row id reads,
+on ragged, long-row, packed and malformed CSRs."""
 import numpy as np
 import pytest
 
@@ -86,14 +88,18 @@ def test_every_pair_pass_shape_is_exact(ctx, shape):
     _check(ctx, dbs, ms, 2)
 
 
-@pytest.mark.parametrize("block", [32, 64])
-def test_build_blocks_are_exact(ctx, block):
-    # ragged transaction counts around the 1,024 / 2,048-row blocks and the
-    # 4,096-row column padding; duplicates and empty rows
+@pytest.mark.parametrize("block,coal", [(16, 1), (32, 1), (64, 1), (32, 0), (16, 0)])
+def test_build_blocks_are_exact(ctx, block, coal):
+    # ragged transaction counts around the 512 / 1,024 / 2,048-row blocks and
+    # the 4,096-row column padding; duplicates and empty rows; rows long
+    # enough that a warp reads its 32 rows' ids in several rounds of 256;
+    # databases packed back to back, so that their item ids start at every
+    # alignment
     fim.fim_set_tuning(ctx, "batch_build_block", block)
+    fim.fim_set_tuning(ctx, "batch_build_coal", coal)
     rng = np.random.default_rng(block)
     dbs, ms = [], []
-    for i, n in enumerate([1, 31, 1023, 1024, 1025, 2047, 2049, 4095, 4097, 9000]):
+    for i, n in enumerate([1, 31, 511, 513, 1023, 1024, 1025, 2047, 2049, 4095, 4097, 9000]):
         m = int(rng.integers(3, 400))
         rows = [list(rng.integers(0, m, int(rng.integers(0, 9)))) for _ in range(n)]
         c = datagen.from_lists(rows, m)
@@ -101,6 +107,42 @@ def test_build_blocks_are_exact(ctx, block):
         ms.append(max(1, n // 40))
     fim.fim_mine_batched(ctx, dbs, ms)
     _check(ctx, dbs, ms, 0)
+    # long rows (pairs only: their supports depend on every bit's position)
+    rng = np.random.default_rng(7)
+    for i, (n, L, m) in enumerate([(700, 40, 450), (1500, 25, 300), (300, 90, 500), (2100, 12, 100)]):
+        rows = [list(rng.integers(0, m, int(rng.integers(L // 2, 2 * L)))) for _ in range(n)]
+        dbs.append(datagen.from_lists(rows, m))
+        p = 1.25 * L / m
+        ms.append(max(2, int(n * p * p / 2)))
+    ptr = np.concatenate([c.indptr for c in dbs])
+    idx = np.concatenate([c.indices for c in dbs])
+    packed, po, io = [], 0, 0
+    for c in dbs:
+        packed.append(datagen.Csr(indptr=ptr[po:po + c.n + 1], indices=idx[io:io + c.nnz], m=c.m))
+        po += c.n + 1
+        io += c.nnz
+    for batch in (dbs, packed):
+        fim.fim_mine_batched(ctx, batch, ms, fim.FIM_MAXLEN(2))
+        _check(ctx, dbs, ms, 2)
+
+
+@pytest.mark.parametrize("block,coal", [(16, 1), (32, 1), (32, 0)])
+def test_build_flags_malformed_rows(ctx, block, coal):
+    # a row that ends before it starts, a row offset past the last id and an
+    # item id out of range are each reported, whatever the block and build
+    fim.fim_set_tuning(ctx, "batch_build_block", block)
+    fim.fim_set_tuning(ctx, "batch_build_coal", coal)
+    good = [datagen.zipf_baskets(3000, 100, 0.8, 6.0, [3, i]) for i in range(3)]
+    bad = [datagen.Csr(np.array([0, 3, 1, 4], np.int64), np.array([0, 1, 2, 3], np.int32), 5),
+           datagen.Csr(np.array([0, 9, 4], np.int64), np.array([0, 1, 2, 3], np.int32), 5),
+           datagen.Csr(np.array([0, 2, 4], np.int64), np.array([0, 1, 7, 3], np.int32), 5)]
+    for b in bad:
+        with pytest.raises(fim.FimError) as e:
+            fim.fim_mine_batched(ctx, good[:1] + [b] + good[1:], [30, 1, 30, 30])
+        assert e.value.code == fim.FIM_E_INVAL
+    ms = [30] * len(good)
+    fim.fim_mine_batched(ctx, good, ms)
+    _check(ctx, good, ms, 0)
 
 
 def test_autotuned_batch_shape_is_exact(ctx):

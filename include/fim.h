@@ -177,10 +177,12 @@ int fim_get_stats(const fim_ctx *ctx, fim_stats *out);
  *                                candidates first (1, default).  Either way a root whose
  *                                class has no candidate is dropped before the
  *                                prefix extension starts
- *   "batch_segments"   1..8      fim_mine_batched pipelines this many groups of
+ *   "batch_segments"   0..8      fim_mine_batched pipelines this many groups of
  *                                databases (about equal transactions): a group's
- *                                pair pass runs while the next group is built
- *                                (default 1 = one group)
+ *                                pair pass runs while the next group is built;
+ *                                0 (default) = eight groups when the build reads
+ *                                page-locked host input over the link (the build
+ *                                then one CTA per SM), else one
  *   "dfs_warp"         0, 1      fim_mine_batched with every database's columns at
  *                                most 4,096 words: one warp per prefix-extension
  *                                worker instead of one CTA (default 1)
@@ -220,9 +222,14 @@ int fim_get_stats(const fim_ctx *ctx, fim_stats *out);
  *                                memory (cudaHostAlloc, cudaHostRegister) is read
  *                                by the build kernel in place over the host link,
  *                                without a staging copy (default 1; other host
- *                                memory is copied; a batch is read in place when
- *                                its arrays form at most 64 contiguous runs, each
- *                                inside one such allocation)
+ *                                memory is copied; a batch counts as page-locked
+ *                                when its arrays form at most 64 contiguous runs,
+ *                                each inside one such allocation)
+ *   "batch_stream_copies" 0, 1   a page-locked host batch (as above) goes up by
+ *                                copies of database groups inside the batch's
+ *                                graph, each group's build starting when its copy
+ *                                lands, beside the later groups' uploads (default
+ *                                1); 0 = the build reads it in place
  *   "upload_chunks"    1..16     host input to fim_build_bitmaps: the indices go
  *                                up in this many chunks, each built as soon as it
  *                                lands (default 4; 1 = one copy, then the build)

@@ -35,7 +35,7 @@ BATCH_SPACE = {
     "split_depth": [4, 8],
     "dfs_warp_ctas": [2, 3],
 }
-BATCH_DEFAULT = dict(DEFAULT, batch_pairs_shape=0, batch_build_block=32, batch_segments=1, dfs_warp_ctas=2)
+BATCH_DEFAULT = dict(DEFAULT, batch_pairs_shape=0, batch_build_block=32, batch_segments=0, dfs_warp_ctas=2)
 
 
 def valid(cfg: dict) -> bool:

@@ -38,6 +38,17 @@ void fim_set_cuda_error(cudaError_t e, const char *what, const char *file, int l
     (void)cudaGetLastError();  // clear a sticky-free error so the ctx stays usable
 }
 
+// The ctx's side stream, at the device's highest priority: work put there
+// (a group's pair pass beside the next group's build) is scheduled first
+// where the two kernels compete for an SM.
+int fim_aux_stream(fim_ctx *ctx) {
+    if (ctx->aux_stream) return FIM_OK;
+    int least = 0, greatest = 0;
+    FIM_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    FIM_CUDA_TRY(cudaStreamCreateWithPriority(&ctx->aux_stream, cudaStreamNonBlocking, greatest));
+    return FIM_OK;
+}
+
 int fim_reserve(fim_ctx *ctx, DevBuf &b, size_t bytes) {
     if (bytes == 0) bytes = 16;
     if (bytes <= b.bytes) return FIM_OK;
@@ -171,6 +182,9 @@ void fim_destroy(fim_ctx *ctx) {
         if (u) cudaStreamDestroy(u);
     if (ctx->aux_stream) cudaStreamDestroy(ctx->aux_stream);
     for (cudaEvent_t e : ctx->seg_ev)
+        if (e) cudaEventDestroy(e);
+    if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+    for (cudaEvent_t e : ctx->copy_ev)
         if (e) cudaEventDestroy(e);
     for (cudaEvent_t e : ctx->aux_ev)
         if (e) cudaEventDestroy(e);
@@ -322,7 +336,7 @@ int mine_once(fim_ctx *ctx, uint32_t thr, uint32_t flags, MineState &ms, bool *r
     const bool sp_items = do_dfs && sp_cap > 0 && (double)mf * (double)sp_cap * 8.0 <= (double)(1ull << 30);
     if (sp_items) {
         FIM_TRY(reserve_sparse_items(ctx, mf, sp_cap));
-        if (!ctx->aux_stream) FIM_CUDA_TRY(cudaStreamCreateWithFlags(&ctx->aux_stream, cudaStreamNonBlocking));
+        FIM_TRY(fim_aux_stream(ctx));
         for (auto &e : ctx->aux_ev)
             if (!e) FIM_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
         FIM_CUDA_TRY(cudaEventRecord(ctx->aux_ev[0], st));
@@ -594,6 +608,7 @@ int fim_set_tuning(fim_ctx *ctx, const char *key, int64_t v) {
         {"upload_chunks", &ctx->upload_chunks, 1, 16},
         {"compact_cluster", &ctx->compact_cluster, 0, 1},
         {"upload_mapped", &ctx->upload_mapped, 0, 1},
+        {"batch_stream_copies", &ctx->batch_stream_copies, 0, 1},
         {"spin_limit_ms", &ctx->spin_limit_ms, 1, 600000},
         {"debug_checks", &ctx->debug_checks, 0, 1},
         {"test_withhold_task", &ctx->test_withhold_task, -1, 1 << 20},
@@ -603,7 +618,7 @@ int fim_set_tuning(fim_ctx *ctx, const char *key, int64_t v) {
         {"batch_build_coal", &ctx->batch_build_coal, 0, 1},
         {"root_sort", &ctx->root_sort, 0, 1},
         {"record_chunk", &ctx->rec_chunk, 1, 1024},
-        {"batch_segments", &ctx->batch_segments, 1, 8},
+        {"batch_segments", &ctx->batch_segments, 0, 8},
         {"dfs_warp", &ctx->dfs_warp, 0, 1},
         {"dfs_warp_ctas", &ctx->dfs_warp_ctas, 2, 3},
     };

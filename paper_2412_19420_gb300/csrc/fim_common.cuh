@@ -279,11 +279,14 @@ struct fim_ctx {
     int batch_build_coal = 1;   // batched build: a warp reads its rows' ids coalesced
     int root_sort = 1;          // root order without the network: 0 pair-pass order, 1 candidate count
     int rec_chunk = 1;          // record slots a DFS worker reserves at a time
-    int batch_segments = 1;     // database groups the batch graph pipelines (build || pairs)
+    int batch_segments = 0;     // database groups the batch graph pipelines (build || pairs); 0 automatic
     int dfs_warp = 1;           // batches of short columns: one warp per prefix-extension worker
     int dfs_warp_ctas = 2;      // CTAs of warp workers per SM (2 or 3)
     bool force_cta_dfs = false; // set while a batch is re-mined with CTA workers
     cudaEvent_t seg_ev[10] = {};  // fork, join and per-group events of that pipeline
+    int batch_stream_copies = 1;  // page-locked host batches go up group by group beside the mine
+    cudaStream_t copy_stream = nullptr;  // those uploads
+    cudaEvent_t copy_ev[10] = {};        // fork and per-group events of the uploads
     int compact_cluster = 1;    // small outputs: sort in one cluster launch
     int csort_cl[5] = {0, 0, 0, 0, 0};  // cluster size per key width (0 unknown, -1 none)
     int debug_checks = 0;       // device-side invariant checks after build and mine
@@ -305,6 +308,7 @@ struct fim_ctx {
 };
 
 int fim_reserve(fim_ctx *ctx, DevBuf &b, size_t bytes);
+int fim_aux_stream(fim_ctx *ctx);  // create the side stream (highest priority) once
 void fim_release(fim_ctx *ctx, DevBuf &b);
 
 // ---------------------------------------------------------------- launchers

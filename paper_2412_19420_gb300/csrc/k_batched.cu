@@ -98,19 +98,20 @@ batch_build_kernel(const DbDesc *__restrict__ dbs, int n_db, const int64_t *__re
 // column's popcount over the block rides along: a shuffle sum over those
 // lanes, added into S(I_j) (Eq. 3), so no second pass reads the columns.
 // Blocks past the last transaction hold padding words only and just write
-// zeros.  A CTA finds its database in a unit -> database map.
+// zeros.  A CTA finds its database in a unit -> database map.  The
+// persistent form (one CTA per SM walking the units) serves host input read
+// over the link, where it leaves each SM room for the pair pass of an earlier
+// group of databases.
 constexpr int BUILD_ROWS_THREADS = 512;
 template <int WBK, bool COAL>
-__global__ void __launch_bounds__(BUILD_ROWS_THREADS)
-batch_build_rows_kernel(const DbDesc *__restrict__ dbs, const int *__restrict__ unit_db,
-                        const int64_t *__restrict__ unit_prefix, int64_t unit_base, uint32_t *__restrict__ bm,
-                        uint32_t *__restrict__ sup, int *__restrict__ flag) {
+__device__ __forceinline__ void build_rows_unit(const DbDesc *__restrict__ dbs, const int *__restrict__ unit_db,
+                                                const int64_t *__restrict__ unit_prefix, int64_t unit,
+                                                uint32_t *__restrict__ bm, uint32_t *__restrict__ sup,
+                                                int *__restrict__ flag, uint32_t *tile) {
     static_assert(WBK % 4 == 0 && WBK / 4 <= 32 && 32 % (WBK / 4) == 0, "a column's chunks share a warp");
     constexpr int NWARP = BUILD_ROWS_THREADS / 32;
     constexpr int QPC = WBK / 4;  // 16-byte chunks of a column in this block
-    extern __shared__ __align__(16) uint32_t tile[];  // [WBK][ms]
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t unit = unit_base + blockIdx.x;
     const int d = unit_db[unit];
     const DbDesc &D = dbs[d];
     const int m = D.m, ms = m | 1;  // odd pitch: the transposed reads below are conflict-free
@@ -227,6 +228,33 @@ batch_build_rows_kernel(const DbDesc *__restrict__ dbs, const int *__restrict__ 
     }
 }
 
+template <int WBK, bool COAL, bool PERSIST>
+__global__ void __launch_bounds__(BUILD_ROWS_THREADS)
+batch_build_rows_kernel(const DbDesc *__restrict__ dbs, const int *__restrict__ unit_db,
+                        const int64_t *__restrict__ unit_prefix, int64_t unit_base, int64_t unit_end,
+                        uint32_t *__restrict__ bm, uint32_t *__restrict__ sup, int *__restrict__ flag) {
+    extern __shared__ __align__(16) uint32_t tile[];  // [WBK][ms]
+    if (!PERSIST) {
+        build_rows_unit<WBK, COAL>(dbs, unit_db, unit_prefix, unit_base + blockIdx.x, bm, sup, flag, tile);
+        return;
+    }
+    for (int64_t u = unit_base + blockIdx.x; u < unit_end; u += gridDim.x) {
+        build_rows_unit<WBK, COAL>(dbs, unit_db, unit_prefix, u, bm, sup, flag, tile);
+        __syncthreads();  // the tile has been written out before the next unit clears it
+    }
+}
+
+using BuildRowsFn = void (*)(const DbDesc *, const int *, const int64_t *, int64_t, int64_t, uint32_t *, uint32_t *,
+                             int *);
+template <int WBK>
+BuildRowsFn build_rows_fn_w(bool coal, bool persist) {
+    return coal ? (persist ? batch_build_rows_kernel<WBK, true, true> : batch_build_rows_kernel<WBK, true, false>)
+                : (persist ? batch_build_rows_kernel<WBK, false, true> : batch_build_rows_kernel<WBK, false, false>);
+}
+BuildRowsFn build_rows_fn(int wbk, bool coal, bool persist) {
+    return wbk == 64 ? build_rows_fn_w<64>(coal, persist)
+           : wbk == 16 ? build_rows_fn_w<16>(coal, persist) : build_rows_fn_w<32>(coal, persist);
+}
 
 // unit -> database map of the rows build: one CTA per database
 __global__ void batch_unit_db_kernel(const int64_t *__restrict__ unit_prefix, int *__restrict__ unit_db) {
@@ -850,7 +878,7 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
     // (the build kernel streams them over the host link, which caps copies
     // and in-kernel reads alike, so the upload and the build become one pass);
     // other host memory goes up in one staging copy per contiguous run
-    bool mapped = false;
+    bool mapped = false, streamed = false;
     if (!on_device && ctx->upload_mapped) {
         // contiguous host ranges of the indptr arrays and of the index arrays
         std::vector<std::pair<const char *, size_t>> rp, ri;
@@ -866,7 +894,11 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
             note(ri, in[d].indices, sizeof(int32_t) * (size_t)in[d].indptr[in[d].n_trans]);
         }
         rp.insert(rp.end(), ri.begin(), ri.end());
-        mapped = rp.size() <= 64 && mapped_host_ranges(rp);
+        // page-locked: streamed up group by group inside the graph (copies
+        // beside the mine), or read in place by the build
+        const bool locked = rp.size() <= 64 && mapped_host_ranges(rp);
+        streamed = locked && ctx->batch_stream_copies;
+        mapped = locked && !streamed;
         if (mapped)
             for (int d = 0; d < n_db; d++) {
                 L.dbs[d].indptr = in[d].indptr;  // unified addressing: the host address is the device address
@@ -901,8 +933,11 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
         for (int d = 0; d < n_db; d++) {
             const fim_db_desc &x = in[d];
             const int64_t nnz = x.indptr[x.n_trans];
-            FIM_TRY(add(rp, x.indptr, ctx->csr_ptr.as<int64_t>() + po, sizeof(int64_t) * (size_t)(x.n_trans + 1)));
-            if (nnz > 0) FIM_TRY(add(ri, x.indices, ctx->csr_idx.as<int32_t>() + io, sizeof(int32_t) * (size_t)nnz));
+            if (!streamed) {  // streamed: the graph copies each group of databases
+                FIM_TRY(add(rp, x.indptr, ctx->csr_ptr.as<int64_t>() + po, sizeof(int64_t) * (size_t)(x.n_trans + 1)));
+                if (nnz > 0)
+                    FIM_TRY(add(ri, x.indices, ctx->csr_idx.as<int32_t>() + io, sizeof(int32_t) * (size_t)nnz));
+            }
             L.dbs[d].indptr = ctx->csr_ptr.as<int64_t>() + po;
             L.dbs[d].indices = ctx->csr_idx.as<int32_t>() + io;
             po += x.n_trans + 1;
@@ -916,14 +951,19 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
             L.dbs[d].indices = in[d].indices;
         }
     }
-    const bool coal = ctx->batch_build_coal != 0;  // warp-coalesced id loads in the one-CTA-per-block build
+    const bool coal = ctx->batch_build_coal != 0;  // warp-coalesced id loads in the build
     // Pipelined groups of databases: group s is built and ranked on the ctx
     // stream while the pair pass of group s - 1 runs on the side stream.
     // Groups hold about equal transactions.  Only the fast paths pipeline:
     // rows build, per-database rank and finalize, tensor-core pairs.
     const bool pairs_tc_wanted = !(flags & FIM_PAIRS_POPC);
+    // Automatic (batch_segments 0): with page-locked host input the link
+    // bounds the mine, so eight groups: each group's upload (streamed) or
+    // build reading host memory in place (mapped, the build then one CTA per
+    // SM) runs beside the earlier groups' work; else one group.
+    const int seg_want = ctx->batch_segments > 0 ? ctx->batch_segments : (mapped || streamed ? 8 : 1);
     int n_seg = (pairs_tc_wanted && rows_build && L.m_max <= RANK_CAP && L.m_max <= FIN_CAP && maxlen != 1)
-                    ? ctx->batch_segments : 1;
+                    ? seg_want : 1;
     if (n_seg > n_db) n_seg = n_db > 0 ? n_db : 1;
     std::vector<int> seg_db(n_seg + 1, 0);
     {
@@ -949,6 +989,31 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
     if (!pairs_tc) {
         n_seg = 1;
         seg_db.assign({0, n_db});
+    }
+    const bool persist_build = mapped && n_seg > 1;
+    // streamed uploads: each group's runs of contiguous host arrays
+    struct HostCopy {
+        const char *src;
+        char *dst;
+        size_t bytes;
+    };
+    std::vector<std::vector<HostCopy>> seg_copies(streamed ? n_seg : 0);
+    for (int sg = 0; streamed && sg < n_seg; sg++) {
+        std::vector<HostCopy> cp_ptr, cp_idx;
+        auto note = [](std::vector<HostCopy> &v, const void *src, const void *dst, size_t bytes) {
+            if (!bytes) return;
+            if (!v.empty() && v.back().src + v.back().bytes == (const char *)src &&
+                v.back().dst + v.back().bytes == (const char *)dst)
+                v.back().bytes += bytes;
+            else
+                v.push_back({(const char *)src, (char *)dst, bytes});
+        };
+        for (int d = seg_db[sg]; d < seg_db[sg + 1]; d++) {
+            note(cp_ptr, in[d].indptr, L.dbs[d].indptr, sizeof(int64_t) * (size_t)(in[d].n_trans + 1));
+            note(cp_idx, in[d].indices, L.dbs[d].indices, sizeof(int32_t) * (size_t)in[d].indptr[in[d].n_trans]);
+        }
+        seg_copies[sg] = cp_ptr;
+        seg_copies[sg].insert(seg_copies[sg].end(), cp_idx.begin(), cp_idx.end());
     }
     // ---- device buffers -------------------------------------------------------
     const int workers = ctx->num_sms * ctx->dfs_ctas_per_sm;
@@ -1079,6 +1144,10 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
         mix(&pairs_tc, sizeof(pairs_tc));
         mix(&wbk, sizeof(wbk));
         mix(&coal, sizeof(coal));
+        mix(&persist_build, sizeof(persist_build));
+        mix(&streamed, sizeof(streamed));
+        for (const auto &v : seg_copies)
+            for (const HostCopy &c : v) mix(&c, sizeof(c));
         const void *udb_ptr = ctx->batch_unit_db.p;
         mix(&udb_ptr, sizeof(udb_ptr));
         // every launch-shape knob the captured launches depend on
@@ -1099,12 +1168,8 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
                                           (int)smem_build));
         const size_t smem_rows = (size_t)(L.m_max | 1) * wbk * sizeof(uint32_t);
         if (rows_build) {
-            auto (*const kern)(const DbDesc *, const int *, const int64_t *, int64_t, uint32_t *, uint32_t *,
-                               int *) -> void =
-                wbk == 64   ? (coal ? batch_build_rows_kernel<64, true> : batch_build_rows_kernel<64, false>)
-                : wbk == 16 ? (coal ? batch_build_rows_kernel<16, true> : batch_build_rows_kernel<16, false>)
-                            : (coal ? batch_build_rows_kernel<32, true> : batch_build_rows_kernel<32, false>);
-            FIM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_rows));
+            FIM_CUDA_TRY(cudaFuncSetAttribute(build_rows_fn(wbk, coal, persist_build),
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_rows));
         }
         const bool reuse = ctx->batch_graph_exec && ctx->batch_graph_key == key;
         if (!reuse) {
@@ -1114,9 +1179,15 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
             }
             cudaGraph_t g = nullptr;
             if (n_seg > 1) {  // the side stream and the group events, made outside the capture
-                if (!ctx->aux_stream) FIM_CUDA_TRY(cudaStreamCreateWithFlags(&ctx->aux_stream, cudaStreamNonBlocking));
+                FIM_TRY(fim_aux_stream(ctx));
                 for (int sg = 0; sg <= n_seg; sg++)
                     if (!ctx->seg_ev[sg]) FIM_CUDA_TRY(cudaEventCreateWithFlags(&ctx->seg_ev[sg], cudaEventDisableTiming));
+            }
+            if (streamed) {  // the upload stream and its events
+                if (!ctx->copy_stream) FIM_CUDA_TRY(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+                for (int sg = 0; sg <= n_seg; sg++)
+                    if (!ctx->copy_ev[sg])
+                        FIM_CUDA_TRY(cudaEventCreateWithFlags(&ctx->copy_ev[sg], cudaEventDisableTiming));
             }
             FIM_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
             // phase boundaries as event-record nodes of the graph: graph start
@@ -1126,6 +1197,17 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
             cudaMemsetAsync(d_ctr, 0, sizeof(MineCounters), st);
             cudaMemsetAsync(ctx->dev_flag.p, 0, sizeof(int), st);
             launch_epoch_bump(ctx);
+            if (streamed) {
+                // group sg's CSRs go up on the upload stream; its build waits
+                // for copy_ev[sg] only, so later uploads overlap its work
+                cudaEventRecord(ctx->copy_ev[n_seg], st);
+                cudaStreamWaitEvent(ctx->copy_stream, ctx->copy_ev[n_seg], 0);
+                for (int sg = 0; sg < n_seg; sg++) {
+                    for (const HostCopy &c : seg_copies[sg])
+                        cudaMemcpyAsync(c.dst, c.src, c.bytes, cudaMemcpyHostToDevice, ctx->copy_stream);
+                    cudaEventRecord(ctx->copy_ev[sg], ctx->copy_stream);
+                }
+            }
             const int64_t units = L.unit_prefix[n_db], items = L.item_prefix[n_db], tiles = L.tile_prefix[n_db];
             // rows-per-thread build with fused supports when every database's
             // block of columns fits shared memory (ib == m_max <= 1,024)
@@ -1139,15 +1221,9 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
                 int *const udb = ctx->batch_unit_db.as<int>();
                 uint32_t *const bmp = ctx->bm.as<uint32_t>(), *const sup = ctx->item_sup.as<uint32_t>();
                 int *const flg = ctx->dev_flag.as<int>();
-                auto go = [&](auto kern) {
-                    kern<<<grid, BUILD_ROWS_THREADS, smem_rows, s_>>>(d_dbs, udb, d_unit, u0, bmp, sup, flg);
-                };
-                if (wbk == 64)
-                    coal ? go(batch_build_rows_kernel<64, true>) : go(batch_build_rows_kernel<64, false>);
-                else if (wbk == 16)
-                    coal ? go(batch_build_rows_kernel<16, true>) : go(batch_build_rows_kernel<16, false>);
-                else
-                    coal ? go(batch_build_rows_kernel<32, true>) : go(batch_build_rows_kernel<32, false>);
+                const unsigned g = persist_build ? (unsigned)(u1 - u0 < ctx->num_sms ? u1 - u0 : ctx->num_sms) : grid;
+                build_rows_fn(wbk, coal, persist_build)<<<g, BUILD_ROWS_THREADS, smem_rows, s_>>>(
+                    d_dbs, udb, d_unit, u0, u1, bmp, sup, flg);
             };
             auto rank_db = [&](int da, int db_, cudaStream_t s_) {
                 if (db_ > da)
@@ -1170,6 +1246,7 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
                 cudaStream_t aux = ctx->aux_stream;
                 for (int sg = 0; sg < n_seg; sg++) {
                     const int da = seg_db[sg], db_ = seg_db[sg + 1];
+                    if (streamed) cudaStreamWaitEvent(st, ctx->copy_ev[sg], 0);
                     build_rows(L.unit_prefix[da], L.unit_prefix[db_], st);
                     rank_db(da, db_, st);
                     cudaEventRecord(ctx->seg_ev[sg], st);
@@ -1184,6 +1261,7 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
                 cudaEventRecord(ctx->seg_ev[n_seg], aux);
                 cudaStreamWaitEvent(st, ctx->seg_ev[n_seg], 0);
             } else {
+                if (streamed) cudaStreamWaitEvent(st, ctx->copy_ev[0], 0);
                 if (units > 0) {
                     if (rows_build)
                         build_rows(0, units, st);
@@ -1240,7 +1318,8 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
             if (rc_launch != FIM_OK) { if (g) cudaGraphDestroy(g); return rc_launch; }
             if (ce != cudaSuccess) { fim_set_cuda_error(ce, "capture", __FILE__, __LINE__); return FIM_E_CUDA; }
             cudaGraphExec_t ex = nullptr;
-            const cudaError_t ie = cudaGraphInstantiate(&ex, g, 0);
+            // node priorities as captured: the side stream's pair passes go first
+            const cudaError_t ie = cudaGraphInstantiate(&ex, g, cudaGraphInstantiateFlagUseNodePriority);
             cudaGraphDestroy(g);
             if (ie != cudaSuccess) { fim_set_cuda_error(ie, "instantiate", __FILE__, __LINE__); return FIM_E_CUDA; }
             ctx->batch_graph_exec = ex;

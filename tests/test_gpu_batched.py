@@ -127,11 +127,15 @@ def test_batched_workload_sample(ctx):
         assert got.sha256() == want.sha256()
 
 
-def test_pinned_host_input_read_in_place(ctx):
-    # page-locked host CSRs packed back to back: the build reads them over
-    # the host link in place; a batch with one pageable database among them
-    # goes up by staging copies instead -- both exact
+@pytest.mark.parametrize("streamed", [1, 0])
+def test_pinned_host_input_read_in_place(ctx, streamed):
+    # page-locked host CSRs packed back to back: uploaded group by group
+    # inside the batch graph beside the earlier groups' mining (streamed), or
+    # read over the host link in place by the build; a batch with one
+    # pageable database among them goes up by staging copies instead -- all
+    # exact
     import torch
+    fim.fim_set_tuning(ctx, "batch_stream_copies", streamed)
     dbs, ms = _mixed_batch(7, 24)
     ptr = torch.from_numpy(np.concatenate([c.indptr for c in dbs])).pin_memory()
     idx = torch.from_numpy(np.concatenate([c.indices for c in dbs] + [np.zeros(1, np.int32)])).pin_memory()
@@ -148,12 +152,18 @@ def test_pinned_host_input_read_in_place(ctx):
     mixed[5] = dbs[5]  # pageable
     fim.fim_mine_batched(ctx, mixed, ms)
     _check_all(ctx, dbs, ms)
+    for seg in (1, 3):  # explicit group counts
+        fim.fim_set_tuning(ctx, "batch_segments", seg)
+        fim.fim_mine_batched(ctx, packed, ms)
+        _check_all(ctx, dbs, ms)
+    fim.fim_set_tuning(ctx, "batch_segments", 0)
     fim.fim_set_tuning(ctx, "upload_mapped", 0)
     try:
         fim.fim_mine_batched(ctx, packed, ms)
         _check_all(ctx, dbs, ms)
     finally:
         fim.fim_set_tuning(ctx, "upload_mapped", 1)
+        fim.fim_set_tuning(ctx, "batch_stream_copies", 1)
 
 
 @pytest.mark.parametrize("warp_workers,ctas", [(1, 2), (1, 3), (0, 2)])

@@ -177,12 +177,12 @@ int fim_get_stats(const fim_ctx *ctx, fim_stats *out);
  *                                candidates first (1, default).  Either way a root whose
  *                                class has no candidate is dropped before the
  *                                prefix extension starts
- *   "batch_segments"   0..8      fim_mine_batched pipelines this many groups of
+ *   "batch_segments"   0..16     fim_mine_batched pipelines this many groups of
  *                                databases (about equal transactions): a group's
  *                                pair pass runs while the next group is built;
- *                                0 (default) = eight groups when the build reads
- *                                page-locked host input over the link (the build
- *                                then one CTA per SM), else one
+ *                                0 (default) = eight groups for page-locked host
+ *                                input (uploaded group by group, or read in place
+ *                                by a build of one CTA per SM), else one
  *   "dfs_warp"         0, 1      fim_mine_batched with every database's columns at
  *                                most 4,096 words: one warp per prefix-extension
  *                                worker instead of one CTA (default 1)

@@ -618,7 +618,7 @@ int fim_set_tuning(fim_ctx *ctx, const char *key, int64_t v) {
         {"batch_build_coal", &ctx->batch_build_coal, 0, 1},
         {"root_sort", &ctx->root_sort, 0, 1},
         {"record_chunk", &ctx->rec_chunk, 1, 1024},
-        {"batch_segments", &ctx->batch_segments, 0, 8},
+        {"batch_segments", &ctx->batch_segments, 0, 16},
         {"dfs_warp", &ctx->dfs_warp, 0, 1},
         {"dfs_warp_ctas", &ctx->dfs_warp_ctas, 2, 3},
     };

@@ -283,10 +283,10 @@ struct fim_ctx {
     int dfs_warp = 1;           // batches of short columns: one warp per prefix-extension worker
     int dfs_warp_ctas = 2;      // CTAs of warp workers per SM (2 or 3)
     bool force_cta_dfs = false; // set while a batch is re-mined with CTA workers
-    cudaEvent_t seg_ev[10] = {};  // fork, join and per-group events of that pipeline
+    cudaEvent_t seg_ev[18] = {};  // fork, join and per-group events of that pipeline
     int batch_stream_copies = 1;  // page-locked host batches go up group by group beside the mine
     cudaStream_t copy_stream = nullptr;  // those uploads
-    cudaEvent_t copy_ev[10] = {};        // fork and per-group events of the uploads
+    cudaEvent_t copy_ev[18] = {};        // fork and per-group events of the uploads
     int compact_cluster = 1;    // small outputs: sort in one cluster launch
     int csort_cl[5] = {0, 0, 0, 0, 0};  // cluster size per key width (0 unknown, -1 none)
     int debug_checks = 0;       // device-side invariant checks after build and mine

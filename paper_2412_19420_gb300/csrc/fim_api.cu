@@ -316,6 +316,7 @@ int mine_once(fim_ctx *ctx, uint32_t thr, uint32_t flags, MineState &ms, bool *r
         d.thr = thr;
         d.maxlen = maxlen;
         FIM_TRY(fim_reserve(ctx, ctx->dbdesc, sizeof(DbDesc)));
+        ctx->up_desc.clear();  // the batched mine's table is overwritten
         FIM_CUDA_TRY(cudaMemcpyAsync(ctx->dbdesc.p, &d, sizeof(DbDesc), cudaMemcpyHostToDevice, st));
     }
     cudaEventRecord(ctx->ev[1], st);

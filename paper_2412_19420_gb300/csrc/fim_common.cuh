@@ -254,7 +254,19 @@ struct fim_ctx {
     int batch_n_db = 0;
     std::vector<unsigned long long> batch_set_start, batch_item_start;
     void *batch_graph_exec = nullptr;   // cudaGraphExec_t
-    uint64_t batch_graph_key = 0;
+    std::vector<unsigned char> batch_graph_blob, batch_graph_blob_next;  // what the graph was captured for
+    // the batched pair pass's units, kept while each database's (m, words)
+    // and the grouping repeat
+    std::vector<int64_t> pair_units_sig;
+    std::vector<unsigned long long> pair_units_cache;
+    std::vector<int64_t> pair_seg_unit_cache;
+    bool pair_units_ok = false;
+    // what the batched mine last copied into dbdesc / batch_prefix /
+    // batch_units, and that buffer's (address, capacity) then: a call whose
+    // bytes and buffer repeat skips the copy (a buffer that grew is a new
+    // one); a single-database mine, which writes dbdesc, clears up_desc
+    std::vector<unsigned char> up_desc, up_pre, up_units;
+    std::pair<const void *, size_t> up_desc_buf{}, up_pre_buf{}, up_units_buf{};
     uint64_t batch_graph_launches = 0;
     // compactor pass sequence, captured when a shape repeats
     // (two slots: a split mine alternates the shard's and the merge's shapes)

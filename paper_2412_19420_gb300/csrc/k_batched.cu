@@ -979,13 +979,33 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
         seg_db[n_seg] = n_db;
     }
     // the tensor-core pair pass's (database, tile) units, each group's longest first
-    std::vector<unsigned long long> pair_units;
-    std::vector<int64_t> seg_unit(n_seg + 1, 0);
+    // (they depend only on each database's (m, words) and the grouping: the
+    // last batch's are reused when those repeat)
     bool pairs_tc = pairs_tc_wanted;
-    for (int sg = 0; sg < n_seg && pairs_tc; sg++) {
-        pairs_tc = batch_pairs_tc_units(L.dbs, seg_db[sg], seg_db[sg + 1], pair_units, (size_t)1 << 24);
-        seg_unit[sg + 1] = (int64_t)pair_units.size();
+    if (pairs_tc) {
+        std::vector<int64_t> sig;
+        sig.reserve(2 * (size_t)n_db + (size_t)n_seg + 2);
+        sig.push_back(n_seg);
+        for (int sg = 0; sg <= n_seg; sg++) sig.push_back(seg_db[sg]);
+        for (int d = 0; d < n_db; d++) {
+            sig.push_back(L.dbs[d].m);
+            sig.push_back(L.dbs[d].nw);
+        }
+        if (sig != ctx->pair_units_sig) {
+            ctx->pair_units_cache.clear();
+            ctx->pair_seg_unit_cache.assign(n_seg + 1, 0);
+            ctx->pair_units_ok = true;
+            for (int sg = 0; sg < n_seg && ctx->pair_units_ok; sg++) {
+                ctx->pair_units_ok = batch_pairs_tc_units(L.dbs, seg_db[sg], seg_db[sg + 1], ctx->pair_units_cache,
+                                                          (size_t)1 << 24);
+                ctx->pair_seg_unit_cache[sg + 1] = (int64_t)ctx->pair_units_cache.size();
+            }
+            ctx->pair_units_sig.swap(sig);
+        }
+        pairs_tc = ctx->pair_units_ok;
     }
+    const std::vector<unsigned long long> &pair_units = ctx->pair_units_cache;
+    const std::vector<int64_t> &seg_unit = ctx->pair_seg_unit_cache;
     if (!pairs_tc) {
         n_seg = 1;
         seg_db.assign({0, n_db});
@@ -1076,15 +1096,23 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
         FIM_TRY(fim_reserve(ctx, ctx->rec_sup, sizeof(uint32_t) * ctx->rec_cap));
         FIM_TRY(fim_reserve(ctx, ctx->rec_db, sizeof(uint32_t) * ctx->rec_cap));
         FIM_TRY(fim_reserve(ctx, ctx->rec_items, sizeof(uint32_t) * ctx->rec_items_cap));
-        // per-call inputs (outside the graph): descriptor table, prefixes
-        FIM_CUDA_TRY(cudaMemcpyAsync(d_dbs, L.dbs.data(), tbl, cudaMemcpyHostToDevice, st));
-        FIM_CUDA_TRY(cudaMemcpyAsync(ctx->batch_prefix.p, pre.data(), sizeof(int64_t) * pre.size(),
-                                     cudaMemcpyHostToDevice, st));
+        // per-call inputs (outside the graph): descriptor table, prefixes,
+        // pair units -- copied from ctx-held host copies, and only when their
+        // bytes or their destination differ from the last copy
+        auto upload = [&](std::vector<unsigned char> &last, std::pair<const void *, size_t> &last_buf,
+                          const DevBuf &dst, const void *src, size_t bytes) -> int {
+            const std::pair<const void *, size_t> buf{dst.p, dst.bytes};
+            if (last_buf == buf && last.size() == bytes && memcmp(last.data(), src, bytes) == 0) return FIM_OK;
+            last.assign((const unsigned char *)src, (const unsigned char *)src + bytes);
+            last_buf = buf;
+            FIM_CUDA_TRY(cudaMemcpyAsync(dst.p, last.data(), bytes, cudaMemcpyHostToDevice, st));
+            return FIM_OK;
+        };
+        FIM_TRY(upload(ctx->up_desc, ctx->up_desc_buf, ctx->dbdesc, L.dbs.data(), tbl));
+        FIM_TRY(upload(ctx->up_pre, ctx->up_pre_buf, ctx->batch_prefix, pre.data(), sizeof(int64_t) * pre.size()));
         if (pairs_tc && !pair_units.empty())
-            FIM_CUDA_TRY(cudaMemcpyAsync(ctx->batch_units.p, pair_units.data(),
-                                         sizeof(unsigned long long) * pair_units.size(),
-                                         cudaMemcpyHostToDevice, st));
-        FIM_CUDA_TRY(cudaStreamSynchronize(st));  // host staging vectors go out of scope later
+            FIM_TRY(upload(ctx->up_units, ctx->up_units_buf, ctx->batch_units, pair_units.data(),
+                           sizeof(unsigned long long) * pair_units.size()));
 
         DfsParams p{};
         p.dbs = d_dbs;
@@ -1130,11 +1158,13 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
         p.rec_chunk = ctx->rec_chunk;
         p.root_reverse = ctx->root_reverse;
 
-        // graph key: everything the captured launches depend on
-        uint64_t key = 1469598103934665603ull;
+        // graph key: everything the captured launches depend on, kept whole
+        // and compared in full
+        std::vector<unsigned char> &key = ctx->batch_graph_blob_next;
+        key.clear();
         auto mix = [&key](const void *data, size_t n) {
             const unsigned char *b = (const unsigned char *)data;
-            for (size_t i = 0; i < n; i++) key = (key ^ b[i]) * 1099511628211ull;
+            key.insert(key.end(), b, b + n);
         };
         mix(&n_db, sizeof(n_db));
         mix(&flags, sizeof(flags));
@@ -1159,7 +1189,7 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
         if (pairs_tc) {
             const void *up = ctx->batch_units.p;
             mix(&up, sizeof(up));
-            for (unsigned long long w : pair_units) key = (key ^ w) * 1099511628211ull;  // word at a time
+            mix(pair_units.data(), sizeof(unsigned long long) * pair_units.size());
             const int64_t nu = (int64_t)pair_units.size();
             mix(&nu, sizeof(nu));
         }
@@ -1171,7 +1201,7 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
             FIM_CUDA_TRY(cudaFuncSetAttribute(build_rows_fn(wbk, coal, persist_build),
                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_rows));
         }
-        const bool reuse = ctx->batch_graph_exec && ctx->batch_graph_key == key;
+        const bool reuse = ctx->batch_graph_exec && ctx->batch_graph_blob == key;
         if (!reuse) {
             if (ctx->batch_graph_exec) {
                 cudaGraphExecDestroy((cudaGraphExec_t)ctx->batch_graph_exec);
@@ -1323,7 +1353,7 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
             cudaGraphDestroy(g);
             if (ie != cudaSuccess) { fim_set_cuda_error(ie, "instantiate", __FILE__, __LINE__); return FIM_E_CUDA; }
             ctx->batch_graph_exec = ex;
-            ctx->batch_graph_key = key;
+            ctx->batch_graph_blob.swap(key);
             ctx->batch_graph_launches = 10;  // unit map, build, rank, pairs, finalize, 3 root plan, DFS, epoch
         }
         FIM_CUDA_TRY(cudaGraphLaunch((cudaGraphExec_t)ctx->batch_graph_exec, st));

@@ -249,6 +249,7 @@ int fim_merge_results(fim_ctx *ctx, int64_t n_trans, int32_t n_items, int n_part
     ctx->host_db.n = n_trans;
     ctx->host_db.m = n_items;
     FIM_TRY(fim_reserve(ctx, ctx->dbdesc, sizeof(DbDesc)));
+    ctx->up_desc.clear();  // the batched mine's table is overwritten
     FIM_CUDA_TRY(cudaMemcpyAsync(ctx->dbdesc.p, &ctx->host_db, sizeof(DbDesc), cudaMemcpyHostToDevice, st));
     ctx->host_ctr = MineCounters{};
     ctx->host_ctr.n_records = R;

@@ -180,3 +180,23 @@ def test_warp_and_cta_workers_agree(ctx, warp_workers, ctas):
     finally:
         fim.fim_set_tuning(ctx, "dfs_warp", 1)
         fim.fim_set_tuning(ctx, "dfs_warp_ctas", 2)
+
+
+def test_single_mines_between_batches(ctx):
+    # the same batch mined again after single-database mines (which reuse the
+    # ctx's descriptor buffer) and after a larger batch: exact every time
+    dbs, ms = _mixed_batch(9, 30)
+    desc = fim.BatchDescriptor(dbs, ms)
+    fim.fim_mine_batched(ctx, desc)
+    _check_all(ctx, dbs, ms)
+    c = dbs[3]
+    fim.fim_build_bitmaps(ctx, c.indptr, c.indices, c.m)
+    fim.fim_mine(ctx, ms[3])
+    assert fim.fim_fetch_results(ctx).sha256() == oracle.apriori(c.indptr, c.indices, c.m, ms[3]).sha256()
+    fim.fim_mine_batched(ctx, desc)
+    _check_all(ctx, dbs, ms)
+    big, bms = _mixed_batch(10, 90)
+    fim.fim_mine_batched(ctx, big, bms)
+    _check_all(ctx, big, bms)
+    fim.fim_mine_batched(ctx, desc)
+    _check_all(ctx, dbs, ms)

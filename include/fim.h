@@ -246,6 +246,11 @@ int fim_get_stats(const fim_ctx *ctx, fim_stats *out);
  *                                fim_mine_batched's build covers (32 x that many
  *                                transactions); a block that does not fit shared
  *                                memory falls back to the next smaller (default 32)
+ *   "batch_pairs_pack" 0, 1      fim_mine_batched's tensor-core pair pass: its units
+ *                                are planned on the device once m' is known, and two
+ *                                databases with at most 64 frequent items (and about
+ *                                as many transactions) share one 128 x 128 tile
+ *                                (default 1); 0 = a tile per database
  *   "batch_build_coal" 0, 1      fim_mine_batched's build: a warp reads its 32
  *                                rows' item ids 32 at a time (coalesced) and finds
  *                                each id's row among the lanes; 0 = lane-per-row

@@ -174,6 +174,7 @@ void fim_destroy(fim_ctx *ctx) {
     fim_release(ctx, ctx->batch_prefix);
     fim_release(ctx, ctx->batch_units);
     fim_release(ctx, ctx->batch_unit_db);
+    fim_release(ctx, ctx->batch_plan);
     fim_release(ctx, ctx->batch_slices);
     if (ctx->batch_graph_exec) cudaGraphExecDestroy((cudaGraphExec_t)ctx->batch_graph_exec);
     for (void *g : ctx->compact_graph_exec)
@@ -617,6 +618,7 @@ int fim_set_tuning(fim_ctx *ctx, const char *key, int64_t v) {
         {"batch_pairs_shape", &ctx->batch_pairs_shape, 0, kBatchPairsShapeCount - 1},
         {"batch_build_block", &ctx->batch_build_block, 16, 64},
         {"batch_build_coal", &ctx->batch_build_coal, 0, 1},
+        {"batch_pairs_pack", &ctx->batch_pairs_pack, 0, 1},
         {"root_sort", &ctx->root_sort, 0, 1},
         {"record_chunk", &ctx->rec_chunk, 1, 1024},
         {"batch_segments", &ctx->batch_segments, 0, 16},

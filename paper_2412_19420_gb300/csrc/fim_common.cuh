@@ -260,7 +260,12 @@ struct fim_ctx {
     std::vector<int64_t> pair_units_sig;
     std::vector<unsigned long long> pair_units_cache;
     std::vector<int64_t> pair_seg_unit_cache;
+    std::vector<int> pair_ord_cache;  // each group's databases, most transactions first
     bool pair_units_ok = false;
+    int batch_pairs_pack = 1;   // the batch's pair units planned on the device, small databases two to a tile
+    DevBuf batch_plan;          // that plan's unit counts, database order and scratch
+    std::vector<unsigned char> up_ord;
+    std::pair<const void *, size_t> up_ord_buf{};
     // what the batched mine last copied into dbdesc / batch_prefix /
     // batch_units, and that buffer's (address, capacity) then: a call whose
     // bytes and buffer repeat skips the copy (a buffer that grew is a new
@@ -377,8 +382,17 @@ int launch_cluster_sort(fim_ctx *ctx, const unsigned long long *keys, uint64_t R
 // k_batch_pairs_tc.cu: the batch's pair supports on the tensor cores
 bool batch_pairs_tc_units(const std::vector<DbDesc> &dbs, int d0, int d1, std::vector<unsigned long long> &units,
                           size_t max_units);
+// d_n_units: the unit count written on the device by the plan kernel (null:
+// n_units itself); n_units is then the capacity, which sizes the grid
 int launch_batch_pairs_tc(fim_ctx *ctx, const DbDesc *d_dbs, const unsigned long long *d_units, int64_t n_units,
-                          cudaStream_t st);
+                          const long long *d_n_units, cudaStream_t st);
+// Device plan of one group's pair units once m'_d is known: ord[0 .. n) the
+// group's databases, most transactions first; databases with at most 64
+// frequent items are packed two to a tile; *d_n_units gets the count.
+// scratch: batch_pair_plan_scratch(n) bytes.
+int launch_batch_pair_plan(fim_ctx *ctx, const DbDesc *d_dbs, const int *d_ord, int n, unsigned long long *d_units,
+                           long long *d_n_units, void *scratch, cudaStream_t st);
+size_t batch_pair_plan_scratch(int n);
 extern const int kBatchPairsShapeCount;
 
 // k_dfs_warp.cu: the prefix extension with one warp per worker

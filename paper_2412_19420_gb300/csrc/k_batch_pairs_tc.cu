@@ -80,26 +80,58 @@ struct __align__(1024) BtcSmem {
     int abort;
 };
 
+// Unit codes: a tile (d << 32 | ta << 16 | tb), or -- bit 63 set -- two
+// databases of at most PACK_MAX frequent items sharing one diagonal tile
+// (d1 << 32 | d2, d2 = PACK_NONE when d1 has no partner): rows and columns
+// 0 .. 63 hold d1's items, 64 .. 127 d2's; the MMA's cross blocks are never
+// read.
+constexpr unsigned long long PACK = 1ull << 63;
+constexpr uint32_t PACK_NONE = 0xFFFFFFFFu;
+constexpr int PACK_MAX = BT / 2;
+
 // What every role of the CTA derives from a unit code, identically.
 struct BUnit {
-    const DbDesc *D;
-    int ta, tb, mf, N;
-    int64_t S;      // stages of 128 transactions
+    const DbDesc *D;   // the database (the first of a packed pair)
+    const DbDesc *D2;  // a packed pair's second database, or null
+    int ta, tb, mf, mf2, N;
+    int64_t S;         // stages of 128 transactions (the longer database of a pair)
+    int64_t S1, S2;    // a packed pair's own stage counts
     bool diag;
     bool empty;
+    bool packed;
 };
 
 __device__ __forceinline__ BUnit decode_unit(const DbDesc *__restrict__ dbs, unsigned long long code) {
     BUnit u;
+    u.packed = (code & PACK) != 0;
+    if (u.packed) {
+        const uint32_t d2 = (uint32_t)code;
+        u.D = dbs + ((code >> 32) & 0x7FFFFFFFull);
+        u.D2 = d2 != PACK_NONE ? dbs + d2 : nullptr;
+        u.ta = u.tb = 0;
+        u.mf = *(volatile const int32_t *)&u.D->mfreq;
+        u.mf2 = u.D2 ? *(volatile const int32_t *)&u.D2->mfreq : 0;
+        u.diag = true;
+        u.empty = false;  // the plan packs only databases with pairs
+        u.N = u.D2 ? PACK_MAX + ((u.mf2 + 15) & ~15) : (u.mf + 15) & ~15;
+        u.S1 = (u.D->nw + 3) / 4;
+        u.S2 = u.D2 ? (u.D2->nw + 3) / 4 : 0;
+        u.S = u.S1 > u.S2 ? u.S1 : u.S2;
+        return u;
+    }
     u.D = dbs + (code >> 32);
+    u.D2 = nullptr;
     u.ta = (int)((code >> 16) & 0xFFFFu);
     u.tb = (int)(code & 0xFFFFu);
     u.mf = *(volatile const int32_t *)&u.D->mfreq;  // written by the rank pass of this mine
+    u.mf2 = 0;
     u.diag = u.ta == u.tb;
     u.empty = u.mf < 2 || u.D->maxlen == 1 || u.tb * BT >= u.mf;
     const int cols = u.empty ? 16 : min(BT, u.mf - u.tb * BT);
     u.N = (cols + 15) & ~15;
     u.S = (u.D->nw + 3) / 4;
+    u.S1 = u.S;
+    u.S2 = 0;
     return u;
 }
 
@@ -112,7 +144,8 @@ __device__ __forceinline__ bool bwait(S &s, uint64_t *b, uint32_t parity) {
 template <int STG, int DEPTH, int MINB, int BG>
 __global__ void __launch_bounds__(BTHREADS, MINB)
 batch_pairs_tc_kernel(const DbDesc *__restrict__ dbs, const unsigned long long *__restrict__ units,
-                      int64_t n_units, const uint32_t *__restrict__ bm, const int32_t *__restrict__ perm_base,
+                      int64_t n_units_host, const long long *__restrict__ n_units_dev,
+                      const uint32_t *__restrict__ bm, const int32_t *__restrict__ perm_base,
                       int *__restrict__ pair_cnt, int kd, int *__restrict__ err) {
     static_assert(DEPTH % 4 == 0 && DEPTH >= 8, "raw bits go in quads, two or more in flight");
     static_assert(BG == 2 || BG == 4, "a quad publishes in two or one fences");
@@ -122,6 +155,8 @@ batch_pairs_tc_kernel(const DbDesc *__restrict__ dbs, const unsigned long long *
     extern __shared__ uint8_t smem_raw[];
     Smem &s = *reinterpret_cast<Smem *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // the units the plan kernel wrote (this launch's stream, before it), or the host's
+    const int64_t n_units = n_units_dev ? (int64_t)*n_units_dev : n_units_host;
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < BSTAGES; i++) { mbar_init(&s.full[i], BNPROD / 32); mbar_init(&s.empty[i], 1); }
@@ -154,12 +189,17 @@ batch_pairs_tc_kernel(const DbDesc *__restrict__ dbs, const unsigned long long *
         for (int64_t ui = blockIdx.x; ui < n_units && ok; ui += gridDim.x) {
             const BUnit u = decode_unit(dbs, units[ui]);
             if (u.empty) continue;
-            const DbDesc &D = *u.D;
             const bool store = !(is_a && u.diag);  // warp-uniform: a warp's rows are all A or all B
-            const int item = (is_a ? u.ta : u.tb) * BT + r;
+            // the row's database, item and stage count (a packed pair: rows
+            // 0 .. 63 the first database's items, 64 .. 127 the second's)
+            const DbDesc *const Dr = u.packed ? (r < PACK_MAX ? u.D : u.D2) : u.D;
+            const int item = u.packed ? (r & (PACK_MAX - 1)) : (is_a ? u.ta : u.tb) * BT + r;
+            const int mfr = u.packed ? (r < PACK_MAX ? u.mf : u.mf2) : u.mf;
+            const int64_t lenr = u.packed ? (r < PACK_MAX ? u.S1 : u.S2) : u.S;
             const uint32_t *col =
-                (store && item < u.mf) ? bm + D.bm_off + (int64_t)__ldg(perm_base + D.item_off + item) * D.nwp
-                                       : nullptr;
+                (store && Dr && item < mfr)
+                    ? bm + Dr->bm_off + (int64_t)__ldg(perm_base + Dr->item_off + item) * Dr->nwp
+                    : nullptr;
             const int64_t len = u.S;
             // stage k of the unit lives in stg[k % BD]; a quad of 4 stages is
             // refilled at a time, 4 lanes per row copying 64 contiguous bytes
@@ -170,7 +210,8 @@ batch_pairs_tc_kernel(const DbDesc *__restrict__ dbs, const unsigned long long *
                     const int64_t k = q0 + (piece & 3);
                     const uint32_t *c = reinterpret_cast<const uint32_t *>(
                         __shfl_sync(0xffffffffu, reinterpret_cast<uintptr_t>(col), rw));
-                    if (c && k < len) cp_async16(smem_addr(&s.stg[k % BD][row0 + rw]), c + k * 4);
+                    const int64_t lr = __shfl_sync(0xffffffffu, lenr, rw);
+                    if (c && k < lr) cp_async16(smem_addr(&s.stg[k % BD][row0 + rw]), c + k * 4);
                 }
                 cp_async_commit();
             };
@@ -184,9 +225,12 @@ batch_pairs_tc_kernel(const DbDesc *__restrict__ dbs, const unsigned long long *
                     const int cnt = (int)min64(BG, len - k0);
                     if (cnt <= 0 || !ok) break;
                     uint4 x[BG];
+                    bool has[BG];  // my row holds bits at stage k0 + v (else a zero row)
 #pragma unroll
-                    for (int v = 0; v < BG; v++)
-                        x[v] = (col && v < cnt) ? my[((k0 + v) % BD) * BNPROD] : make_uint4(0, 0, 0, 0);
+                    for (int v = 0; v < BG; v++) {
+                        has[v] = col && v < cnt && k0 + v < lenr;
+                        x[v] = has[v] ? my[((k0 + v) % BD) * BNPROD] : make_uint4(0, 0, 0, 0);
+                    }
                     bool wok = true;  // lane 0 waits for the warp
                     if (lane == 0) {
 #pragma unroll
@@ -215,7 +259,7 @@ batch_pairs_tc_kernel(const DbDesc *__restrict__ dbs, const unsigned long long *
                         for (int v = 0; v < BG; v++)
                             if (v < cnt) {
                                 const int sl = (it + v) % BSTAGES;
-                                if (col) {
+                                if (has[v]) {
                                     store_row(s.b[sl], r, x[v]);
                                     zeroed &= ~(1u << sl);
                                 } else if (!(zeroed & (1u << sl))) {
@@ -245,8 +289,15 @@ batch_pairs_tc_kernel(const DbDesc *__restrict__ dbs, const unsigned long long *
         for (int64_t ui = blockIdx.x; ui < n_units && ok; ui += gridDim.x) {
             const BUnit u = decode_unit(dbs, units[ui]);
             if (u.empty) continue;
-            const int a = u.ta * BT + q * 32 + lane;
-            int *const row = pair_cnt + u.D->pair_off + (int64_t)a * u.mf;
+            // my accumulator row: item a of database Da (a packed pair's rows
+            // 64 .. 127 are the second database's, its columns 64 .. 127 too)
+            const int lr = q * 32 + lane;
+            const bool second = u.packed && lr >= PACK_MAX;
+            const DbDesc *const Da = second ? u.D2 : u.D;
+            const int a = u.packed ? (lr & (PACK_MAX - 1)) : u.ta * BT + lr;
+            const int mfa = second ? u.mf2 : u.mf;
+            const int coff = u.packed ? (second ? -PACK_MAX : 0) : u.tb * BT;  // column c holds item c + coff
+            int *const row = Da ? pair_cnt + Da->pair_off + (int64_t)a * mfa : nullptr;
             for (int64_t st0 = 0; st0 < u.S; st0 += kd, j++) {
                 const int buf = j & 1;
                 // warp-uniform: tcgen05.ld below is a .sync.aligned warp instruction
@@ -266,11 +317,11 @@ batch_pairs_tc_kernel(const DbDesc *__restrict__ dbs, const unsigned long long *
                         : "r"(taddr)
                         : "memory");
                     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                    if (a < u.mf) {
+                    if (row && a < mfa) {
 #pragma unroll
                         for (int c = 0; c < 16; c++) {
-                            const int b = u.tb * BT + x * 16 + c;
-                            if (a < b && b < u.mf) {
+                            const int b = x * 16 + c + coff;
+                            if (a < b && b < mfa) {
                                 const int val = __float2int_rn(__uint_as_float(v[c])) >> 2;
                                 row[b] = st0 == 0 ? val : row[b] + val;
                             }
@@ -332,6 +383,95 @@ batch_pairs_tc_kernel(const DbDesc *__restrict__ dbs, const unsigned long long *
     }
 }
 
+// Block-wide exclusive scan over 1024 threads; *total gets the block's sum.
+__device__ long long block_scan_excl(long long v, long long *s_warp, long long *total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    long long x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        long long w = s_warp[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        s_warp[lane] = w;
+    }
+    __syncthreads();
+    const long long before = (warp > 0 ? s_warp[warp - 1] : 0) + x - v;
+    *total = s_warp[31];
+    __syncthreads();  // s_warp serves the next scan
+    return before;
+}
+
+// The pair units of one group of databases, planned on the device once the
+// rank pass has set every m'_d: ord[0 .. n) lists the group's databases in
+// work order (most transactions first).  A database with 2 <= m'_d <=
+// PACK_MAX shares a tile with the next such database in that order (so the
+// two have about as many transactions); a larger one gets its upper-triangle
+// tiles of 128 items; a database without pairs gets nothing.  Units are
+// written in work order; *n_units receives their count.  One CTA of 1024
+// threads; scratch holds 4 n ints and n long longs.
+__global__ void __launch_bounds__(1024)
+batch_pair_plan_kernel(const DbDesc *__restrict__ dbs, const int *__restrict__ ord, int n,
+                       int *__restrict__ srank, long long *__restrict__ off, int *__restrict__ small_list,
+                       unsigned long long *__restrict__ units, long long *__restrict__ n_units) {
+    __shared__ long long s_warp[32];
+    long long base_small = 0, base_units = 0;
+    for (int c0 = 0; c0 < n; c0 += 1024) {
+        const int i = c0 + (int)threadIdx.x;
+        int small = 0;
+        long long tiles = 0;
+        if (i < n) {
+            const DbDesc &D = dbs[ord[i]];
+            const int mf = *(volatile const int32_t *)&D.mfreq;
+            const bool live = mf >= 2 && D.maxlen != 1;
+            small = live && mf <= PACK_MAX;
+            if (live && !small) {
+                const long long nt = (mf + BT - 1) / BT;
+                tiles = nt * (nt + 1) / 2;
+            }
+        }
+        long long t_small, t_units;
+        const long long sr = block_scan_excl(small, s_warp, &t_small) + base_small;
+        const long long cnt = small ? ((sr & 1) == 0 ? 1 : 0) : tiles;  // a pair opens at even ranks
+        const long long o = block_scan_excl(cnt, s_warp, &t_units) + base_units;
+        if (i < n) {
+            srank[i] = small ? (int)sr : -1;
+            off[i] = o;
+            if (small) small_list[sr] = ord[i];
+        }
+        base_small += t_small;
+        base_units += t_units;
+    }
+    __syncthreads();  // small_list is complete
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int d = ord[i], sr = srank[i];
+        long long o = off[i];
+        if (sr >= 0) {
+            if ((sr & 1) == 0) {
+                const uint32_t d2 = sr + 1 < base_small ? (uint32_t)small_list[sr + 1] : PACK_NONE;
+                units[o] = PACK | ((unsigned long long)d << 32) | d2;
+            }
+        } else {
+            const int mf = *(volatile const int32_t *)&dbs[d].mfreq;
+            if (mf >= 2 && dbs[d].maxlen != 1) {
+                const int nt = (mf + BT - 1) / BT;
+                for (int ta = 0; ta < nt; ta++)
+                    for (int tb = ta; tb < nt; tb++)
+                        units[o++] = ((unsigned long long)d << 32) | ((unsigned long long)ta << 16) | (unsigned)tb;
+            }
+        }
+    }
+    if (threadIdx.x == 0) *n_units = base_units;
+}
+
 }  // namespace
 
 // The batch's (database, tile) units in the order the pass takes them.  The
@@ -373,7 +513,7 @@ namespace {
 
 template <int STG, int DEPTH, int MINB, int BG>
 int launch_shape(fim_ctx *ctx, const DbDesc *d_dbs, const unsigned long long *d_units, int64_t n_units,
-                 cudaStream_t st) {
+                 const long long *d_n_units, cudaStream_t st) {
     using Smem = BtcSmem<STG, DEPTH>;
     static_assert(sizeof(Smem) + 1024 <= 232448, "shared memory per CTA");
     // MINB CTAs share an SM: their tensor memory and shared memory must fit
@@ -391,7 +531,7 @@ int launch_shape(fim_ctx *ctx, const DbDesc *d_dbs, const unsigned long long *d_
     FIM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int *err = &ctx->counters.as<MineCounters>()->err;  // zeroed at the start of every batch
     ctx->launches++;
-    kern<<<(unsigned)grid, BTHREADS, smem, st>>>(d_dbs, d_units, n_units, ctx->bm.as<uint32_t>(),
+    kern<<<(unsigned)grid, BTHREADS, smem, st>>>(d_dbs, d_units, n_units, d_n_units, ctx->bm.as<uint32_t>(),
                                                  ctx->perm.as<int32_t>(), ctx->pair_cnt.as<int>(), kd, err);
     FIM_CUDA_TRY(cudaGetLastError());
     return FIM_OK;
@@ -407,15 +547,31 @@ const int kBatchPairsShapes[][4] = {{8, 8, 1, 2}, {6, 8, 1, 2}, {8, 16, 1, 2}, {
 const int kBatchPairsShapeCount = (int)(sizeof(kBatchPairsShapes) / sizeof(kBatchPairsShapes[0]));
 
 int launch_batch_pairs_tc(fim_ctx *ctx, const DbDesc *d_dbs, const unsigned long long *d_units, int64_t n_units,
-                          cudaStream_t st) {
+                          const long long *d_n_units, cudaStream_t st) {
     if (n_units <= 0) return FIM_OK;
     switch (ctx->batch_pairs_shape) {
-        case 1: return launch_shape<6, 8, 1, 2>(ctx, d_dbs, d_units, n_units, st);
-        case 2: return launch_shape<8, 16, 1, 2>(ctx, d_dbs, d_units, n_units, st);
-        case 3: return launch_shape<4, 8, 1, 2>(ctx, d_dbs, d_units, n_units, st);
-        case 4: return launch_shape<7, 12, 1, 2>(ctx, d_dbs, d_units, n_units, st);
-        case 5: return launch_shape<8, 8, 1, 4>(ctx, d_dbs, d_units, n_units, st);
-        case 6: return launch_shape<8, 16, 1, 4>(ctx, d_dbs, d_units, n_units, st);
-        default: return launch_shape<8, 8, 1, 2>(ctx, d_dbs, d_units, n_units, st);
+        case 1: return launch_shape<6, 8, 1, 2>(ctx, d_dbs, d_units, n_units, d_n_units, st);
+        case 2: return launch_shape<8, 16, 1, 2>(ctx, d_dbs, d_units, n_units, d_n_units, st);
+        case 3: return launch_shape<4, 8, 1, 2>(ctx, d_dbs, d_units, n_units, d_n_units, st);
+        case 4: return launch_shape<7, 12, 1, 2>(ctx, d_dbs, d_units, n_units, d_n_units, st);
+        case 5: return launch_shape<8, 8, 1, 4>(ctx, d_dbs, d_units, n_units, d_n_units, st);
+        case 6: return launch_shape<8, 16, 1, 4>(ctx, d_dbs, d_units, n_units, d_n_units, st);
+        default: return launch_shape<8, 8, 1, 2>(ctx, d_dbs, d_units, n_units, d_n_units, st);
     }
+}
+
+int launch_batch_pair_plan(fim_ctx *ctx, const DbDesc *d_dbs, const int *d_ord, int n, unsigned long long *d_units,
+                           long long *d_n_units, void *scratch, cudaStream_t st) {
+    if (n <= 0) return FIM_OK;
+    int *const srank = static_cast<int *>(scratch);
+    int *const small_list = srank + n;
+    long long *const off = reinterpret_cast<long long *>(small_list + n);  // 8n bytes in: aligned
+    ctx->launches++;
+    batch_pair_plan_kernel<<<1, 1024, 0, st>>>(d_dbs, d_ord, n, srank, off, small_list, d_units, d_n_units);
+    FIM_CUDA_TRY(cudaGetLastError());
+    return FIM_OK;
+}
+
+size_t batch_pair_plan_scratch(int n) {
+    return sizeof(int) * 2 * (size_t)n + sizeof(long long) * (size_t)n;
 }

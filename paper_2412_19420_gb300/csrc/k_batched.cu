@@ -20,6 +20,7 @@
 // replayed for later batches of the same shape.
 #include <cuda.h>
 
+#include <algorithm>
 #include <cstring>
 #include <vector>
 
@@ -1000,12 +1001,22 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
                                                           (size_t)1 << 24);
                 ctx->pair_seg_unit_cache[sg + 1] = (int64_t)ctx->pair_units_cache.size();
             }
+            // the device plan's database order: each group's, most transactions first
+            ctx->pair_ord_cache.resize(n_db);
+            for (int sg = 0; sg < n_seg; sg++) {
+                for (int d = seg_db[sg]; d < seg_db[sg + 1]; d++) ctx->pair_ord_cache[d] = d;
+                std::stable_sort(ctx->pair_ord_cache.begin() + seg_db[sg], ctx->pair_ord_cache.begin() + seg_db[sg + 1],
+                                 [&](int x, int y) { return L.dbs[x].nw > L.dbs[y].nw; });
+            }
             ctx->pair_units_sig.swap(sig);
         }
         pairs_tc = ctx->pair_units_ok;
     }
     const std::vector<unsigned long long> &pair_units = ctx->pair_units_cache;
     const std::vector<int64_t> &seg_unit = ctx->pair_seg_unit_cache;
+    // pair units planned on the device after the rank pass (two small
+    // databases to a tile); the host's units then only bound their number
+    const bool pack = pairs_tc && ctx->batch_pairs_pack;
     if (!pairs_tc) {
         n_seg = 1;
         seg_db.assign({0, n_db});
@@ -1071,6 +1082,10 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
     const int plan_mode = ((flags & FIM_LEARNED) && ctx->learned_order) ? 2 : ctx->root_sort;
     if (pairs_tc)
         FIM_TRY(fim_reserve(ctx, ctx->batch_units, sizeof(unsigned long long) * (pair_units.size() ? pair_units.size() : 1)));
+    // plan buffer: 32 unit counts, the database order, the plan's scratch
+    const size_t plan_ord_off = 32 * sizeof(long long);
+    const size_t plan_scr_off = plan_ord_off + ((sizeof(int) * (size_t)n_db + 255) & ~(size_t)255);
+    if (pack) FIM_TRY(fim_reserve(ctx, ctx->batch_plan, plan_scr_off + batch_pair_plan_scratch(n_db)));
     if (rows_build)
         FIM_TRY(fim_reserve(ctx, ctx->batch_unit_db, sizeof(int) * (size_t)(L.unit_prefix[n_db] ? L.unit_prefix[n_db] : 1)));
     if (ctx->rec_cap < (1ull << 22)) {
@@ -1110,9 +1125,13 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
         };
         FIM_TRY(upload(ctx->up_desc, ctx->up_desc_buf, ctx->dbdesc, L.dbs.data(), tbl));
         FIM_TRY(upload(ctx->up_pre, ctx->up_pre_buf, ctx->batch_prefix, pre.data(), sizeof(int64_t) * pre.size()));
-        if (pairs_tc && !pair_units.empty())
+        if (pairs_tc && !pair_units.empty() && !pack)
             FIM_TRY(upload(ctx->up_units, ctx->up_units_buf, ctx->batch_units, pair_units.data(),
                            sizeof(unsigned long long) * pair_units.size()));
+        if (pack) {
+            DevBuf ord_buf{static_cast<char *>(ctx->batch_plan.p) + plan_ord_off, ctx->batch_plan.bytes};
+            FIM_TRY(upload(ctx->up_ord, ctx->up_ord_buf, ord_buf, ctx->pair_ord_cache.data(), sizeof(int) * (size_t)n_db));
+        }
 
         DfsParams p{};
         p.dbs = d_dbs;
@@ -1186,6 +1205,11 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
         mix(&warp_dfs, sizeof(warp_dfs));
         mix(&ctx->dfs_warp_ctas, sizeof(ctx->dfs_warp_ctas));
         mix(shape, sizeof(shape));
+        mix(&pack, sizeof(pack));
+        if (pack) {
+            const void *pp = ctx->batch_plan.p;
+            mix(&pp, sizeof(pp));
+        }
         if (pairs_tc) {
             const void *up = ctx->batch_units.p;
             mix(&up, sizeof(up));
@@ -1269,6 +1293,19 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
                         roots + 2 * rc, roots + 3 * rc);
             };
             int rc_pairs = FIM_OK;
+            // group sg's tensor-core pair pass (planned on the device first
+            // when packing; the host's units give the capacity)
+            auto pair_pass = [&](int sg, cudaStream_t s_) -> int {
+                unsigned long long *const u = ctx->batch_units.as<unsigned long long>() + seg_unit[sg];
+                const int64_t cap = seg_unit[sg + 1] - seg_unit[sg];
+                if (!pack) return launch_batch_pairs_tc(ctx, d_dbs, u, cap, nullptr, s_);
+                char *const plan = static_cast<char *>(ctx->batch_plan.p);
+                long long *const cnt = reinterpret_cast<long long *>(plan) + sg;
+                const int *const ord = reinterpret_cast<const int *>(plan + plan_ord_off) + seg_db[sg];
+                const int rc = launch_batch_pair_plan(ctx, d_dbs, ord, seg_db[sg + 1] - seg_db[sg], u, cnt,
+                                                      plan + plan_scr_off, s_);
+                return rc != FIM_OK ? rc : launch_batch_pairs_tc(ctx, d_dbs, u, cap, cnt, s_);
+            };
             if (n_seg > 1) {
                 // group s: build + rank on the ctx stream, then its pair pass
                 // and finalize on the side stream, overlapping group s + 1's
@@ -1281,10 +1318,7 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
                     rank_db(da, db_, st);
                     cudaEventRecord(ctx->seg_ev[sg], st);
                     cudaStreamWaitEvent(aux, ctx->seg_ev[sg], 0);
-                    if (rc_pairs == FIM_OK)
-                        rc_pairs = launch_batch_pairs_tc(ctx, d_dbs,
-                                                         ctx->batch_units.as<unsigned long long>() + seg_unit[sg],
-                                                         seg_unit[sg + 1] - seg_unit[sg], aux);
+                    if (rc_pairs == FIM_OK) rc_pairs = pair_pass(sg, aux);
                     finalize_db(da, db_, aux);
                 }
                 cudaEventRecordWithFlags(ctx->ev[1], st, cudaEventRecordExternal);
@@ -1314,8 +1348,7 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
                 cudaEventRecordWithFlags(ctx->ev[1], st, cudaEventRecordExternal);
                 if (tiles > 0 && maxlen != 1) {
                     if (pairs_tc)
-                        rc_pairs = launch_batch_pairs_tc(ctx, d_dbs, ctx->batch_units.as<unsigned long long>(),
-                                                         (int64_t)pair_units.size(), st);
+                        rc_pairs = pair_pass(0, st);
                     else
                         batch_pairs_kernel<<<(unsigned)tiles, 256, 0, st>>>(d_dbs, n_db, d_tile,
                                                                             ctx->bm.as<uint32_t>(),

@@ -167,3 +167,21 @@ def test_pipelined_groups_are_exact(ctx, segments):
     for _ in range(2):
         fim.fim_mine_batched(ctx, dbs, ms)
         _check(ctx, dbs, ms, 0)
+
+
+@pytest.mark.parametrize("pack", [1, 0])
+def test_small_databases_packed_two_to_a_tile(ctx, pack):
+    # databases with at most 64 frequent items share a tile pairwise (planned
+    # on the device once m' is known): partners of unequal length, an odd one
+    # out, databases without pairs in between, and larger ones mixed in
+    fim.fim_set_tuning(ctx, "batch_pairs_pack", pack)
+    rng = np.random.default_rng(21)
+    dbs, ms = [], []
+    for i in range(37):
+        n = int(rng.integers(1, 6000))
+        m = int(rng.choice([1, 2, 5, 33, 63, 64, 65, 90, 140]))
+        dbs.append(_dense(n, m, float(rng.uniform(0.05, 0.3)), [31, i]))
+        ms.append(max(1, n // int(rng.choice([4, 10, 50]))))
+    for flags, ml in ((fim.FIM_MAXLEN(2), 2), (fim.FIM_MAXLEN(3), 3)):
+        fim.fim_mine_batched(ctx, dbs, ms, flags)
+        _check(ctx, dbs, ms, ml)

@@ -49,6 +49,18 @@ int fim_aux_stream(fim_ctx *ctx) {
     return FIM_OK;
 }
 
+// Phase times of the last single-database mine, once its work has finished
+// (events ev[1..4] of that mine; called before anything records them again).
+int fim_finish_phase_times(fim_ctx *ctx) {
+    if (!ctx->phase_times_pending) return FIM_OK;
+    ctx->phase_times_pending = false;
+    FIM_CUDA_TRY(cudaEventSynchronize(ctx->ev[4]));
+    cudaEventElapsedTime(&ctx->stats.ms_pairs, ctx->ev[1], ctx->ev[2]);
+    cudaEventElapsedTime(&ctx->stats.ms_dfs, ctx->ev[2], ctx->ev[3]);
+    cudaEventElapsedTime(&ctx->stats.ms_compact, ctx->ev[3], ctx->ev[4]);
+    return FIM_OK;
+}
+
 int fim_reserve(fim_ctx *ctx, DevBuf &b, size_t bytes) {
     if (bytes == 0) bytes = 16;
     if (bytes <= b.bytes) return FIM_OK;
@@ -205,6 +217,7 @@ int fim_build_bitmaps(fim_ctx *ctx, const int64_t *indptr, const int32_t *indice
     if (!indptr) return FIM_E_INVAL;
     DeviceGuard g(ctx->device);
     if (!g.ok) return FIM_E_CUDA;
+    FIM_TRY(fim_finish_phase_times(ctx));  // before the events are recorded again
     ctx->built = false;
     ctx->mined = false;
     ctx->n = n_trans;
@@ -249,12 +262,9 @@ int fim_build_bitmaps(fim_ctx *ctx, const int64_t *indptr, const int32_t *indice
         d_ptr = ctx->csr_ptr.as<int64_t>();
         d_idx = ctx->csr_idx.as<int32_t>();
         h_nnz = nnz;
-    } else if (flags & FIM_INPUT_DEVICE) {
-        int64_t first = -1;
-        FIM_CUDA_TRY(cudaMemcpyAsync(&first, indptr, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-        FIM_CUDA_TRY(cudaStreamSynchronize(st));
-        if (first != 0) return FIM_E_INVAL;
     }
+    // device input: indptr[0] == 0 and indptr[n] >= 0 are checked by the build
+    // kernel (no host round trip)
     const size_t mm = (size_t)(n_items > 0 ? n_items : 1);
     FIM_TRY(fim_reserve(ctx, ctx->bm, sizeof(uint32_t) * (size_t)ctx->nwp * mm));
     FIM_TRY(fim_reserve(ctx, ctx->item_sup, sizeof(uint32_t) * mm));
@@ -483,11 +493,10 @@ int mine_once(fim_ctx *ctx, uint32_t thr, uint32_t flags, MineState &ms, bool *r
     ctx->host_ctr.max_len = lmax;
     FIM_TRY(launch_compact(ctx, c.n_records, n_sets, 1, ctx->m));
     cudaEventRecord(ctx->ev[4], st);
-    FIM_CUDA_TRY(cudaStreamSynchronize(st));
     FIM_CUDA_TRY(cudaGetLastError());
-    cudaEventElapsedTime(&ctx->stats.ms_pairs, ctx->ev[1], ctx->ev[2]);
-    cudaEventElapsedTime(&ctx->stats.ms_dfs, ctx->ev[2], ctx->ev[3]);
-    cudaEventElapsedTime(&ctx->stats.ms_compact, ctx->ev[3], ctx->ev[4]);
+    // the mine returns with the compaction queued: the next call that reads
+    // results (or these phase times) synchronises the stream first
+    ctx->phase_times_pending = true;
     return FIM_OK;
 }
 
@@ -502,6 +511,7 @@ int fim_mine(fim_ctx *ctx, uint64_t minsup, uint32_t flags) {
     if (!(flags & FIM_STRICT) && minsup == 0) return FIM_E_INVAL;
     DeviceGuard g(ctx->device);
     if (!g.ok) return FIM_E_CUDA;
+    FIM_TRY(fim_finish_phase_times(ctx));  // before the events are recorded again
     ctx->mined = false;
     ctx->mflags = flags;
     uint64_t thr64 = (flags & FIM_STRICT) ? minsup + 1 : minsup;
@@ -590,6 +600,9 @@ int fim_fetch_results(fim_ctx *ctx, uint64_t *n_sets, uint64_t *n_items_total, u
 int fim_get_stats(const fim_ctx *ctx, fim_stats *out) {
     FIM_NVTX("fim_get_stats");
     if (!ctx || !out) return FIM_E_INVAL;
+    // the ctx is the caller's own (non-const) object; the phase times of a
+    // mine still in flight are read here, after it has finished
+    FIM_TRY(fim_finish_phase_times(const_cast<fim_ctx *>(ctx)));
     *out = ctx->stats;
     return FIM_OK;
 }

@@ -262,6 +262,7 @@ struct fim_ctx {
     std::vector<int64_t> pair_seg_unit_cache;
     std::vector<int> pair_ord_cache;  // each group's databases, most transactions first
     bool pair_units_ok = false;
+    bool phase_times_pending = false;  // a single mine's ev[1..4] still to be read
     int batch_pairs_pack = 1;   // the batch's pair units planned on the device, small databases two to a tile
     DevBuf batch_plan;          // that plan's unit counts, database order and scratch
     std::vector<unsigned char> up_ord;
@@ -326,6 +327,7 @@ struct fim_ctx {
 
 int fim_reserve(fim_ctx *ctx, DevBuf &b, size_t bytes);
 int fim_aux_stream(fim_ctx *ctx);  // create the side stream (highest priority) once
+int fim_finish_phase_times(fim_ctx *ctx);  // the last single mine's phase times, once it has finished
 void fim_release(fim_ctx *ctx, DevBuf &b);
 
 // ---------------------------------------------------------------- launchers

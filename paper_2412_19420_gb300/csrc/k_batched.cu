@@ -818,6 +818,7 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
     cudaStream_t st = ctx->stream;
     const bool on_device = flags & FIM_INPUT_DEVICE;
     const uint32_t maxlen = flags >> 24;
+    FIM_TRY(fim_finish_phase_times(ctx));  // before the events are recorded again
     ctx->mined = false;
     ctx->built = false;
     ctx->batch_mined = false;

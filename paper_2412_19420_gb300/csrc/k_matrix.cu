@@ -29,10 +29,15 @@ build_bitmaps_kernel(const int64_t *__restrict__ indptr, const int32_t *__restri
     const int icount = min(ib, m - i0);
     const int64_t t0 = w0 * 32;
     const int64_t t1 = min(n, t0 + WB * 32);
+    int bad = 0, my_max = 0;
+    if (nnz < 0) {  // device input: indptr[n] read here, and indptr[0] checked once
+        nnz = indptr[n];
+        if (nnz < 0) bad = 1;
+        if (blockIdx.x == 0 && blockIdx.y == 0 && blk0 == 0 && threadIdx.x == 0 && indptr[0] != 0) bad = 1;
+    }
 
     for (int k = threadIdx.x; k < WB * ms; k += blockDim.x) tile[k] = 0u;
     __syncthreads();
-    int bad = 0, my_max = 0;
     // warp w takes 32-row groups: lane i holds the group's start of row i, the
     // warp streams the group's elements 32 at a time (coalesced) and each
     // element finds its row by a binary search over the lanes' starts
@@ -164,11 +169,7 @@ int launch_build_bitmaps(fim_ctx *ctx, const int64_t *d_indptr, const int32_t *d
     cudaStream_t st = ctx->stream;
     FIM_CUDA_TRY(cudaMemsetAsync(flag, 0, 2 * sizeof(int), st));
     if (nblk <= 0 || ctx->m <= 0) return FIM_OK;
-    if (nnz < 0) {  // device input: nnz is read on the host before the launch (indptr[n])
-        FIM_CUDA_TRY(cudaMemcpyAsync(&nnz, d_indptr + ctx->n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-        FIM_CUDA_TRY(cudaStreamSynchronize(st));
-        if (nnz < 0) return FIM_E_INVAL;
-    }
+    // device input (nnz < 0): the kernel reads indptr[n] itself
     // Host input: the indices go up in chunks of row blocks on side streams,
     // and each chunk's blocks are built as soon as its copy has landed, so the
     // upload overlaps the construction.  A chunk needs the elements

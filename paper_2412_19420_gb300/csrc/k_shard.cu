@@ -186,6 +186,7 @@ int fim_merge_results(fim_ctx *ctx, int64_t n_trans, int32_t n_items, int n_part
                       const uint32_t *const *supports, uint32_t flags) {
     FIM_NVTX("fim_merge_results");
     if (!ctx || n_parts < 1 || !n_sets || !n_items_total || !offsets || !items || !supports) return FIM_E_INVAL;
+    FIM_TRY(fim_finish_phase_times(ctx));  // before the events are recorded again
     if (n_trans < 0 || n_trans > FIM_MAX_TRANS || n_items < 0 || n_items > FIM_MAX_ITEMS) return FIM_E_INVAL;
     unsigned long long R = 0, T = 0;
     for (int p = 0; p < n_parts; p++) {

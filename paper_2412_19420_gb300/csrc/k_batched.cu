@@ -104,21 +104,33 @@ batch_build_kernel(const DbDesc *__restrict__ dbs, int n_db, const int64_t *__re
 // over the link, where it leaves each SM room for the pair pass of an earlier
 // group of databases.
 constexpr int BUILD_ROWS_THREADS = 512;
+// What a build CTA needs of its unit, written per unit by the unit-map
+// kernel: one 64-byte load instead of map -> database table -> prefix.
+struct __align__(16) BuildUnit {
+    const int64_t *indptr;  // the database's CSR
+    const int32_t *indices;
+    uint32_t *col0;         // its first bit column
+    int64_t n;              // its transactions
+    int64_t nwp;            // column pitch in words
+    int64_t item_off;       // its first entry of the item supports
+    int64_t w0;             // the unit's first word
+    int32_t m;              // its items
+    int32_t pad;
+};
+static_assert(sizeof(BuildUnit) == 64, "one unit per 64 bytes");
+
 template <int WBK, bool COAL>
-__device__ __forceinline__ void build_rows_unit(const DbDesc *__restrict__ dbs, const int *__restrict__ unit_db,
-                                                const int64_t *__restrict__ unit_prefix, int64_t unit,
-                                                uint32_t *__restrict__ bm, uint32_t *__restrict__ sup,
-                                                int *__restrict__ flag, uint32_t *tile) {
+__device__ __forceinline__ void build_rows_unit(const BuildUnit *__restrict__ units, int64_t unit,
+                                                uint32_t *__restrict__ sup, int *__restrict__ flag, uint32_t *tile) {
     static_assert(WBK % 4 == 0 && WBK / 4 <= 32 && 32 % (WBK / 4) == 0, "a column's chunks share a warp");
     constexpr int NWARP = BUILD_ROWS_THREADS / 32;
     constexpr int QPC = WBK / 4;  // 16-byte chunks of a column in this block
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int d = unit_db[unit];
-    const DbDesc &D = dbs[d];
+    const BuildUnit D = units[unit];
     const int m = D.m, ms = m | 1;  // odd pitch: the transposed reads below are conflict-free
-    const int64_t w0 = (unit - unit_prefix[d]) * WBK;
+    const int64_t w0 = D.w0;
     const int64_t n = D.n;
-    uint32_t *const col0 = bm + D.bm_off;
+    uint32_t *const col0 = D.col0;
     const int64_t t0 = w0 * 32;
     if (t0 >= n) {  // padding words only
         for (int k = threadIdx.x; k < m * QPC; k += BUILD_ROWS_THREADS)
@@ -231,22 +243,20 @@ __device__ __forceinline__ void build_rows_unit(const DbDesc *__restrict__ dbs, 
 
 template <int WBK, bool COAL, bool PERSIST>
 __global__ void __launch_bounds__(BUILD_ROWS_THREADS)
-batch_build_rows_kernel(const DbDesc *__restrict__ dbs, const int *__restrict__ unit_db,
-                        const int64_t *__restrict__ unit_prefix, int64_t unit_base, int64_t unit_end,
-                        uint32_t *__restrict__ bm, uint32_t *__restrict__ sup, int *__restrict__ flag) {
+batch_build_rows_kernel(const BuildUnit *__restrict__ units, int64_t unit_base, int64_t unit_end,
+                        uint32_t *__restrict__ sup, int *__restrict__ flag) {
     extern __shared__ __align__(16) uint32_t tile[];  // [WBK][ms]
     if (!PERSIST) {
-        build_rows_unit<WBK, COAL>(dbs, unit_db, unit_prefix, unit_base + blockIdx.x, bm, sup, flag, tile);
+        build_rows_unit<WBK, COAL>(units, unit_base + blockIdx.x, sup, flag, tile);
         return;
     }
     for (int64_t u = unit_base + blockIdx.x; u < unit_end; u += gridDim.x) {
-        build_rows_unit<WBK, COAL>(dbs, unit_db, unit_prefix, u, bm, sup, flag, tile);
+        build_rows_unit<WBK, COAL>(units, u, sup, flag, tile);
         __syncthreads();  // the tile has been written out before the next unit clears it
     }
 }
 
-using BuildRowsFn = void (*)(const DbDesc *, const int *, const int64_t *, int64_t, int64_t, uint32_t *, uint32_t *,
-                             int *);
+using BuildRowsFn = void (*)(const BuildUnit *, int64_t, int64_t, uint32_t *, int *);
 template <int WBK>
 BuildRowsFn build_rows_fn_w(bool coal, bool persist) {
     return coal ? (persist ? batch_build_rows_kernel<WBK, true, true> : batch_build_rows_kernel<WBK, true, false>)
@@ -257,10 +267,25 @@ BuildRowsFn build_rows_fn(int wbk, bool coal, bool persist) {
            : wbk == 16 ? build_rows_fn_w<16>(coal, persist) : build_rows_fn_w<32>(coal, persist);
 }
 
-// unit -> database map of the rows build: one CTA per database
-__global__ void batch_unit_db_kernel(const int64_t *__restrict__ unit_prefix, int *__restrict__ unit_db) {
+// the rows build's unit table: one CTA per database writes its units
+__global__ void batch_unit_db_kernel(const DbDesc *__restrict__ dbs, const int64_t *__restrict__ unit_prefix,
+                                     int wbk, uint32_t *__restrict__ bm, BuildUnit *__restrict__ units) {
     const int d = blockIdx.x;
-    for (int64_t u = unit_prefix[d] + threadIdx.x; u < unit_prefix[d + 1]; u += blockDim.x) unit_db[u] = d;
+    const DbDesc &D = dbs[d];
+    const int64_t u0 = unit_prefix[d];
+    for (int64_t u = u0 + threadIdx.x; u < unit_prefix[d + 1]; u += blockDim.x) {
+        BuildUnit b;
+        b.indptr = D.indptr;
+        b.indices = D.indices;
+        b.col0 = bm + D.bm_off;
+        b.n = D.n;
+        b.nwp = D.nwp;
+        b.item_off = D.item_off;
+        b.w0 = (u - u0) * wbk;
+        b.m = D.m;
+        b.pad = 0;
+        units[u] = b;
+    }
 }
 
 // One CTA per item column of the batch: S(I_j) by popcount.
@@ -1088,7 +1113,8 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
     const size_t plan_scr_off = plan_ord_off + ((sizeof(int) * (size_t)n_db + 255) & ~(size_t)255);
     if (pack) FIM_TRY(fim_reserve(ctx, ctx->batch_plan, plan_scr_off + batch_pair_plan_scratch(n_db)));
     if (rows_build)
-        FIM_TRY(fim_reserve(ctx, ctx->batch_unit_db, sizeof(int) * (size_t)(L.unit_prefix[n_db] ? L.unit_prefix[n_db] : 1)));
+        FIM_TRY(fim_reserve(ctx, ctx->batch_unit_db,
+                            sizeof(BuildUnit) * (size_t)(L.unit_prefix[n_db] ? L.unit_prefix[n_db] : 1)));
     if (ctx->rec_cap < (1ull << 22)) {
         ctx->rec_cap = 1ull << 22;
         ctx->rec_items_cap = 1ull << 24;
@@ -1269,16 +1295,17 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
             if (rows_build && items > 0)
                 cudaMemsetAsync(ctx->item_sup.p, 0, sizeof(uint32_t) * (size_t)items, st);
             if (rows_build && units > 0)
-                batch_unit_db_kernel<<<(unsigned)n_db, 256, 0, st>>>(d_unit, ctx->batch_unit_db.as<int>());
+                batch_unit_db_kernel<<<(unsigned)n_db, 256, 0, st>>>(d_dbs, d_unit, wbk, ctx->bm.as<uint32_t>(),
+                                                                     ctx->batch_unit_db.as<BuildUnit>());
             auto build_rows = [&](int64_t u0, int64_t u1, cudaStream_t s_) {
                 if (u1 <= u0) return;
                 const unsigned grid = (unsigned)(u1 - u0);
-                int *const udb = ctx->batch_unit_db.as<int>();
-                uint32_t *const bmp = ctx->bm.as<uint32_t>(), *const sup = ctx->item_sup.as<uint32_t>();
+                const BuildUnit *const bu = ctx->batch_unit_db.as<BuildUnit>();
+                uint32_t *const sup = ctx->item_sup.as<uint32_t>();
                 int *const flg = ctx->dev_flag.as<int>();
                 const unsigned g = persist_build ? (unsigned)(u1 - u0 < ctx->num_sms ? u1 - u0 : ctx->num_sms) : grid;
-                build_rows_fn(wbk, coal, persist_build)<<<g, BUILD_ROWS_THREADS, smem_rows, s_>>>(
-                    d_dbs, udb, d_unit, u0, u1, bmp, sup, flg);
+                build_rows_fn(wbk, coal, persist_build)<<<g, BUILD_ROWS_THREADS, smem_rows, s_>>>(bu, u0, u1, sup,
+                                                                                                 flg);
             };
             auto rank_db = [&](int da, int db_, cudaStream_t s_) {
                 if (db_ > da)

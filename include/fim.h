@@ -251,6 +251,12 @@ int fim_get_stats(const fim_ctx *ctx, fim_stats *out);
  *                                databases with at most 64 frequent items (and about
  *                                as many transactions) share one 128 x 128 tile
  *                                (default 1); 0 = a tile per database
+ *   "batch_group_dfs"  0, 1      fim_mine_batched with pipelined groups (more than
+ *                                one): each group's root classes are planned and
+ *                                mined (warp workers) right after its pair pass,
+ *                                beside the later groups' uploads and builds
+ *                                (default 1); 0 = one prefix extension after all
+ *                                groups
  *   "batch_build_coal" 0, 1      fim_mine_batched's build: a warp reads its 32
  *                                rows' item ids 32 at a time (coalesced) and finds
  *                                each id's row among the lanes; 0 = lane-per-row

@@ -187,6 +187,7 @@ void fim_destroy(fim_ctx *ctx) {
     fim_release(ctx, ctx->batch_units);
     fim_release(ctx, ctx->batch_unit_db);
     fim_release(ctx, ctx->batch_plan);
+    fim_release(ctx, ctx->batch_windows);
     fim_release(ctx, ctx->batch_slices);
     if (ctx->batch_graph_exec) cudaGraphExecDestroy((cudaGraphExec_t)ctx->batch_graph_exec);
     for (void *g : ctx->compact_graph_exec)
@@ -446,7 +447,7 @@ int mine_once(fim_ctx *ctx, uint32_t thr, uint32_t flags, MineState &ms, bool *r
         {   // candidate-less roots dropped, the others ordered
             const int mode = (p.learned && ctx->learned_order) ? 2 : ctx->root_sort;
             FIM_TRY(reserve_root_plan(ctx, npairs));
-            FIM_TRY(launch_root_plan(ctx, d_ctr, npairs, nullptr, mode, st));
+            FIM_TRY(launch_root_plan(ctx, d_ctr, npairs, nullptr, mode, nullptr, st));
             p.root_order = ctx->root_order.as<uint32_t>();
         }
         p.trace = (flags & FIM_TRACE) ? 1 : 0;
@@ -632,6 +633,7 @@ int fim_set_tuning(fim_ctx *ctx, const char *key, int64_t v) {
         {"batch_build_block", &ctx->batch_build_block, 16, 64},
         {"batch_build_coal", &ctx->batch_build_coal, 0, 1},
         {"batch_pairs_pack", &ctx->batch_pairs_pack, 0, 1},
+        {"batch_group_dfs", &ctx->batch_group_dfs, 0, 1},
         {"root_sort", &ctx->root_sort, 0, 1},
         {"record_chunk", &ctx->rec_chunk, 1, 1024},
         {"batch_segments", &ctx->batch_segments, 0, 16},

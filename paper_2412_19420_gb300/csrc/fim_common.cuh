@@ -135,6 +135,14 @@ struct DbDesc {
     uint32_t maxlen;
 };
 
+// A window of the root arrays: the roots one group of a batch's databases
+// appended (base, count), the part its root plan kept (kept, in
+// root_order[base ..]) and the ticket counter of the prefix extension over
+// them.
+struct RootWindow {
+    unsigned long long base, count, kept, ticket;
+};
+
 // One frame of a worker's DFS stack lives in global memory.
 struct DfsParams {
     // mine-wide arrays; a database's part starts at its DbDesc offsets
@@ -189,6 +197,7 @@ struct DfsParams {
     int learned_kmin;               // FIM_LEARNED consults the network for classes with >= this many candidates
     int rec_chunk;                  // record slots a DFS worker reserves at a time (1: exactly per class)
     int root_reverse;               // hand out the root classes in reverse emission order
+    RootWindow *win;                // warp workers: only this window's roots (null: all of them)
 };
 
 // ---------------------------------------------------------------- the ctx
@@ -264,6 +273,8 @@ struct fim_ctx {
     bool pair_units_ok = false;
     bool phase_times_pending = false;  // a single mine's ev[1..4] still to be read
     int batch_pairs_pack = 1;   // the batch's pair units planned on the device, small databases two to a tile
+    int batch_group_dfs = 1;    // pipelined groups: each group's roots mined right after its finalize
+    DevBuf batch_windows;       // those groups' root windows
     DevBuf batch_plan;          // that plan's unit counts, database order and scratch
     std::vector<unsigned char> up_ord;
     std::pair<const void *, size_t> up_ord_buf{};
@@ -365,7 +376,9 @@ int launch_sparse_items(fim_ctx *ctx, int mf, int64_t cap, cudaStream_t st);
 // the pair pass's order, 1 by candidate count, 2 by the network's predicted
 // subtree work); d_dbs = the batch's table, or null for a single database
 int reserve_root_plan(fim_ctx *ctx, size_t root_cap);
-int launch_root_plan(fim_ctx *ctx, MineCounters *d_ctr, size_t root_cap, const DbDesc *d_dbs, int mode,
+// win (non-null): plan only the window's roots, leaving the root count to
+// the groups that append after it
+int launch_root_plan(fim_ctx *ctx, MineCounters *d_ctr, size_t root_cap, const DbDesc *d_dbs, int mode, RootWindow *win,
                      cudaStream_t st);
 
 // k_compact.cu

@@ -267,6 +267,16 @@ BuildRowsFn build_rows_fn(int wbk, bool coal, bool persist) {
            : wbk == 16 ? build_rows_fn_w<16>(coal, persist) : build_rows_fn_w<32>(coal, persist);
 }
 
+// a group's window of the root arrays: where its finalize starts appending,
+// and how many roots it appended
+__global__ void window_begin_kernel(const MineCounters *__restrict__ ctr, RootWindow *__restrict__ w) {
+    w->base = *(volatile const unsigned long long *)&ctr->n_roots;
+    w->count = w->kept = w->ticket = 0;
+}
+__global__ void window_end_kernel(const MineCounters *__restrict__ ctr, RootWindow *__restrict__ w) {
+    w->count = *(volatile const unsigned long long *)&ctr->n_roots - w->base;
+}
+
 // the rows build's unit table: one CTA per database writes its units
 __global__ void batch_unit_db_kernel(const DbDesc *__restrict__ dbs, const int64_t *__restrict__ unit_prefix,
                                      int wbk, uint32_t *__restrict__ bm, BuildUnit *__restrict__ units) {
@@ -1079,6 +1089,10 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
     // the batch with CTA workers
     constexpr int kWarpDfsMaxWords = 4096, WARP_DEPTH = 24;
     const bool warp_dfs = ctx->dfs_warp && !ctx->force_cta_dfs && L.nwp_max <= kWarpDfsMaxWords;
+    // pipelined groups: each group's roots planned and mined right after its
+    // finalize, on the side stream, while later groups are uploaded and built
+    const bool group_dfs = ctx->batch_group_dfs && n_seg > 1 && warp_dfs && (maxlen == 0 || maxlen >= 3);
+    if (group_dfs) FIM_TRY(fim_reserve(ctx, ctx->batch_windows, sizeof(RootWindow) * (size_t)n_seg));
     const int n_warps = ctx->num_sms * ctx->dfs_warp_ctas * dfs_warp_per_cta();
     const int dfs_workers = warp_dfs ? n_warps : workers;
     int depth_cap = (int)(L.max_row_bound < 240 ? L.max_row_bound : 240);
@@ -1221,6 +1235,11 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
         mix(&wbk, sizeof(wbk));
         mix(&coal, sizeof(coal));
         mix(&persist_build, sizeof(persist_build));
+        mix(&group_dfs, sizeof(group_dfs));
+        if (group_dfs) {
+            const void *wp = ctx->batch_windows.p;
+            mix(&wp, sizeof(wp));
+        }
         mix(&streamed, sizeof(streamed));
         for (const auto &v : seg_copies)
             for (const HostCopy &c : v) mix(&c, sizeof(c));
@@ -1347,7 +1366,19 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
                     cudaEventRecord(ctx->seg_ev[sg], st);
                     cudaStreamWaitEvent(aux, ctx->seg_ev[sg], 0);
                     if (rc_pairs == FIM_OK) rc_pairs = pair_pass(sg, aux);
+                    RootWindow *const win = group_dfs ? ctx->batch_windows.as<RootWindow>() + sg : nullptr;
+                    if (win) window_begin_kernel<<<1, 1, 0, aux>>>(d_ctr, win);
                     finalize_db(da, db_, aux);
+                    if (win) {  // the group's own root plan and prefix extension, on the side stream
+                        window_end_kernel<<<1, 1, 0, aux>>>(d_ctr, win);
+                        if (rc_pairs == FIM_OK)
+                            rc_pairs = launch_root_plan(ctx, d_ctr, rc, d_dbs, plan_mode, win, aux);
+                        if (rc_pairs == FIM_OK) {
+                            DfsParams pw = p;
+                            pw.win = win;
+                            rc_pairs = launch_dfs_warp(ctx, pw, n_warps, ctx->dfs_warp_ctas, aux);
+                        }
+                    }
                 }
                 cudaEventRecordWithFlags(ctx->ev[1], st, cudaEventRecordExternal);
                 cudaEventRecord(ctx->seg_ev[n_seg], aux);
@@ -1399,8 +1430,8 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
             }
             cudaEventRecordWithFlags(ctx->ev[2], st, cudaEventRecordExternal);
             int rc_launch = FIM_OK;
-            if (maxlen == 0 || maxlen >= 3) {
-                rc_launch = launch_root_plan(ctx, d_ctr, rc, d_dbs, plan_mode, st);
+            if (!group_dfs && (maxlen == 0 || maxlen >= 3)) {
+                rc_launch = launch_root_plan(ctx, d_ctr, rc, d_dbs, plan_mode, nullptr, st);
                 if (rc_launch == FIM_OK)
                     rc_launch = warp_dfs ? launch_dfs_warp(ctx, p, n_warps, ctx->dfs_warp_ctas, st)
                                          : launch_dfs(ctx, p, workers, ctx->dfs_block);

@@ -152,7 +152,11 @@ dfs_warp_kernel(const DfsParams p) {
     uint32_t *fi = p.frame_items + wid * p.frame_pool;
     uint32_t *fs = p.frame_sups + wid * p.frame_pool;
     uint32_t *stk = p.stack_bits + wid * (int64_t)p.depth_cap * p.nwp_max;
-    const unsigned long long nr = *(volatile const unsigned long long *)&p.ctr->n_roots;
+    // the roots of a window (one group of databases), or all of them
+    const unsigned long long nr = p.win ? *(volatile const unsigned long long *)&p.win->kept
+                                        : *(volatile const unsigned long long *)&p.ctr->n_roots;
+    const unsigned long long rbase = p.win ? p.win->base : 0ull;
+    unsigned long long *const ticket = p.win ? &p.win->ticket : &p.ctr->ticket;
     unsigned long long busy = 0, t_task = 0;
     if (lane == 0) atomicCAS(&p.ctr->t_first, 0ull, globaltimer_ns());
     unsigned int iter = 0;
@@ -160,7 +164,7 @@ dfs_warp_kernel(const DfsParams p) {
         unsigned long long t = 0;
         int err = 0;
         if (lane == 0) {
-            t = atomicAdd(&p.ctr->ticket, 1ull);
+            t = atomicAdd(ticket, 1ull);
             err = *(volatile int *)&p.ctr->err;
             t_task = globaltimer_ns();
         }
@@ -168,7 +172,7 @@ dfs_warp_kernel(const DfsParams p) {
         err = __shfl_sync(0xffffffffu, err, 0);
         if (t >= nr || err) break;
         const unsigned long long tt = p.root_reverse ? nr - 1 - t : t;
-        const unsigned long long rt = p.root_order ? p.root_order[tt] : tt;
+        const unsigned long long rt = p.root_order ? p.root_order[rbase + tt] : rbase + tt;
         const uint32_t a = p.root_a[rt], b = p.root_b[rt], sab = p.root_sup[rt];
         const uint32_t dbi = p.root_db ? p.root_db[rt] : 0u;
         if (lane == 0) {

@@ -219,16 +219,17 @@ struct RootView {
 __global__ void __launch_bounds__(256)
 root_plan_kernel(const uint32_t *__restrict__ root_a, const uint32_t *__restrict__ root_b,
                  const uint32_t *__restrict__ root_sup, const uint32_t *__restrict__ root_db,
-                 const MineCounters *ctr, const DbDesc *__restrict__ dbs, RootView single, int mode,
-                 const __nv_bfloat16 *__restrict__ wbf, uint8_t *__restrict__ bucket, uint32_t *__restrict__ hist) {
+                 const MineCounters *ctr, const RootWindow *win, const DbDesc *__restrict__ dbs, RootView single,
+                 int mode, const __nv_bfloat16 *__restrict__ wbf, uint8_t *__restrict__ bucket,
+                 uint32_t *__restrict__ hist) {
     __shared__ float w[P];
     __shared__ uint32_t h[NBUCKET];
     if (mode == 2)
         for (int i = threadIdx.x; i < P; i += blockDim.x) w[i] = __bfloat162float(wbf[i]);
     for (int i = threadIdx.x; i < NBUCKET; i += blockDim.x) h[i] = 0;
     __syncthreads();
-    const unsigned long long nr = ctr->n_roots;
-    for (unsigned long long r = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; r < nr;
+    const unsigned long long r0 = win ? win->base : 0ull, nr = win ? r0 + win->count : ctr->n_roots;
+    for (unsigned long long r = r0 + (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; r < nr;
          r += (unsigned long long)gridDim.x * blockDim.x) {
         RootView v = single;
         if (dbs) {  // a batch: the root's database
@@ -295,25 +296,29 @@ root_plan_kernel(const uint32_t *__restrict__ root_a, const uint32_t *__restrict
 }
 
 // Exclusive scan of the bucket counts; the dropped roots leave the root
-// count and the pending-task count.  hist[NBUCKET] keeps the count before.
-__global__ void root_plan_scan_kernel(uint32_t *hist, MineCounters *ctr) {
+// count (a window's kept count instead) and the pending-task count.
+// hist[NBUCKET] keeps the count before.
+__global__ void root_plan_scan_kernel(uint32_t *hist, MineCounters *ctr, RootWindow *win) {
     if (threadIdx.x == 0) {
-        const unsigned long long total = ctr->n_roots;
+        const unsigned long long total = win ? win->count : ctr->n_roots;
         const uint32_t dropped = hist[DROP];
         uint32_t acc = 0;
         for (int i = 0; i < NBUCKET; i++) { const uint32_t v = hist[i]; hist[i] = acc; acc += v; }
         hist[NBUCKET] = (uint32_t)total;
-        ctr->n_roots = total - dropped;
+        if (win)
+            win->kept = total - dropped;
+        else
+            ctr->n_roots = total - dropped;
         ctr->pending -= (long long)dropped;
     }
 }
 
 __global__ void root_plan_scatter_kernel(const uint8_t *__restrict__ bucket, uint32_t *__restrict__ hist,
-                                         uint32_t *__restrict__ order) {
-    const unsigned long long nr = hist[NBUCKET];
-    for (unsigned long long r = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; r < nr;
+                                         const RootWindow *win, uint32_t *__restrict__ order) {
+    const unsigned long long r0 = win ? win->base : 0ull, nr = r0 + hist[NBUCKET];
+    for (unsigned long long r = r0 + (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; r < nr;
          r += (unsigned long long)gridDim.x * blockDim.x)
-        if (bucket[r] != DROP) order[atomicAdd(&hist[bucket[r]], 1u)] = (uint32_t)r;
+        if (bucket[r] != DROP) order[r0 + atomicAdd(&hist[bucket[r]], 1u)] = (uint32_t)r;
 }
 
 }  // namespace
@@ -328,7 +333,7 @@ int reserve_root_plan(fim_ctx *ctx, size_t root_cap) {
 // (allocates nothing: it may run inside a stream capture once
 // reserve_root_plan has sized the buffers)
 int launch_root_plan(fim_ctx *ctx, MineCounters *d_ctr, size_t root_cap, const DbDesc *d_dbs, int mode,
-                     cudaStream_t st) {
+                     RootWindow *win, cudaStream_t st) {
     if (mode == 2 && !ctx->has_weights) return FIM_E_STATE;
     FIM_CUDA_TRY(cudaMemsetAsync(ctx->root_hist.p, 0, sizeof(uint32_t) * (NBUCKET + 1), st));
     const uint32_t *roots = ctx->roots.as<uint32_t>();
@@ -351,12 +356,12 @@ int launch_root_plan(fim_ctx *ctx, MineCounters *d_ctr, size_t root_cap, const D
     if (grid > resident) grid = resident;
     ctx->launches += 3;
     root_plan_kernel<<<(unsigned)grid, 256, 0, st>>>(roots, roots + root_cap, roots + 2 * root_cap,
-                                           d_dbs ? roots + 3 * root_cap : nullptr, d_ctr, d_dbs, v, mode,
+                                           d_dbs ? roots + 3 * root_cap : nullptr, d_ctr, win, d_dbs, v, mode,
                                            ctx->mlp_wbf.as<__nv_bfloat16>(), ctx->root_bucket.as<uint8_t>(),
                                            ctx->root_hist.as<uint32_t>());
-    root_plan_scan_kernel<<<1, 32, 0, st>>>(ctx->root_hist.as<uint32_t>(), d_ctr);
+    root_plan_scan_kernel<<<1, 32, 0, st>>>(ctx->root_hist.as<uint32_t>(), d_ctr, win);
     root_plan_scatter_kernel<<<(unsigned)grid, 256, 0, st>>>(ctx->root_bucket.as<uint8_t>(), ctx->root_hist.as<uint32_t>(),
-                                                   ctx->root_order.as<uint32_t>());
+                                                   win, ctx->root_order.as<uint32_t>());
     FIM_CUDA_TRY(cudaGetLastError());
     return FIM_OK;
 }

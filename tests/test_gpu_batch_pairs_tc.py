@@ -155,18 +155,22 @@ def test_autotuned_batch_shape_is_exact(ctx):
     _check(ctx, dbs, ms, 0)
 
 
-@pytest.mark.parametrize("segments", [1, 2, 3, 8])
-def test_pipelined_groups_are_exact(ctx, segments):
+@pytest.mark.parametrize("segments,group_dfs", [(1, 1), (2, 1), (3, 1), (8, 1), (8, 0)])
+def test_pipelined_groups_are_exact(ctx, segments, group_dfs):
     # the batch graph pipelines groups of databases (build and rank of one
-    # group beside the pair pass of the one before); any grouping is exact,
-    # and so is a graph re-captured for another grouping
+    # group beside the pair pass, root plan and prefix extension of the one
+    # before, or the prefix extension once after all groups); any grouping
+    # is exact, and so is a graph re-captured for another grouping
     fim.fim_set_tuning(ctx, "batch_segments", segments)
+    fim.fim_set_tuning(ctx, "batch_group_dfs", group_dfs)
     dbs = [datagen.batched_db(s) for s in datagen.batched_specs(40, seed=5)]
     dbs[7] = datagen.from_lists([], 9)  # an empty database inside a group
     ms = [datagen.minsup_from_ppm(c.n, 20_000) for c in dbs]
-    for _ in range(2):
-        fim.fim_mine_batched(ctx, dbs, ms)
-        _check(ctx, dbs, ms, 0)
+    for flags, ml in ((0, 0), (0, 0), (fim.FIM_STRICT, 0), (fim.FIM_MAXLEN(3), 3)):
+        fim.fim_mine_batched(ctx, dbs, ms, flags)
+        for d, (c, m) in enumerate(zip(dbs, ms)):
+            want = oracle.apriori(c.indptr, c.indices, c.m, m, strict=bool(flags & fim.FIM_STRICT), max_len=ml)
+            assert fim.fim_fetch_batched(ctx, d).sha256() == want.sha256(), (d, flags)
 
 
 @pytest.mark.parametrize("pack", [1, 0])

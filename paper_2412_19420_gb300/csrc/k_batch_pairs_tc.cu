@@ -9,12 +9,12 @@
 // an integer <= 2^22, exact in f32), as in the single-database pass.
 //
 // Work: the units are (database, ta, tb) with ta <= tb, the 128 x 128 tiles of
-// each database's item blocks, listed by the host tile number first and then
-// by descending stage count (128 transactions per stage) of the database.
-// Which units hold pairs depends on m'_d, known only on the device: a unit
-// with 128 tb >= m'_d is empty, and every role of the CTA skips it alike.  CTA c takes units c,
-// c + grid, c + 2 grid, ...: the longest first, so the persistent grid ends
-// nearly together.  A unit's K range runs in segments of at most kdrain
+// each database's item blocks, longest first (or the device plan's units,
+// see batch_pair_plan_kernel).  Which units hold pairs depends on m'_d,
+// known only on the device: a unit with 128 tb >= m'_d is empty, and every
+// role of the CTA skips it alike.  CTA c takes units c, 2G - 1 - c, 2G + c,
+// ... (G CTAs, the rounds alternating direction), so that the persistent
+// grid ends nearly together.  A unit's K range runs in segments of at most kdrain
 // stages; each segment is one accumulator run, and the two accumulator
 // buffers let a segment's drain overlap the next segment's MMAs.
 //
@@ -157,6 +157,11 @@ batch_pairs_tc_kernel(const DbDesc *__restrict__ dbs, const unsigned long long *
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // the units the plan kernel wrote (this launch's stream, before it), or the host's
     const int64_t n_units = n_units_dev ? (int64_t)*n_units_dev : n_units_host;
+    // CTA c's k-th unit: units come longest first, so the rounds alternate
+    // direction (c, 2G - 1 - c, 2G + c, ...) to even out the CTAs' totals;
+    // every role walks the same sequence
+    const int64_t G = gridDim.x, c_ = blockIdx.x;
+    auto unit_of = [G, c_](int64_t k) { return k * G + ((k & 1) ? G - 1 - c_ : c_); };
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < BSTAGES; i++) { mbar_init(&s.full[i], BNPROD / 32); mbar_init(&s.empty[i], 1); }
@@ -186,7 +191,7 @@ batch_pairs_tc_kernel(const DbDesc *__restrict__ dbs, const unsigned long long *
         uint32_t zeroed = 0;                  // bit q: my row of ring slot q holds zeros
         int it = 0;                           // stages produced by this CTA (ring position)
         bool ok = true;
-        for (int64_t ui = blockIdx.x; ui < n_units && ok; ui += gridDim.x) {
+        for (int64_t k = 0, ui = unit_of(0); ui < n_units && ok; ui = unit_of(++k)) {
             const BUnit u = decode_unit(dbs, units[ui]);
             if (u.empty) continue;
             const bool store = !(is_a && u.diag);  // warp-uniform: a warp's rows are all A or all B
@@ -286,7 +291,7 @@ batch_pairs_tc_kernel(const DbDesc *__restrict__ dbs, const unsigned long long *
         const int q = warp & 3;  // TMEM lane quarter this warp may read
         int j = 0;               // segments drained by this CTA
         bool ok = true;
-        for (int64_t ui = blockIdx.x; ui < n_units && ok; ui += gridDim.x) {
+        for (int64_t k = 0, ui = unit_of(0); ui < n_units && ok; ui = unit_of(++k)) {
             const BUnit u = decode_unit(dbs, units[ui]);
             if (u.empty) continue;
             // my accumulator row: item a of database Da (a packed pair's rows
@@ -336,7 +341,7 @@ batch_pairs_tc_kernel(const DbDesc *__restrict__ dbs, const unsigned long long *
         // ---------------- MMA issuer ----------------
         bool ok = true;
         int it = 0, j = 0;
-        for (int64_t ui = blockIdx.x; ui < n_units && ok; ui += gridDim.x) {
+        for (int64_t k = 0, ui = unit_of(0); ui < n_units && ok; ui = unit_of(++k)) {
             const BUnit u = decode_unit(dbs, units[ui]);
             if (u.empty) continue;
             const uint32_t idesc = idesc_f8(BT, u.N);

@@ -38,6 +38,11 @@ struct WarpState {
     uint32_t path[WMAXP];
     int nF[WMAXP], cur[WMAXP];
     long long base[WMAXP + 1];
+    // the worker's statistics, summed here by lane 0 and added to the global
+    // counters once, at exit: per-class atomics on those few shared words
+    // queued every worker's ticket and record atomics behind them
+    unsigned long long n_sup, n_words, n_bytes, n_touched, n_classes, n_roots_done;
+    int max_len;
 };
 
 __device__ __forceinline__ const uint32_t *wcol(const WarpState &s, uint32_t item) {
@@ -132,12 +137,12 @@ __device__ int warp_class_pass(const DfsParams &p, WarpState &s, const uint32_t 
     }
     if (lane == 0) {
         const unsigned long long src_bytes = 4ull * nw * (2ull + (store ? 1ull : 0ull));
-        atomicAdd(&p.ctr->supports_dfs, (unsigned long long)k);
-        atomicAdd(&p.ctr->dfs_words, (unsigned long long)k * (unsigned long long)nw);
-        atomicAdd(&p.ctr->dfs_bytes, 4ull * nw * (unsigned long long)k + src_bytes);
-        atomicAdd(&p.ctr->dfs_touched, 32ull * secs * (unsigned long long)k + src_bytes);
-        atomicAdd(&p.ctr->classes, 1ull);
-        if (nF > 0) atomicMax(&p.ctr->max_len, plen + 1);
+        s.n_sup += (unsigned long long)k;
+        s.n_words += (unsigned long long)k * (unsigned long long)nw;
+        s.n_bytes += 4ull * nw * (unsigned long long)k + src_bytes;
+        s.n_touched += 32ull * secs * (unsigned long long)k + src_bytes;
+        s.n_classes += 1ull;
+        if (nF > 0 && plen + 1 > s.max_len) s.max_len = plen + 1;
     }
     return nF;
 }
@@ -158,7 +163,11 @@ dfs_warp_kernel(const DfsParams p) {
     const unsigned long long rbase = p.win ? p.win->base : 0ull;
     unsigned long long *const ticket = p.win ? &p.win->ticket : &p.ctr->ticket;
     unsigned long long busy = 0, t_task = 0;
-    if (lane == 0) atomicCAS(&p.ctr->t_first, 0ull, globaltimer_ns());
+    if (lane == 0) {
+        atomicCAS(&p.ctr->t_first, 0ull, globaltimer_ns());
+        s.n_sup = s.n_words = s.n_bytes = s.n_touched = s.n_classes = s.n_roots_done = 0ull;
+        s.max_len = 0;
+    }
     unsigned int iter = 0;
     // Roots are taken TCH at a time, and the next chunk's ticket is fetched
     // when a chunk starts: one contended atomic per TCH roots, its latency
@@ -321,11 +330,20 @@ dfs_warp_kernel(const DfsParams p) {
             }
         }
         if (lane == 0) {
-            atomicAdd((unsigned long long *)&p.ctr->pending, (unsigned long long)(-1ll));
+            s.n_roots_done += 1ull;
             busy += globaltimer_ns() - t_task;
         }
     }
     if (lane == 0) {
+        if (s.n_roots_done) atomicAdd((unsigned long long *)&p.ctr->pending, 0ull - s.n_roots_done);
+        if (s.n_classes) {
+            atomicAdd(&p.ctr->supports_dfs, s.n_sup);
+            atomicAdd(&p.ctr->dfs_words, s.n_words);
+            atomicAdd(&p.ctr->dfs_bytes, s.n_bytes);
+            atomicAdd(&p.ctr->dfs_touched, s.n_touched);
+            atomicAdd(&p.ctr->classes, s.n_classes);
+        }
+        if (s.max_len) atomicMax(&p.ctr->max_len, s.max_len);
         atomicAdd(&p.ctr->busy_ns, busy);
         atomicMax(&p.ctr->t_last, globaltimer_ns());
     }

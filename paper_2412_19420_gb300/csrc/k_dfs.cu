@@ -79,6 +79,11 @@ struct Smem {
     int lz[MAXPATH];                     // entries of each level's stored bitmap; -1 = dense
     unsigned long long n_roots;          // root count (fixed once the DFS runs)
     unsigned long long busy, root_busy, t_task;  // thread 0's worker timing
+    // the worker's class statistics, summed by thread 0 and added to the
+    // global counters once, at exit (per-class atomics on those shared words
+    // delay every worker's ticket and record atomics on the same lines)
+    unsigned long long n_sup, n_words, n_bytes, n_touched, n_classes, n_diff;
+    int max_len;
     int err_seen;                        // last error flag read
     uint32_t epoch;                      // this mine's task epoch
     unsigned int iter;                   // classes since the worker started
@@ -564,13 +569,13 @@ __device__ int class_pass(const DfsParams &p, Smem &s, const uint32_t *cand, con
             sparse_parent ? 40ull * (unsigned long long)pz + (store ? 8ull * s.zcount : 0ull)
                           : 4ull * db.nw * ((unsigned long long)nsrc) +
                                 (store ? (store_sparse ? 8ull * s.zcount : 4ull * db.nw) : 0ull);
-        atomicAdd(&p.ctr->supports_dfs, (unsigned long long)k);
-        atomicAdd(&p.ctr->dfs_words, (unsigned long long)k * (unsigned long long)db.nw);
-        atomicAdd(&p.ctr->dfs_bytes, 4ull * db.nw * (unsigned long long)k + src_bytes);
-        atomicAdd(&p.ctr->dfs_touched, 32ull * secs * (unsigned long long)k + src_touched);
-        atomicAdd(&p.ctr->classes, 1ull);
-        if (diff) atomicAdd(&p.ctr->diffset, 1ull);
-        if (nF > 0) atomicMax(&p.ctr->max_len, plen + 1);
+        s.n_sup += (unsigned long long)k;
+        s.n_words += (unsigned long long)k * (unsigned long long)db.nw;
+        s.n_bytes += 4ull * db.nw * (unsigned long long)k + src_bytes;
+        s.n_touched += 32ull * secs * (unsigned long long)k + src_touched;
+        s.n_classes += 1ull;
+        if (diff) s.n_diff += 1ull;
+        if (nF > 0 && plen + 1 > s.max_len) s.max_len = plen + 1;
     }
     return nF;
 }
@@ -785,6 +790,8 @@ dfs_kernel(const DfsParams p) {
         s.iter = 0;
         s.rec_next = s.rec_end = 0;
         s.it_next = s.it_end = 0;
+        s.n_sup = s.n_words = s.n_bytes = s.n_touched = s.n_classes = s.n_diff = 0ull;
+        s.max_len = 0;
     }
 
     while (true) {
@@ -1052,6 +1059,15 @@ dfs_kernel(const DfsParams p) {
     }
     if (threadIdx.x == 0) {
         retire_slots(p, s);  // the worker's unused slots become holes
+        if (s.n_classes) {
+            atomicAdd(&p.ctr->supports_dfs, s.n_sup);
+            atomicAdd(&p.ctr->dfs_words, s.n_words);
+            atomicAdd(&p.ctr->dfs_bytes, s.n_bytes);
+            atomicAdd(&p.ctr->dfs_touched, s.n_touched);
+            atomicAdd(&p.ctr->classes, s.n_classes);
+            if (s.n_diff) atomicAdd(&p.ctr->diffset, s.n_diff);
+        }
+        if (s.max_len) atomicMax(&p.ctr->max_len, s.max_len);
         atomicAdd(&p.ctr->busy_ns, s.busy);
         atomicAdd(&p.ctr->root_ns, s.root_busy);
         atomicMax(&p.ctr->t_last, globaltimer_ns());

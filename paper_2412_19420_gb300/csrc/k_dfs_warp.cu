@@ -176,26 +176,42 @@ dfs_warp_kernel(const DfsParams p) {
     constexpr unsigned long long TCH = 4;
     unsigned long long t_cur = 0, t_end = 0, t_pref = 0;  // lane 0's chunk and the prefetched start
     int err = 0;
+    // lane j < TCH holds root j of the current chunk: all of a chunk's root
+    // records are loaded at once, not one dependent chain per root
+    uint32_t my_a = 0, my_b = 0, my_db = 0;
     if (lane == 0) t_pref = atomicAdd(ticket, TCH);
     while (true) {
         unsigned long long t = 0;
+        int fresh = 0, jr = 0;
         if (lane == 0) {
             if (t_cur >= t_end) {  // chunk done: take the prefetched one, prefetch the next
                 t_cur = t_pref;
                 t_end = t_pref + TCH;
                 if (t_cur < nr) t_pref = atomicAdd(ticket, TCH);
                 err = *(volatile int *)&p.ctr->err;
+                fresh = 1;
             }
+            jr = (int)(t_cur - (t_end - TCH));  // the root's place in its chunk
             t = t_cur++;
             t_task = globaltimer_ns();
         }
         t = __shfl_sync(0xffffffffu, t, 0);
         err = __shfl_sync(0xffffffffu, err, 0);
+        fresh = __shfl_sync(0xffffffffu, fresh, 0);
+        jr = __shfl_sync(0xffffffffu, jr, 0);
         if (t >= nr || err) break;
-        const unsigned long long tt = p.root_reverse ? nr - 1 - t : t;
-        const unsigned long long rt = p.root_order ? p.root_order[rbase + tt] : rbase + tt;
-        const uint32_t a = p.root_a[rt], b = p.root_b[rt], sab = p.root_sup[rt];
-        const uint32_t dbi = p.root_db ? p.root_db[rt] : 0u;
+        if (fresh) {  // t is the chunk's first root
+            const unsigned long long tl = t + (unsigned long long)lane;
+            if (lane < (int)TCH && tl < nr) {
+                const unsigned long long tt = p.root_reverse ? nr - 1 - tl : tl;
+                const unsigned long long rt = p.root_order ? p.root_order[rbase + tt] : rbase + tt;
+                my_a = p.root_a[rt];
+                my_b = p.root_b[rt];
+                my_db = p.root_db ? p.root_db[rt] : 0u;
+            }
+        }
+        const uint32_t a = __shfl_sync(0xffffffffu, my_a, jr), b = __shfl_sync(0xffffffffu, my_b, jr);
+        const uint32_t dbi = __shfl_sync(0xffffffffu, my_db, jr);
         if (lane == 0) {
             const DbDesc &d = p.dbs[dbi];
             s.bm = p.bm + d.bm_off;
@@ -258,7 +274,6 @@ dfs_warp_kernel(const DfsParams p) {
             // level 0: the root class {a, b}, b_Y = col(a) AND col(b)
             const uint32_t *ca = wcol(s, a), *cb = wcol(s, b);
             int nF = warp_class_pass(p, s, ca, cb, fi, k, 2, k >= 2 ? stk : nullptr, fi, fs);
-            (void)sab;
             if (lane == 0) {
                 s.nF[0] = nF;
                 s.cur[0] = 0;

@@ -83,6 +83,9 @@ def _args():
                     help="also time association rules at this confidence (ppm); -1 skips")
     ap.add_argument("--n-db", type=int, default=4096,
                     help="batched workload: mine only its first N databases (profiling captures)")
+    ap.add_argument("--csr", default="compact", choices=["compact", "wide"],
+                    help="batched workload: the CSRs every arm reads, compact (uint32 row offsets, "
+                         "uint16 item ids; FIM_CSR_COMPACT) or wide (int64, int32)")
     ap.add_argument("--learned", action="store_true",
                     help="single database: mine with FIM_LEARNED, the network trained on the GPU "
                          "from plain-miner traces of the same generator at another seed")
@@ -298,15 +301,17 @@ def run_reference_batched(args):
     _emit(line)
 
 
-def _batched_roofline(st, phase, dbs, m_freq, probes):
+def _batched_roofline(st, phase, dbs, m_freq, probes, compact=False):
     """Roofline of the batch graph's dominant phase.  st: fim_get_stats of a
-    timed learned+batched mine; phase: mean CUDA-event phase times (ms)."""
+    timed learned+batched mine; phase: mean CUDA-event phase times (ms);
+    compact: the CSRs hold uint32 row offsets and uint16 item ids."""
     hbm, _, _, src = _peaks()
     dom = max(("ms_build", "ms_pairs", "ms_dfs", "ms_compact"), key=lambda p: phase[p])
     sec = phase[dom] / 1000
     if dom == "ms_build":
         # CSR read once, bit columns written once, the singleton supports fused
-        nbytes = sum(8 * (c.n + 1) + 4 * c.nnz + 4 * c.m * ((c.n + 31) // 32) for c in dbs)
+        po, pi = (4, 2) if compact else (8, 4)
+        nbytes = sum(po * (c.n + 1) + pi * c.nnz + 4 * c.m * ((c.n + 31) // 32) for c in dbs)
         ach = nbytes / sec / 1e9
         roof = {"kernel": "batch_build_rows_kernel", "bound": "hbm", "achieved": ach, "peak": hbm,
                 "unit": "GB/s", "frac": ach / hbm, "traffic": _kernel_traffic("batch_build_rows_kernel", "batched_4096"),
@@ -371,6 +376,12 @@ def run_batched(args):
         torch.cuda.synchronize()
 
     dbs, ms, cfg = _batched_workload(args.n_db)
+    compact = args.csr == "compact"
+    cfg = dict(cfg, csr=("compact: uint32 row offsets, uint16 item ids (FIM_CSR_COMPACT), every arm"
+                         if compact else "wide: int64 row offsets, int32 item ids, every arm"))
+    # the arrays every arm reads: the generator's CSR, or the same rows with
+    # narrower element types (bit patterns kept in the signed torch dtypes)
+    ptr_dt, idx_dt = (np.uint32, np.uint16) if compact else (np.int64, np.int32)
     stream = torch.cuda.Stream()
     ctx = fim.fim_create(local, stream)
     # the network: trained on the GPU from plain-miner traces of 48 other
@@ -379,10 +390,13 @@ def run_batched(args):
     train_sample = [(c, datagen.minsup_from_ppm(c.n, BATCH_PPM)) for c in train_sample]
     train_info = _train_scheduler(ctx, fim, sched, datagen, train_sample)
 
+    t_ptr, t_idx = (np.int32, np.int16) if compact else (np.int64, np.int32)
+
     class Dev:
         def __init__(self, c):
-            self.indptr = torch.from_numpy(c.indptr).cuda()
-            self.indices = torch.from_numpy(c.indices if c.nnz else np.zeros(1, np.int32)).cuda()
+            ix = c.indices if c.nnz else np.zeros(1, np.int32)
+            self.indptr = torch.from_numpy(c.indptr.astype(ptr_dt).view(t_ptr)).cuda()
+            self.indices = torch.from_numpy(ix.astype(idx_dt).view(t_idx)).cuda()
             self.m = c.m
     ddbs = [Dev(c) for c in dbs]
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
@@ -477,8 +491,8 @@ def run_batched(args):
     # contiguous databases in one copy per array)
     n_ptr = sum(c.n + 1 for c in dbs)
     n_idx = sum(c.nnz for c in dbs)
-    ptr_h = torch.empty(n_ptr, dtype=torch.int64).pin_memory().numpy()
-    idx_h = torch.empty(max(n_idx, 1), dtype=torch.int32).pin_memory().numpy()
+    ptr_h = torch.empty(n_ptr, dtype=torch.int32 if compact else torch.int64).pin_memory().numpy().view(ptr_dt)
+    idx_h = torch.empty(max(n_idx, 1), dtype=torch.int16 if compact else torch.int32).pin_memory().numpy().view(idx_dt)
     hdbs, po, io = [], 0, 0
     for c in dbs:
         ptr_h[po:po + c.n + 1] = c.indptr
@@ -508,7 +522,7 @@ def run_batched(args):
     e2e_t = torch.tensor([statistics.mean(e2e_lb)], dtype=torch.float64, device="cuda")
     if world > 1:
         dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-    h2d = sum(c.indptr.nbytes + c.indices.nbytes for c in dbs)
+    h2d = sum(c.indptr.nbytes + c.indices.nbytes for c in hdbs)
     d2h = 8 * (R + 1) + 4 * T + 4 * R
 
     # frequent items per database (the sets of size 1 of each slice)
@@ -521,7 +535,7 @@ def run_batched(args):
     m_freq = [int(csum[sl[d + 1]] - csum[sl[d]]) for d in range(len(dbs))]
 
     probes = _probes(fim, ctx)
-    roof = _batched_roofline(st, phase, dbs, m_freq, probes)
+    roof = _batched_roofline(st, phase, dbs, m_freq, probes, compact)
     med = statistics.median
     compare = {
         "unit": f"ms per mine of all {len(dbs):,} databases",

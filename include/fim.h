@@ -52,6 +52,12 @@ extern "C" {
 /* fim_build_bitmaps / fim_mine_batched: where the CSR arrays live */
 #define FIM_INPUT_HOST 0u
 #define FIM_INPUT_DEVICE 0x100u
+/* fim_build_bitmaps / fim_mine_batched: the CSR's element types.  Default
+ * (wide): indptr int64_t[n_trans + 1], indices int32_t[nnz].  Compact:
+ * indptr uint32_t[n_trans + 1], indices uint16_t[nnz] -- the same matrix in
+ * 2 + 4 / (items per row) bytes per item instead of 4 + 8 / (items per row),
+ * for inputs with nnz < 2^32 (every item id fits: FIM_MAX_ITEMS < 2^16). */
+#define FIM_CSR_COMPACT 0x400u
 
 /* fim_mine / fim_mine_batched */
 #define FIM_STRICT 0x1u       /* frequent iff S(X) > minsup (Eq. 3 literally); default S(X) >= minsup */
@@ -98,10 +104,11 @@ typedef struct {
     uint32_t reserved;
 } fim_stats;
 
-/* One database of a batch (fim_mine_batched).  CSR as for fim_build_bitmaps. */
+/* One database of a batch (fim_mine_batched).  CSR as for fim_build_bitmaps;
+ * the batch's flags say whether every database's arrays are wide or compact. */
 typedef struct {
-    const int64_t *indptr;   /* [n_trans + 1] */
-    const int32_t *indices;  /* [indptr[n_trans]] */
+    const void *indptr;      /* [n_trans + 1]: int64_t, or uint32_t if FIM_CSR_COMPACT */
+    const void *indices;     /* [indptr[n_trans]]: int32_t, or uint16_t if FIM_CSR_COMPACT */
     int64_t n_trans;
     int32_t n_items;
     int32_t pad;
@@ -121,13 +128,14 @@ void fim_destroy(fim_ctx *ctx);
  * as indices[indptr[i] : indptr[i+1]]; repeated items inside a transaction
  * collapse (set membership), empty transactions are allowed and count toward
  * n_trans.  Input arrays are host pointers (FIM_INPUT_HOST) or device pointers
- * (FIM_INPUT_DEVICE); they are copied and may be freed when the call returns.
+ * (FIM_INPUT_DEVICE), wide or compact (FIM_CSR_COMPACT: the element types
+ * above); they are copied and may be freed when the call returns.
  * The ctx keeps the matrix as item-major bit columns: column j is
  * ceil(n_trans/32) uint32 words, bit (i mod 32) of word i/32 = M[i,j].
  * Errors: FIM_E_INVAL if indptr[0] != 0, indptr decreases, an item is outside
  * [0, n_items), n_items > FIM_MAX_ITEMS or n_trans > FIM_MAX_TRANS (the ctx
  * then holds no matrix); FIM_E_NOMEM; FIM_E_CUDA. */
-int fim_build_bitmaps(fim_ctx *ctx, const int64_t *indptr, const int32_t *indices,
+int fim_build_bitmaps(fim_ctx *ctx, const void *indptr, const void *indices,
                       int64_t n_trans, int32_t n_items, uint32_t flags);
 
 /* fim_mine -- support calculation and frequent-itemset extraction

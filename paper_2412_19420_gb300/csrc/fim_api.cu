@@ -210,7 +210,7 @@ void fim_destroy(fim_ctx *ctx) {
     delete ctx;
 }
 
-int fim_build_bitmaps(fim_ctx *ctx, const int64_t *indptr, const int32_t *indices, int64_t n_trans,
+int fim_build_bitmaps(fim_ctx *ctx, const void *indptr, const void *indices, int64_t n_trans,
                       int32_t n_items, uint32_t flags) {
     FIM_NVTX("fim_build_bitmaps");
     if (!ctx) return FIM_E_INVAL;
@@ -229,13 +229,16 @@ int fim_build_bitmaps(fim_ctx *ctx, const int64_t *indptr, const int32_t *indice
     cudaEventRecord(ctx->ev[0], st);
     const uint64_t launches0 = ctx->launches;
 
-    const int64_t *d_ptr = indptr;
-    const int32_t *d_idx = indices;
+    // the CSR's element types (FIM_CSR_COMPACT: uint32 row offsets, uint16 ids)
+    const bool cmp = (flags & FIM_CSR_COMPACT) != 0;
+    const size_t pb = csr_off_bytes(cmp), ib = csr_id_bytes(cmp);
+    const void *d_ptr = indptr;
+    const void *d_idx = indices;
     int64_t h_nnz = -1;
     bool mapped = false;  // pinned host CSR read by the build kernel in place
     if (!(flags & FIM_INPUT_DEVICE)) {
-        const int64_t nnz = indptr[n_trans];
-        if (indptr[0] != 0 || nnz < 0 || (nnz > 0 && !indices)) return FIM_E_INVAL;
+        const int64_t nnz = csr_off(indptr, cmp, n_trans);
+        if (csr_off(indptr, cmp, 0) != 0 || nnz < 0 || (nnz > 0 && !indices)) return FIM_E_INVAL;
         if (ctx->upload_mapped) {
             // page-locked, mapped host memory is addressable from the GPU: the
             // kernel streams it over the host link, no staging copy
@@ -246,22 +249,21 @@ int fim_build_bitmaps(fim_ctx *ctx, const int64_t *indptr, const int32_t *indice
                                            ai.type == cudaMemoryTypeHost && ai.devicePointer != nullptr);
             cudaGetLastError();  // a query on unregistered memory leaves no sticky error
             if (ok_p && ok_i) {
-                d_ptr = static_cast<const int64_t *>(ap.devicePointer);
-                d_idx = nnz ? static_cast<const int32_t *>(ai.devicePointer) : indices;
+                d_ptr = ap.devicePointer;
+                d_idx = nnz ? ai.devicePointer : indices;
                 h_nnz = nnz;
                 mapped = true;
             }
         }
     }
     if (!(flags & FIM_INPUT_DEVICE) && !mapped) {
-        const int64_t nnz = indptr[n_trans];
-        FIM_TRY(fim_reserve(ctx, ctx->csr_ptr, sizeof(int64_t) * (size_t)(n_trans + 1)));
-        FIM_TRY(fim_reserve(ctx, ctx->csr_idx, sizeof(int32_t) * (size_t)(nnz > 0 ? nnz : 1)));
-        FIM_CUDA_TRY(cudaMemcpyAsync(ctx->csr_ptr.p, indptr, sizeof(int64_t) * (size_t)(n_trans + 1),
-                                     cudaMemcpyHostToDevice, st));
+        const int64_t nnz = csr_off(indptr, cmp, n_trans);
+        FIM_TRY(fim_reserve(ctx, ctx->csr_ptr, pb * (size_t)(n_trans + 1)));
+        FIM_TRY(fim_reserve(ctx, ctx->csr_idx, ib * (size_t)(nnz > 0 ? nnz : 1)));
+        FIM_CUDA_TRY(cudaMemcpyAsync(ctx->csr_ptr.p, indptr, pb * (size_t)(n_trans + 1), cudaMemcpyHostToDevice, st));
         // (the indices go up inside launch_build_bitmaps, overlapped with the build)
-        d_ptr = ctx->csr_ptr.as<int64_t>();
-        d_idx = ctx->csr_idx.as<int32_t>();
+        d_ptr = ctx->csr_ptr.p;
+        d_idx = ctx->csr_idx.p;
         h_nnz = nnz;
     }
     // device input: indptr[0] == 0 and indptr[n] >= 0 are checked by the build
@@ -271,9 +273,9 @@ int fim_build_bitmaps(fim_ctx *ctx, const int64_t *indptr, const int32_t *indice
     FIM_TRY(fim_reserve(ctx, ctx->item_sup, sizeof(uint32_t) * mm));
     FIM_TRY(fim_reserve(ctx, ctx->perm, sizeof(int32_t) * mm));
     FIM_TRY(fim_reserve(ctx, ctx->rank, sizeof(int32_t) * mm));
-    if (flags & FIM_INPUT_DEVICE) FIM_TRY(launch_build_bitmaps(ctx, d_ptr, d_idx, -1, nullptr, nullptr));
-    else if (mapped) FIM_TRY(launch_build_bitmaps(ctx, d_ptr, d_idx, h_nnz, nullptr, nullptr));
-    else FIM_TRY(launch_build_bitmaps(ctx, d_ptr, d_idx, h_nnz, indptr, h_nnz > 0 ? indices : nullptr));
+    if (flags & FIM_INPUT_DEVICE) FIM_TRY(launch_build_bitmaps(ctx, d_ptr, d_idx, -1, nullptr, nullptr, cmp));
+    else if (mapped) FIM_TRY(launch_build_bitmaps(ctx, d_ptr, d_idx, h_nnz, nullptr, nullptr, cmp));
+    else FIM_TRY(launch_build_bitmaps(ctx, d_ptr, d_idx, h_nnz, indptr, h_nnz > 0 ? indices : nullptr, cmp));
     cudaEventRecord(ctx->ev[1], st);
     FIM_TRY(launch_item_support(ctx));
     cudaEventRecord(ctx->ev[2], st);

@@ -122,8 +122,8 @@ struct Task {
 // pair bitset).  fim_mine uses a one-entry table; fim_mine_batched one entry
 // per database.  mfreq is written on the device by the ranking kernel.
 struct DbDesc {
-    const int64_t *indptr;
-    const int32_t *indices;
+    const void *indptr;  // int64_t[n + 1], or uint32_t[n + 1] when compact
+    const void *indices; // int32_t[nnz], or uint16_t[nnz] when compact
     int64_t n, nw, nwp;
     int64_t bm_off;      // words into the bit-column array
     int64_t item_off;    // entries into item_sup / rank / perm
@@ -133,7 +133,23 @@ struct DbDesc {
     int32_t mfreq;
     uint32_t thr;
     uint32_t maxlen;
+    int32_t compact;     // 1: the CSR is compact (FIM_CSR_COMPACT)
+    int32_t pad;
 };
+
+// A CSR's row offset i and item id e, wide (int64 offsets, int32 ids) or
+// compact (uint32 offsets, uint16 ids).
+__host__ __device__ __forceinline__ int64_t csr_off(const void *indptr, bool compact, int64_t i) {
+    return compact ? (int64_t) static_cast<const uint32_t *>(indptr)[i] : static_cast<const int64_t *>(indptr)[i];
+}
+#ifdef __CUDACC__
+__device__ __forceinline__ int32_t csr_id(const void *indices, bool compact, int64_t e) {
+    return compact ? (int32_t)__ldg(static_cast<const unsigned short *>(indices) + e)
+                   : __ldg(static_cast<const int32_t *>(indices) + e);
+}
+#endif
+inline size_t csr_off_bytes(bool compact) { return compact ? sizeof(uint32_t) : sizeof(int64_t); }
+inline size_t csr_id_bytes(bool compact) { return compact ? sizeof(uint16_t) : sizeof(int32_t); }
 
 // A window of the root arrays: the roots one group of a batch's databases
 // appended (base, count), the part its root plan kept (kept, in
@@ -345,8 +361,9 @@ void fim_release(fim_ctx *ctx, DevBuf &b);
 // k_matrix.cu
 // nnz < 0: read indptr[n] from the device.  h_indptr/h_indices (host input):
 // the indices are uploaded into d_indices chunk by chunk, overlapping the build.
-int launch_build_bitmaps(fim_ctx *ctx, const int64_t *d_indptr, const int32_t *d_indices, int64_t nnz,
-                         const int64_t *h_indptr, const int32_t *h_indices);
+// compact: the CSR holds uint32 row offsets and uint16 item ids.
+int launch_build_bitmaps(fim_ctx *ctx, const void *d_indptr, const void *d_indices, int64_t nnz,
+                         const void *h_indptr, const void *h_indices, bool compact);
 int launch_item_support(fim_ctx *ctx);
 int launch_rank_items(fim_ctx *ctx, uint32_t thr, MineCounters *d_ctr);
 int launch_emit_singletons(fim_ctx *ctx, MineCounters *d_ctr);

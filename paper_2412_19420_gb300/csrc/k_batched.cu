@@ -22,6 +22,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include "fim_common.cuh"
@@ -58,12 +59,13 @@ batch_build_kernel(const DbDesc *__restrict__ dbs, int n_db, const int64_t *__re
     const int i0 = (int)(local % nib) * ib;
     const int icount = min(ib, D.m - i0);
     const int64_t n = D.n;
-    const int64_t nnz = n > 0 ? D.indptr[n] : 0;
+    const bool cmp = D.compact != 0;
+    const int64_t nnz = n > 0 ? csr_off(D.indptr, cmp, n) : 0;
     const int64_t t0 = w0 * 32, t1 = min64(n, t0 + WB * 32);
     const int rows = t1 > t0 ? (int)(t1 - t0) : 0;
     for (int k = threadIdx.x; k < icount * WB; k += blockDim.x) tile[k] = 0u;
     if (rows > 0)
-        for (int k = threadIdx.x; k <= rows; k += blockDim.x) s_ptr[k] = D.indptr[t0 + k];
+        for (int k = threadIdx.x; k <= rows; k += blockDim.x) s_ptr[k] = csr_off(D.indptr, cmp, t0 + k);
     __syncthreads();
     int bad = 0;
     if (rows > 0) {
@@ -71,7 +73,7 @@ batch_build_kernel(const DbDesc *__restrict__ dbs, int n_db, const int64_t *__re
             if (s_ptr[k + 1] < s_ptr[k] || s_ptr[k] < 0 || s_ptr[k + 1] > nnz) bad = 1;
         const int64_t e0 = max64(0, s_ptr[0]), e1 = min64(nnz, s_ptr[rows]);
         for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-            const int32_t it = D.indices[e];
+            const int32_t it = csr_id(D.indices, cmp, e);
             if (it < 0 || it >= D.m) { bad = 1; continue; }
             if (it < i0 || it >= i0 + icount) continue;
             int lo = 0, hi = rows;
@@ -107,26 +109,27 @@ constexpr int BUILD_ROWS_THREADS = 512;
 // What a build CTA needs of its unit, written per unit by the unit-map
 // kernel: one 64-byte load instead of map -> database table -> prefix.
 struct __align__(16) BuildUnit {
-    const int64_t *indptr;  // the database's CSR
-    const int32_t *indices;
+    const void *indptr;     // the database's CSR (wide, or compact)
+    const void *indices;
     uint32_t *col0;         // its first bit column
     int64_t n;              // its transactions
     int64_t nwp;            // column pitch in words
     int64_t item_off;       // its first entry of the item supports
     int64_t w0;             // the unit's first word
     int32_t m;              // its items
-    int32_t pad;
+    int32_t compact;        // 1: uint32 row offsets and uint16 item ids
 };
 static_assert(sizeof(BuildUnit) == 64, "one unit per 64 bytes");
 
-template <int WBK, bool COAL>
-__device__ __forceinline__ void build_rows_unit(const BuildUnit *__restrict__ units, int64_t unit,
-                                                uint32_t *__restrict__ sup, int *__restrict__ flag, uint32_t *tile) {
+template <int WBK, bool COAL, bool CMP>
+__device__ __forceinline__ void build_rows_unit(const BuildUnit &D, uint32_t *__restrict__ sup,
+                                                int *__restrict__ flag, uint32_t *tile) {
     static_assert(WBK % 4 == 0 && WBK / 4 <= 32 && 32 % (WBK / 4) == 0, "a column's chunks share a warp");
     constexpr int NWARP = BUILD_ROWS_THREADS / 32;
     constexpr int QPC = WBK / 4;  // 16-byte chunks of a column in this block
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const BuildUnit D = units[unit];
+    using Id = typename std::conditional<CMP, unsigned short, int32_t>::type;
+    const Id *const ids = static_cast<const Id *>(D.indices);
     const int m = D.m, ms = m | 1;  // odd pitch: the transposed reads below are conflict-free
     const int64_t w0 = D.w0;
     const int64_t n = D.n;
@@ -138,7 +141,7 @@ __device__ __forceinline__ void build_rows_unit(const BuildUnit *__restrict__ un
                 make_uint4(0u, 0u, 0u, 0u);
         return;
     }
-    const int64_t nnz = D.indptr[n];
+    const int64_t nnz = csr_off(D.indptr, CMP, n);
     for (int k = threadIdx.x; k < WBK * ms / 4; k += BUILD_ROWS_THREADS)
         reinterpret_cast<uint4 *>(tile)[k] = make_uint4(0u, 0u, 0u, 0u);
     __syncthreads();
@@ -152,7 +155,8 @@ __device__ __forceinline__ void build_rows_unit(const BuildUnit *__restrict__ un
             const int64_t r0 = t0 + 32 * g;
             if (r0 >= n) break;  // warp-uniform
             const int nrw = (int)min64(n - r0, 32);
-            const int64_t a = D.indptr[r0 + (lane < nrw ? lane : nrw)], B = D.indptr[r0 + nrw];
+            const int64_t a = csr_off(D.indptr, CMP, r0 + (lane < nrw ? lane : nrw));
+            const int64_t B = csr_off(D.indptr, CMP, r0 + nrw);
             const int64_t A = __shfl_sync(0xffffffffu, a, 0);
             int64_t nx = __shfl_down_sync(0xffffffffu, a, 1);
             if (lane == 31) nx = B;
@@ -162,14 +166,14 @@ __device__ __forceinline__ void build_rows_unit(const BuildUnit *__restrict__ un
                 continue;
             }
             const int ar = (int)(a - A), span = (int)(B - A);  // lanes past the last row hold span
-            const int32_t *const src = D.indices + A;
+            const Id *const src = ids + A;
             uint32_t *const trow = tile + g * ms;
             for (int base = 0; base < span; base += 32 * U) {
                 int32_t it[U];
 #pragma unroll
                 for (int u = 0; u < U; u++) {
                     const int p = base + 32 * u + lane;
-                    it[u] = p < span ? __ldg(src + p) : 0;
+                    it[u] = p < span ? (int32_t)__ldg(src + p) : 0;
                 }
 #pragma unroll
                 for (int u = 0; u < U; u++) {
@@ -195,7 +199,7 @@ __device__ __forceinline__ void build_rows_unit(const BuildUnit *__restrict__ un
         for (int g = warp; g < WBK; g += NWARP) {
             const int64_t r = t0 + 32 * g + lane;
             if (r < n) {
-                int64_t e0 = D.indptr[r], e1 = D.indptr[r + 1];
+                int64_t e0 = csr_off(D.indptr, CMP, r), e1 = csr_off(D.indptr, CMP, r + 1);
                 if (e1 < e0 || e0 < 0 || e1 > nnz) {  // a malformed row: flagged, not read
                     bad = 1;
                     e1 = e0;
@@ -206,7 +210,7 @@ __device__ __forceinline__ void build_rows_unit(const BuildUnit *__restrict__ un
                 for (int64_t e = e0; e < e1; e += 4) {
                     int32_t it[4];
 #pragma unroll
-                    for (int u = 0; u < 4; u++) it[u] = e + u < e1 ? __ldg(D.indices + e + u) : 0;
+                    for (int u = 0; u < 4; u++) it[u] = e + u < e1 ? (int32_t)__ldg(ids + e + u) : 0;
 #pragma unroll
                     for (int u = 0; u < 4; u++)
                         if (e + u < e1) {
@@ -246,12 +250,17 @@ __global__ void __launch_bounds__(BUILD_ROWS_THREADS)
 batch_build_rows_kernel(const BuildUnit *__restrict__ units, int64_t unit_base, int64_t unit_end,
                         uint32_t *__restrict__ sup, int *__restrict__ flag) {
     extern __shared__ __align__(16) uint32_t tile[];  // [WBK][ms]
+    auto one = [&](int64_t u) {
+        const BuildUnit D = units[u];
+        if (D.compact) build_rows_unit<WBK, COAL, true>(D, sup, flag, tile);
+        else build_rows_unit<WBK, COAL, false>(D, sup, flag, tile);
+    };
     if (!PERSIST) {
-        build_rows_unit<WBK, COAL>(units, unit_base + blockIdx.x, sup, flag, tile);
+        one(unit_base + blockIdx.x);
         return;
     }
     for (int64_t u = unit_base + blockIdx.x; u < unit_end; u += gridDim.x) {
-        build_rows_unit<WBK, COAL>(units, u, sup, flag, tile);
+        one(u);
         __syncthreads();  // the tile has been written out before the next unit clears it
     }
 }
@@ -293,7 +302,7 @@ __global__ void batch_unit_db_kernel(const DbDesc *__restrict__ dbs, const int64
         b.item_off = D.item_off;
         b.w0 = (u - u0) * wbk;
         b.m = D.m;
-        b.pad = 0;
+        b.compact = D.compact;
         units[u] = b;
     }
 }
@@ -872,6 +881,10 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
     int wbk = ctx->batch_build_block == 64 ? 64 : ctx->batch_build_block == 16 ? 16 : 32;
     if ((size_t)wbk * (size_t)(L.m_max | 1) * sizeof(uint32_t) > 227u * 1024u) wbk = 32;
     const int unit_words = rows_build ? wbk : WB;
+    // the CSR's element types (FIM_CSR_COMPACT: uint32 row offsets, uint16 ids)
+    const bool cmp = (flags & FIM_CSR_COMPACT) != 0;
+    const size_t pb = csr_off_bytes(cmp), ib = csr_id_bytes(cmp);
+    auto host_nnz = [cmp](const fim_db_desc &x) { return csr_off(x.indptr, cmp, x.n_trans); };
     int64_t host_nnz_total = 0, host_ptr_total = 0;
     for (int d = 0; d < n_db; d++) {
         const fim_db_desc &x = in[d];
@@ -889,6 +902,7 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
         if ((flags & FIM_STRICT) && x.minsup == UINT64_MAX) thr = UINT64_MAX;
         D.thr = thr > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)thr;
         D.maxlen = maxlen;
+        D.compact = cmp ? 1 : 0;
         D.bm_off = L.words;
         D.item_off = L.items;
         D.pair_off = L.pairs;
@@ -905,9 +919,9 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
         L.tile_prefix[d + 1] = L.tile_prefix[d] + (int64_t)nt * (nt + 1) / 2;
         if (D.m > L.max_row_bound) L.max_row_bound = D.m;
         if (!on_device) {
-            if (x.indptr[0] != 0 || x.indptr[x.n_trans] < 0 || (x.indptr[x.n_trans] > 0 && !x.indices))
-                return FIM_E_INVAL;
-            host_nnz_total += x.indptr[x.n_trans];
+            const int64_t nnz = host_nnz(x);
+            if (csr_off(x.indptr, cmp, 0) != 0 || nnz < 0 || (nnz > 0 && !x.indices)) return FIM_E_INVAL;
+            host_nnz_total += nnz;
             host_ptr_total += x.n_trans + 1;
         }
     }
@@ -927,8 +941,8 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
                 runs.push_back({(const char *)p, bytes});
         };
         for (int d = 0; d < n_db && rp.size() + ri.size() <= 64; d++) {
-            note(rp, in[d].indptr, sizeof(int64_t) * (size_t)(in[d].n_trans + 1));
-            note(ri, in[d].indices, sizeof(int32_t) * (size_t)in[d].indptr[in[d].n_trans]);
+            note(rp, in[d].indptr, pb * (size_t)(in[d].n_trans + 1));
+            note(ri, in[d].indices, ib * (size_t)host_nnz(in[d]));
         }
         rp.insert(rp.end(), ri.begin(), ri.end());
         // page-locked: streamed up group by group inside the graph (copies
@@ -943,8 +957,8 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
             }
     }
     if (!on_device && !mapped) {
-        FIM_TRY(fim_reserve(ctx, ctx->csr_ptr, sizeof(int64_t) * (size_t)(host_ptr_total ? host_ptr_total : 1)));
-        FIM_TRY(fim_reserve(ctx, ctx->csr_idx, sizeof(int32_t) * (size_t)(host_nnz_total ? host_nnz_total : 1)));
+        FIM_TRY(fim_reserve(ctx, ctx->csr_ptr, pb * (size_t)(host_ptr_total ? host_ptr_total : 1)));
+        FIM_TRY(fim_reserve(ctx, ctx->csr_idx, ib * (size_t)(host_nnz_total ? host_nnz_total : 1)));
         // databases whose arrays follow each other in host memory (one packed
         // buffer) go up in one copy per run instead of one per database
         struct Run { const char *src = nullptr; char *dst = nullptr; size_t bytes = 0; };
@@ -966,17 +980,17 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
             r.bytes = bytes;
             return FIM_OK;
         };
-        int64_t po = 0, io = 0;
+        int64_t po = 0, io = 0;  // elements of the staging arrays
+        char *const sp = ctx->csr_ptr.as<char>(), *const si = ctx->csr_idx.as<char>();
         for (int d = 0; d < n_db; d++) {
             const fim_db_desc &x = in[d];
-            const int64_t nnz = x.indptr[x.n_trans];
+            const int64_t nnz = host_nnz(x);
             if (!streamed) {  // streamed: the graph copies each group of databases
-                FIM_TRY(add(rp, x.indptr, ctx->csr_ptr.as<int64_t>() + po, sizeof(int64_t) * (size_t)(x.n_trans + 1)));
-                if (nnz > 0)
-                    FIM_TRY(add(ri, x.indices, ctx->csr_idx.as<int32_t>() + io, sizeof(int32_t) * (size_t)nnz));
+                FIM_TRY(add(rp, x.indptr, sp + pb * (size_t)po, pb * (size_t)(x.n_trans + 1)));
+                if (nnz > 0) FIM_TRY(add(ri, x.indices, si + ib * (size_t)io, ib * (size_t)nnz));
             }
-            L.dbs[d].indptr = ctx->csr_ptr.as<int64_t>() + po;
-            L.dbs[d].indices = ctx->csr_idx.as<int32_t>() + io;
+            L.dbs[d].indptr = sp + pb * (size_t)po;
+            L.dbs[d].indices = si + ib * (size_t)io;
             po += x.n_trans + 1;
             io += nnz;
         }
@@ -1076,8 +1090,8 @@ int fim_mine_batched(fim_ctx *ctx, int n_db, const fim_db_desc *in, uint32_t fla
                 v.push_back({(const char *)src, (char *)dst, bytes});
         };
         for (int d = seg_db[sg]; d < seg_db[sg + 1]; d++) {
-            note(cp_ptr, in[d].indptr, L.dbs[d].indptr, sizeof(int64_t) * (size_t)(in[d].n_trans + 1));
-            note(cp_idx, in[d].indices, L.dbs[d].indices, sizeof(int32_t) * (size_t)in[d].indptr[in[d].n_trans]);
+            note(cp_ptr, in[d].indptr, L.dbs[d].indptr, pb * (size_t)(in[d].n_trans + 1));
+            note(cp_idx, in[d].indices, L.dbs[d].indices, ib * (size_t)host_nnz(in[d]));
         }
         seg_copies[sg] = cp_ptr;
         seg_copies[sg].insert(seg_copies[sg].end(), cp_idx.begin(), cp_idx.end());

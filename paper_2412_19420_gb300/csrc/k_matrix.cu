@@ -7,7 +7,10 @@
 // membership of Eq. 1 -- and the tile goes out as WB-word (64-byte) runs of
 // each item column with 16-byte stores.  A 64-byte run keeps the tile at
 // 64 KB for 1,024 items, so several CTAs share an SM.  The CTA also validates
-// its slice of the CSR (monotone indptr, items in [0, m)).
+// its slice of the CSR (monotone indptr, items in [0, m)).  CMP: the CSR is
+// compact (uint32 row offsets, uint16 item ids) instead of int64 / int32.
+#include <type_traits>
+
 #include "fim_common.cuh"
 
 namespace {
@@ -15,10 +18,15 @@ namespace {
 constexpr int WB = 16;          // words per CTA tile row (64 bytes)
 constexpr int BUILD_THREADS = 512;
 
+template <bool CMP>
 __global__ void __launch_bounds__(BUILD_THREADS)
-build_bitmaps_kernel(const int64_t *__restrict__ indptr, const int32_t *__restrict__ indices,
+build_bitmaps_kernel(const void *__restrict__ indptr_v, const void *__restrict__ indices_v,
                      int64_t n, int32_t m, int64_t nnz, int64_t nwp, int ib, int64_t blk0,
                      uint32_t *__restrict__ bm, int *__restrict__ flag, int *__restrict__ max_len) {
+    using Off = typename std::conditional<CMP, uint32_t, int64_t>::type;
+    using Id = typename std::conditional<CMP, unsigned short, int32_t>::type;
+    const Off *const indptr = static_cast<const Off *>(indptr_v);
+    const Id *const indices = static_cast<const Id *>(indices_v);
     // [WB][ib + 1], word-major and padded: the 32 rows of a warp's group share
     // their word, so their items' bits spread over the banks
     extern __shared__ __align__(16) uint32_t tile[];
@@ -31,7 +39,7 @@ build_bitmaps_kernel(const int64_t *__restrict__ indptr, const int32_t *__restri
     const int64_t t1 = min(n, t0 + WB * 32);
     int bad = 0, my_max = 0;
     if (nnz < 0) {  // device input: indptr[n] read here, and indptr[0] checked once
-        nnz = indptr[n];
+        nnz = (int64_t)indptr[n];
         if (nnz < 0) bad = 1;
         if (blockIdx.x == 0 && blockIdx.y == 0 && blk0 == 0 && threadIdx.x == 0 && indptr[0] != 0) bad = 1;
     }
@@ -43,8 +51,8 @@ build_bitmaps_kernel(const int64_t *__restrict__ indptr, const int32_t *__restri
     // element finds its row by a binary search over the lanes' starts
     for (int64_t rb = t0 + 32 * warp; rb < t1; rb += 32 * (int64_t)(blockDim.x >> 5)) {
         const int nr = (int)min64(32, t1 - rb);
-        const int64_t off = indptr[rb + (lane < nr ? lane : nr)];
-        const int64_t e_end = indptr[rb + nr];
+        const int64_t off = (int64_t)indptr[rb + (lane < nr ? lane : nr)];
+        const int64_t e_end = (int64_t)indptr[rb + nr];
         int64_t off_next = __shfl_down_sync(0xffffffffu, off, 1);
         if (lane == nr - 1) off_next = e_end;
         if (lane < nr) {
@@ -57,7 +65,7 @@ build_bitmaps_kernel(const int64_t *__restrict__ indptr, const int32_t *__restri
         for (int64_t e0 = e_begin; e0 < e_end; e0 += 32) {
             const int64_t e = e0 + lane;
             const bool v = e < e_end;
-            const int32_t it = v ? indices[e] : 0;
+            const int32_t it = v ? (int32_t)indices[e] : 0;
             int r = 0;  // largest r < nr with start(r) <= e
 #pragma unroll
             for (int step = 16; step > 0; step >>= 1) {
@@ -156,15 +164,16 @@ __global__ void emit_singletons_kernel(const uint32_t *__restrict__ sup, const i
 
 }  // namespace
 
-int launch_build_bitmaps(fim_ctx *ctx, const int64_t *d_indptr, const int32_t *d_indices, int64_t nnz,
-                         const int64_t *h_indptr, const int32_t *h_indices) {
+int launch_build_bitmaps(fim_ctx *ctx, const void *d_indptr, const void *d_indices, int64_t nnz,
+                         const void *h_indptr, const void *h_indices, bool cmp) {
+    auto kern = cmp ? build_bitmaps_kernel<true> : build_bitmaps_kernel<false>;
+    const size_t ib_bytes = csr_id_bytes(cmp);
     const int64_t nblk = ctx->nwp / WB;
     int ib = ctx->m < 1024 ? ctx->m : 1024;
     if (ib < 1) ib = 1;
     const int niblk = (int)ceil_div64(ctx->m > 0 ? ctx->m : 1, ib);
     const size_t smem = (size_t)(ib + 1) * WB * sizeof(uint32_t);
-    FIM_CUDA_TRY(cudaFuncSetAttribute(build_bitmaps_kernel,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    FIM_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int *flag = ctx->dev_flag.as<int>();
     cudaStream_t st = ctx->stream;
     FIM_CUDA_TRY(cudaMemsetAsync(flag, 0, 2 * sizeof(int), st));
@@ -193,21 +202,22 @@ int launch_build_bitmaps(fim_ctx *ctx, const int64_t *d_indptr, const int32_t *d
         if (b0 >= b1) break;
         if (h_indices) {
             const int64_t t0 = min64(ctx->n, b0 * tpb), t1 = min64(ctx->n, b1 * tpb);
-            int64_t lo = h_indptr[t0], hi = h_indptr[t1];
+            int64_t lo = csr_off(h_indptr, cmp, t0), hi = csr_off(h_indptr, cmp, t1);
             lo = lo < 0 ? 0 : (lo > nnz ? nnz : lo);
             hi = hi < lo ? lo : (hi > nnz ? nnz : hi);
             if (hi > lo) {
                 cudaStream_t cs = ctx->up_stream[c % nstreams];
-                FIM_CUDA_TRY(cudaMemcpyAsync(const_cast<int32_t *>(d_indices) + lo, h_indices + lo,
-                                             sizeof(int32_t) * (size_t)(hi - lo), cudaMemcpyHostToDevice, cs));
+                FIM_CUDA_TRY(cudaMemcpyAsync(static_cast<char *>(const_cast<void *>(d_indices)) + ib_bytes * (size_t)lo,
+                                             static_cast<const char *>(h_indices) + ib_bytes * (size_t)lo,
+                                             ib_bytes * (size_t)(hi - lo), cudaMemcpyHostToDevice, cs));
                 FIM_CUDA_TRY(cudaEventRecord(ctx->up_ev[c], cs));
                 FIM_CUDA_TRY(cudaStreamWaitEvent(st, ctx->up_ev[c], 0));
             }
         }
         dim3 grid((unsigned)(b1 - b0), (unsigned)niblk);
         ctx->launches++;
-        build_bitmaps_kernel<<<grid, BUILD_THREADS, smem, st>>>(d_indptr, d_indices, ctx->n, ctx->m, nnz, ctx->nwp,
-                                                                ib, b0, ctx->bm.as<uint32_t>(), flag, flag + 1);
+        kern<<<grid, BUILD_THREADS, smem, st>>>(d_indptr, d_indices, ctx->n, ctx->m, nnz, ctx->nwp, ib, b0,
+                                                ctx->bm.as<uint32_t>(), flag, flag + 1);
         FIM_CUDA_TRY(cudaGetLastError());
     }
     return FIM_OK;

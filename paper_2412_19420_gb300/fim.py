@@ -26,6 +26,7 @@ FIM_E_INVAL, FIM_E_NOMEM, FIM_E_CUDA, FIM_E_TIMEOUT = -1, -2, -3, -4
 FIM_E_STACK, FIM_E_TOO_SMALL, FIM_E_STATE, FIM_E_NODEV = -5, -6, -7, -8
 FIM_E_CHECK = -9
 FIM_INPUT_HOST, FIM_INPUT_DEVICE = 0, 0x100
+FIM_CSR_COMPACT = 0x400
 FIM_OUTPUT_HOST, FIM_OUTPUT_DEVICE = 0, 0x200
 FIM_STRICT, FIM_LEARNED, FIM_PAIRS_POPC, FIM_TRACE = 0x1, 0x2, 0x4, 0x8
 FIM_DIFFSET_RULE, FIM_NO_SPLIT = 0x10, 0x20
@@ -135,6 +136,22 @@ def _sync_torch(*arrays) -> None:
             return
 
 
+def _itemsize(a) -> int:
+    return int(a.element_size()) if hasattr(a, "element_size") else int(a.itemsize)
+
+
+def _csr_format(indptr, indices) -> int:
+    """FIM_CSR_COMPACT for 4-byte row offsets with 2-byte item ids (uint32 /
+    uint16, or torch int32 / int16 holding those bits), 0 for the wide int64 /
+    int32 CSR; any other pairing is rejected."""
+    sp, si = _itemsize(indptr), _itemsize(indices)
+    if (sp, si) == (8, 4):
+        return 0
+    if (sp, si) == (4, 2):
+        return FIM_CSR_COMPACT
+    raise ValueError(f"CSR element sizes ({sp}, {si}) are neither (8, 4) nor (4, 2)")
+
+
 def _ptr(a):
     """(pointer, is_device) of a numpy array or torch tensor (contiguous)."""
     if a is None:
@@ -163,10 +180,17 @@ def fim_destroy(ctx) -> None:
 
 
 def fim_build_bitmaps(ctx, indptr, indices, n_items: int, flags: int | None = None) -> None:
-    """CSR (int64 indptr, int32 indices) -> the ctx's bit columns (Eq. 1)."""
+    """CSR -> the ctx's bit columns (Eq. 1).  Wide (int64 indptr, int32
+    indices) or compact (uint32 indptr, uint16 indices: FIM_CSR_COMPACT, set
+    from the arrays' element sizes)."""
     if not hasattr(indptr, "data_ptr"):
-        indptr = np.ascontiguousarray(indptr, dtype=np.int64)
-        indices = np.ascontiguousarray(indices, dtype=np.int32)
+        indptr = np.asarray(indptr)
+        indices = np.asarray(indices)
+        if (indptr.dtype, indices.dtype) != (np.dtype(np.uint32), np.dtype(np.uint16)):
+            indptr = np.ascontiguousarray(indptr, dtype=np.int64)
+            indices = np.ascontiguousarray(indices, dtype=np.int32)
+        else:
+            indptr, indices = np.ascontiguousarray(indptr), np.ascontiguousarray(indices)
     _sync_torch(indptr, indices)
     p, dev = _ptr(indptr)
     q, dev2 = _ptr(indices)
@@ -174,6 +198,7 @@ def fim_build_bitmaps(ctx, indptr, indices, n_items: int, flags: int | None = No
         raise ValueError("indptr and indices must both be host or both be device")
     if flags is None:
         flags = FIM_INPUT_DEVICE if dev else FIM_INPUT_HOST
+    flags = int(flags) | _csr_format(indptr, indices)
     n = int(indptr.shape[0]) - 1
     _check(_lib.fim_build_bitmaps(ctx, p, q, n, int(n_items), int(flags)), "fim_build_bitmaps")
 
@@ -363,17 +388,27 @@ class BatchDescriptor:
         self.arr = (fim_db_desc * max(1, n))()
         self.keep = []
         self.on_dev = None
+        self.csr = None  # 0 (wide) or FIM_CSR_COMPACT, the same for every database
         for i, (c, ms) in enumerate(zip(dbs, minsups)):
             ip, ix = c.indptr, c.indices
             if not hasattr(ip, "data_ptr"):
-                ip = np.ascontiguousarray(ip, dtype=np.int64)
-                ix = np.ascontiguousarray(ix, dtype=np.int32)
+                ip, ix = np.asarray(ip), np.asarray(ix)
+                if (ip.dtype, ix.dtype) != (np.dtype(np.uint32), np.dtype(np.uint16)):
+                    ip = np.ascontiguousarray(ip, dtype=np.int64)
+                    ix = np.ascontiguousarray(ix, dtype=np.int32)
+                else:
+                    ip, ix = np.ascontiguousarray(ip), np.ascontiguousarray(ix)
             p, dev = _ptr(ip)
             q, _ = _ptr(ix)
             if self.on_dev is None:
                 self.on_dev = dev
             elif self.on_dev != dev:
                 raise ValueError("all databases must be host or all device")
+            fmt = _csr_format(ip, ix)
+            if self.csr is None:
+                self.csr = fmt
+            elif self.csr != fmt:
+                raise ValueError("all databases must be wide or all compact")
             self.keep.append((ip, ix))
             self.arr[i] = fim_db_desc(p, q, int(ip.shape[0]) - 1, int(c.m), 0, int(ms))
 
@@ -383,7 +418,7 @@ def fim_mine_batched(ctx, dbs, minsups=None, flags: int = 0) -> None:
     BatchDescriptor, or a sequence of databases with minsups (one absolute
     threshold per database)."""
     desc = dbs if isinstance(dbs, BatchDescriptor) else BatchDescriptor(dbs, minsups)
-    f = int(flags) | (FIM_INPUT_DEVICE if desc.on_dev else 0)
+    f = int(flags) | (FIM_INPUT_DEVICE if desc.on_dev else 0) | (desc.csr or 0)
     if desc.on_dev and desc.keep:
         _sync_torch(desc.keep[0][0])
     _check(_lib.fim_mine_batched(ctx, desc.n, ctypes.cast(desc.arr, ctypes.c_void_p), f), "fim_mine_batched")

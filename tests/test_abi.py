@@ -106,3 +106,34 @@ def test_binding_argument_counts_match_the_header():
         assert len(f.argtypes) == n, (name, len(f.argtypes), n)
         checked += 1
     assert checked >= 20
+
+
+def test_flag_values_match_the_header():
+    # every FIM_* flag the binding defines has the header's value
+    from paper_2412_19420_gb300 import fim
+    txt = open(os.path.join(ROOT, "include", "fim.h")).read()
+    defs = {m.group(1): int(m.group(2), 16) for m in re.finditer(r"#define (FIM_\w+) (0x[0-9a-fA-F]+)u", txt)}
+    for name in ("FIM_INPUT_DEVICE", "FIM_OUTPUT_DEVICE", "FIM_CSR_COMPACT", "FIM_STRICT", "FIM_LEARNED",
+                 "FIM_PAIRS_POPC", "FIM_TRACE", "FIM_DIFFSET_RULE", "FIM_NO_SPLIT"):
+        assert getattr(fim, name) == defs[name], name
+
+
+def test_csr_format_from_element_sizes():
+    # the binding marshals a CSR as wide (int64 offsets, int32 ids) or compact
+    # (4-byte offsets, 2-byte ids) from the arrays' element sizes alone, and
+    # rejects any other pairing rather than guessing
+    import numpy as np
+    from paper_2412_19420_gb300 import fim
+    assert fim._csr_format(np.zeros(3, np.int64), np.zeros(2, np.int32)) == 0
+    assert fim._csr_format(np.zeros(3, np.uint32), np.zeros(2, np.uint16)) == fim.FIM_CSR_COMPACT
+    assert fim._csr_format(np.zeros(3, np.int32), np.zeros(0, np.int16)) == fim.FIM_CSR_COMPACT
+    for ip, ix in ((np.int64, np.int16), (np.int32, np.int32), (np.uint8, np.uint8)):
+        with pytest.raises(ValueError):
+            fim._csr_format(np.zeros(3, ip), np.zeros(2, ix))
+    try:
+        import torch
+    except ImportError:
+        return
+    assert fim._csr_format(torch.zeros(3, dtype=torch.int32), torch.zeros(2, dtype=torch.int16)) == \
+        fim.FIM_CSR_COMPACT
+    assert fim._csr_format(torch.zeros(3, dtype=torch.int64), torch.zeros(2, dtype=torch.int32)) == 0

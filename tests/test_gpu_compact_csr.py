@@ -157,3 +157,33 @@ def test_malformed_compact_rejected(ctx):
     assert fim.fim_fetch_results(ctx).sha256() == oracle.apriori(good.indptr, good.indices, good.m, 30).sha256()
     fim.fim_mine_batched(ctx, [k, _compact(good)], [30, 45])
     _check_batch(ctx, [good, good], [30, 45])
+
+
+@pytest.mark.parametrize("block", [16, 32, 64])
+@pytest.mark.parametrize("coal", [1, 0])
+def test_batch_build_shapes(ctx, block, coal):
+    # every build block and both id-read orders on compact CSRs, with rows
+    # long and short, empty rows and databases whose arrays start at odd
+    # 16-bit offsets inside one buffer (the two-ids-per-load read meets
+    # both alignments)
+    rng = np.random.default_rng(block * 2 + coal)
+    dbs, ms = [], []
+    for d in range(14):
+        rows = []
+        for t in range(int(rng.integers(1, 2500))):
+            k = int(rng.choice([0, 1, 2, 3, 5, 9, 40]))
+            rows.append(sorted(rng.choice(120, size=min(k, 120), replace=False).tolist()))
+        dbs.append(datagen.from_lists(rows, 120))
+        ms.append(max(1, len(rows) // 15))
+    packed = _pinned_packed([_compact(c) for c in dbs])
+    fim.fim_set_tuning(ctx, "batch_build_block", block)
+    fim.fim_set_tuning(ctx, "batch_build_coal", coal)
+    try:
+        for inp in (packed, [_compact(c) for c in dbs]):
+            fim.fim_mine_batched(ctx, inp, ms, fim.FIM_MAXLEN(3))
+            for d, (c, m) in enumerate(zip(dbs, ms)):
+                got = fim.fim_fetch_batched(ctx, d)
+                assert got.sha256() == oracle.apriori(c.indptr, c.indices, c.m, m, max_len=3).sha256(), d
+    finally:
+        fim.fim_set_tuning(ctx, "batch_build_block", 32)
+        fim.fim_set_tuning(ctx, "batch_build_coal", 1)
